@@ -1,0 +1,220 @@
+"""FP64 CPU oracle for probabilistic shape-from-silhouette (test infrastructure).
+
+The arithmetic lives in `psfs_oracle.c` (plain C, double precision), compiled
+here with gcc and called through ctypes.  This package is for the test suite,
+the smoke check and the CPU-baseline leg of the benchmark only; the CUDA
+library never imports it and shares nothing with it.
+
+Inputs are numpy arrays; grids and cameras may be objects or dicts with the
+fields (nx, ny, nz, origin, voxel_size) and (width, height, K, R, t).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "psfs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_f32p = ctypes.POINTER(ctypes.c_float)
+_i32p = ctypes.POINTER(ctypes.c_int)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2, IEEE double, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-std=c11", "-shared",
+           "-fPIC", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_slm.argtypes = [ctypes.c_int64, _u8p, _f32p, _f32p, ctypes.c_double, _dp]
+            lib.oracle_slm.restype = None
+            lib.oracle_project.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _i32p, _i32p,
+                                           _dp, _dp]
+            lib.oracle_project.restype = ctypes.c_int
+            lib.oracle_fuse.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+                                        ctypes.c_double, ctypes.c_int, _i32p, _dp, _dp,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, _dp, _dp, _u8p, _u8p,
+                                        _u8p]
+            lib.oracle_fuse.restype = None
+            lib.oracle_compact.argtypes = [ctypes.c_int64, _u8p, _u32p]
+            lib.oracle_compact.restype = ctypes.c_int64
+            lib.oracle_backward_slm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+                                                ctypes.c_double, ctypes.c_int, _i32p, _dp, _dp,
+                                                ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, _dp, _dp]
+            lib.oracle_backward_slm.restype = None
+            lib.oracle_backward_background.argtypes = [ctypes.c_int64, _u8p, _f32p, _f32p, _dp,
+                                                       _dp, _dp, _dp]
+            lib.oracle_backward_background.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _get(o, name):
+    return o[name] if isinstance(o, dict) else getattr(o, name)
+
+
+def _grid_args(grid):
+    origin = np.ascontiguousarray(np.asarray(_get(grid, "origin"), dtype=np.float64))
+    return (int(_get(grid, "nx")), int(_get(grid, "ny")), int(_get(grid, "nz")), origin,
+            float(_get(grid, "voxel_size")))
+
+
+def _cam_args(cams):
+    wh = np.array([[int(_get(c, "width")), int(_get(c, "height"))] for c in cams],
+                  dtype=np.int32).reshape(-1)
+    rec = np.array([np.concatenate([np.asarray(_get(c, "K"), np.float64).ravel(),
+                                    np.asarray(_get(c, "R"), np.float64).ravel(),
+                                    np.asarray(_get(c, "t"), np.float64).ravel()])
+                    for c in cams], dtype=np.float64).reshape(-1)
+    return np.ascontiguousarray(wh), np.ascontiguousarray(rec)
+
+
+def _param(params, name, default=None):
+    if params is None:
+        return default
+    if isinstance(params, dict):
+        return params.get(name, default)
+    return getattr(params, name, default)
+
+
+def slm(images: np.ndarray, mean: np.ndarray, var: np.ndarray,
+        log_fg_density: float = -3.0 * np.log(256.0)) -> np.ndarray:
+    """Silhouette likelihood map (Eq. 1-2), float64 with the images' leading shape."""
+    lib = _load()
+    img = np.ascontiguousarray(images, dtype=np.uint8)
+    mu = np.ascontiguousarray(mean, dtype=np.float32)
+    va = np.ascontiguousarray(var, dtype=np.float32)
+    assert img.shape == mu.shape == va.shape and img.shape[-1] == 3
+    out = np.empty(img.shape[:-1], dtype=np.float64)
+    lib.oracle_slm(int(out.size), _ptr(img, _u8p), _ptr(mu, _f32p), _ptr(va, _f32p),
+                   float(log_fg_density), _ptr(out, _dp))
+    return out
+
+
+def project(cam, X):
+    """(visible, (px, py), (x, y), w) for a world point X, FP64."""
+    lib = _load()
+    wh, rec = _cam_args([cam])
+    Xa = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    px = ctypes.c_int(-1)
+    py = ctypes.c_int(-1)
+    xy = np.zeros(2)
+    w = np.zeros(1)
+    vis = lib.oracle_project(_ptr(rec, _dp), int(wh[0]), int(wh[1]), _ptr(Xa, _dp),
+                             ctypes.byref(px), ctypes.byref(py), _ptr(xy, _dp), _ptr(w, _dp))
+    return bool(vis), (px.value, py.value), (float(xy[0]), float(xy[1])), float(w[0])
+
+
+def fuse(grid, cams, slm_maps: np.ndarray, params=None, edge_eps: float = 1e-3) -> dict:
+    """Voxel posterior (Eq. 3-9) from per-camera SLM maps (list or stacked array)."""
+    lib = _load()
+    nx, ny, nz, origin, vs = _grid_args(grid)
+    wh, rec = _cam_args(cams)
+    if isinstance(slm_maps, (list, tuple)):
+        flat = np.concatenate([np.asarray(m, np.float64).ravel() for m in slm_maps])
+    else:
+        flat = np.asarray(slm_maps, np.float64).ravel()
+    flat = np.ascontiguousarray(flat)
+    expect = int(sum(int(wh[2 * c]) * int(wh[2 * c + 1]) for c in range(len(cams))))
+    assert flat.size == expect, (flat.size, expect)
+    nv = nx * ny * nz
+    occ = np.empty(nv)
+    lo = np.empty(nv)
+    occupied = np.empty(nv, np.uint8)
+    boundary = np.empty(nv, np.uint8)
+    n_seen = np.empty(nv, np.uint8)
+    lib.oracle_fuse(nx, ny, nz, _ptr(origin, _dp), vs, len(cams), _ptr(wh, _i32p),
+                    _ptr(rec, _dp), _ptr(flat, _dp),
+                    float(_param(params, "p_detect", 0.9)),
+                    float(_param(params, "p_false_alarm", 0.1)),
+                    float(_param(params, "prior", 0.5)),
+                    float(_param(params, "threshold", 0.5)), float(edge_eps),
+                    _ptr(occ, _dp), _ptr(lo, _dp), _ptr(occupied, _u8p), _ptr(boundary, _u8p),
+                    _ptr(n_seen, _u8p))
+    lst = np.empty(int(occupied.sum()), np.uint32)
+    n = lib.oracle_compact(nv, _ptr(occupied, _u8p), _ptr(lst, _u32p) if lst.size else None)
+    assert n == lst.size
+    return {"occ": occ, "logodds": lo, "occupied": occupied.astype(bool),
+            "boundary": boundary.astype(bool), "n_seen": n_seen, "list": lst}
+
+
+def reconstruct(grid, cams, images, mean, var, params=None, edge_eps: float = 1e-3) -> dict:
+    """Whole path: SLM maps (Eq. 1-2), posterior (Eq. 3-9), threshold, list."""
+    lfd = _param(params, "log_fg_density", -3.0 * np.log(256.0))
+    s = slm(images, mean, var, lfd)
+    out = fuse(grid, cams, s, params, edge_eps)
+    out["slm"] = s
+    return out
+
+
+def backward_slm(grid, cams, slm_maps, d_occ, params=None) -> np.ndarray:
+    """dLoss/dSLM (same shape as the stacked maps) given dLoss/docc per voxel."""
+    lib = _load()
+    nx, ny, nz, origin, vs = _grid_args(grid)
+    wh, rec = _cam_args(cams)
+    s = np.ascontiguousarray(np.asarray(slm_maps, np.float64))
+    d = np.ascontiguousarray(np.asarray(d_occ, np.float64).ravel())
+    assert d.size == nx * ny * nz
+    out = np.empty_like(s)
+    lib.oracle_backward_slm(nx, ny, nz, _ptr(origin, _dp), vs, len(cams), _ptr(wh, _i32p),
+                            _ptr(rec, _dp), _ptr(s, _dp),
+                            float(_param(params, "p_detect", 0.9)),
+                            float(_param(params, "p_false_alarm", 0.1)),
+                            float(_param(params, "prior", 0.5)), _ptr(d, _dp), _ptr(out, _dp))
+    return out
+
+
+def backward_background(images, mean, var, slm_maps, d_slm):
+    """(dLoss/dmean, dLoss/dvar) from dLoss/dSLM through Eq. 1-2."""
+    lib = _load()
+    img = np.ascontiguousarray(images, dtype=np.uint8)
+    mu = np.ascontiguousarray(mean, dtype=np.float32)
+    va = np.ascontiguousarray(var, dtype=np.float32)
+    s = np.ascontiguousarray(np.asarray(slm_maps, np.float64))
+    ds = np.ascontiguousarray(np.asarray(d_slm, np.float64))
+    dm = np.empty(img.shape, np.float64)
+    dv = np.empty(img.shape, np.float64)
+    lib.oracle_backward_background(int(s.size), _ptr(img, _u8p), _ptr(mu, _f32p),
+                                   _ptr(va, _f32p), _ptr(s, _dp), _ptr(ds, _dp),
+                                   _ptr(dm, _dp), _ptr(dv, _dp))
+    return dm, dv
+
+
+def backward(grid, cams, images, mean, var, d_occ, params=None):
+    """(d_slm, d_mean, d_var) for a loss with gradient d_occ on the occupancy."""
+    lfd = _param(params, "log_fg_density", -3.0 * np.log(256.0))
+    s = slm(images, mean, var, lfd)
+    ds = backward_slm(grid, cams, s, d_occ, params)
+    dm, dv = backward_background(images, mean, var, s, ds)
+    return ds, dm, dv

@@ -1,0 +1,258 @@
+/*
+ * psfs_oracle.c -- FP64 CPU oracle for probabilistic shape-from-silhouette.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the reconstruction computes, written from the paper
+ * (Section 2.2.2, Eq. 1-9).  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.  The CUDA library never links,
+ * includes or calls it, and it shares no header, helper or constant with it.
+ *
+ * Every quantity is double precision.  Nothing here is blocked, fused or
+ * reordered: each function follows the equations in the paper's order.
+ *
+ * Conventions (the readings of the paper where it is silent; each is also
+ * listed with its reason in the design notes of the repository):
+ *   - pixel colour I is an RGB triple; the background likelihood is a single
+ *     Gaussian per pixel with independent channels (diagonal covariance,
+ *     variance given per channel)                               (Eq. 1, text)
+ *   - the foreground likelihood is uniform over the RGB cube, density U,
+ *     passed as log U (default -3 log 256)                      (Eq. 1, text)
+ *   - equal priors P(F=1) = P(F=0) = 1/2                        (Eq. 1-2)
+ *   - camera: x_cam = R X + t, (u, v, w) = K x_cam, image point (u/w, v/w);
+ *     pixel (x, y) covers [x, x+1) x [y, y+1); the voxel centre is projected
+ *     and looked up in the pixel containing it                  (Eq. 3 text)
+ *   - a camera in which the voxel centre is behind the camera or outside the
+ *     image contributes no factor                               (silent)
+ *   - sensor model with detection rate P_D and false-alarm rate P_FA; with
+ *     P_D = 1, P_FA = 0 it is exactly Eq. 6-9                   (Eq. 5-9)
+ *   - occupied  <=>  posterior > threshold (strict)             (Sec. 2.2.2 end)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* camera record: K[9], R[9], t[3] (row-major), 21 doubles per camera */
+#define ORACLE_CAM_STRIDE 21
+
+/* --------------------------------------------------------------------- */
+/* Eq. 1-2: silhouette likelihood map.                                    */
+/*   N = prod_c (2 pi var_c)^(-1/2) exp(-(I_c - mu_c)^2 / (2 var_c))      */
+/*   SLM = U P(F=1) / (U P(F=1) + N P(F=0)) = U / (U + N)   (priors 1/2)  */
+/* --------------------------------------------------------------------- */
+void oracle_slm(int64_t n_pix, const uint8_t *img, const float *mean, const float *var,
+                double log_fg_density, double *slm)
+{
+    const double U = exp(log_fg_density);
+    const double pi = 3.14159265358979323846;
+    for (int64_t p = 0; p < n_pix; ++p) {
+        double N = 1.0;
+        for (int c = 0; c < 3; ++c) {
+            double I = (double)img[3 * p + c];
+            double mu = (double)mean[3 * p + c];
+            double v = (double)var[3 * p + c];
+            double d = I - mu;
+            N *= exp(-d * d / (2.0 * v)) / sqrt(2.0 * pi * v);
+        }
+        double pf1 = 0.5, pf0 = 0.5;
+        slm[p] = U * pf1 / (U * pf1 + N * pf0);
+    }
+}
+
+/* --------------------------------------------------------------------- */
+/* Projection of a world point (the "projection of voxel V_i", Eq. 3).    */
+/* Returns 1 and the pixel if the point is in front of the camera and     */
+/* inside the image; *xy gets the continuous image position either way    */
+/* (when w > 0).  Returns 0 if not seen.                                  */
+/* --------------------------------------------------------------------- */
+int oracle_project(const double *cam, int W, int H, const double X[3],
+                   int *px, int *py, double xy[2], double *w_out)
+{
+    const double *K = cam, *R = cam + 9, *t = cam + 18;
+    double xc[3];
+    for (int r = 0; r < 3; ++r)
+        xc[r] = R[3 * r + 0] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
+    double uvw[3];
+    for (int r = 0; r < 3; ++r)
+        uvw[r] = K[3 * r + 0] * xc[0] + K[3 * r + 1] * xc[1] + K[3 * r + 2] * xc[2];
+    *w_out = uvw[2];
+    if (!(uvw[2] > 0.0)) return 0;
+    double x = uvw[0] / uvw[2];
+    double y = uvw[1] / uvw[2];
+    xy[0] = x;
+    xy[1] = y;
+    if (!(x >= 0.0 && x < (double)W && y >= 0.0 && y < (double)H)) return 0;
+    *px = (int)floor(x);
+    *py = (int)floor(y);
+    return 1;
+}
+
+static double dist_to_integer(double x)
+{
+    return fabs(x - floor(x + 0.5));
+}
+
+/* --------------------------------------------------------------------- */
+/* Eq. 5 with Eq. 6-9 generalised by the rates:                           */
+/*   P(S | O=0, V=0) = P_FA s + (1 - P_FA)(1 - s)          ("nothing")     */
+/*   P(S | O, V) with O = 1 or V = 1 = P_D s + (1 - P_D)(1 - s)            */
+/*   P(S | V=1) = sum_O P(S | O, V=1) P(O) = a                             */
+/*   P(S | V=0) = P(O=0) f + P(O=1) a = (f + a) / 2                        */
+/* --------------------------------------------------------------------- */
+static void sensor_terms(double s, double pd, double pfa, double *a, double *b)
+{
+    double p_o1 = 0.5, p_o0 = 0.5;
+    double something = pd * s + (1.0 - pd) * (1.0 - s);   /* V = 1 or O = 1 */
+    double nothing = pfa * s + (1.0 - pfa) * (1.0 - s);   /* V = 0 and O = 0 */
+    *a = something * p_o0 + something * p_o1;              /* V = 1 */
+    *b = nothing * p_o0 + something * p_o1;                /* V = 0 */
+}
+
+/* --------------------------------------------------------------------- */
+/* Eq. 3-4: voxel posterior, literal product over the cameras.            */
+/*   occ = prior prod a / (prior prod a + (1 - prior) prod b)             */
+/* Outputs per voxel (linear index i + nx (j + ny k)):                     */
+/*   occ, logodds = log(prior prod a) - log((1-prior) prod b),            */
+/*   occupied = occ > threshold, boundary = 1 if in some camera the        */
+/*   continuous projection lies within edge_eps px of a pixel edge or of   */
+/*   the image border, n_seen = number of cameras that see the centre.     */
+/* --------------------------------------------------------------------- */
+void oracle_fuse(int nx, int ny, int nz, const double origin[3], double voxel_size,
+                 int n_cams, const int *wh, const double *cams, const double *slm,
+                 double pd, double pfa, double prior, double threshold, double edge_eps,
+                 double *occ, double *logodds, uint8_t *occupied, uint8_t *boundary,
+                 uint8_t *n_seen)
+{
+    /* per-camera offsets into the concatenated maps */
+    int64_t *map_off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_cams > 0 ? n_cams : 1));
+    int64_t off = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        map_off[c] = off;
+        off += (int64_t)wh[2 * c] * wh[2 * c + 1];
+    }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t v = (int64_t)i + (int64_t)nx * ((int64_t)j + (int64_t)ny * k);
+                double X[3] = {origin[0] + (i + 0.5) * voxel_size,
+                               origin[1] + (j + 0.5) * voxel_size,
+                               origin[2] + (k + 0.5) * voxel_size};
+                double A = 1.0, B = 1.0;   /* P({S}|V=1), P({S}|V=0), Eq. 4 */
+                int bnd = 0, seen = 0;
+                for (int c = 0; c < n_cams; ++c) {
+                    int W = wh[2 * c], H = wh[2 * c + 1];
+                    int px = 0, py = 0;
+                    double xy[2] = {-1e300, -1e300}, w = 0.0;
+                    int vis = oracle_project(cams + ORACLE_CAM_STRIDE * c, W, H, X, &px, &py, xy, &w);
+                    if (w > 0.0 && xy[0] >= -edge_eps && xy[0] <= W + edge_eps &&
+                        xy[1] >= -edge_eps && xy[1] <= H + edge_eps &&
+                        (dist_to_integer(xy[0]) < edge_eps || dist_to_integer(xy[1]) < edge_eps))
+                        bnd = 1;
+                    if (!vis) continue;
+                    ++seen;
+                    double s = slm[map_off[c] + (int64_t)py * W + px];
+                    double a, b;
+                    sensor_terms(s, pd, pfa, &a, &b);
+                    A *= a;
+                    B *= b;
+                }
+                double num = prior * A;
+                double den = prior * A + (1.0 - prior) * B;
+                occ[v] = num / den;
+                logodds[v] = log(prior * A) - log((1.0 - prior) * B);
+                occupied[v] = occ[v] > threshold ? 1 : 0;
+                boundary[v] = (uint8_t)bnd;
+                n_seen[v] = (uint8_t)(seen > 255 ? 255 : seen);
+            }
+    free(map_off);
+}
+
+/* Thresholded voxels as ascending linear indices; returns the count. */
+int64_t oracle_compact(int64_t n_vox, const uint8_t *occupied, uint32_t *list)
+{
+    int64_t n = 0;
+    for (int64_t v = 0; v < n_vox; ++v)
+        if (occupied[v]) list[n++] = (uint32_t)v;
+    return n;
+}
+
+/* --------------------------------------------------------------------- */
+/* Adjoint of Eq. 3-4 with respect to the maps.                           */
+/* Given dLoss/docc per voxel:                                            */
+/*   dLoss/dlogodds_v = docc_v occ_v (1 - occ_v)                          */
+/*   dlogodds_v/ds = (da/ds)/a - (db/ds)/b at the pixel v projects to,    */
+/*   da/ds = 2 P_D - 1, df/ds = 2 P_FA - 1, db/ds = (da/ds + df/ds) / 2   */
+/*   dLoss/ds_p = sum over voxels that project to p (free scatter here).  */
+/* --------------------------------------------------------------------- */
+void oracle_backward_slm(int nx, int ny, int nz, const double origin[3], double voxel_size,
+                         int n_cams, const int *wh, const double *cams, const double *slm,
+                         double pd, double pfa, double prior, const double *d_occ,
+                         double *d_slm)
+{
+    int64_t *map_off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_cams > 0 ? n_cams : 1));
+    int64_t off = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        map_off[c] = off;
+        off += (int64_t)wh[2 * c] * wh[2 * c + 1];
+    }
+    memset(d_slm, 0, sizeof(double) * (size_t)off);
+    int *pxs = (int *)malloc(sizeof(int) * (size_t)(n_cams > 0 ? n_cams : 1));
+    int *pys = (int *)malloc(sizeof(int) * (size_t)(n_cams > 0 ? n_cams : 1));
+    int *vis = (int *)malloc(sizeof(int) * (size_t)(n_cams > 0 ? n_cams : 1));
+    const double da = 2.0 * pd - 1.0, df = 2.0 * pfa - 1.0, db = 0.5 * (da + df);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t v = (int64_t)i + (int64_t)nx * ((int64_t)j + (int64_t)ny * k);
+                double X[3] = {origin[0] + (i + 0.5) * voxel_size,
+                               origin[1] + (j + 0.5) * voxel_size,
+                               origin[2] + (k + 0.5) * voxel_size};
+                double A = 1.0, B = 1.0;
+                for (int c = 0; c < n_cams; ++c) {
+                    double xy[2], w;
+                    vis[c] = oracle_project(cams + ORACLE_CAM_STRIDE * c, wh[2 * c], wh[2 * c + 1],
+                                            X, &pxs[c], &pys[c], xy, &w);
+                    if (!vis[c]) continue;
+                    double s = slm[map_off[c] + (int64_t)pys[c] * wh[2 * c] + pxs[c]];
+                    double a, b;
+                    sensor_terms(s, pd, pfa, &a, &b);
+                    A *= a;
+                    B *= b;
+                }
+                double occ = prior * A / (prior * A + (1.0 - prior) * B);
+                double dl = d_occ[v] * occ * (1.0 - occ);
+                for (int c = 0; c < n_cams; ++c) {
+                    if (!vis[c]) continue;
+                    int64_t p = map_off[c] + (int64_t)pys[c] * wh[2 * c] + pxs[c];
+                    double s = slm[p];
+                    double a, b;
+                    sensor_terms(s, pd, pfa, &a, &b);
+                    d_slm[p] += dl * (da / a - db / b);
+                }
+            }
+    free(pxs);
+    free(pys);
+    free(vis);
+    free(map_off);
+}
+
+/* --------------------------------------------------------------------- */
+/* Adjoint of Eq. 1-2 with respect to the background mean and variance.  */
+/*   ds/dmu_c  = -s (1 - s) (I_c - mu_c) / var_c                           */
+/*   ds/dvar_c =  s (1 - s) (1 / (2 var_c) - (I_c - mu_c)^2 / (2 var_c^2)) */
+/* --------------------------------------------------------------------- */
+void oracle_backward_background(int64_t n_pix, const uint8_t *img, const float *mean,
+                                const float *var, const double *slm, const double *d_slm,
+                                double *d_mean, double *d_var)
+{
+    for (int64_t p = 0; p < n_pix; ++p) {
+        double s = slm[p];
+        double g = d_slm[p] * s * (1.0 - s);
+        for (int c = 0; c < 3; ++c) {
+            double d = (double)img[3 * p + c] - (double)mean[3 * p + c];
+            double v = (double)var[3 * p + c];
+            d_mean[3 * p + c] = -g * d / v;
+            d_var[3 * p + c] = g * (1.0 / (2.0 * v) - d * d / (2.0 * v * v));
+        }
+    }
+}
