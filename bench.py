@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Throughput of GB300 probabilistic shape-from-silhouette (PSFS) on the
+128^3-voxel x 8-camera (640x480) walking-sequence workload.
+
+One step = the whole hot path (per-pixel likelihood kernel + per-voxel
+fusion / threshold / compaction kernel) over every frame of the synthetic
+100-frame sequence, inputs resident in HBM.  The metric is Gvoxel-camera
+evaluations per second (frames x voxels x cameras / time); frames/s is in
+`config`.  With torchrun (N > 1) every rank runs its own copy of the
+sequence (frames are independent: weak scaling, no collective on the data
+path); the timed region is bracketed by barriers and the max over ranks is
+taken.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead (one
+frame per step, a bounded sample of the same workload).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+GRID_N, N_CAMS, WIDTH, HEIGHT = 128, 8, 640, 480
+METRIC = "Gvoxel-camera evals/s (128^3 x 8 cams)"
+UNIT = "Gvox-cam/s"
+WORKLOAD = "psfs 128^3 grid x 8 cams 640x480, walking sequence"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=100, help="frames per step (the sequence length)")
+    ap.add_argument("--map-dtype", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-sample-frames", type=int, default=6,
+                    help="frames the CPU oracle baseline times (bounded sample)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workers", type=int, default=min(8, os.cpu_count() or 1),
+                    help="processes rendering the synthetic frames")
+    return ap.parse_args(argv)
+
+
+# --------------------------------------------------------------------------- #
+# distributed plumbing (one process per GPU)
+# --------------------------------------------------------------------------- #
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return ws, rank
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- #
+# clocks during the timed region
+# --------------------------------------------------------------------------- #
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.15)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- #
+# helpers
+# --------------------------------------------------------------------------- #
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1311_6811_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        rec = d.get("kernels", {}).get(kernel)
+        if not rec or rec.get("csrc_sha") != csrc_digest():
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except (ValueError, KeyError, OSError):
+        return None
+
+
+def make_scene(args):
+    from synth import scene as S
+    return S.scene_128cube_8cam(seed=args.seed, n_frames=args.frames, workers=args.workers)
+
+
+def cpu_baseline(sc, n_frames: int):
+    """The FP64 oracle as it stands, single-threaded, on `n_frames` frames."""
+    import oracle
+    oracle.build()
+    v = sc.grid.n_voxels * sc.n_cams
+    t0 = time.perf_counter()
+    for f in range(n_frames):
+        oracle.reconstruct(sc.grid, sc.cams, sc.images[f], sc.mean, sc.var, sc.params)
+    dt = time.perf_counter() - t0
+    return {"value": n_frames * v / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_frames} frames of the sequence (FP64 C oracle, 1 thread), {dt:.1f} s"}
+
+
+# --------------------------------------------------------------------------- #
+# reference arm: the oracle on the host cores
+# --------------------------------------------------------------------------- #
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    from synth import scene as S
+    n_frames = max(args.steps + args.warmup, 1)
+    sc = S.scene_128cube_8cam(seed=args.seed, n_frames=min(n_frames, args.frames) if args.frames > 1 else 1,
+                              workers=args.workers)
+    imgs = sc.images if sc.images.ndim == 5 else sc.images[None]
+    v = sc.grid.n_voxels * sc.n_cams
+    for w in range(args.warmup):
+        oracle.reconstruct(sc.grid, sc.cams, imgs[w % len(imgs)], sc.mean, sc.var, sc.params)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.reconstruct(sc.grid, sc.cams, imgs[(args.warmup + s) % len(imgs)], sc.mean, sc.var, sc.params)
+    dt = time.perf_counter() - t0
+    value = args.steps * v / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (one frame per step)", "grid": GRID_N, "cams": N_CAMS,
+                       "width": WIDTH, "height": HEIGHT, "frames_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one frame per step, {args.steps} steps, FP64 C oracle, 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- #
+# our arm
+# --------------------------------------------------------------------------- #
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    # render the synthetic sequence before any CUDA call (the renderer may fork workers)
+    sc = make_scene(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist_init("nccl")
+    from paper_1311_6811_gb300 import psfs
+
+    F = args.frames
+    images = sc.images if sc.images.ndim == 5 else sc.images[None]
+    F = images.shape[0]
+    V = sc.grid.n_voxels
+    K = sc.n_cams
+    n_pix = K * HEIGHT * WIDTH
+    stream = torch.cuda.Stream(device=dev)
+    cap = 1 << 20
+    with torch.cuda.stream(stream):
+        d_images = torch.from_numpy(images).to(dev)
+        occ = torch.empty((F, V), dtype=torch.float32, device=dev)
+        lists = torch.empty((F, cap), dtype=torch.int32, device=dev)
+        counts = torch.zeros((F, 4), dtype=torch.int32, device=dev)
+        rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=args.map_dtype, stream=stream,
+                                 device=dev, capacity=cap)
+        rec.set_background(torch.from_numpy(sc.mean).to(dev), torch.from_numpy(sc.var).to(dev))
+    stream.synchronize()
+    h = rec.handle
+
+    def step():
+        for f in range(F):
+            psfs.psfs_reconstruct(h, d_images[f], occ[f], lists[f], cap, counts[f])
+
+    for _ in range(args.warmup):
+        step()
+    st = psfs.psfs_sync(h)
+    if st != psfs.PSFS_OK:
+        raise RuntimeError(f"warm-up frame failed: {psfs.psfs_status_string(st)}")
+
+    # timed region: device time with events on the launching stream; every
+    # launch bracketed by the library's event profiler for per-kernel times
+    psfs.psfs_profile_enable(h, 2 * F * args.steps + 8)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms_local = e0.elapsed_time(e1)
+    prof = psfs.psfs_profile_read(h)
+    psfs.psfs_profile_enable(h, 0)
+    st = psfs.psfs_sync(h)
+    if st != psfs.PSFS_OK:
+        raise RuntimeError(f"timed frame failed: {psfs.psfs_status_string(st)}")
+    ms = max_over_ranks(ms_local, dev)
+    total_evals = sum_over_ranks(float(F * V * K * args.steps), dev)
+    value = total_evals / (ms * 1e-3) / 1e9
+    ms_per_step = ms / max(args.steps, 1)
+    mean_count = float(counts[:, 0].double().mean().item())
+
+    # roofline of the dominant kernel (algorithmic bytes / average launch time)
+    map_elem = 4 if args.map_dtype == "f32" else 2
+    alg_bytes = {"likelihood": n_pix * (3 + 24 + map_elem),
+                 "fuse": n_pix * map_elem + V * 4 + mean_count * 4}
+    kern_names = {"likelihood": "likelihood_kernel", "fuse": "fuse_kernel"}
+    stages = {}
+    for name, (t_ms, n) in prof.items():
+        avg = t_ms / n
+        stages[name] = {"launches": n, "avg_us": 1e3 * avg, "share": None,
+                        "alg_bytes_per_launch": alg_bytes.get(name),
+                        "achieved_gbs": alg_bytes[name] / (avg * 1e-3) / 1e9 if name in alg_bytes else None}
+    tot = sum(v["avg_us"] * v["launches"] for v in stages.values())
+    for v in stages.values():
+        v["share"] = v["avg_us"] * v["launches"] / tot if tot else None
+    dom = max(stages, key=lambda k: stages[k]["avg_us"] * stages[k]["launches"])
+    peak, peak_kind = measured_peaks()
+    ach = stages[dom]["achieved_gbs"]
+    traffic = ncu_traffic(kern_names.get(dom, dom))
+    roofline = {"bound": "hbm", "kernel": kern_names.get(dom, dom), "achieved": ach, "peak": peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": traffic,
+                "alg_bytes_per_launch": stages[dom]["alg_bytes_per_launch"]}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        h_images = torch.from_numpy(images).pin_memory()
+        h_occ = torch.empty((V,), dtype=torch.float32).pin_memory()
+        h_list = torch.empty((cap,), dtype=torch.int32).pin_memory()
+        h_cnt = torch.zeros((4,), dtype=torch.int32).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+        for f in range(min(F, 3)):
+            psfs.psfs_reconstruct_host(h, h_images[f], h_occ, h_list, cap, h_cnt)
+        d2h = 0
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for f in range(F):
+                psfs.psfs_reconstruct_host(h, h_images[f], h_occ, h_list, cap, h_cnt)
+                d2h += V * 4 + 4 + 4 * min(int(h_cnt[0]), cap)
+        dt = max_over_ranks(time.perf_counter() - t0, dev)
+        barrier()
+        e2e = {"value": sum_over_ranks(float(F * V * K * e2e_steps), dev) / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": F * n_pix * 3, "d2h_bytes_per_step": int(d2h / e2e_steps),
+               "steps": e2e_steps, "path": "psfs_reconstruct_host per frame (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(sc, min(args.cpu_sample_frames, F))
+
+    rec.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.map_dtype == "f32" else
+                f"f32 (maps {args.map_dtype})", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": GRID_N, "cams": N_CAMS, "width": WIDTH,
+                           "height": HEIGHT, "frames_per_step": F, "map_dtype": args.map_dtype,
+                           "frames_per_s": F * args.steps * ws / (ms * 1e-3),
+                           "occupied_voxels_per_frame": mean_count,
+                           "l2": f"inputs larger than L2: {F * n_pix * 3 / 1e6:.0f} MB of images per step",
+                           "parallelism": f"replicas x{ws} (frames independent)"},
+                "stages": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": sum(v["launches"] for v in stages.values()), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * psfs.h -- C ABI of libpsfs: probabilistic shape-from-silhouette (PSFS) on
+ * GB300 (sm_103a).
+ *
+ * The library computes, per frame, the reconstruction stage of Song, Bian,
+ * Yan, Zhao, Liu, "Digitize Your Body and Action in 3-D at Over 10 FPS"
+ * (Section 2.2.2):
+ *
+ *   1. per pixel, the silhouette likelihood SLM = P(F = 1 | I) of a single
+ *      Gaussian colour background against a uniform foreground with equal
+ *      priors (Eq. 1-2);
+ *   2. per voxel, the projection of its centre into every camera (Eq. 3),
+ *      the sensor model with a latent occluder marginalised out (Eq. 5-9,
+ *      generalised with a detection rate P_D and a false-alarm rate P_FA),
+ *      and the posterior as a product over cameras (Eq. 3-4), evaluated as a
+ *      sum of per-camera log ratios;
+ *   3. thresholding of the posterior ("perform a thresholding process",
+ *      end of Section 2.2.2) and stream compaction of the occupied voxels
+ *      into a list.
+ *
+ * Conventions used by every call:
+ *   - grid: voxel (i, j, k) has its centre at
+ *       origin + (i + 1/2, j + 1/2, k + 1/2) * voxel_size
+ *     and linear index i + nx * (j + ny * k) (x fastest);
+ *   - camera: x_cam = R X + t, (u, v, w) = K x_cam; a point is seen iff
+ *     w > 0 and 0 <= u/w < width and 0 <= v/w < height; it then falls in
+ *     pixel (floor(u/w), floor(v/w)).  A camera that does not see a voxel
+ *     centre contributes no factor to that voxel;
+ *   - images: uint8 [n_cams][height][width][3] (RGB interleaved); background
+ *     mean and variance: float32 [n_cams][height][width][3]; every camera of
+ *     a handle has the same width and height;
+ *   - occupancy: float32 [nz][ny][nx]; the voxel list holds uint32 linear
+ *     indices in unspecified order.
+ *
+ * Memory: "device" arguments are CUDA device pointers of the handle's device;
+ * "host" arguments are host pointers (pinned memory gives the fastest copies).
+ * Device arrays must be 16-byte aligned, except the voxel list and the count
+ * (4-byte aligned).  The caller owns every buffer
+ * it passes; the handle owns its scratch (likelihood maps, packed background,
+ * status word) and frees it in psfs_destroy.
+ *
+ * Asynchrony and errors: every call checks its arguments on the host and
+ * returns PSFS_ERR_INVALID_ARG at once if one is wrong.  Calls that take
+ * device pointers only enqueue work on the handle's stream and return; a
+ * problem found on the device (voxel list overflow) is recorded in the
+ * handle's status word and reported by the next psfs_sync.  Calls taking host
+ * pointers synchronise the stream before they return and report device
+ * problems themselves.  A handle is not thread-safe; use one per stream.
+ */
+#ifndef PSFS_H
+#define PSFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSFS_MAX_CAMS 32
+
+typedef enum {
+    PSFS_OK = 0,
+    PSFS_ERR_INVALID_ARG = 1,  /* an argument failed the host-side checks        */
+    PSFS_ERR_NOT_READY = 2,    /* psfs_set_background has not succeeded yet      */
+    PSFS_ERR_CAPACITY = 3,     /* voxel list overflow: count holds the true count */
+    PSFS_ERR_CUDA = 4,         /* a CUDA runtime call failed                      */
+    PSFS_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out              */
+    PSFS_ERR_NOMEM = 6         /* device or pinned allocation failed              */
+} psfs_status;
+
+typedef enum {
+    PSFS_MAP_F32 = 0,   /* likelihood maps stored as float32                      */
+    PSFS_MAP_F16 = 1,   /* stored as IEEE half; accumulation stays float32        */
+    PSFS_MAP_BF16 = 2   /* stored as bfloat16; accumulation stays float32         */
+} psfs_map_dtype;
+
+/* Regular voxel grid (Section 2.2.2, "volume of interest"). */
+typedef struct {
+    int32_t nx, ny, nz;     /* voxels per axis, each >= 1, product < 2^32        */
+    double origin[3];       /* world position of the grid's minimum corner (m)   */
+    double voxel_size;      /* edge length (m), > 0                               */
+} psfs_grid;
+
+/* Calibrated pinhole camera (perspective projection, Section 2.2.1). */
+typedef struct {
+    int32_t width, height;  /* pixels, >= 1                                       */
+    double K[9];            /* intrinsics, row-major                              */
+    double R[9];            /* world-to-camera rotation, row-major                */
+    double t[3];            /* world-to-camera translation                        */
+} psfs_camera;
+
+/* Model parameters. */
+typedef struct {
+    double p_detect;        /* P_D in [0, 1]: P(S | something on the line) uses
+                               P_D s + (1 - P_D)(1 - s)                  (Eq. 7-9) */
+    double p_false_alarm;   /* P_FA in [0, 1]: P(S | nothing on the line) uses
+                               P_FA s + (1 - P_FA)(1 - s)                   (Eq. 6) */
+    double prior;           /* P(V = 1) in (0, 1)                          (Eq. 3) */
+    double threshold;       /* occupied iff posterior > threshold, in (0, 1)       */
+    double log_fg_density;  /* log U of the uniform foreground colour density
+                               (Eq. 1); -3 log 256 = uniform over the RGB cube     */
+    int32_t map_dtype;      /* psfs_map_dtype of the stored likelihood maps        */
+} psfs_params;
+
+typedef struct psfs_handle psfs_handle;
+
+/* Fills `p` with P_D = 0.9, P_FA = 0.1, prior = 0.5, threshold = 0.5,
+ * log U = -3 log 256, float32 maps.  With P_D = 1 and P_FA = 0 the sensor
+ * model is Eq. 6-9 of the paper verbatim. */
+void psfs_params_default(psfs_params *p);
+
+/* Creates a handle for one grid and one camera rig on the current CUDA
+ * device.  `stream` is a cudaStream_t (NULL = the legacy default stream) on
+ * which every later call enqueues its work.  Requirements: 1 <= n_cams <=
+ * PSFS_MAX_CAMS, all cameras of the same size, finite matrices, valid
+ * parameters with (P_D + P_FA) / 2 strictly between 0 and 1.  Allocates the
+ * handle's device scratch.  On success *out receives the handle.
+ * Errors: INVALID_ARG, NOMEM, CUDA. */
+psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t n_cams,
+                        const psfs_params *params, void *stream, psfs_handle **out);
+
+/* Sets the per-pixel background model of Eq. 1: `mean` and `var` are device
+ * float32 [n_cams][height][width][3]; each variance must be finite and in
+ * [1e-6, 1e12], each mean finite.  The handle keeps a packed copy (mean and
+ * 1 / (2 var)), so the caller may free its buffers afterwards.  Synchronises
+ * the stream.  Errors: INVALID_ARG (also for out-of-range values found on the
+ * device), CUDA. */
+psfs_status psfs_set_background(psfs_handle *h, const float *mean, const float *var);
+
+/* One frame of the reconstruction (Eq. 1-9, threshold, compaction).
+ *   images     device uint8 [n_cams][height][width][3]
+ *   occupancy  device float32 [nz][ny][nx], posterior P(V = 1 | S)   (Eq. 3)
+ *   voxel_list device uint32 [capacity], linear indices of the voxels with
+ *              posterior > threshold, unspecified order (may be NULL if
+ *              capacity == 0)
+ *   count      device uint32 [1], number of occupied voxels (even beyond
+ *              capacity; only the first `capacity` are written)
+ * Enqueues two kernels and returns.  Overflow is reported by psfs_sync as
+ * PSFS_ERR_CAPACITY.  Errors: INVALID_ARG, NOT_READY, CUDA. */
+psfs_status psfs_reconstruct(psfs_handle *h, const uint8_t *images, float *occupancy,
+                             uint32_t *voxel_list, uint32_t capacity, uint32_t *count);
+
+/* psfs_reconstruct with HOST buffers: copies the images to the device, runs
+ * the frame, copies the occupancy, the count and min(count, capacity) list
+ * entries back, and synchronises.  Host buffers have the shapes of
+ * psfs_reconstruct; h_occupancy may be NULL to skip its copy.  Returns
+ * PSFS_ERR_CAPACITY on overflow (the list then holds `capacity` entries).
+ * Errors: INVALID_ARG, NOT_READY, CAPACITY, NOMEM, CUDA. */
+psfs_status psfs_reconstruct_host(psfs_handle *h, const uint8_t *h_images, float *h_occupancy,
+                                  uint32_t *h_list, uint32_t capacity, uint32_t *h_count);
+
+/* Steps 2-3 only, from caller-supplied likelihood maps: `slm` is device
+ * float32 [n_cams][height][width] holding SLM = P(F = 1 | I) in [0, 1]
+ * (Eq. 2).  Outputs as psfs_reconstruct.  Values outside [0, 1] give
+ * unspecified results.  Errors: INVALID_ARG, CUDA. */
+psfs_status psfs_fuse_slm(psfs_handle *h, const float *slm, float *occupancy,
+                          uint32_t *voxel_list, uint32_t capacity, uint32_t *count);
+
+/* The silhouette likelihood maps SLM (Eq. 2) of a frame, float32
+ * [n_cams][height][width] into device `slm_out`.  For inspection and tests;
+ * the reconstruction stores log-ratio maps internally instead.
+ * Errors: INVALID_ARG, NOT_READY, CUDA. */
+psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *slm_out);
+
+/* Adjoint of psfs_reconstruct.  Given d_occ = dLoss/d occupancy (device
+ * float32 [nz][ny][nx]) for the frame `images`, recomputes the forward and
+ * writes (each may be NULL to skip it)
+ *   d_slm   device float32 [n_cams][height][width]     dLoss/dSLM
+ *   d_mean  device float32 [n_cams][height][width][3]  dLoss/d mean
+ *   d_var   device float32 [n_cams][height][width][3]  dLoss/d var
+ * Pixels that no voxel centre projects to get exactly zero.  Deterministic:
+ * no atomics; each pixel's sum is formed by the thread that owns it.
+ * Errors: INVALID_ARG, NOT_READY, CUDA. */
+psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_occ,
+                          float *d_slm, float *d_mean, float *d_var);
+
+/* Waits for the handle's stream, then returns and clears the first problem
+ * recorded on the device since the last psfs_sync (PSFS_ERR_CAPACITY), or
+ * PSFS_OK.  Errors: CUDA. */
+psfs_status psfs_sync(psfs_handle *h);
+
+/* Frees the handle and its scratch (after waiting for its stream).  NULL is a
+ * no-op. */
+void psfs_destroy(psfs_handle *h);
+
+/* Stages timed by the profiler below. */
+typedef enum {
+    PSFS_STAGE_LIKELIHOOD = 0,   /* per-pixel kernel (Eq. 1-2 and log ratio)        */
+    PSFS_STAGE_FUSE = 1,         /* per-voxel kernel (Eq. 3-9, threshold, list)     */
+    PSFS_STAGE_BACKWARD_VOXEL = 2,  /* adjoint: recomputed log-odds -> dLoss/dL     */
+    PSFS_STAGE_BACKWARD_PIXEL = 3,  /* adjoint: per-pixel owner pass + chain rule   */
+    PSFS_STAGE_BATCH = 4,        /* batched persistent launch                       */
+    PSFS_N_STAGES = 8
+} psfs_stage;
+
+/* Tracing: with max_launches > 0, every later kernel launch of the handle is
+ * bracketed by two CUDA events on its stream (a pool sized for max_launches
+ * launches between two reads; launches beyond it are not timed).  0 turns it
+ * off and frees the pool.  Errors: INVALID_ARG, CUDA. */
+psfs_status psfs_profile_enable(psfs_handle *h, int32_t max_launches);
+
+/* Waits for the stream and writes, per psfs_stage, the summed device time in
+ * milliseconds and the number of timed launches since the previous read
+ * (arrays of PSFS_N_STAGES entries), then resets them.  Errors: INVALID_ARG,
+ * CUDA. */
+psfs_status psfs_profile_read(psfs_handle *h, double *ms, int32_t *launches);
+
+/* Static English name of a status code. */
+const char *psfs_status_string(psfs_status s);
+
+/* Text describing the last failure returned to the calling thread (which
+ * argument, which CUDA call).  Valid until the thread's next failing call. */
+const char *psfs_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSFS_H */

@@ -1,0 +1,582 @@
+// psfs_api.cu -- host side of libpsfs: the C ABI declared in include/psfs.h.
+//
+// Argument checking, handle state, device scratch, and the order of the
+// kernel launches of each call.  No arithmetic of the method runs here
+// beyond the per-camera projection matrices and scalar constants, which are
+// formed once in double precision at handle creation.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "psfs_internal.cuh"
+
+using namespace psfs;
+
+struct psfs_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    psfs_grid grid{};
+    std::vector<psfs_camera> cams;
+    int n_cams = 0;
+    int W = 0, H = 0;
+    psfs_params params{};
+    int64_t n_pix = 0;          // n_cams * H * W
+    size_t map_elem = 4;
+
+    SensorConsts sc{};
+    float c0 = 0.0f;
+    FuseArgs fuse{};            // per-call pointers filled in at launch
+
+    void *maps = nullptr;       // [n_cams][H][W] of g
+    float *bg_mean = nullptr;   // [n_pix][3]
+    float *bg_hinv = nullptr;   // [n_pix][3]
+    bool bg_ready = false;
+    uint32_t *d_words = nullptr;    // [0] status, [1] scratch counter, [2] host-path count
+    uint32_t *h_words = nullptr;    // pinned mirror
+    uint64_t *tiles = nullptr;
+    int n_tiles = 0;
+
+    // host-buffer path staging (allocated on first use)
+    uint8_t *st_images = nullptr;
+    float *st_occ = nullptr;
+    uint32_t *st_list = nullptr;
+    uint32_t st_list_cap = 0;
+
+    // tracing: CUDA event pairs around each launch
+    int prof_cap = 0;
+    std::vector<cudaEvent_t> prof_ev;      // 2 * prof_cap events
+    std::vector<int> prof_stage;           // stage of each recorded pair
+    int prof_n = 0;
+
+    // adjoint scratch (allocated on first use)
+    float *dl = nullptr;        // [n_vox] dLoss / dlogodds
+    float *dg = nullptr;        // [n_pix] dLoss / dg
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+psfs_status fail(psfs_status s, const char *what)
+{
+    g_last_error = what;
+    return s;
+}
+
+psfs_status fail_cuda(cudaError_t e, const char *where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return PSFS_ERR_CUDA;
+}
+
+#define PSFS_CK(call)                                                  \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return fail_cuda(e_, #call);            \
+    } while (0)
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+bool finite_all(const double *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+uint64_t spread3(uint64_t x)
+{
+    // spread the low 21 bits of x to every third bit
+    x &= 0x1FFFFFull;
+    x = (x | (x << 32)) & 0x1F00000000FFFFull;
+    x = (x | (x << 16)) & 0x1F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+psfs_status check_params(const psfs_params *p)
+{
+    if (!p) return fail(PSFS_ERR_INVALID_ARG, "params is NULL");
+    const double v[5] = {p->p_detect, p->p_false_alarm, p->prior, p->threshold, p->log_fg_density};
+    if (!finite_all(v, 5)) return fail(PSFS_ERR_INVALID_ARG, "params: non-finite value");
+    if (p->p_detect < 0 || p->p_detect > 1) return fail(PSFS_ERR_INVALID_ARG, "p_detect outside [0, 1]");
+    if (p->p_false_alarm < 0 || p->p_false_alarm > 1)
+        return fail(PSFS_ERR_INVALID_ARG, "p_false_alarm outside [0, 1]");
+    const double q = 0.5 * (p->p_detect + p->p_false_alarm);
+    if (!(q > 0 && q < 1)) return fail(PSFS_ERR_INVALID_ARG, "(p_detect + p_false_alarm) / 2 must be in (0, 1)");
+    if (!(p->prior > 0 && p->prior < 1)) return fail(PSFS_ERR_INVALID_ARG, "prior outside (0, 1)");
+    if (!(p->threshold > 0 && p->threshold < 1)) return fail(PSFS_ERR_INVALID_ARG, "threshold outside (0, 1)");
+    if (p->map_dtype != PSFS_MAP_F32 && p->map_dtype != PSFS_MAP_F16 && p->map_dtype != PSFS_MAP_BF16)
+        return fail(PSFS_ERR_INVALID_ARG, "unknown map_dtype");
+    return PSFS_OK;
+}
+
+void prof_free(psfs_handle *h);
+
+void free_handle(psfs_handle *h)
+{
+    if (!h) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->maps);
+    cudaFree(h->bg_mean);
+    cudaFree(h->bg_hinv);
+    cudaFree(h->d_words);
+    cudaFreeHost(h->h_words);
+    cudaFree(h->tiles);
+    cudaFree(h->st_images);
+    cudaFree(h->st_occ);
+    cudaFree(h->st_list);
+    cudaFree(h->dl);
+    cudaFree(h->dg);
+    prof_free(h);
+    cudaSetDevice(prev);
+    delete h;
+}
+
+void prof_free(psfs_handle *h)
+{
+    for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+    h->prof_ev.clear();
+    h->prof_stage.clear();
+    h->prof_cap = 0;
+    h->prof_n = 0;
+}
+
+// Brackets one launch with an event pair when tracing is on.
+struct ProfScope {
+    psfs_handle *h;
+    int slot = -1;
+    ProfScope(psfs_handle *hh, int stage) : h(hh)
+    {
+        if (h->prof_cap > 0 && h->prof_n < h->prof_cap) {
+            slot = h->prof_n++;
+            h->prof_stage[slot] = stage;
+            cudaEventRecord(h->prof_ev[2 * slot], h->stream);
+        }
+    }
+    ~ProfScope()
+    {
+        if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], h->stream);
+    }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+psfs_status fill_fuse_args(psfs_handle *h, float *occ, uint32_t *list, uint32_t capacity,
+                           uint32_t *count, FuseArgs *a)
+{
+    *a = h->fuse;
+    a->occ = occ;
+    a->list = list;
+    a->capacity = capacity;
+    a->count = count;
+    return PSFS_OK;
+}
+
+psfs_status check_frame_outputs(const float *occupancy, const uint32_t *voxel_list, uint32_t capacity,
+                                const uint32_t *count)
+{
+    if (!occupancy || !aligned(occupancy, 16)) return fail(PSFS_ERR_INVALID_ARG, "occupancy NULL or not 16-byte aligned");
+    if (capacity > 0 && (!voxel_list || !aligned(voxel_list, 4)))
+        return fail(PSFS_ERR_INVALID_ARG, "voxel_list NULL or not 4-byte aligned");
+    if (!count || !aligned(count, 4)) return fail(PSFS_ERR_INVALID_ARG, "count NULL or not 4-byte aligned");
+    return PSFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *psfs_status_string(psfs_status s)
+{
+    switch (s) {
+    case PSFS_OK: return "ok";
+    case PSFS_ERR_INVALID_ARG: return "invalid argument";
+    case PSFS_ERR_NOT_READY: return "background not set";
+    case PSFS_ERR_CAPACITY: return "voxel list capacity exceeded";
+    case PSFS_ERR_CUDA: return "CUDA error";
+    case PSFS_ERR_TIMEOUT: return "device wait timed out";
+    case PSFS_ERR_NOMEM: return "out of memory";
+    }
+    return "unknown status";
+}
+
+const char *psfs_last_error_message(void) { return g_last_error.c_str(); }
+
+void psfs_params_default(psfs_params *p)
+{
+    if (!p) return;
+    p->p_detect = 0.9;
+    p->p_false_alarm = 0.1;
+    p->prior = 0.5;
+    p->threshold = 0.5;
+    p->log_fg_density = -3.0 * std::log(256.0);
+    p->map_dtype = PSFS_MAP_F32;
+}
+
+psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t n_cams,
+                        const psfs_params *params, void *stream, psfs_handle **out)
+{
+    if (!out) return fail(PSFS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid) return fail(PSFS_ERR_INVALID_ARG, "grid is NULL");
+    if (!cams) return fail(PSFS_ERR_INVALID_ARG, "cams is NULL");
+    if (n_cams < 1 || n_cams > PSFS_MAX_CAMS) return fail(PSFS_ERR_INVALID_ARG, "n_cams outside [1, PSFS_MAX_CAMS]");
+    psfs_status st = check_params(params);
+    if (st != PSFS_OK) return st;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(PSFS_ERR_INVALID_ARG, "grid size < 1");
+    const uint64_t n_vox = (uint64_t)grid->nx * grid->ny * grid->nz;
+    if (n_vox >= (1ull << 32)) return fail(PSFS_ERR_INVALID_ARG, "grid has 2^32 voxels or more");
+    if (grid->nx > (1 << 24) || grid->ny > (1 << 24) || grid->nz > (1 << 24))
+        return fail(PSFS_ERR_INVALID_ARG, "grid axis longer than 2^24");
+    if (!finite_all(grid->origin, 3) || !std::isfinite(grid->voxel_size) || !(grid->voxel_size > 0))
+        return fail(PSFS_ERR_INVALID_ARG, "grid origin / voxel_size not finite or voxel_size <= 0");
+    const int W = cams[0].width, H = cams[0].height;
+    if (W < 1 || H < 1 || W > 16384 || H > 16384) return fail(PSFS_ERR_INVALID_ARG, "camera size outside [1, 16384]");
+    for (int c = 0; c < n_cams; ++c) {
+        if (cams[c].width != W || cams[c].height != H)
+            return fail(PSFS_ERR_INVALID_ARG, "cameras differ in width or height");
+        if (!finite_all(cams[c].K, 9) || !finite_all(cams[c].R, 9) || !finite_all(cams[c].t, 3))
+            return fail(PSFS_ERR_INVALID_ARG, "camera matrix not finite");
+    }
+
+    psfs_handle *h = new (std::nothrow) psfs_handle();
+    if (!h) return fail(PSFS_ERR_NOMEM, "host allocation");
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail_cuda(e, "cudaGetDevice");
+    }
+    h->stream = (cudaStream_t)stream;
+    h->grid = *grid;
+    h->cams.assign(cams, cams + n_cams);
+    h->n_cams = n_cams;
+    h->W = W;
+    h->H = H;
+    h->params = *params;
+    h->n_pix = (int64_t)n_cams * W * H;
+    h->map_elem = params->map_dtype == PSFS_MAP_F32 ? 4 : 2;
+
+    // sensor constants of g(r)
+    const double pd = params->p_detect, q = 0.5 * (params->p_detect + params->p_false_alarm);
+    h->sc.pd = (float)pd;
+    h->sc.one_minus_pd = (float)(1.0 - pd);
+    h->sc.q = (float)q;
+    h->sc.one_minus_q = (float)(1.0 - q);
+    h->sc.a_zero_const_pos = (pd == 0.0);
+    h->sc.a_zero_const_neg = (pd == 1.0);
+    h->c0 = (float)(params->log_fg_density + 1.5 * std::log(M_PI));
+
+    // projection matrices in centred voxel-index space
+    FuseArgs &f = h->fuse;
+    std::memset(&f, 0, sizeof(f));
+    f.W = W;
+    f.H = H;
+    f.map_stride = (int64_t)W * H;
+    f.n_cams = n_cams;
+    f.nx = grid->nx;
+    f.ny = grid->ny;
+    f.nz = grid->nz;
+    f.ci = 0.5f * (float)(grid->nx - 1);
+    f.cj = 0.5f * (float)(grid->ny - 1);
+    f.ck = 0.5f * (float)(grid->nz - 1);
+    const double vs = grid->voxel_size;
+    const double centre[3] = {grid->origin[0] + 0.5 * grid->nx * vs, grid->origin[1] + 0.5 * grid->ny * vs,
+                              grid->origin[2] + 0.5 * grid->nz * vs};
+    for (int c = 0; c < n_cams; ++c) {
+        const double *K = cams[c].K, *R = cams[c].R, *t = cams[c].t;
+        double KR[9], xc[3];
+        for (int r = 0; r < 3; ++r) {
+            for (int col = 0; col < 3; ++col)
+                KR[3 * r + col] = K[3 * r + 0] * R[0 + col] + K[3 * r + 1] * R[3 + col] + K[3 * r + 2] * R[6 + col];
+            xc[r] = R[3 * r + 0] * centre[0] + R[3 * r + 1] * centre[1] + R[3 * r + 2] * centre[2] + t[r];
+        }
+        for (int r = 0; r < 3; ++r) {
+            for (int col = 0; col < 3; ++col) f.cam[c].m[4 * r + col] = (float)(KR[3 * r + col] * vs);
+            f.cam[c].m[4 * r + 3] = (float)(K[3 * r + 0] * xc[0] + K[3 * r + 1] * xc[1] + K[3 * r + 2] * xc[2]);
+        }
+    }
+    f.logit_prior = (float)std::log(params->prior / (1.0 - params->prior));
+    f.logit_tau = (float)std::log(params->threshold / (1.0 - params->threshold));
+
+    // tiles in Morton order
+    const int ntx = (grid->nx + 31) / 32, nty = (grid->ny + FUSE_WY - 1) / FUSE_WY,
+              ntz = (grid->nz + FUSE_TZ - 1) / FUSE_TZ;
+    std::vector<std::pair<uint64_t, uint64_t>> order;
+    order.reserve((size_t)ntx * nty * ntz);
+    for (int z = 0; z < ntz; ++z)
+        for (int y = 0; y < nty; ++y)
+            for (int x = 0; x < ntx; ++x)
+                order.emplace_back(spread3(x) | (spread3(y) << 1) | (spread3(z) << 2), pack_tile(x, y, z));
+    std::sort(order.begin(), order.end());
+    std::vector<uint64_t> tiles(order.size());
+    for (size_t n = 0; n < order.size(); ++n) tiles[n] = order[n].second;
+    h->n_tiles = (int)tiles.size();
+    f.n_tiles = h->n_tiles;
+
+    DeviceGuard guard(h->device);
+    const size_t pix_bytes = (size_t)h->n_pix;
+    if (cudaMalloc(&h->maps, pix_bytes * h->map_elem) != cudaSuccess ||
+        cudaMalloc(&h->bg_mean, pix_bytes * 3 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&h->bg_hinv, pix_bytes * 3 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&h->d_words, 16 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&h->h_words, 16 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&h->tiles, tiles.size() * sizeof(uint64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        free_handle(h);
+        return fail(PSFS_ERR_NOMEM, "device scratch allocation");
+    }
+    f.maps = h->maps;
+    f.tiles = h->tiles;
+    f.status = h->d_words;
+    e = cudaMemcpy(h->tiles, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->d_words, 0, 16 * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        free_handle(h);
+        return fail_cuda(e, "psfs_create upload");
+    }
+    std::memset(h->h_words, 0, 16 * sizeof(uint32_t));
+    *out = h;
+    return PSFS_OK;
+}
+
+psfs_status psfs_set_background(psfs_handle *h, const float *mean, const float *var)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (!mean || !var || !aligned(mean, 16) || !aligned(var, 16))
+        return fail(PSFS_ERR_INVALID_ARG, "mean / var NULL or not 16-byte aligned");
+    DeviceGuard guard(h->device);
+    h->bg_ready = false;
+    PSFS_CK(cudaMemsetAsync(h->d_words + 1, 0, sizeof(uint32_t), h->stream));
+    PSFS_CK(launch_pack_background(mean, var, h->n_pix, h->bg_mean, h->bg_hinv, h->d_words + 1, h->stream));
+    PSFS_CK(cudaMemcpyAsync(h->h_words + 1, h->d_words + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    PSFS_CK(cudaStreamSynchronize(h->stream));
+    if (h->h_words[1] != 0) return fail(PSFS_ERR_INVALID_ARG, "background: non-finite mean or variance outside [1e-6, 1e12]");
+    h->bg_ready = true;
+    return PSFS_OK;
+}
+
+static psfs_status enqueue_reconstruct(psfs_handle *h, const uint8_t *images, float *occupancy,
+                                       uint32_t *voxel_list, uint32_t capacity, uint32_t *count)
+{
+    LikelihoodArgs la{};
+    la.img = images;
+    la.mean = h->bg_mean;
+    la.hinv = h->bg_hinv;
+    la.n_pix = h->n_pix;
+    la.c0 = h->c0;
+    la.sc = h->sc;
+    la.out = h->maps;
+    la.zero_word = count;
+    {
+        ProfScope ps(h, PSFS_STAGE_LIKELIHOOD);
+        PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, h->stream));
+    }
+    FuseArgs fa;
+    fill_fuse_args(h, occupancy, voxel_list, capacity, count, &fa);
+    {
+        ProfScope ps(h, PSFS_STAGE_FUSE);
+        PSFS_CK(launch_fuse(fa, h->params.map_dtype, h->stream));
+    }
+    return PSFS_OK;
+}
+
+psfs_status psfs_reconstruct(psfs_handle *h, const uint8_t *images, float *occupancy,
+                             uint32_t *voxel_list, uint32_t capacity, uint32_t *count)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (!images || !aligned(images, 16)) return fail(PSFS_ERR_INVALID_ARG, "images NULL or not 16-byte aligned");
+    psfs_status st = check_frame_outputs(occupancy, voxel_list, capacity, count);
+    if (st != PSFS_OK) return st;
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    DeviceGuard guard(h->device);
+    return enqueue_reconstruct(h, images, occupancy, voxel_list, capacity, count);
+}
+
+psfs_status psfs_reconstruct_host(psfs_handle *h, const uint8_t *h_images, float *h_occupancy,
+                                  uint32_t *h_list, uint32_t capacity, uint32_t *h_count)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (!h_images) return fail(PSFS_ERR_INVALID_ARG, "h_images is NULL");
+    if (capacity > 0 && !h_list) return fail(PSFS_ERR_INVALID_ARG, "h_list is NULL");
+    if (!h_count) return fail(PSFS_ERR_INVALID_ARG, "h_count is NULL");
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    DeviceGuard guard(h->device);
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    if (!h->st_images) {
+        if (cudaMalloc(&h->st_images, (size_t)h->n_pix * 3) != cudaSuccess ||
+            cudaMalloc(&h->st_occ, n_vox * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "host-path staging allocation");
+        }
+    }
+    if (capacity > h->st_list_cap) {
+        cudaFree(h->st_list);
+        h->st_list = nullptr;
+        h->st_list_cap = 0;
+        if (cudaMalloc(&h->st_list, (size_t)capacity * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "host-path list allocation");
+        }
+        h->st_list_cap = capacity;
+    }
+    PSFS_CK(cudaMemcpyAsync(h->st_images, h_images, (size_t)h->n_pix * 3, cudaMemcpyHostToDevice, h->stream));
+    psfs_status st = enqueue_reconstruct(h, h->st_images, h->st_occ, h->st_list, capacity, h->d_words + 2);
+    if (st != PSFS_OK) return st;
+    if (h_occupancy)
+        PSFS_CK(cudaMemcpyAsync(h_occupancy, h->st_occ, n_vox * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    PSFS_CK(cudaMemcpyAsync(h->h_words + 2, h->d_words + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    PSFS_CK(cudaStreamSynchronize(h->stream));
+    const uint32_t n = h->h_words[2];
+    *h_count = n;
+    const uint32_t ncopy = std::min(n, capacity);
+    if (ncopy) {
+        PSFS_CK(cudaMemcpyAsync(h_list, h->st_list, (size_t)ncopy * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+        PSFS_CK(cudaStreamSynchronize(h->stream));
+    }
+    // the capacity bit may have been set by this frame: clear it here
+    PSFS_CK(cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t), h->stream));
+    if (n > capacity) return fail(PSFS_ERR_CAPACITY, "voxel list capacity exceeded");
+    return PSFS_OK;
+}
+
+psfs_status psfs_fuse_slm(psfs_handle *h, const float *slm, float *occupancy, uint32_t *voxel_list,
+                          uint32_t capacity, uint32_t *count)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (!slm || !aligned(slm, 16)) return fail(PSFS_ERR_INVALID_ARG, "slm NULL or not 16-byte aligned");
+    psfs_status st = check_frame_outputs(occupancy, voxel_list, capacity, count);
+    if (st != PSFS_OK) return st;
+    DeviceGuard guard(h->device);
+    const double pd = h->params.p_detect, q = 0.5 * (h->params.p_detect + h->params.p_false_alarm);
+    SlmToMapArgs sa{};
+    sa.slm = slm;
+    sa.n_pix = h->n_pix;
+    sa.da = (float)(2.0 * pd - 1.0);
+    sa.one_minus_pd = (float)(1.0 - pd);
+    sa.db = (float)(2.0 * q - 1.0);
+    sa.one_minus_q = (float)(1.0 - q);
+    sa.out = h->maps;
+    sa.zero_word = count;
+    {
+        ProfScope ps(h, PSFS_STAGE_LIKELIHOOD);
+        PSFS_CK(launch_slm_to_map(sa, h->params.map_dtype, h->stream));
+    }
+    FuseArgs fa;
+    fill_fuse_args(h, occupancy, voxel_list, capacity, count, &fa);
+    {
+        ProfScope ps(h, PSFS_STAGE_FUSE);
+        PSFS_CK(launch_fuse(fa, h->params.map_dtype, h->stream));
+    }
+    return PSFS_OK;
+}
+
+psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *slm_out)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (!images || !aligned(images, 16)) return fail(PSFS_ERR_INVALID_ARG, "images NULL or not 16-byte aligned");
+    if (!slm_out || !aligned(slm_out, 16)) return fail(PSFS_ERR_INVALID_ARG, "slm_out NULL or not 16-byte aligned");
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    DeviceGuard guard(h->device);
+    LikelihoodArgs la{};
+    la.img = images;
+    la.mean = h->bg_mean;
+    la.hinv = h->bg_hinv;
+    la.n_pix = h->n_pix;
+    la.c0 = h->c0;
+    la.sc = h->sc;
+    la.out = slm_out;
+    la.zero_word = nullptr;
+    PSFS_CK(launch_likelihood(la, PSFS_MAP_F32, true, h->stream));
+    return PSFS_OK;
+}
+
+psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_occ, float *d_slm,
+                          float *d_mean, float *d_var)
+{
+    (void)images;
+    (void)d_occ;
+    (void)d_slm;
+    (void)d_mean;
+    (void)d_var;
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    return fail(PSFS_ERR_INVALID_ARG, "psfs_backward: not available in this build");
+}
+
+psfs_status psfs_sync(psfs_handle *h)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard guard(h->device);
+    PSFS_CK(cudaMemcpyAsync(h->h_words, h->d_words, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    PSFS_CK(cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t), h->stream));
+    PSFS_CK(cudaStreamSynchronize(h->stream));
+    const uint32_t w = h->h_words[0];
+    if (w & kStatusCapacity) return fail(PSFS_ERR_CAPACITY, "voxel list capacity exceeded");
+    if (w & kStatusTimeout) return fail(PSFS_ERR_TIMEOUT, "device wait timed out");
+    return PSFS_OK;
+}
+
+psfs_status psfs_profile_enable(psfs_handle *h, int32_t max_launches)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (max_launches < 0) return fail(PSFS_ERR_INVALID_ARG, "max_launches < 0");
+    DeviceGuard guard(h->device);
+    PSFS_CK(cudaStreamSynchronize(h->stream));
+    prof_free(h);
+    if (max_launches == 0) return PSFS_OK;
+    h->prof_ev.resize(2 * (size_t)max_launches, nullptr);
+    h->prof_stage.assign((size_t)max_launches, 0);
+    for (auto &e : h->prof_ev) {
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) {
+            prof_free(h);
+            return fail_cuda(err, "cudaEventCreate");
+        }
+    }
+    h->prof_cap = max_launches;
+    return PSFS_OK;
+}
+
+psfs_status psfs_profile_read(psfs_handle *h, double *ms, int32_t *launches)
+{
+    if (!h || !ms || !launches) return fail(PSFS_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(h->device);
+    PSFS_CK(cudaStreamSynchronize(h->stream));
+    for (int s = 0; s < PSFS_N_STAGES; ++s) {
+        ms[s] = 0.0;
+        launches[s] = 0;
+    }
+    for (int n = 0; n < h->prof_n; ++n) {
+        float t = 0.0f;
+        PSFS_CK(cudaEventElapsedTime(&t, h->prof_ev[2 * n], h->prof_ev[2 * n + 1]));
+        ms[h->prof_stage[n]] += t;
+        launches[h->prof_stage[n]] += 1;
+    }
+    h->prof_n = 0;
+    return PSFS_OK;
+}
+
+void psfs_destroy(psfs_handle *h) { free_handle(h); }
+
+}  // extern "C"

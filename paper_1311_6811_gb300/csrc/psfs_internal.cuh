@@ -1,0 +1,174 @@
+// psfs_internal.cuh -- shared declarations of libpsfs (kernels + host side).
+//
+// Numerical form used on the device (Section 2.2.2 of the paper, restated):
+//
+//   Eq. 1-2   SLM s = U / (U + N), N = prod_c (2 pi var_c)^(-1/2)
+//             exp(-(I_c - mu_c)^2 / (2 var_c)).  Written with r = log U - log N
+//             this is s = sigmoid(r), and with h_c = 1 / (2 var_c)
+//               r = log U + 1.5 log(pi) - 0.5 log(h0 h1 h2) + sum_c (I_c - mu_c)^2 h_c.
+//   Eq. 5-9   a(s) = P_D s + (1 - P_D)(1 - s)           = P(S | V = 1)
+//             f(s) = P_FA s + (1 - P_FA)(1 - s)
+//             b(s) = (a + f) / 2                         = P(S | V = 0)
+//             With s = sigmoid(r) the common factor 1 / (1 + e^r) cancels:
+//               g(r) = log(a / b) = log(P_D e^r + 1 - P_D) - log(q e^r + 1 - q),
+//             q = (P_D + P_FA) / 2.  The likelihood kernel stores g per pixel.
+//   Eq. 3-4   log-odds L_v = logit(prior) + sum over cameras that see v of g
+//             at the pixel of v; posterior = 1 / (1 + exp(-L_v)); occupied iff
+//             L_v > logit(threshold).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "psfs.h"
+
+namespace psfs {
+
+constexpr uint32_t kStatusCapacity = 1u;
+constexpr uint32_t kStatusTimeout = 2u;
+constexpr uint32_t kStatusBadValue = 4u;
+
+// Projection of voxel index space into one camera: (u, v, w) = M (i', j', k', 1)
+// with i' = i - (nx - 1) / 2 (likewise j', k'), rows u, v, w of 4 floats.
+struct CamMat {
+    float m[12];
+};
+
+// Constants of g(r) above.
+struct SensorConsts {
+    float pd, one_minus_pd;   // A(r) = P_D e^r + (1 - P_D)
+    float q, one_minus_q;     // B(r) = q e^r + (1 - q)
+    int a_zero_const_pos;     // P_D == 0: for r > 0, A e^-r = e^-r exactly
+    int a_zero_const_neg;     // P_D == 1: for r <= 0, A = e^r exactly
+};
+
+struct LikelihoodArgs {
+    const uint8_t *img;       // [n_pix][3]
+    const float *mean;        // [n_pix][3]
+    const float *hinv;        // [n_pix][3], 1 / (2 var)
+    int64_t n_pix;
+    float c0;                 // log U + 1.5 log(pi)
+    SensorConsts sc;
+    void *out;                // [n_pix] map of g (f32 / f16 / bf16) or of s (f32)
+    uint32_t *zero_word;      // if non-null, set to 0 by one thread
+};
+
+struct SlmToMapArgs {
+    const float *slm;         // [n_pix] s in [0, 1]
+    int64_t n_pix;
+    float da, one_minus_pd;   // a(s) = (1 - P_D) + (2 P_D - 1) s
+    float db, one_minus_q;    // b(s) = (1 - q) + (2 q - 1) s
+    void *out;
+    uint32_t *zero_word;
+};
+
+struct FuseArgs {
+    const void *maps;         // [n_cams][H][W] of g, dtype per map_dtype
+    int W, H;
+    int64_t map_stride;       // W * H
+    int n_cams;
+    int nx, ny, nz;
+    float ci, cj, ck;         // (n - 1) / 2 per axis
+    const uint64_t *tiles;    // packed tile coordinates, Morton order
+    int n_tiles;
+    float logit_prior, logit_tau;
+    float *occ;               // [nz][ny][nx]
+    uint32_t *list;
+    uint32_t capacity;
+    uint32_t *count;
+    uint32_t *status;
+    CamMat cam[PSFS_MAX_CAMS];
+};
+
+// Tile shape of the fuse kernel: 32 voxels along x (one warp), FUSE_WY warps
+// along y, FUSE_TZ voxels along z per thread.
+constexpr int FUSE_WY = 4;
+constexpr int FUSE_TZ = 8;
+
+__host__ __device__ inline uint64_t pack_tile(uint32_t tx, uint32_t ty, uint32_t tz)
+{
+    return (uint64_t)tx | ((uint64_t)ty << 21) | ((uint64_t)tz << 42);
+}
+
+// ---------------------------------------------------------------------------
+// device helpers shared by the forward and adjoint kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// floor(x) for 0 <= x < 2^22: adding 1.5 * 2^23 with round-down leaves
+// floor(x) in the low mantissa bits.
+__device__ __forceinline__ int floor_nonneg(float x)
+{
+    return __float_as_int(__fadd_rd(x, 12582912.0f)) - 0x4B400000;
+}
+
+// Projection of voxel (fi, fj, fk) (centred index coordinates) into camera
+// `m`.  Returns true and the pixel offset py * W + px if the centre is seen.
+// The forward and the adjoint both call this, so their pixel choice is
+// identical bit for bit.
+__device__ __forceinline__ bool project_voxel(const float *m, float fi, float fj, float fk,
+                                              float Wf, float Hf, int W, int *pix)
+{
+    float u = fmaf(m[2], fk, fmaf(m[0], fi, fmaf(m[1], fj, m[3])));
+    float v = fmaf(m[6], fk, fmaf(m[4], fi, fmaf(m[5], fj, m[7])));
+    float w = fmaf(m[10], fk, fmaf(m[8], fi, fmaf(m[9], fj, m[11])));
+    float rw = rcp_approx(w);
+    float x = u * rw;
+    float y = v * rw;
+    bool vis = (w > 0.0f) & (x >= 0.0f) & (x < Wf) & (y >= 0.0f) & (y < Hf);
+    *pix = vis ? floor_nonneg(y) * W + floor_nonneg(x) : 0;
+    return vis;
+}
+
+template <typename T>
+__device__ __forceinline__ float map_load(const T *p);
+template <>
+__device__ __forceinline__ float map_load<float>(const float *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float map_load<__half>(const __half *p) { return __half2float(__ldg(p)); }
+template <>
+__device__ __forceinline__ float map_load<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(__ldg(p));
+}
+
+// g(r) = log(P_D e^r + 1 - P_D) - log(q e^r + 1 - q), evaluated with
+// e^-|r| only, so it neither overflows nor loses the constant terms.
+__device__ __forceinline__ float log_ratio_of_r(float r, const SensorConsts &c)
+{
+    float ar = fabsf(r);
+    float u = expf(-ar);
+    float A, B;
+    bool deg;
+    if (r > 0.0f) {   // divide both by e^r
+        A = fmaf(c.one_minus_pd, u, c.pd);
+        B = fmaf(c.one_minus_q, u, c.q);
+        deg = c.a_zero_const_pos;
+    } else {
+        A = fmaf(c.pd, u, c.one_minus_pd);
+        B = fmaf(c.q, u, c.one_minus_q);
+        deg = c.a_zero_const_neg;
+    }
+    if (deg) return -ar - logf(B);   // A = e^-|r| exactly
+    return logf(A / B);
+}
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+cudaError_t launch_pack_background(const float *mean, const float *var, int64_t n_pix,
+                                   float *mean_out, float *hinv_out, uint32_t *bad,
+                                   cudaStream_t s);
+cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_out,
+                              cudaStream_t s);
+cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s);
+cudaError_t launch_fuse(const FuseArgs &a, int map_dtype, cudaStream_t s);
+
+}  // namespace psfs

@@ -1,0 +1,385 @@
+"""ctypes binding of libpsfs (include/psfs.h), one Python function per C entry
+point, same names.  Marshalling only: tensors become device pointers, structs
+become ctypes structs, statuses become exceptions.  Every step of the
+reconstruction runs in the CUDA library; if it cannot be loaded, the calls
+raise instead of falling back to anything else.
+
+Device arguments accept CUDA torch tensors (contiguous, the dtype and shape
+given in the header) or raw integer pointers.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+PSFS_MAX_CAMS = 32
+
+PSFS_OK = 0
+PSFS_ERR_INVALID_ARG = 1
+PSFS_ERR_NOT_READY = 2
+PSFS_ERR_CAPACITY = 3
+PSFS_ERR_CUDA = 4
+PSFS_ERR_TIMEOUT = 5
+PSFS_ERR_NOMEM = 6
+
+PSFS_MAP_F32 = 0
+PSFS_MAP_F16 = 1
+PSFS_MAP_BF16 = 2
+MAP_DTYPES = {"f32": PSFS_MAP_F32, "f16": PSFS_MAP_F16, "bf16": PSFS_MAP_BF16}
+
+
+class psfs_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("origin", ctypes.c_double * 3), ("voxel_size", ctypes.c_double)]
+
+
+class psfs_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("K", ctypes.c_double * 9), ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
+
+
+class psfs_params(ctypes.Structure):
+    _fields_ = [("p_detect", ctypes.c_double), ("p_false_alarm", ctypes.c_double),
+                ("prior", ctypes.c_double), ("threshold", ctypes.c_double),
+                ("log_fg_density", ctypes.c_double), ("map_dtype", ctypes.c_int32)]
+
+
+class PsfsError(RuntimeError):
+    def __init__(self, status: int, func: str, message: str):
+        self.status = status
+        super().__init__(f"{func}: {_status_name(status)} ({message})")
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpsfs.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise OSError(f"libpsfs.so not built ({path})")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        st = ctypes.c_int
+        sig = {
+            "psfs_params_default": (None, [ctypes.POINTER(psfs_params)]),
+            "psfs_create": (st, [ctypes.POINTER(psfs_grid), ctypes.POINTER(psfs_camera), ctypes.c_int32,
+                                 ctypes.POINTER(psfs_params), _vp, ctypes.POINTER(_vp)]),
+            "psfs_set_background": (st, [_vp, _vp, _vp]),
+            "psfs_reconstruct": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+            "psfs_reconstruct_host": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+            "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+            "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
+            "psfs_backward": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
+            "psfs_sync": (st, [_vp]),
+            "psfs_destroy": (None, [_vp]),
+            "psfs_profile_enable": (st, [_vp, ctypes.c_int32]),
+            "psfs_profile_read": (st, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+            "psfs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "psfs_last_error_message": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _status_name(s: int) -> str:
+    try:
+        return load().psfs_status_string(s).decode()
+    except Exception:  # pragma: no cover - only when the library itself is missing
+        return f"status {s}"
+
+
+def _check(status: int, func: str):
+    if status != PSFS_OK:
+        msg = load().psfs_last_error_message().decode(errors="replace")
+        raise PsfsError(status, func, msg)
+
+
+def _dev_ptr(x, name: str, dtype=None, numel: Optional[int] = None):
+    """Device pointer of a CUDA tensor (checked) or a raw integer / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name}: expected a CUDA tensor or an int pointer")
+    if not x.is_cuda:
+        raise ValueError(f"{name}: tensor must be on a CUDA device")
+    if not x.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    if dtype is not None and x.dtype != dtype:
+        raise ValueError(f"{name}: expected dtype {dtype}, got {x.dtype}")
+    if numel is not None and x.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {x.numel()}")
+    return x.data_ptr()
+
+
+def _host_ptr(x, name: str, dtype=None, numel: Optional[int] = None):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name}: array must be C-contiguous")
+        if numel is not None and x.size != numel:
+            raise ValueError(f"{name}: expected {numel} elements, got {x.size}")
+        return x.ctypes.data
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda or not x.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous host tensor")
+        if dtype is not None and x.dtype != dtype:
+            raise ValueError(f"{name}: expected dtype {dtype}, got {x.dtype}")
+        if numel is not None and x.numel() != numel:
+            raise ValueError(f"{name}: expected {numel} elements, got {x.numel()}")
+        return x.data_ptr()
+    raise TypeError(f"{name}: expected a host array")
+
+
+# --------------------------------------------------------------------------- #
+# struct builders
+# --------------------------------------------------------------------------- #
+def _get(o, name):
+    return o[name] if isinstance(o, dict) else getattr(o, name)
+
+
+def make_grid(grid) -> psfs_grid:
+    g = psfs_grid()
+    g.nx, g.ny, g.nz = int(_get(grid, "nx")), int(_get(grid, "ny")), int(_get(grid, "nz"))
+    g.origin[:] = [float(v) for v in _get(grid, "origin")]
+    g.voxel_size = float(_get(grid, "voxel_size"))
+    return g
+
+
+def make_cameras(cams) -> ctypes.Array:
+    arr = (psfs_camera * len(cams))()
+    for n, c in enumerate(cams):
+        arr[n].width = int(_get(c, "width"))
+        arr[n].height = int(_get(c, "height"))
+        arr[n].K[:] = [float(v) for v in np.asarray(_get(c, "K"), np.float64).ravel()]
+        arr[n].R[:] = [float(v) for v in np.asarray(_get(c, "R"), np.float64).ravel()]
+        arr[n].t[:] = [float(v) for v in np.asarray(_get(c, "t"), np.float64).ravel()]
+    return arr
+
+
+def psfs_params_default() -> psfs_params:
+    p = psfs_params()
+    load().psfs_params_default(ctypes.byref(p))
+    return p
+
+
+def make_params(params=None, map_dtype=None) -> psfs_params:
+    p = psfs_params_default()
+    if params is not None:
+        for name in ("p_detect", "p_false_alarm", "prior", "threshold", "log_fg_density"):
+            v = params.get(name) if isinstance(params, dict) else getattr(params, name, None)
+            if v is not None:
+                setattr(p, name, float(v))
+        md = params.get("map_dtype") if isinstance(params, dict) else getattr(params, "map_dtype", None)
+        if md is not None:
+            p.map_dtype = MAP_DTYPES.get(md, md) if isinstance(md, str) else int(md)
+    if map_dtype is not None:
+        p.map_dtype = MAP_DTYPES[map_dtype] if isinstance(map_dtype, str) else int(map_dtype)
+    return p
+
+
+# --------------------------------------------------------------------------- #
+# entry points (names of include/psfs.h)
+# --------------------------------------------------------------------------- #
+def psfs_create(grid, cams, params=None, stream=None, map_dtype=None) -> int:
+    """Returns the handle (an integer pointer).  `stream` is a torch CUDA stream,
+    an integer cudaStream_t or None (the current torch stream)."""
+    lib = load()
+    g = make_grid(grid) if not isinstance(grid, psfs_grid) else grid
+    c = make_cameras(cams) if not isinstance(cams, ctypes.Array) else cams
+    p = params if isinstance(params, psfs_params) else make_params(params, map_dtype)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    out = _vp()
+    _check(lib.psfs_create(ctypes.byref(g), c, len(c), ctypes.byref(p), _vp(stream), ctypes.byref(out)),
+           "psfs_create")
+    return out.value
+
+
+def psfs_set_background(h: int, mean, var):
+    import torch
+    _check(load().psfs_set_background(h, _dev_ptr(mean, "mean", torch.float32),
+                                      _dev_ptr(var, "var", torch.float32)), "psfs_set_background")
+
+
+def psfs_reconstruct(h: int, images, occupancy, voxel_list, capacity: int, count):
+    import torch
+    _check(load().psfs_reconstruct(h, _dev_ptr(images, "images", torch.uint8),
+                                   _dev_ptr(occupancy, "occupancy", torch.float32),
+                                   _dev_ptr(voxel_list, "voxel_list"), int(capacity),
+                                   _dev_ptr(count, "count")), "psfs_reconstruct")
+
+
+def psfs_reconstruct_host(h: int, images, occupancy, voxel_list, capacity: int, count) -> int:
+    """Host buffers (numpy arrays or CPU tensors, pinned for speed).  Returns the
+    status code: PSFS_OK or PSFS_ERR_CAPACITY (anything else raises)."""
+    st = load().psfs_reconstruct_host(h, _host_ptr(images, "images"), _host_ptr(occupancy, "occupancy"),
+                                      _host_ptr(voxel_list, "voxel_list"), int(capacity),
+                                      _host_ptr(count, "count"))
+    if st not in (PSFS_OK, PSFS_ERR_CAPACITY):
+        _check(st, "psfs_reconstruct_host")
+    return st
+
+
+def psfs_fuse_slm(h: int, slm, occupancy, voxel_list, capacity: int, count):
+    import torch
+    _check(load().psfs_fuse_slm(h, _dev_ptr(slm, "slm", torch.float32),
+                                _dev_ptr(occupancy, "occupancy", torch.float32),
+                                _dev_ptr(voxel_list, "voxel_list"), int(capacity),
+                                _dev_ptr(count, "count")), "psfs_fuse_slm")
+
+
+def psfs_get_likelihood(h: int, images, slm_out):
+    import torch
+    _check(load().psfs_get_likelihood(h, _dev_ptr(images, "images", torch.uint8),
+                                      _dev_ptr(slm_out, "slm_out", torch.float32)), "psfs_get_likelihood")
+
+
+def psfs_backward(h: int, images, d_occ, d_slm=None, d_mean=None, d_var=None):
+    import torch
+    _check(load().psfs_backward(h, _dev_ptr(images, "images", torch.uint8),
+                                _dev_ptr(d_occ, "d_occ", torch.float32),
+                                _dev_ptr(d_slm, "d_slm", torch.float32),
+                                _dev_ptr(d_mean, "d_mean", torch.float32),
+                                _dev_ptr(d_var, "d_var", torch.float32)), "psfs_backward")
+
+
+def psfs_sync(h: int) -> int:
+    """Waits for the handle's stream; returns PSFS_OK or PSFS_ERR_CAPACITY."""
+    st = load().psfs_sync(h)
+    if st not in (PSFS_OK, PSFS_ERR_CAPACITY):
+        _check(st, "psfs_sync")
+    return st
+
+
+def psfs_destroy(h: int):
+    if h:
+        load().psfs_destroy(h)
+
+
+PSFS_N_STAGES = 8
+STAGE_NAMES = ["likelihood", "fuse", "backward_voxel", "backward_pixel", "batch"]
+
+
+def psfs_profile_enable(h: int, max_launches: int):
+    _check(load().psfs_profile_enable(h, int(max_launches)), "psfs_profile_enable")
+
+
+def psfs_profile_read(h: int) -> dict:
+    """{stage name: (milliseconds, launches)} since the previous read."""
+    ms = (ctypes.c_double * PSFS_N_STAGES)()
+    n = (ctypes.c_int32 * PSFS_N_STAGES)()
+    _check(load().psfs_profile_read(h, ms, n), "psfs_profile_read")
+    return {STAGE_NAMES[i]: (ms[i], n[i]) for i in range(len(STAGE_NAMES)) if n[i]}
+
+
+def psfs_status_string(s: int) -> str:
+    return load().psfs_status_string(int(s)).decode()
+
+
+def psfs_last_error_message() -> str:
+    return load().psfs_last_error_message().decode(errors="replace")
+
+
+# --------------------------------------------------------------------------- #
+# owning wrapper: handle lifetime + output allocation (torch device memory)
+# --------------------------------------------------------------------------- #
+class Reconstructor:
+    """One grid + camera rig on one CUDA device.  Allocates outputs with torch
+    and calls the entry points above; computes nothing itself."""
+
+    def __init__(self, grid, cams, params=None, *, map_dtype=None, stream=None, device=None,
+                 capacity: Optional[int] = None):
+        import torch
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.handle = psfs_create(grid, cams, params, self.stream, map_dtype)
+        g = make_grid(grid)
+        self.shape = (g.nz, g.ny, g.nx)
+        self.n_voxels = g.nx * g.ny * g.nz
+        c0 = cams[0]
+        self.n_cams = len(cams)
+        self.image_shape = (self.n_cams, int(_get(c0, "height")), int(_get(c0, "width")), 3)
+        self.capacity = int(capacity) if capacity is not None else self.n_voxels
+        self.grid, self.cams, self.params = grid, list(cams), params
+
+    def close(self):
+        if getattr(self, "handle", None):
+            psfs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_background(self, mean, var):
+        psfs_set_background(self.handle, mean, var)
+
+    def alloc_outputs(self):
+        import torch
+        occ = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        lst = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=self.device)
+        cnt = torch.zeros(1, dtype=torch.int32, device=self.device)
+        return occ, lst, cnt
+
+    def reconstruct(self, images, out=None):
+        """Enqueue one frame; returns (occupancy, list buffer, count tensor)."""
+        occ, lst, cnt = out if out is not None else self.alloc_outputs()
+        psfs_reconstruct(self.handle, images, occ, lst, self.capacity, cnt)
+        return occ, lst, cnt
+
+    def fuse_slm(self, slm, out=None):
+        occ, lst, cnt = out if out is not None else self.alloc_outputs()
+        psfs_fuse_slm(self.handle, slm, occ, lst, self.capacity, cnt)
+        return occ, lst, cnt
+
+    def likelihood(self, images):
+        import torch
+        out = torch.empty(self.image_shape[:3], dtype=torch.float32, device=self.device)
+        psfs_get_likelihood(self.handle, images, out)
+        return out
+
+    def sync(self) -> int:
+        return psfs_sync(self.handle)
+
+
+def voxel_list(lst, cnt, capacity: int):
+    """Occupied-voxel indices as a sorted int64 CPU tensor (after the frame)."""
+    n = min(int(cnt.item()) & 0xFFFFFFFF, capacity)
+    return (lst[:n].to("cpu").long() & 0xFFFFFFFF).sort().values

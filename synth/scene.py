@@ -369,19 +369,28 @@ def make_background(rng: np.random.Generator, n_cams: int, H: int, W: int,
 def render_images(rng: np.random.Generator, cams: Sequence[Camera], capsules: Sequence[Capsule],
                   bg_mean: np.ndarray, bg_sigma: np.ndarray,
                   labels_out: Optional[list] = None) -> np.ndarray:
-    """uint8 [n_cams][H][W][3]: background draw + capsule colours + N(0, 4) noise."""
+    """uint8 [n_cams][H][W][3].
+
+    Background pixel: mean + N(0, sigma^2) + N(0, 4), drawn as one Gaussian of
+    variance sigma^2 + 4; foreground pixel: capsule colour + N(0, 4).  Then
+    rounded and clamped to [0, 255].
+    """
     n = len(cams)
     H, W = cams[0].height, cams[0].width
-    img = bg_mean + bg_sigma * rng.standard_normal((n, H, W, 3))
-    cols = np.array([c.colour for c in capsules]) if len(capsules) else np.zeros((0, 3))
+    z = rng.standard_normal((n, H, W, 3), dtype=np.float32)
+    std = np.sqrt(bg_sigma.astype(np.float32) ** 2 + np.float32(SENSOR_NOISE_VAR))
+    img = bg_mean.astype(np.float32) + std * z
+    cols = np.array([c.colour for c in capsules], np.float32) if len(capsules) else np.zeros((0, 3), np.float32)
+    noise_sd = np.float32(math.sqrt(SENSOR_NOISE_VAR))
     for k, cam in enumerate(cams):
         lab = render_labels(cam, capsules)
         if labels_out is not None:
             labels_out.append(lab)
         fg = lab >= 0
-        img[k][fg] = cols[lab[fg]]
-    img += math.sqrt(SENSOR_NOISE_VAR) * rng.standard_normal(img.shape)
-    return np.clip(np.rint(img), 0, 255).astype(np.uint8)
+        img[k][fg] = cols[lab[fg]] + noise_sd * z[k][fg]
+    np.rint(img, out=img)
+    np.clip(img, 0, 255, out=img)
+    return img.astype(np.uint8)
 
 
 # --------------------------------------------------------------------------- #
@@ -438,11 +447,23 @@ def _colours(rng, n=10):
     return rng.uniform(0.0, 255.0, size=(n, 3))
 
 
+def _render_frame(args):
+    seed, frame, cams, caps, mean, sigma = args
+    rng = np.random.default_rng([seed, 1 + frame])
+    return render_images(rng, cams, caps, mean, sigma)
+
+
 def make_scene(*, seed: int, grid_n: int, cube_side: float, n_cams: int, width: int,
                height: int, focal: float, n_frames: int = 1, heights=(1.5, 1.5),
                n_bodies: int = 1, walking: bool = False, ring_radius: float = 3.0,
-               params: Optional[Params] = None) -> Scene:
-    """Body (or bodies) on a ring of cameras, per-pixel Gaussian background."""
+               params: Optional[Params] = None, workers: int = 1) -> Scene:
+    """Body (or bodies) on a ring of cameras, per-pixel Gaussian background.
+
+    Cameras, background, colours and poses come from one generator seeded with
+    `seed`; the noise of frame f from a generator seeded with (seed, 1 + f), so
+    frames can be rendered by `workers` processes (spawned) with identical
+    results.
+    """
     rng = np.random.default_rng(seed)
     grid = cube_grid(grid_n, cube_side)
     target = (0.0, 0.0, cube_side / 2.0)
@@ -459,13 +480,19 @@ def make_scene(*, seed: int, grid_n: int, cube_side: float, n_cams: int, width: 
         tracks = [walking_poses(rng, n_frames, centre_xy=o) for o in offsets]
     else:
         tracks = [[random_pose(rng, root_xy=o) for _ in range(n_frames)] for o in offsets]
-    frames, caps_per_frame = [], []
+    caps_per_frame = []
     for f in range(n_frames):
         caps = []
         for b in range(n_bodies):
             caps.extend(body_capsules(tracks[b][f], body_cols[b]))
         caps_per_frame.append(caps)
-        frames.append(render_images(rng, cams, caps, mean, sigma))
+    jobs = [(seed, f, cams, caps_per_frame[f], mean, sigma) for f in range(n_frames)]
+    if workers > 1 and n_frames > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, n_frames)) as pool:
+            frames = pool.map(_render_frame, jobs, chunksize=1)
+    else:
+        frames = [_render_frame(j) for j in jobs]
     images = np.stack(frames) if n_frames > 1 else frames[0]
     return Scene(grid, cams, images, mean.astype(np.float32), var.astype(np.float32),
                  params or Params(), caps_per_frame)
@@ -478,11 +505,12 @@ def scene_64cube_4cam(seed: int = 0) -> Scene:
                       focal=300.0)
 
 
-def scene_128cube_8cam(seed: int = 1, n_frames: int = 100) -> Scene:
+def scene_128cube_8cam(seed: int = 1, n_frames: int = 100, workers: int = 1) -> Scene:
     """128^3 grid over a 2.2 m cube, 8 cameras 640x480 (f = 600 px), heights 1.2-2.2 m,
     a walking sequence of `n_frames` frames."""
     return make_scene(seed=seed, grid_n=128, cube_side=2.2, n_cams=8, width=640, height=480,
-                      focal=600.0, n_frames=n_frames, heights=(1.2, 2.2), walking=True)
+                      focal=600.0, n_frames=n_frames, heights=(1.2, 2.2), walking=True,
+                      workers=workers)
 
 
 def scene_256cube_16cam(seed: int = 2) -> Scene:

@@ -1,0 +1,196 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded
+synthetic scenes.  Tolerances are stated in tests/gpu_helpers.py."""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1311_6811_gb300 import psfs  # noqa: E402
+from synth import scene as S  # noqa: E402
+from tests.gpu_helpers import compare, gpu_reconstruct, to_dev  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    psfs.load()
+
+
+def test_likelihood_map_matches_oracle():
+    """Eq. 1-2 per pixel: FP32 kernel vs FP64 oracle, 64^3 x 4 x 320x240 scene."""
+    sc = S.scene_64cube_4cam(seed=0)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    s = rec.likelihood(to_dev(sc.images)).cpu().numpy().astype(np.float64)
+    ref = oracle.slm(sc.images, sc.mean, sc.var, sc.params.log_fg_density)
+    np.testing.assert_allclose(s, ref, rtol=2e-5, atol=2e-6)
+    rec.close()
+
+
+def test_64cube_4cam_frame():
+    sc = S.scene_64cube_4cam(seed=0)
+    got = gpu_reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    rep = compare(got, ref)
+    assert ref["list"].size > 1000
+    print(rep)
+
+
+@pytest.mark.slow
+def test_128cube_8cam_frames_full_size():
+    """Full-size 128^3 x 8 x 640x480 frames of the walking sequence."""
+    sc = S.scene_128cube_8cam(seed=1, n_frames=2)
+    for f in range(2):
+        got = gpu_reconstruct(sc.grid, sc.cams, sc.images[f], sc.mean, sc.var, sc.params)
+        ref = oracle.reconstruct(sc.grid, sc.cams, sc.images[f], sc.mean, sc.var, sc.params)
+        rep = compare(got, ref)
+        assert ref["list"].size > 10000
+        print(f, rep)
+
+
+def test_ragged_grid_and_odd_image():
+    """Grid 37 x 29 x 23 (ragged in every tile dimension), 3 cameras of 101 x 77
+    pixels (3 * 101 * 77 is not a multiple of 4: the scalar tail runs)."""
+    rng = np.random.default_rng(3)
+    cams = S.ring_cameras(rng, 3, 101, 77, 95.0, (0.0, 0.0, 1.0))
+    grid = S.Grid(37, 29, 23, (-0.9, -0.7, 0.1), 0.05)
+    mean, sigma = S.make_background(rng, 3, 77, 101)
+    var = (sigma ** 2 + 4).astype(np.float32)
+    caps = S.body_capsules(S.random_pose(rng), rng.uniform(0, 255, (10, 3)))
+    img = S.render_images(rng, cams, caps, mean, sigma)
+    p = S.Params()
+    got = gpu_reconstruct(grid, cams, img, mean.astype(np.float32), var, p)
+    ref = oracle.reconstruct(grid, cams, img, mean.astype(np.float32), var, p)
+    compare(got, ref)
+    assert ref["list"].size > 50
+
+
+@pytest.mark.parametrize("prior,thr", [(0.5, 0.5), (0.3, 0.6), (0.7, 0.4)])
+def test_other_rates_prior_threshold(prior, thr):
+    sc = S.make_scene(seed=8, grid_n=48, cube_side=2.0, n_cams=5, width=200, height=150, focal=190.0)
+    p = S.Params(p_detect=0.8, p_false_alarm=0.25, prior=prior, threshold=thr)
+    got = gpu_reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, p)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, p)
+    compare(got, ref, threshold=thr)
+
+
+def test_literal_eq6_to_9_rates():
+    """P_D = 1, P_FA = 0 (Eq. 6-9 verbatim): the degenerate branch of the log ratio."""
+    sc = S.make_scene(seed=9, grid_n=40, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0)
+    p = S.Params(p_detect=1.0, p_false_alarm=0.0)
+    got = gpu_reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, p)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, p)
+    compare(got, ref)
+
+
+def test_visual_hull_from_binary_maps():
+    """psfs_fuse_slm on near-binary maps with P_D = 1, P_FA = 0: the set must
+    equal the oracle's (the visual hull), excluding pixel-edge voxels."""
+    rng = np.random.default_rng(12)
+    cams = S.ring_cameras(rng, 4, 96, 72, 85.0, (0.0, 0.0, 1.0))
+    caps = [S.Capsule(np.array([-0.2, 0.1, 0.7]), np.array([0.25, -0.1, 1.35]), 0.2, np.zeros(3))]
+    eps = 1e-6
+    maps = np.stack([np.where(S.render_labels(c, caps) >= 0, 1 - eps, eps) for c in cams]).astype(np.float32)
+    grid = {"nx": 32, "ny": 32, "nz": 32, "origin": (-0.6, -0.6, 0.4), "voxel_size": 1.2 / 32}
+    p = {"p_detect": 1.0, "p_false_alarm": 0.0, "prior": 0.5, "threshold": 0.5}
+    rec = psfs.Reconstructor(grid, cams, p)
+    occ, lst, cnt = rec.fuse_slm(to_dev(maps))
+    assert rec.sync() == psfs.PSFS_OK
+    got = {"occ": occ.cpu().numpy().ravel().astype(np.float64), "count": int(cnt.item()),
+           "list": psfs.voxel_list(lst, cnt, rec.capacity).numpy(), "status": 0}
+    ref = oracle.fuse(grid, cams, maps.astype(np.float64), p)
+    # the carved set: occupied iff every seeing camera sees the capsule
+    compare(got, ref, occ_tol=1e-5)
+    assert ref["list"].size > 100
+    rec.close()
+
+
+def test_empty_scene_and_unseen_grid():
+    """No body: nothing occupied.  A grid no camera sees keeps the prior."""
+    rng = np.random.default_rng(4)
+    cams = S.ring_cameras(rng, 4, 128, 96, 120.0, (0.0, 0.0, 1.0))
+    mean, sigma = S.make_background(rng, 4, 96, 128)
+    img = S.render_images(rng, cams, [], mean, sigma)
+    var = (sigma ** 2 + 4).astype(np.float32)
+    grid = S.Grid(24, 24, 24, (-1.0, -1.0, 0.0), 2.0 / 24)
+    got = gpu_reconstruct(grid, cams, img, mean.astype(np.float32), var, S.Params())
+    assert got["count"] == 0
+    far = S.Grid(16, 16, 16, (30.0, 30.0, 30.0), 0.1)
+    for prior, n_expect in [(0.5, 0), (0.7, 16 ** 3)]:
+        got = gpu_reconstruct(far, cams, img, mean.astype(np.float32), var, S.Params(prior=prior))
+        assert np.all(np.abs(got["occ"] - prior) <= 1e-7)
+        assert got["count"] == n_expect
+
+
+def test_capacity_overflow_reports_true_count():
+    sc = S.scene_64cube_4cam(seed=0)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    cap = 100
+    got = gpu_reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params, capacity=cap)
+    assert got["status"] == psfs.PSFS_ERR_CAPACITY
+    assert abs(got["count"] - ref["list"].size) <= int(ref["boundary"].sum())
+    assert got["list"].size == cap
+    assert np.isin(got["list"], np.flatnonzero(ref["occupied"] | ref["boundary"])).all()
+
+
+def test_host_buffer_path_equals_device_path():
+    sc = S.scene_64cube_4cam(seed=2)
+    dev = gpu_reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    occ = np.empty(sc.grid.n_voxels, np.float32)
+    lst = np.empty(sc.grid.n_voxels, np.uint32)
+    cnt = np.zeros(1, np.uint32)
+    st = psfs.psfs_reconstruct_host(rec.handle, np.ascontiguousarray(sc.images), occ, lst, lst.size, cnt)
+    assert st == psfs.PSFS_OK
+    np.testing.assert_array_equal(occ.astype(np.float64), dev["occ"])
+    np.testing.assert_array_equal(np.sort(lst[:cnt[0]]), dev["list"])
+    # overflow through the host path
+    st = psfs.psfs_reconstruct_host(rec.handle, np.ascontiguousarray(sc.images), None, lst, 10, cnt)
+    assert st == psfs.PSFS_ERR_CAPACITY and cnt[0] == dev["count"]
+    rec.close()
+
+
+@pytest.mark.parametrize("dtype,bound", [("f16", 5e-3), ("bf16", 5e-2)])
+def test_reduced_precision_maps_error_reported(dtype, bound):
+    """FP16 / BF16 maps: error against FP64 is reported; a loose sanity bound
+    guards against a broken conversion."""
+    sc = S.scene_64cube_4cam(seed=0)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    got = gpu_reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params, map_dtype=dtype)
+    rep = compare(got, ref, exact=False)
+    print(dtype, rep)
+    assert rep["max_abs_err"] < bound
+    assert rep["set_diff"] < 0.02 * max(1, ref["list"].size)
+
+
+def test_background_validation_and_not_ready():
+    sc = S.scene_64cube_4cam(seed=0)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    occ, lst, cnt = rec.alloc_outputs()
+    with pytest.raises(psfs.PsfsError) as e:
+        psfs.psfs_reconstruct(rec.handle, to_dev(sc.images), occ, lst, rec.capacity, cnt)
+    assert e.value.status == psfs.PSFS_ERR_NOT_READY
+    bad = sc.var.copy()
+    bad[1, 2, 3, 1] = 0.0
+    with pytest.raises(psfs.PsfsError) as e:
+        rec.set_background(to_dev(sc.mean), to_dev(bad))
+    assert e.value.status == psfs.PSFS_ERR_INVALID_ARG
+    bad = sc.mean.copy()
+    bad[0, 0, 0, 0] = np.nan
+    with pytest.raises(psfs.PsfsError):
+        rec.set_background(to_dev(bad), to_dev(sc.var))
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    # misaligned device pointer
+    img = to_dev(sc.images.ravel())
+    with pytest.raises(psfs.PsfsError) as e:
+        psfs.psfs_reconstruct(rec.handle, img.data_ptr() + 1, occ, lst, rec.capacity, cnt)
+    assert e.value.status == psfs.PSFS_ERR_INVALID_ARG
+    rec.close()
