@@ -38,6 +38,7 @@ struct psfs_handle {
     uint32_t *d_words = nullptr;    // [0] status, [1] scratch counter, [2] host-path count
     uint32_t *h_words = nullptr;    // pinned mirror
     uint64_t *tiles = nullptr;
+    int4 *tilecam = nullptr;    // [n_tiles][n_cams] staging records
     int n_tiles = 0;
 
     // host-buffer path staging (allocated on first use)
@@ -100,6 +101,94 @@ uint64_t spread3(uint64_t x)
     return x;
 }
 
+// Staging records of every (tile, camera) pair; see FuseArgs in
+// psfs_internal.cuh.  Everything here is double precision on the host; the
+// fast paths it enables are taken only where a bound on the float32
+// projection error of the kernels stays below a quarter pixel, well inside
+// the one-pixel margin of each box.
+void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, const FuseArgs &f,
+                   const std::vector<uint64_t> &tiles, int elem_bytes, int cap_elems,
+                   std::vector<int4> &out)
+{
+    const int W = cams[0].width, H = cams[0].height;
+    const int chunk = 16 / elem_bytes;
+    const bool can_stage = ((int64_t)W * elem_bytes) % 16 == 0;
+    const double vs = g.voxel_size;
+    const double eps32 = std::ldexp(1.0, -24);
+    // per camera: magnitude bounds of the float32 projection sums
+    std::vector<double> Su(n_cams), Sv(n_cams), Sw(n_cams);
+    const double half[3] = {0.5 * g.nx + 1, 0.5 * g.ny + 1, 0.5 * g.nz + 1};
+    for (int c = 0; c < n_cams; ++c) {
+        const float *m = f.cam[c].m;
+        double su = std::fabs(m[3]), sv = std::fabs(m[7]), sw = std::fabs(m[11]);
+        for (int a = 0; a < 3; ++a) {
+            su += std::fabs(m[a]) * half[a];
+            sv += std::fabs(m[4 + a]) * half[a];
+            sw += std::fabs(m[8 + a]) * half[a];
+        }
+        Su[c] = su;
+        Sv[c] = sv;
+        Sw[c] = sw;
+    }
+    out.assign(tiles.size() * (size_t)n_cams, make_int4(0, 0, 0, 0));
+    for (size_t n = 0; n < tiles.size(); ++n) {
+        const uint64_t tc = tiles[n];
+        const int tx = (int)(tc & 0x1FFFFF), ty = (int)((tc >> 21) & 0x1FFFFF), tz = (int)(tc >> 42);
+        const int i0 = tx * 32, i1 = std::min(g.nx, i0 + 32) - 1;
+        const int j0 = ty * FUSE_WY, j1 = std::min(g.ny, j0 + FUSE_WY) - 1;
+        const int k0 = tz * FUSE_TZ, k1 = std::min(g.nz, k0 + FUSE_TZ) - 1;
+        for (int c = 0; c < n_cams; ++c) {
+            const double *K = cams[c].K, *R = cams[c].R, *t = cams[c].t;
+            double wmin = 1e300, wmax = -1e300, xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+            for (int corner = 0; corner < 8; ++corner) {
+                const int ii = (corner & 1) ? i1 : i0, jj = (corner & 2) ? j1 : j0, kk = (corner & 4) ? k1 : k0;
+                const double X[3] = {g.origin[0] + (ii + 0.5) * vs, g.origin[1] + (jj + 0.5) * vs,
+                                     g.origin[2] + (kk + 0.5) * vs};
+                double xc[3], uvw[3];
+                for (int r = 0; r < 3; ++r) xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
+                for (int r = 0; r < 3; ++r) uvw[r] = K[3 * r] * xc[0] + K[3 * r + 1] * xc[1] + K[3 * r + 2] * xc[2];
+                wmin = std::min(wmin, uvw[2]);
+                wmax = std::max(wmax, uvw[2]);
+                if (uvw[2] > 0) {
+                    const double x = uvw[0] / uvw[2], y = uvw[1] / uvw[2];
+                    xmin = std::min(xmin, x);
+                    xmax = std::max(xmax, x);
+                    ymin = std::min(ymin, y);
+                    ymax = std::max(ymax, y);
+                }
+            }
+            int4 &rec = out[n * (size_t)n_cams + c];
+            const double dw = 8 * eps32 * Sw[c];   // bound on the float32 error of w
+            if (wmax < -2 * dw) {   // every centre behind the camera, also in float32
+                rec.w = kTcSkip << 16;
+                continue;
+            }
+            if (wmin <= 1e-3 * Sw[c]) continue;   // near or across the camera plane: checked global path
+            const double xa = std::max(std::fabs(xmin), std::fabs(xmax)), ya = std::max(std::fabs(ymin), std::fabs(ymax));
+            const double ex = 2 * ((8 * eps32 * Su[c] + xa * dw) / wmin + xa * std::ldexp(1.0, -21));
+            const double ey = 2 * ((8 * eps32 * Sv[c] + ya * dw) / wmin + ya * std::ldexp(1.0, -21));
+            if (!(ex < 0.25 && ey < 0.25) || xa > 1e6 || ya > 1e6) continue;
+            const int64_t xlo = (int64_t)std::floor(xmin) - 1, xhi = (int64_t)std::floor(xmax) + 2;
+            const int64_t ylo = (int64_t)std::floor(ymin) - 1, yhi = (int64_t)std::floor(ymax) + 2;
+            const bool inside = xlo >= 0 && xhi <= W && ylo >= 0 && yhi <= H;
+            const int64_t cx0 = std::max<int64_t>(0, xlo), cx1 = std::min<int64_t>(W, xhi);
+            const int64_t cy0 = std::max<int64_t>(0, ylo), cy1 = std::min<int64_t>(H, yhi);
+            if (cx0 >= cx1 || cy0 >= cy1) {
+                rec.w = kTcSkip << 16;
+                continue;
+            }
+            if (!can_stage) continue;
+            const int64_t ax0 = cx0 / chunk * chunk, ax1 = (cx1 + chunk - 1) / chunk * chunk;
+            const int64_t sw = ax1 - ax0, sh = cy1 - cy0;
+            if (sw * sh > cap_elems) continue;
+            rec.x = (int)ax0;
+            rec.y = (int)cy0;
+            rec.z = (int)sw;
+            rec.w = (int)sh | ((kTcStaged | (inside ? kTcInside : 0)) << 16);
+        }
+    }
+}
+
 psfs_status check_params(const psfs_params *p)
 {
     if (!p) return fail(PSFS_ERR_INVALID_ARG, "params is NULL");
@@ -132,6 +221,7 @@ void free_handle(psfs_handle *h)
     cudaFree(h->d_words);
     cudaFreeHost(h->h_words);
     cudaFree(h->tiles);
+    cudaFree(h->tilecam);
     cudaFree(h->st_images);
     cudaFree(h->st_occ);
     cudaFree(h->st_list);
@@ -334,6 +424,9 @@ psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t 
     for (size_t n = 0; n < order.size(); ++n) tiles[n] = order[n].second;
     h->n_tiles = (int)tiles.size();
     f.n_tiles = h->n_tiles;
+    f.smem_cap = fuse_smem_cap(params->map_dtype);
+    std::vector<int4> tilecam;
+    build_tilecam(*grid, cams, n_cams, f, tiles, (int)h->map_elem, f.smem_cap, tilecam);
 
     DeviceGuard guard(h->device);
     const size_t pix_bytes = (size_t)h->n_pix;
@@ -342,15 +435,19 @@ psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t 
         cudaMalloc(&h->bg_hinv, pix_bytes * 3 * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&h->d_words, 16 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&h->h_words, 16 * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&h->tiles, tiles.size() * sizeof(uint64_t)) != cudaSuccess) {
+        cudaMalloc(&h->tiles, tiles.size() * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&h->tilecam, tilecam.size() * sizeof(int4)) != cudaSuccess) {
         cudaGetLastError();
         free_handle(h);
         return fail(PSFS_ERR_NOMEM, "device scratch allocation");
     }
     f.maps = h->maps;
     f.tiles = h->tiles;
+    f.tilecam = h->tilecam;
     f.status = h->d_words;
     e = cudaMemcpy(h->tiles, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->tilecam, tilecam.data(), tilecam.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->d_words, 0, 16 * sizeof(uint32_t));
     if (e != cudaSuccess) {
         free_handle(h);

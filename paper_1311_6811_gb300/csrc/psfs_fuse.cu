@@ -3,14 +3,18 @@
 // sum over cameras (log form of the product of Eq. 4), posterior, strict
 // threshold and compaction of the occupied voxels.
 //
-// Work decomposition.  A CTA owns a tile of 32 (x) x FUSE_WY (y) x FUSE_TZ (z)
-// voxels: each warp is one run of 32 voxels along x, so the occupancy stores
-// of a warp are 128 contiguous bytes and its 32 gathers of one camera land in
-// a short projected segment of that camera's map; each thread walks FUSE_TZ
-// voxels along z, sharing the x/y part of the projection.  CTAs are issued in
-// Morton order of their tiles so that neighbouring CTAs gather neighbouring
-// map regions.  Cameras are looped inside the thread; the per-voxel sum stays
-// in registers.
+// Work decomposition.  A CTA owns a tile of 32 (x) x WY (y) x TZ (z) voxels:
+// each warp is one run of 32 voxels along x (128-byte occupancy stores) and
+// each thread walks TZ voxels along z, sharing the x/y part of the
+// projection.  CTAs are issued in Morton order of their tiles.
+//
+// Gather.  For each camera the CTA copies the image box that its voxel
+// centres project into (computed on the host per tile and camera, 16-byte
+// aligned rows) from the L2-resident map into shared memory with cp.async,
+// then every voxel reads its pixel from shared memory.  A box that does not
+// fit the buffer falls back to gathers from global memory.  When the host
+// has proven that every voxel centre of the tile is in front of the camera
+// and inside the image, the per-voxel visibility test is skipped.
 //
 // Compaction: per warp a ballot per z step, per CTA one atomicAdd on the
 // global count, then each warp writes its indices at its prefix offset.
@@ -20,14 +24,40 @@ namespace psfs {
 
 namespace {
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ float smem_load(const T *p);
+template <>
+__device__ __forceinline__ float smem_load<float>(const float *p) { return *p; }
+template <>
+__device__ __forceinline__ float smem_load<__half>(const __half *p) { return __half2float(*p); }
+template <>
+__device__ __forceinline__ float smem_load<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(*p);
+}
+
 template <typename MapT, int WY, int TZ>
 __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ FuseArgs a)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MapT *sbuf = reinterpret_cast<MapT *>(smem_raw);
     __shared__ uint32_t s_warp_off[WY];
     __shared__ uint32_t s_base;
 
     const int lane = threadIdx.x;
     const int wy = threadIdx.y;
+    const int tid = wy * 32 + lane;
     const uint64_t tc = a.tiles[blockIdx.x];
     const int tx = (int)(tc & 0x1FFFFFu);
     const int ty = (int)((tc >> 21) & 0x1FFFFFu);
@@ -37,23 +67,61 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
     const int k0 = tz * TZ;
     const float fi = (float)i - a.ci;
     const float fj = (float)j - a.cj;
-    const float Wf = (float)a.W, Hf = (float)a.H;
+    const uint32_t W = (uint32_t)a.W, H = (uint32_t)a.H;
+    constexpr int kChunk = 16 / (int)sizeof(MapT);   // elements per 16-byte copy
 
+    float fk[TZ];
     float L[TZ];
 #pragma unroll
-    for (int t = 0; t < TZ; ++t) L[t] = 0.0f;
+    for (int t = 0; t < TZ; ++t) {
+        fk[t] = (float)(k0 + t) - a.ck;
+        L[t] = 0.0f;
+    }
 
     const MapT *maps = reinterpret_cast<const MapT *>(a.maps);
+    const int4 *tcrec = a.tilecam + (int64_t)blockIdx.x * a.n_cams;
     for (int c = 0; c < a.n_cams; ++c) {
+        const int4 rec = __ldg(tcrec + c);
+        const int flags = rec.w >> 16;
+        if (flags & kTcSkip) continue;
         const float *m = a.cam[c].m;
         const MapT *map = maps + (int64_t)c * a.map_stride;
+        float bu, bv, bw;
+        project_base(m, fi, fj, &bu, &bv, &bw);
+        if (flags & kTcStaged) {
+            const int bx0 = rec.x, by0 = rec.y, sw = rec.z, sh = rec.w & 0xFFFF;
+            __syncthreads();   // the previous camera's gathers are done with the buffer
+            const MapT *src = map + (int64_t)by0 * W + bx0;
+            const int row_chunks = sw / kChunk;
+            for (int r = wy; r < sh; r += WY)
+                for (int q = lane; q < row_chunks; q += 32)
+                    cp_async16(sbuf + r * sw + q * kChunk, src + (int64_t)r * W + q * kChunk);
+            cp_async_wait_all();
+            __syncthreads();
+            const uint32_t ox = kFloorBias + (uint32_t)bx0, oy = kFloorBias + (uint32_t)by0;
+            if (flags & kTcInside) {
 #pragma unroll
-        for (int t = 0; t < TZ; ++t) {
-            const float fk = (float)(k0 + t) - a.ck;
-            int pix;
-            if (project_voxel(m, fi, fj, fk, Wf, Hf, a.W, &pix)) L[t] += map_load<MapT>(map + pix);
+                for (int t = 0; t < TZ; ++t) {
+                    const Proj p = project_biased(m, bu, bv, bw, fk[t]);
+                    L[t] += smem_load<MapT>(sbuf + (p.by - oy) * (uint32_t)sw + (p.bx - ox));
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < TZ; ++t) {
+                    const Proj p = project_biased(m, bu, bv, bw, fk[t]);
+                    const uint32_t sx = p.bx - ox, sy = p.by - oy;
+                    if ((sx < (uint32_t)sw) & (sy < (uint32_t)sh)) L[t] += smem_load<MapT>(sbuf + sy * (uint32_t)sw + sx);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) {
+                int pix;
+                if (proj_pixel(project_biased(m, bu, bv, bw, fk[t]), W, H, &pix)) L[t] += map_load<MapT>(map + pix);
+            }
         }
     }
+    (void)tid;
 
     // posterior, threshold, compaction
     const bool in_xy = (i < a.nx) && (j < a.ny);
@@ -66,7 +134,7 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
         const float lo = L[t] + a.logit_prior;
         if (valid) {
             const uint32_t lin = (uint32_t)i + (uint32_t)a.nx * ((uint32_t)j + (uint32_t)a.ny * (uint32_t)k);
-            __stcs(a.occ + lin, 1.0f / (1.0f + expf(-lo)));
+            __stcs(a.occ + lin, __fdividef(1.0f, 1.0f + __expf(-lo)));
         }
         ballots[t] = __ballot_sync(0xFFFFFFFFu, valid && (lo > a.logit_tau));
         warp_count += __popc(ballots[t]);
@@ -77,9 +145,9 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
         uint32_t total = 0;
 #pragma unroll
         for (int w = 0; w < WY; ++w) {
-            const uint32_t c = s_warp_off[w];
+            const uint32_t cnt = s_warp_off[w];
             s_warp_off[w] = total;
-            total += c;
+            total += cnt;
         }
         uint32_t base = 0;
         if (total) {
@@ -105,20 +173,36 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
     }
 }
 
+template <typename MapT>
+cudaError_t launch_typed(const FuseArgs &a, cudaStream_t s)
+{
+    auto kern = fuse_kernel<MapT, FUSE_WY, FUSE_TZ>;
+    const int smem = a.smem_cap * (int)sizeof(MapT);
+    static bool configured[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSE_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    kern<<<a.n_tiles, dim3(32, FUSE_WY), smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int fuse_smem_cap(int map_dtype)
+{
+    return FUSE_SMEM_BYTES / (map_dtype == PSFS_MAP_F32 ? 4 : 2);
+}
 
 cudaError_t launch_fuse(const FuseArgs &a, int map_dtype, cudaStream_t s)
 {
     if (a.n_tiles <= 0) return cudaSuccess;
-    const dim3 block(32, FUSE_WY);
-    if (map_dtype == PSFS_MAP_F16) {
-        fuse_kernel<__half, FUSE_WY, FUSE_TZ><<<a.n_tiles, block, 0, s>>>(a);
-    } else if (map_dtype == PSFS_MAP_BF16) {
-        fuse_kernel<__nv_bfloat16, FUSE_WY, FUSE_TZ><<<a.n_tiles, block, 0, s>>>(a);
-    } else {
-        fuse_kernel<float, FUSE_WY, FUSE_TZ><<<a.n_tiles, block, 0, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (map_dtype == PSFS_MAP_F16) return launch_typed<__half>(a, s);
+    if (map_dtype == PSFS_MAP_BF16) return launch_typed<__nv_bfloat16>(a, s);
+    return launch_typed<float>(a, s);
 }
 
 }  // namespace psfs

@@ -64,6 +64,17 @@ struct SlmToMapArgs {
     uint32_t *zero_word;
 };
 
+// Per (tile, camera) record prepared on the host at handle creation, in
+// double precision from the 8 corner voxel centres of the tile:
+//   x, y   first staged column (rounded down to a 16-byte boundary) and row
+//   bw     staged width in elements (a whole number of 16-byte chunks)
+//   bhf    staged height in rows | flags << 16
+// The staged box covers the projections of every voxel centre of the tile
+// that the camera sees (1 px margin), clipped to the image.
+constexpr int kTcStaged = 1;   // box fits the shared-memory buffer: gather from it
+constexpr int kTcInside = 2;   // every voxel centre is in front and inside the image
+constexpr int kTcSkip = 4;     // the camera sees no voxel centre of the tile
+
 struct FuseArgs {
     const void *maps;         // [n_cams][H][W] of g, dtype per map_dtype
     int W, H;
@@ -72,7 +83,9 @@ struct FuseArgs {
     int nx, ny, nz;
     float ci, cj, ck;         // (n - 1) / 2 per axis
     const uint64_t *tiles;    // packed tile coordinates, Morton order
+    const int4 *tilecam;      // [n_tiles][n_cams] staging records
     int n_tiles;
+    int smem_cap;             // elements of the staging buffer
     float logit_prior, logit_tau;
     float *occ;               // [nz][ny][nx]
     uint32_t *list;
@@ -84,8 +97,9 @@ struct FuseArgs {
 
 // Tile shape of the fuse kernel: 32 voxels along x (one warp), FUSE_WY warps
 // along y, FUSE_TZ voxels along z per thread.
-constexpr int FUSE_WY = 4;
+constexpr int FUSE_WY = 8;
 constexpr int FUSE_TZ = 8;
+constexpr int FUSE_SMEM_BYTES = 48 * 1024;
 
 __host__ __device__ inline uint64_t pack_tile(uint32_t tx, uint32_t ty, uint32_t tz)
 {
@@ -102,29 +116,64 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
-// floor(x) for 0 <= x < 2^22: adding 1.5 * 2^23 with round-down leaves
-// floor(x) in the low mantissa bits.
-__device__ __forceinline__ int floor_nonneg(float x)
+// Pixel coordinate with a bias: fma with round-down of u * rw + 1.5 * 2^23
+// leaves floor(u * rw) in the low mantissa bits, so the bit pattern minus
+// kFloorBias is floor(u / w) for |u / w| < 2^22.  Outside that range, and for
+// inf / NaN, the unsigned difference is >= 2^22, larger than any image side,
+// so a single unsigned compare both floors and bounds-checks.
+constexpr float kFloorMagic = 12582912.0f;   // 1.5 * 2^23
+constexpr uint32_t kFloorBias = 0x4B400000u; // its bit pattern
+
+__device__ __forceinline__ uint32_t biased_floor(float u, float rw)
 {
-    return __float_as_int(__fadd_rd(x, 12582912.0f)) - 0x4B400000;
+    return __float_as_uint(__fmaf_rd(u, rw, kFloorMagic));
 }
 
 // Projection of voxel (fi, fj, fk) (centred index coordinates) into camera
-// `m`.  Returns true and the pixel offset py * W + px if the centre is seen.
-// The forward and the adjoint both call this, so their pixel choice is
-// identical bit for bit.
-__device__ __forceinline__ bool project_voxel(const float *m, float fi, float fj, float fk,
-                                              float Wf, float Hf, int W, int *pix)
+// `m`: the homogeneous image position (u, v, w) = M (fi, fj, fk, 1), its
+// reciprocal depth and the biased pixel coordinates.  Every kernel that maps a
+// voxel to a pixel (forward and adjoint) goes through this function, so their
+// pixel choices are identical bit for bit.
+struct Proj {
+    float w;
+    uint32_t bx, by;   // biased floor(u / w), floor(v / w)
+};
+
+__device__ __forceinline__ Proj project_biased(const float *m, float bu, float bv, float bw, float fk)
 {
-    float u = fmaf(m[2], fk, fmaf(m[0], fi, fmaf(m[1], fj, m[3])));
-    float v = fmaf(m[6], fk, fmaf(m[4], fi, fmaf(m[5], fj, m[7])));
-    float w = fmaf(m[10], fk, fmaf(m[8], fi, fmaf(m[9], fj, m[11])));
-    float rw = rcp_approx(w);
-    float x = u * rw;
-    float y = v * rw;
-    bool vis = (w > 0.0f) & (x >= 0.0f) & (x < Wf) & (y >= 0.0f) & (y < Hf);
-    *pix = vis ? floor_nonneg(y) * W + floor_nonneg(x) : 0;
-    return vis;
+    Proj p;
+    const float u = fmaf(m[2], fk, bu);
+    const float v = fmaf(m[6], fk, bv);
+    p.w = fmaf(m[10], fk, bw);
+    const float rw = rcp_approx(p.w);
+    p.bx = biased_floor(u, rw);
+    p.by = biased_floor(v, rw);
+    return p;
+}
+
+// The k-independent part of the projection of row (fi, fj).
+__device__ __forceinline__ void project_base(const float *m, float fi, float fj, float *bu, float *bv,
+                                             float *bw)
+{
+    *bu = fmaf(m[0], fi, fmaf(m[1], fj, m[3]));
+    *bv = fmaf(m[4], fi, fmaf(m[5], fj, m[7]));
+    *bw = fmaf(m[8], fi, fmaf(m[9], fj, m[11]));
+}
+
+// Seen test and pixel offset py * W + px of a projected voxel centre.
+__device__ __forceinline__ bool proj_pixel(const Proj &p, uint32_t W, uint32_t H, int *pix)
+{
+    const uint32_t ix = p.bx - kFloorBias, iy = p.by - kFloorBias;
+    *pix = (int)(iy * W + ix);
+    return (p.w > 0.0f) & (ix < W) & (iy < H);
+}
+
+__device__ __forceinline__ bool project_voxel(const float *m, float fi, float fj, float fk,
+                                              uint32_t W, uint32_t H, int *pix)
+{
+    float bu, bv, bw;
+    project_base(m, fi, fj, &bu, &bv, &bw);
+    return proj_pixel(project_biased(m, bu, bv, bw, fk), W, H, pix);
 }
 
 template <typename T>
@@ -170,5 +219,6 @@ cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_o
                               cudaStream_t s);
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, int map_dtype, cudaStream_t s);
+int fuse_smem_cap(int map_dtype);
 
 }  // namespace psfs

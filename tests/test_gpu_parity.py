@@ -194,3 +194,43 @@ def test_background_validation_and_not_ready():
         psfs.psfs_reconstruct(rec.handle, img.data_ptr() + 1, occ, lst, rec.capacity, cnt)
     assert e.value.status == psfs.PSFS_ERR_INVALID_ARG
     rec.close()
+
+
+def test_cameras_inside_the_grid():
+    """An 8 m grid that contains the camera ring: voxels behind, beside and in
+    front of every camera (tiles that straddle the camera plane take the
+    checked path, tiles wholly behind are skipped)."""
+    sc = S.make_scene(seed=14, grid_n=48, cube_side=8.0, n_cams=4, width=160, height=120, focal=150.0)
+    got = gpu_reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    compare(got, ref)
+    assert (ref["n_seen"] == 0).any() and (ref["n_seen"] == 4).any()
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_reduced_precision_maps_match_oracle_on_rounded_maps(dtype):
+    """Storage only: with maps rounded to f16 / bf16 the kernel must sum the
+    rounded log ratios exactly as the FP64 fusion of the same rounded values
+    does.  The oracle fuses SLM values, so the rounded log ratio g is mapped
+    back to s with the rates P_D = 1, P_FA = 0, where g = log(2 s)."""
+    sc = S.make_scene(seed=15, grid_n=40, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0)
+    p = S.Params(p_detect=1.0, p_false_alarm=0.0)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, p, map_dtype=dtype)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    s32 = rec.likelihood(to_dev(sc.images)).double().cpu().numpy()
+    occ, lst, cnt = rec.reconstruct(to_dev(sc.images))
+    assert rec.sync() == psfs.PSFS_OK
+    tdt = torch.float16 if dtype == "f16" else torch.bfloat16
+    g = np.log(2.0 * np.maximum(s32, 1e-30))
+    g_rounded = torch.from_numpy(g).float().to(tdt).double().numpy()
+    s_equiv = np.exp(g_rounded) / 2.0
+    ref = oracle.fuse(sc.grid, sc.cams, s_equiv, p)
+    got = {"occ": occ.cpu().numpy().ravel().astype(np.float64), "count": int(cnt.item()),
+           "list": psfs.voxel_list(lst, cnt, rec.capacity).numpy(), "status": 0}
+    rep = compare(got, ref, exact=False)
+    # what is left: a rounding step between the kernel's FP32 g and the g
+    # recomputed here from the FP32 SLM, which now and then lands a value one
+    # storage ulp away; rare, so the mean stays tiny
+    assert rep["max_abs_err"] < (2e-3 if dtype == "f16" else 2e-2), rep
+    assert rep["mean_abs_err"] < 1e-5, rep
+    rec.close()
