@@ -65,8 +65,11 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
     const int i = tx * 32 + lane;
     const int j = ty * WY + wy;
     const int k0 = tz * TZ;
-    const float fi = (float)i - a.ci;
-    const float fj = (float)j - a.cj;
+    // Lanes past the grid edge (ragged tiles) project the nearest voxel of the
+    // grid instead, so every projection stays inside the tile's staged box;
+    // their results are discarded below.
+    const float fi = (float)min(i, a.nx - 1) - a.ci;
+    const float fj = (float)min(j, a.ny - 1) - a.cj;
     const uint32_t W = (uint32_t)a.W, H = (uint32_t)a.H;
     constexpr int kChunk = 16 / (int)sizeof(MapT);   // elements per 16-byte copy
 
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
     float L[TZ];
 #pragma unroll
     for (int t = 0; t < TZ; ++t) {
-        fk[t] = (float)(k0 + t) - a.ck;
+        fk[t] = (float)min(k0 + t, a.nz - 1) - a.ck;
         L[t] = 0.0f;
     }
 
@@ -100,10 +103,13 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
             __syncthreads();
             const uint32_t ox = kFloorBias + (uint32_t)bx0, oy = kFloorBias + (uint32_t)by0;
             if (flags & kTcInside) {
+                // the host proved every centre of the tile lands in the box; the
+                // min() only keeps a violated proof from leaving the buffer
+                const uint32_t last = (uint32_t)(sw * sh - 1);
 #pragma unroll
                 for (int t = 0; t < TZ; ++t) {
                     const Proj p = project_biased(m, bu, bv, bw, fk[t]);
-                    L[t] += smem_load<MapT>(sbuf + (p.by - oy) * (uint32_t)sw + (p.bx - ox));
+                    L[t] += smem_load<MapT>(sbuf + min((p.by - oy) * (uint32_t)sw + (p.bx - ox), last));
                 }
             } else {
 #pragma unroll
@@ -191,11 +197,6 @@ cudaError_t launch_typed(const FuseArgs &a, cudaStream_t s)
 }
 
 }  // namespace
-
-int fuse_smem_cap(int map_dtype)
-{
-    return FUSE_SMEM_BYTES / (map_dtype == PSFS_MAP_F32 ? 4 : 2);
-}
 
 cudaError_t launch_fuse(const FuseArgs &a, int map_dtype, cudaStream_t s)
 {

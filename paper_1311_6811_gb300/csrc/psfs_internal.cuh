@@ -22,6 +22,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "psfs.h"
 
 namespace psfs {
@@ -220,5 +222,10 @@ cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_o
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, int map_dtype, cudaStream_t s);
 int fuse_smem_cap(int map_dtype);
+
+// Host planning (psfs_plan.cu): projection matrices, tile order and staging
+// records of the fuse kernel for one grid and camera rig.
+void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const psfs_params &params,
+               FuseArgs *out, std::vector<uint64_t> *tiles, std::vector<int4> *tilecam);
 
 }  // namespace psfs

@@ -1,0 +1,179 @@
+// psfs_plan.cu -- host-side planning of the fuse kernel for one grid and
+// camera rig, done once at handle creation in double precision:
+//   * the 3x4 projection matrix of every camera in centred voxel-index space;
+//   * the voxel tiles in Morton order;
+//   * per (tile, camera) the staging record (shared-memory box, fast-path
+//     flags) that the fuse kernel reads.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+#include "psfs_internal.cuh"
+
+namespace psfs {
+
+namespace {
+
+uint64_t spread3(uint64_t x)
+{
+    // spread the low 21 bits of x to every third bit
+    x &= 0x1FFFFFull;
+    x = (x | (x << 32)) & 0x1F00000000FFFFull;
+    x = (x | (x << 16)) & 0x1F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Staging records of every (tile, camera) pair; see FuseArgs in
+// psfs_internal.cuh.  Everything here is double precision on the host; the
+// fast paths it enables are taken only where a bound on the float32
+// projection error of the kernels stays below a quarter pixel, well inside
+// the one-pixel margin of each box.
+void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, const FuseArgs &f,
+                   const std::vector<uint64_t> &tiles, int elem_bytes, int cap_elems,
+                   std::vector<int4> &out)
+{
+    const int W = cams[0].width, H = cams[0].height;
+    const int chunk = 16 / elem_bytes;
+    const bool can_stage = ((int64_t)W * elem_bytes) % 16 == 0;
+    const double vs = g.voxel_size;
+    const double eps32 = std::ldexp(1.0, -24);
+    // per camera: magnitude bounds of the float32 projection sums
+    std::vector<double> Su(n_cams), Sv(n_cams), Sw(n_cams);
+    const double half[3] = {0.5 * g.nx + 1, 0.5 * g.ny + 1, 0.5 * g.nz + 1};
+    for (int c = 0; c < n_cams; ++c) {
+        const float *m = f.cam[c].m;
+        double su = std::fabs(m[3]), sv = std::fabs(m[7]), sw = std::fabs(m[11]);
+        for (int a = 0; a < 3; ++a) {
+            su += std::fabs(m[a]) * half[a];
+            sv += std::fabs(m[4 + a]) * half[a];
+            sw += std::fabs(m[8 + a]) * half[a];
+        }
+        Su[c] = su;
+        Sv[c] = sv;
+        Sw[c] = sw;
+    }
+    out.assign(tiles.size() * (size_t)n_cams, make_int4(0, 0, 0, 0));
+    for (size_t n = 0; n < tiles.size(); ++n) {
+        const uint64_t tc = tiles[n];
+        const int tx = (int)(tc & 0x1FFFFF), ty = (int)((tc >> 21) & 0x1FFFFF), tz = (int)(tc >> 42);
+        const int i0 = tx * 32, i1 = std::min(g.nx, i0 + 32) - 1;
+        const int j0 = ty * FUSE_WY, j1 = std::min(g.ny, j0 + FUSE_WY) - 1;
+        const int k0 = tz * FUSE_TZ, k1 = std::min(g.nz, k0 + FUSE_TZ) - 1;
+        for (int c = 0; c < n_cams; ++c) {
+            const double *K = cams[c].K, *R = cams[c].R, *t = cams[c].t;
+            double wmin = 1e300, wmax = -1e300, xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+            for (int corner = 0; corner < 8; ++corner) {
+                const int ii = (corner & 1) ? i1 : i0, jj = (corner & 2) ? j1 : j0, kk = (corner & 4) ? k1 : k0;
+                const double X[3] = {g.origin[0] + (ii + 0.5) * vs, g.origin[1] + (jj + 0.5) * vs,
+                                     g.origin[2] + (kk + 0.5) * vs};
+                double xc[3], uvw[3];
+                for (int r = 0; r < 3; ++r) xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
+                for (int r = 0; r < 3; ++r) uvw[r] = K[3 * r] * xc[0] + K[3 * r + 1] * xc[1] + K[3 * r + 2] * xc[2];
+                wmin = std::min(wmin, uvw[2]);
+                wmax = std::max(wmax, uvw[2]);
+                if (uvw[2] > 0) {
+                    const double x = uvw[0] / uvw[2], y = uvw[1] / uvw[2];
+                    xmin = std::min(xmin, x);
+                    xmax = std::max(xmax, x);
+                    ymin = std::min(ymin, y);
+                    ymax = std::max(ymax, y);
+                }
+            }
+            int4 &rec = out[n * (size_t)n_cams + c];
+            const double dw = 8 * eps32 * Sw[c];   // bound on the float32 error of w
+            if (wmax < -2 * dw) {   // every centre behind the camera, also in float32
+                rec.w = kTcSkip << 16;
+                continue;
+            }
+            if (wmin <= 1e-3 * Sw[c]) continue;   // near or across the camera plane: checked global path
+            const double xa = std::max(std::fabs(xmin), std::fabs(xmax)), ya = std::max(std::fabs(ymin), std::fabs(ymax));
+            const double ex = 2 * ((8 * eps32 * Su[c] + xa * dw) / wmin + xa * std::ldexp(1.0, -21));
+            const double ey = 2 * ((8 * eps32 * Sv[c] + ya * dw) / wmin + ya * std::ldexp(1.0, -21));
+            if (!(ex < 0.25 && ey < 0.25) || xa > 1e6 || ya > 1e6) continue;
+            const int64_t xlo = (int64_t)std::floor(xmin) - 1, xhi = (int64_t)std::floor(xmax) + 2;
+            const int64_t ylo = (int64_t)std::floor(ymin) - 1, yhi = (int64_t)std::floor(ymax) + 2;
+            const bool inside = xlo >= 0 && xhi <= W && ylo >= 0 && yhi <= H;
+            const int64_t cx0 = std::max<int64_t>(0, xlo), cx1 = std::min<int64_t>(W, xhi);
+            const int64_t cy0 = std::max<int64_t>(0, ylo), cy1 = std::min<int64_t>(H, yhi);
+            if (cx0 >= cx1 || cy0 >= cy1) {
+                rec.w = kTcSkip << 16;
+                continue;
+            }
+            if (!can_stage) continue;
+            const int64_t ax0 = cx0 / chunk * chunk, ax1 = (cx1 + chunk - 1) / chunk * chunk;
+            const int64_t sw = ax1 - ax0, sh = cy1 - cy0;
+            if (sw * sh > cap_elems) continue;
+            rec.x = (int)ax0;
+            rec.y = (int)cy0;
+            rec.z = (int)sw;
+            rec.w = (int)sh | ((kTcStaged | (inside ? kTcInside : 0)) << 16);
+        }
+    }
+}
+
+}  // namespace
+
+int fuse_smem_cap(int map_dtype)
+{
+    return FUSE_SMEM_BYTES / (map_dtype == PSFS_MAP_F32 ? 4 : 2);
+}
+
+void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const psfs_params &params,
+               FuseArgs *out, std::vector<uint64_t> *tiles_out, std::vector<int4> *tilecam_out)
+{
+    FuseArgs &f = *out;
+    std::memset(&f, 0, sizeof(f));
+    const int W = cams[0].width, H = cams[0].height;
+    f.W = W;
+    f.H = H;
+    f.map_stride = (int64_t)W * H;
+    f.n_cams = n_cams;
+    f.nx = grid.nx;
+    f.ny = grid.ny;
+    f.nz = grid.nz;
+    f.ci = 0.5f * (float)(grid.nx - 1);
+    f.cj = 0.5f * (float)(grid.ny - 1);
+    f.ck = 0.5f * (float)(grid.nz - 1);
+    // voxel (i, j, k) sits at centre + voxel_size * (i - ci, j - cj, k - ck)
+    const double vs = grid.voxel_size;
+    const double centre[3] = {grid.origin[0] + 0.5 * grid.nx * vs, grid.origin[1] + 0.5 * grid.ny * vs,
+                              grid.origin[2] + 0.5 * grid.nz * vs};
+    for (int c = 0; c < n_cams; ++c) {
+        const double *K = cams[c].K, *R = cams[c].R, *t = cams[c].t;
+        double KR[9], xc[3];
+        for (int r = 0; r < 3; ++r) {
+            for (int col = 0; col < 3; ++col)
+                KR[3 * r + col] = K[3 * r + 0] * R[0 + col] + K[3 * r + 1] * R[3 + col] + K[3 * r + 2] * R[6 + col];
+            xc[r] = R[3 * r + 0] * centre[0] + R[3 * r + 1] * centre[1] + R[3 * r + 2] * centre[2] + t[r];
+        }
+        for (int r = 0; r < 3; ++r) {
+            for (int col = 0; col < 3; ++col) f.cam[c].m[4 * r + col] = (float)(KR[3 * r + col] * vs);
+            f.cam[c].m[4 * r + 3] = (float)(K[3 * r + 0] * xc[0] + K[3 * r + 1] * xc[1] + K[3 * r + 2] * xc[2]);
+        }
+    }
+    f.logit_prior = (float)std::log(params.prior / (1.0 - params.prior));
+    f.logit_tau = (float)std::log(params.threshold / (1.0 - params.threshold));
+
+    const int ntx = (grid.nx + 31) / 32, nty = (grid.ny + FUSE_WY - 1) / FUSE_WY,
+              ntz = (grid.nz + FUSE_TZ - 1) / FUSE_TZ;
+    std::vector<std::pair<uint64_t, uint64_t>> order;
+    order.reserve((size_t)ntx * nty * ntz);
+    for (int z = 0; z < ntz; ++z)
+        for (int y = 0; y < nty; ++y)
+            for (int x = 0; x < ntx; ++x)
+                order.emplace_back(spread3(x) | (spread3(y) << 1) | (spread3(z) << 2), pack_tile(x, y, z));
+    std::sort(order.begin(), order.end());
+    tiles_out->resize(order.size());
+    for (size_t n = 0; n < order.size(); ++n) (*tiles_out)[n] = order[n].second;
+    f.n_tiles = (int)tiles_out->size();
+    f.smem_cap = fuse_smem_cap(params.map_dtype);
+    const int elem = params.map_dtype == PSFS_MAP_F32 ? 4 : 2;
+    build_tilecam(grid, cams, n_cams, f, *tiles_out, elem, f.smem_cap, *tilecam_out);
+}
+
+}  // namespace psfs

@@ -1,0 +1,51 @@
+// Host-only test driver: runs the fuse planner of libpsfs (psfs_plan.cu) on a
+// grid and camera rig read from a text file and prints the projection
+// matrices and every (tile, camera) staging record, so that a test can check
+// the records against the voxel projections without a GPU.
+//
+// input:  nx ny nz ox oy oz voxel_size n_cams map_dtype
+//         then per camera: width height K[9] R[9] t[3]
+// output: n_cams lines of 12 matrix entries, then per record
+//         "tile c x y w h_and_flags"
+#include <cstdio>
+#include <vector>
+
+#include "psfs_internal.cuh"
+
+int main(int argc, char **argv)
+{
+    if (argc < 2) return 2;
+    FILE *f = std::fopen(argv[1], "r");
+    if (!f) return 2;
+    psfs_grid g;
+    int n = 0, map_dtype = 0;
+    if (std::fscanf(f, "%d %d %d %lf %lf %lf %lf %d %d", &g.nx, &g.ny, &g.nz, &g.origin[0], &g.origin[1],
+                    &g.origin[2], &g.voxel_size, &n, &map_dtype) != 9)
+        return 2;
+    std::vector<psfs_camera> cams(n);
+    for (int c = 0; c < n; ++c) {
+        if (std::fscanf(f, "%d %d", &cams[c].width, &cams[c].height) != 2) return 2;
+        for (int q = 0; q < 9; ++q) std::fscanf(f, "%lf", &cams[c].K[q]);
+        for (int q = 0; q < 9; ++q) std::fscanf(f, "%lf", &cams[c].R[q]);
+        for (int q = 0; q < 3; ++q) std::fscanf(f, "%lf", &cams[c].t[q]);
+    }
+    std::fclose(f);
+    psfs_params p;
+    psfs_params_default(&p);
+    p.map_dtype = map_dtype;
+    psfs::FuseArgs fa;
+    std::vector<uint64_t> tiles;
+    std::vector<int4> rec;
+    psfs::plan_fuse(g, cams.data(), n, p, &fa, &tiles, &rec);
+    std::printf("%d %d %d\n", psfs::FUSE_WY, psfs::FUSE_TZ, fa.smem_cap);
+    for (int c = 0; c < n; ++c) {
+        for (int q = 0; q < 12; ++q) std::printf("%.9g ", fa.cam[c].m[q]);
+        std::printf("\n");
+    }
+    for (size_t t = 0; t < tiles.size(); ++t)
+        for (int c = 0; c < n; ++c) {
+            const int4 r = rec[t * n + c];
+            std::printf("%llu %d %d %d %d %d\n", (unsigned long long)tiles[t], c, r.x, r.y, r.z, r.w);
+        }
+    return 0;
+}
