@@ -6,15 +6,16 @@
 // Work decomposition.  A CTA owns a tile of 32 (x) x WY (y) x TZ (z) voxels:
 // each warp is one run of 32 voxels along x (128-byte occupancy stores) and
 // each thread walks TZ voxels along z, sharing the x/y part of the
-// projection.  CTAs are issued in Morton order of their tiles.
+// projection.  CTAs are issued in Morton order of their tiles, so that
+// neighbouring CTAs gather from neighbouring parts of the (L2-resident) maps.
 //
-// Gather.  For each camera the CTA copies the image box that its voxel
-// centres project into (computed on the host per tile and camera, 16-byte
-// aligned rows) from the L2-resident map into shared memory with cp.async,
-// then every voxel reads its pixel from shared memory.  A box that does not
-// fit the buffer falls back to gathers from global memory.  When the host
-// has proven that every voxel centre of the tile is in front of the camera
-// and inside the image, the per-voxel visibility test is skipped.
+// Gather.  The instruction stream per voxel and camera is kept minimal:
+// three fma for (u, v, w), one approximate reciprocal, two fma with
+// round-down that floor u / w and v / w into biased integers, one integer
+// multiply-add for the pixel offset, one load, one add.  The host proves per
+// (tile, camera) when every voxel centre is in front of the camera and inside
+// the image; only the other tiles pay for the visibility test, and cameras
+// that see nothing of a tile are skipped.
 //
 // Compaction: per warp a ballot per z step, per CTA one atomicAdd on the
 // global count, then each warp writes its indices at its prefix offset.
@@ -24,40 +25,18 @@ namespace psfs {
 
 namespace {
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-template <typename T>
-__device__ __forceinline__ float smem_load(const T *p);
-template <>
-__device__ __forceinline__ float smem_load<float>(const float *p) { return *p; }
-template <>
-__device__ __forceinline__ float smem_load<__half>(const __half *p) { return __half2float(*p); }
-template <>
-__device__ __forceinline__ float smem_load<__nv_bfloat16>(const __nv_bfloat16 *p)
-{
-    return __bfloat162float(*p);
-}
-
 template <typename MapT, int WY, int TZ>
 __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ FuseArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    MapT *sbuf = reinterpret_cast<MapT *>(smem_raw);
+    __shared__ int s_flags[PSFS_MAX_CAMS];
     __shared__ uint32_t s_warp_off[WY];
     __shared__ uint32_t s_base;
 
     const int lane = threadIdx.x;
     const int wy = threadIdx.y;
     const int tid = wy * 32 + lane;
+    if (tid < a.n_cams) s_flags[tid] = __ldg(&a.tilecam[(int64_t)blockIdx.x * a.n_cams + tid].w) >> 16;
+
     const uint64_t tc = a.tiles[blockIdx.x];
     const int tx = (int)(tc & 0x1FFFFFu);
     const int ty = (int)((tc >> 21) & 0x1FFFFFu);
@@ -66,12 +45,14 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
     const int j = ty * WY + wy;
     const int k0 = tz * TZ;
     // Lanes past the grid edge (ragged tiles) project the nearest voxel of the
-    // grid instead, so every projection stays inside the tile's staged box;
-    // their results are discarded below.
+    // grid instead, so that the host's per-tile proofs cover them; their
+    // results are discarded below.
     const float fi = (float)min(i, a.nx - 1) - a.ci;
     const float fj = (float)min(j, a.ny - 1) - a.cj;
     const uint32_t W = (uint32_t)a.W, H = (uint32_t)a.H;
-    constexpr int kChunk = 16 / (int)sizeof(MapT);   // elements per 16-byte copy
+    const uint32_t last_pix = W * H - 1u;
+    // pixel offset from biased coordinates: (by - B) W + (bx - B) = by W + bx + bias_off (mod 2^32)
+    const uint32_t bias_off = 0u - (kFloorBias * W + kFloorBias);
 
     float fk[TZ];
     float L[TZ];
@@ -80,44 +61,24 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
         fk[t] = (float)min(k0 + t, a.nz - 1) - a.ck;
         L[t] = 0.0f;
     }
+    __syncthreads();
 
     const MapT *maps = reinterpret_cast<const MapT *>(a.maps);
-    const int4 *tcrec = a.tilecam + (int64_t)blockIdx.x * a.n_cams;
     for (int c = 0; c < a.n_cams; ++c) {
-        const int4 rec = __ldg(tcrec + c);
-        const int flags = rec.w >> 16;
+        const int flags = s_flags[c];
         if (flags & kTcSkip) continue;
-        const float *m = a.cam[c].m;
+        float m[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
         const MapT *map = maps + (int64_t)c * a.map_stride;
         float bu, bv, bw;
         project_base(m, fi, fj, &bu, &bv, &bw);
-        if (flags & kTcStaged) {
-            const int bx0 = rec.x, by0 = rec.y, sw = rec.z, sh = rec.w & 0xFFFF;
-            __syncthreads();   // the previous camera's gathers are done with the buffer
-            const MapT *src = map + (int64_t)by0 * W + bx0;
-            const int row_chunks = sw / kChunk;
-            for (int r = wy; r < sh; r += WY)
-                for (int q = lane; q < row_chunks; q += 32)
-                    cp_async16(sbuf + r * sw + q * kChunk, src + (int64_t)r * W + q * kChunk);
-            cp_async_wait_all();
-            __syncthreads();
-            const uint32_t ox = kFloorBias + (uint32_t)bx0, oy = kFloorBias + (uint32_t)by0;
-            if (flags & kTcInside) {
-                // the host proved every centre of the tile lands in the box; the
-                // min() only keeps a violated proof from leaving the buffer
-                const uint32_t last = (uint32_t)(sw * sh - 1);
+        if (flags & kTcInside) {
 #pragma unroll
-                for (int t = 0; t < TZ; ++t) {
-                    const Proj p = project_biased(m, bu, bv, bw, fk[t]);
-                    L[t] += smem_load<MapT>(sbuf + min((p.by - oy) * (uint32_t)sw + (p.bx - ox), last));
-                }
-            } else {
-#pragma unroll
-                for (int t = 0; t < TZ; ++t) {
-                    const Proj p = project_biased(m, bu, bv, bw, fk[t]);
-                    const uint32_t sx = p.bx - ox, sy = p.by - oy;
-                    if ((sx < (uint32_t)sw) & (sy < (uint32_t)sh)) L[t] += smem_load<MapT>(sbuf + sy * (uint32_t)sw + sx);
-                }
+            for (int t = 0; t < TZ; ++t) {
+                const Proj p = project_biased(m, bu, bv, bw, fk[t]);
+                // the host proved the pixel lies in the image; min() only guards the buffer
+                L[t] += map_load<MapT>(map + min(p.by * W + p.bx + bias_off, last_pix));
             }
         } else {
 #pragma unroll
@@ -127,7 +88,6 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
             }
         }
     }
-    (void)tid;
 
     // posterior, threshold, compaction
     const bool in_xy = (i < a.nx) && (j < a.ny);
@@ -147,7 +107,7 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
     }
     if (lane == 0) s_warp_off[wy] = warp_count;
     __syncthreads();
-    if (wy == 0 && lane == 0) {
+    if (tid == 0) {
         uint32_t total = 0;
 #pragma unroll
         for (int w = 0; w < WY; ++w) {
@@ -179,31 +139,19 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
     }
 }
 
-template <typename MapT>
-cudaError_t launch_typed(const FuseArgs &a, cudaStream_t s)
-{
-    auto kern = fuse_kernel<MapT, FUSE_WY, FUSE_TZ>;
-    const int smem = a.smem_cap * (int)sizeof(MapT);
-    static bool configured[64] = {false};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !configured[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSE_SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        configured[dev] = true;
-    }
-    kern<<<a.n_tiles, dim3(32, FUSE_WY), smem, s>>>(a);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t launch_fuse(const FuseArgs &a, int map_dtype, cudaStream_t s)
 {
     if (a.n_tiles <= 0) return cudaSuccess;
-    if (map_dtype == PSFS_MAP_F16) return launch_typed<__half>(a, s);
-    if (map_dtype == PSFS_MAP_BF16) return launch_typed<__nv_bfloat16>(a, s);
-    return launch_typed<float>(a, s);
+    const dim3 block(32, FUSE_WY);
+    if (map_dtype == PSFS_MAP_F16)
+        fuse_kernel<__half, FUSE_WY, FUSE_TZ><<<a.n_tiles, block, 0, s>>>(a);
+    else if (map_dtype == PSFS_MAP_BF16)
+        fuse_kernel<__nv_bfloat16, FUSE_WY, FUSE_TZ><<<a.n_tiles, block, 0, s>>>(a);
+    else
+        fuse_kernel<float, FUSE_WY, FUSE_TZ><<<a.n_tiles, block, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace psfs

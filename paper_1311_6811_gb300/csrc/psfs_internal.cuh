@@ -55,6 +55,7 @@ struct LikelihoodArgs {
     SensorConsts sc;
     void *out;                // [n_pix] map of g (f32 / f16 / bf16) or of s (f32)
     uint32_t *zero_word;      // if non-null, set to 0 by one thread
+    uint32_t *status;         // device status word (bounded-wait timeouts)
 };
 
 struct SlmToMapArgs {
@@ -67,14 +68,12 @@ struct SlmToMapArgs {
 };
 
 // Per (tile, camera) record prepared on the host at handle creation, in
-// double precision from the 8 corner voxel centres of the tile:
-//   x, y   first staged column (rounded down to a 16-byte boundary) and row
-//   bw     staged width in elements (a whole number of 16-byte chunks)
-//   bhf    staged height in rows | flags << 16
-// The staged box covers the projections of every voxel centre of the tile
-// that the camera sees (1 px margin), clipped to the image.
-constexpr int kTcStaged = 1;   // box fits the shared-memory buffer: gather from it
-constexpr int kTcInside = 2;   // every voxel centre is in front and inside the image
+// double precision from the 8 corner voxel centres of the tile (int4):
+//   x, y, z   unused (reserved for a staged image box)
+//   w         flags << 16
+constexpr int kTcInside = 2;   // every voxel centre of the tile is in front of the
+                               // camera and inside the image, with margin for the
+                               // float32 rounding of the kernel
 constexpr int kTcSkip = 4;     // the camera sees no voxel centre of the tile
 
 struct FuseArgs {
@@ -85,9 +84,8 @@ struct FuseArgs {
     int nx, ny, nz;
     float ci, cj, ck;         // (n - 1) / 2 per axis
     const uint64_t *tiles;    // packed tile coordinates, Morton order
-    const int4 *tilecam;      // [n_tiles][n_cams] staging records
+    const int4 *tilecam;      // [n_tiles][n_cams] records
     int n_tiles;
-    int smem_cap;             // elements of the staging buffer
     float logit_prior, logit_tau;
     float *occ;               // [nz][ny][nx]
     uint32_t *list;
@@ -99,9 +97,8 @@ struct FuseArgs {
 
 // Tile shape of the fuse kernel: 32 voxels along x (one warp), FUSE_WY warps
 // along y, FUSE_TZ voxels along z per thread.
-constexpr int FUSE_WY = 8;
-constexpr int FUSE_TZ = 8;
-constexpr int FUSE_SMEM_BYTES = 48 * 1024;
+constexpr int FUSE_WY = 4;
+constexpr int FUSE_TZ = 16;
 
 __host__ __device__ inline uint64_t pack_tile(uint32_t tx, uint32_t ty, uint32_t tz)
 {
@@ -178,6 +175,82 @@ __device__ __forceinline__ bool project_voxel(const float *m, float fi, float fj
     return proj_pixel(project_biased(m, bu, bv, bw, fk), W, H, pix);
 }
 
+// ---------------------------------------------------------------------------
+// mbarrier + bulk-copy (TMA) helpers, inline PTX for sm_90+ / sm_103a
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// One bulk copy global -> shared, completion counted on `bar` (bytes and both
+// addresses multiples of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of `bar`.  After kWaitNs of polling it
+// records kStatusTimeout, waits once more up to kWaitNs for the copies still
+// in flight, and returns false.  Callers then carry on with whatever the
+// buffer holds, so that every thread still reaches every barrier; the status
+// word marks the result invalid.
+constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t *status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        for (int n = 0; n < 64; ++n)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitNs) break;
+    }
+    if (status) atomicOr(status, kStatusTimeout);
+    const uint64_t t1 = globaltimer_ns();
+    while (globaltimer_ns() - t1 < kWaitNs)
+        if (mbar_try_wait(bar, parity)) break;
+    return false;
+}
+
 template <typename T>
 __device__ __forceinline__ float map_load(const T *p);
 template <>
@@ -191,11 +264,14 @@ __device__ __forceinline__ float map_load<__nv_bfloat16>(const __nv_bfloat16 *p)
 }
 
 // g(r) = log(P_D e^r + 1 - P_D) - log(q e^r + 1 - q), evaluated with
-// e^-|r| only, so it neither overflows nor loses the constant terms.
+// e^-|r| only, so it neither overflows nor loses the constant terms.  The
+// hardware approximations (ex2 / lg2 / rcp) keep the absolute error of g near
+// 2e-7: A / B stays bounded away from 0 and infinity unless P_D
+// is 0 or 1, which takes the branch without the ratio.
 __device__ __forceinline__ float log_ratio_of_r(float r, const SensorConsts &c)
 {
     float ar = fabsf(r);
-    float u = expf(-ar);
+    float u = __expf(-ar);
     float A, B;
     bool deg;
     if (r > 0.0f) {   // divide both by e^r
@@ -207,8 +283,8 @@ __device__ __forceinline__ float log_ratio_of_r(float r, const SensorConsts &c)
         B = fmaf(c.q, u, c.one_minus_q);
         deg = c.a_zero_const_neg;
     }
-    if (deg) return -ar - logf(B);   // A = e^-|r| exactly
-    return logf(A / B);
+    if (deg) return -ar - __logf(B);   // A = e^-|r| exactly
+    return __logf(__fdividef(A, B));
 }
 
 // ---------------------------------------------------------------------------
@@ -221,7 +297,6 @@ cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_o
                               cudaStream_t s);
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, int map_dtype, cudaStream_t s);
-int fuse_smem_cap(int map_dtype);
 
 // Host planning (psfs_plan.cu): projection matrices, tile order and staging
 // records of the fuse kernel for one grid and camera rig.

@@ -2,9 +2,14 @@
 // the per-camera log ratio of Eq. 5-9), plus the background packing kernel.
 //
 // Streaming, HBM-bound: per pixel 3 B of image + 24 B of packed background in,
-// 4 B (f32) or 2 B (f16/bf16) of map out.  One thread handles 4 consecutive
-// pixels: 12 image bytes as three 32-bit loads, 12 means and 12 inverse
-// variances as three 128-bit loads each, and one 128-bit (or 64-bit) store.
+// 4 B (f32) or 2 B (f16/bf16) of map out.  A persistent grid (two CTAs per
+// SM) walks 512-pixel chunks; one thread per CTA streams each chunk's image
+// bytes, means and inverse variances into shared memory with bulk copies
+// (TMA) through a four-stage mbarrier ring, so that about 110 KB per SM are
+// in flight independently of registers, while all threads compute from the
+// previous stages and write the map with coalesced stores.
+#include <algorithm>
+
 #include "psfs_internal.cuh"
 
 namespace psfs {
@@ -25,13 +30,6 @@ int sm_count()
     return cached[dev];
 }
 
-// Exact float of byte `sel` of w: build the bit pattern 0x4B0000bb (2^23 + b)
-// with one byte permute, then subtract 2^23.
-__device__ __forceinline__ float byte_to_float(uint32_t w, uint32_t sel)
-{
-    return __uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - 8388608.0f;
-}
-
 // r = log U - log N (Eq. 1) for one pixel, from its colour, mean and
 // h = 1 / (2 var):  r = c0 - 0.5 log(h0 h1 h2) + sum_c (I_c - mu_c)^2 h_c.
 __device__ __forceinline__ float pixel_log_odds(float i0, float i1, float i2, float m0, float m1,
@@ -39,44 +37,14 @@ __device__ __forceinline__ float pixel_log_odds(float i0, float i1, float i2, fl
 {
     float d0 = i0 - m0, d1 = i1 - m1, d2 = i2 - m2;
     float quad = fmaf(d0 * d0, h0, fmaf(d1 * d1, h1, d2 * d2 * h2));
-    return (c0 - 0.5f * logf(h0 * h1 * h2)) + quad;
+    return (c0 - 0.5f * __logf(h0 * h1 * h2)) + quad;
 }
 
 __device__ __forceinline__ float sigmoid(float r)
 {
-    if (r > 0.0f) return 1.0f / (1.0f + expf(-r));
-    float e = expf(r);
-    return e / (1.0f + e);
-}
-
-template <typename OutT>
-__device__ __forceinline__ void store4(OutT *out, int64_t q, float a, float b, float c, float d);
-
-template <>
-__device__ __forceinline__ void store4<float>(float *out, int64_t q, float a, float b, float c, float d)
-{
-    reinterpret_cast<float4 *>(out)[q] = make_float4(a, b, c, d);
-}
-
-template <>
-__device__ __forceinline__ void store4<__half>(__half *out, int64_t q, float a, float b, float c, float d)
-{
-    __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
-    uint2 v;
-    v.x = *reinterpret_cast<uint32_t *>(&lo);
-    v.y = *reinterpret_cast<uint32_t *>(&hi);
-    reinterpret_cast<uint2 *>(out)[q] = v;
-}
-
-template <>
-__device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16 *out, int64_t q, float a, float b,
-                                                      float c, float d)
-{
-    __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
-    uint2 v;
-    v.x = *reinterpret_cast<uint32_t *>(&lo);
-    v.y = *reinterpret_cast<uint32_t *>(&hi);
-    reinterpret_cast<uint2 *>(out)[q] = v;
+    if (r > 0.0f) return __fdividef(1.0f, 1.0f + __expf(-r));
+    const float e = __expf(r);
+    return __fdividef(e, 1.0f + e);
 }
 
 template <typename OutT>
@@ -91,46 +59,80 @@ __device__ __forceinline__ void store1<__nv_bfloat16>(__nv_bfloat16 *out, int64_
     out[p] = __float2bfloat16_rn(a);
 }
 
+constexpr int kLkChunk = 512;                       // pixels per chunk (multiple of 16)
+constexpr int kLkStages = 4;
+constexpr int kLkThreads = 256;
+constexpr int kLkImgBytes = 3 * kLkChunk;             // 1536
+constexpr int kLkBgBytes = 12 * kLkChunk;             // 6144 (3 floats per pixel)
+constexpr int kLkStageBytes = kLkImgBytes + 2 * kLkBgBytes;
+constexpr int kLkSmemBytes = kLkStages * kLkStageBytes + kLkStages * 8;
+
 template <typename OutT, bool kSlm>
-__global__ void __launch_bounds__(256) likelihood_kernel(const LikelihoodArgs a)
+__device__ __forceinline__ void likelihood_pixel(const LikelihoodArgs &a, OutT *out, int64_t p, float i0,
+                                                 float i1, float i2, const float *m, const float *h)
 {
-    if (a.zero_word && blockIdx.x == 0 && threadIdx.x == 0) *a.zero_word = 0u;
+    const float r = pixel_log_odds(i0, i1, i2, m[0], m[1], m[2], h[0], h[1], h[2], a.c0);
+    store1<OutT>(out, p, kSlm ? sigmoid(r) : log_ratio_of_r(r, a.sc));
+}
+
+// n_tma_pix = n_pix rounded down to 16 pixels (48 image bytes), so every
+// bulk copy has a size and offsets that are multiples of 16 bytes; the last
+// < 16 pixels are read with plain loads by CTA 0.
+template <typename OutT, bool kSlm>
+__global__ void __launch_bounds__(kLkThreads) likelihood_kernel(const LikelihoodArgs a, int64_t n_tma_pix)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kLkStages * kLkStageBytes);
     OutT *out = reinterpret_cast<OutT *>(a.out);
-    const int64_t n_quads = a.n_pix >> 2;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t *img = reinterpret_cast<const uint32_t *>(a.img);
-    const float4 *mean = reinterpret_cast<const float4 *>(a.mean);
-    const float4 *hinv = reinterpret_cast<const float4 *>(a.hinv);
-    for (int64_t q = tid; q < n_quads; q += stride) {
-        uint32_t w0 = __ldcs(img + 3 * q), w1 = __ldcs(img + 3 * q + 1), w2 = __ldcs(img + 3 * q + 2);
-        float4 ma = __ldg(mean + 3 * q), mb = __ldg(mean + 3 * q + 1), mc = __ldg(mean + 3 * q + 2);
-        float4 ha = __ldg(hinv + 3 * q), hb = __ldg(hinv + 3 * q + 1), hc = __ldg(hinv + 3 * q + 2);
-        // channel c of pixel p sits at position 3 p + c of the 12 values
-        float r0 = pixel_log_odds(byte_to_float(w0, 0x7440), byte_to_float(w0, 0x7441),
-                                  byte_to_float(w0, 0x7442), ma.x, ma.y, ma.z, ha.x, ha.y, ha.z, a.c0);
-        float r1 = pixel_log_odds(byte_to_float(w0, 0x7443), byte_to_float(w1, 0x7440),
-                                  byte_to_float(w1, 0x7441), ma.w, mb.x, mb.y, ha.w, hb.x, hb.y, a.c0);
-        float r2 = pixel_log_odds(byte_to_float(w1, 0x7442), byte_to_float(w1, 0x7443),
-                                  byte_to_float(w2, 0x7440), mb.z, mb.w, mc.x, hb.z, hb.w, hc.x, a.c0);
-        float r3 = pixel_log_odds(byte_to_float(w2, 0x7441), byte_to_float(w2, 0x7442),
-                                  byte_to_float(w2, 0x7443), mc.y, mc.z, mc.w, hc.y, hc.z, hc.w, a.c0);
-        if (kSlm) {
-            store4<OutT>(out, q, sigmoid(r0), sigmoid(r1), sigmoid(r2), sigmoid(r3));
-        } else {
-            store4<OutT>(out, q, log_ratio_of_r(r0, a.sc), log_ratio_of_r(r1, a.sc),
-                         log_ratio_of_r(r2, a.sc), log_ratio_of_r(r3, a.sc));
-        }
+    const int tid = threadIdx.x;
+    if (a.zero_word && blockIdx.x == 0 && tid == 0) *a.zero_word = 0u;
+    if (tid == 0) {
+        for (int s = 0; s < kLkStages; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
     }
-    // ragged tail (n_pix not a multiple of 4): scalar loads
-    const int64_t rem = a.n_pix - 4 * n_quads;
-    if (tid < rem) {
-        const int64_t p = 4 * n_quads + tid;
-        const float *m = a.mean + 3 * p, *hh = a.hinv + 3 * p;
-        const uint8_t *im = a.img + 3 * p;
-        float r = pixel_log_odds((float)im[0], (float)im[1], (float)im[2], m[0], m[1], m[2], hh[0],
-                                 hh[1], hh[2], a.c0);
-        store1<OutT>(out, p, kSlm ? sigmoid(r) : log_ratio_of_r(r, a.sc));
+    __syncthreads();
+
+    const int64_t n_chunks = (n_tma_pix + kLkChunk - 1) / kLkChunk;
+    const int64_t my_chunks =
+        (int64_t)blockIdx.x < n_chunks ? (n_chunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto stage_img = [&](int s) { return smem + s * kLkStageBytes; };
+    auto stage_mean = [&](int s) { return reinterpret_cast<float *>(smem + s * kLkStageBytes + kLkImgBytes); };
+    auto stage_hinv = [&](int s) {
+        return reinterpret_cast<float *>(smem + s * kLkStageBytes + kLkImgBytes + kLkBgBytes);
+    };
+    auto issue = [&](int64_t k) {
+        const int s = (int)(k % kLkStages);
+        const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kLkChunk;
+        const uint32_t np = (uint32_t)min((int64_t)kLkChunk, n_tma_pix - p0);
+        mbar_arrive_expect_tx(&bars[s], 27u * np);
+        bulk_g2s(stage_img(s), a.img + 3 * p0, 3u * np, &bars[s]);
+        bulk_g2s(stage_mean(s), a.mean + 3 * p0, 12u * np, &bars[s]);
+        bulk_g2s(stage_hinv(s), a.hinv + 3 * p0, 12u * np, &bars[s]);
+    };
+    if (tid == 0)
+        for (int64_t k = 0; k < my_chunks && k < kLkStages; ++k) issue(k);
+
+    for (int64_t k = 0; k < my_chunks; ++k) {
+        const int s = (int)(k % kLkStages);
+        mbar_wait_bounded(&bars[s], (uint32_t)((k / kLkStages) & 1), a.status);
+        const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kLkChunk;
+        const int np = (int)min((int64_t)kLkChunk, n_tma_pix - p0);
+        const unsigned char *im = stage_img(s);
+        const float *mu = stage_mean(s);
+        const float *hv = stage_hinv(s);
+        for (int q = tid; q < np; q += kLkThreads)
+            likelihood_pixel<OutT, kSlm>(a, out, p0 + q, (float)im[3 * q], (float)im[3 * q + 1],
+                                         (float)im[3 * q + 2], mu + 3 * q, hv + 3 * q);
+        __syncthreads();   // every thread is done with stage s before it is refilled
+        if (tid == 0 && k + kLkStages < my_chunks) issue(k + kLkStages);
+    }
+
+    if (blockIdx.x == 0) {
+        for (int64_t p = n_tma_pix + tid; p < a.n_pix; p += kLkThreads) {
+            const uint8_t *im = a.img + 3 * p;
+            likelihood_pixel<OutT, kSlm>(a, out, p, (float)im[0], (float)im[1], (float)im[2], a.mean + 3 * p,
+                                         a.hinv + 3 * p);
+        }
     }
 }
 
@@ -175,6 +177,26 @@ int grid_for(int64_t work, int threads)
     return (int)blocks;
 }
 
+template <typename OutT, bool kSlm>
+cudaError_t launch_likelihood_typed(const LikelihoodArgs &a, cudaStream_t s)
+{
+    auto kern = likelihood_kernel<OutT, kSlm>;
+    static bool configured[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kLkSmemBytes);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    const int64_t n_tma_pix = a.n_pix / 16 * 16;
+    const int64_t n_chunks = (n_tma_pix + kLkChunk - 1) / kLkChunk;
+    int64_t blocks = std::min<int64_t>(n_chunks, 2 * (int64_t)sm_count());
+    if (blocks < 1) blocks = 1;
+    kern<<<(int)blocks, kLkThreads, kLkSmemBytes, s>>>(a, n_tma_pix);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_pack_background(const float *mean, const float *var, int64_t n_pix,
@@ -187,18 +209,10 @@ cudaError_t launch_pack_background(const float *mean, const float *var, int64_t 
 
 cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_out, cudaStream_t s)
 {
-    const int64_t work = (a.n_pix >> 2) > 0 ? (a.n_pix >> 2) : 1;
-    const int blocks = grid_for(work, 256);
-    if (slm_out) {
-        likelihood_kernel<float, true><<<blocks, 256, 0, s>>>(a);
-    } else if (map_dtype == PSFS_MAP_F16) {
-        likelihood_kernel<__half, false><<<blocks, 256, 0, s>>>(a);
-    } else if (map_dtype == PSFS_MAP_BF16) {
-        likelihood_kernel<__nv_bfloat16, false><<<blocks, 256, 0, s>>>(a);
-    } else {
-        likelihood_kernel<float, false><<<blocks, 256, 0, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (slm_out) return launch_likelihood_typed<float, true>(a, s);
+    if (map_dtype == PSFS_MAP_F16) return launch_likelihood_typed<__half, false>(a, s);
+    if (map_dtype == PSFS_MAP_BF16) return launch_likelihood_typed<__nv_bfloat16, false>(a, s);
+    return launch_likelihood_typed<float, false>(a, s);
 }
 
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s)

@@ -2,8 +2,8 @@
 // camera rig, done once at handle creation in double precision:
 //   * the 3x4 projection matrix of every camera in centred voxel-index space;
 //   * the voxel tiles in Morton order;
-//   * per (tile, camera) the staging record (shared-memory box, fast-path
-//     flags) that the fuse kernel reads.
+//   * per (tile, camera) the record (skip / inside flags) that the fuse
+//     kernel reads.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -28,18 +28,15 @@ uint64_t spread3(uint64_t x)
     return x;
 }
 
-// Staging records of every (tile, camera) pair; see FuseArgs in
-// psfs_internal.cuh.  Everything here is double precision on the host; the
-// fast paths it enables are taken only where a bound on the float32
-// projection error of the kernels stays below a quarter pixel, well inside
-// the one-pixel margin of each box.
+// Records of every (tile, camera) pair; see FuseArgs in psfs_internal.cuh.
+// Everything here is double precision on the host.  A tile is marked
+// "inside" (no per-voxel test in the kernel) or "skip" (camera ignored) only
+// where a bound on the float32 projection error of the kernel stays below a
+// quarter pixel, well inside the one-pixel margin each decision keeps.
 void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, const FuseArgs &f,
-                   const std::vector<uint64_t> &tiles, int elem_bytes, int cap_elems,
-                   std::vector<int4> &out)
+                   const std::vector<uint64_t> &tiles, std::vector<int4> &out)
 {
     const int W = cams[0].width, H = cams[0].height;
-    const int chunk = 16 / elem_bytes;
-    const bool can_stage = ((int64_t)W * elem_bytes) % 16 == 0;
     const double vs = g.voxel_size;
     const double eps32 = std::ldexp(1.0, -24);
     // per camera: magnitude bounds of the float32 projection sums
@@ -104,24 +101,12 @@ void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, cons
                 rec.w = kTcSkip << 16;
                 continue;
             }
-            if (!can_stage) continue;
-            const int64_t ax0 = cx0 / chunk * chunk, ax1 = (cx1 + chunk - 1) / chunk * chunk;
-            const int64_t sw = ax1 - ax0, sh = cy1 - cy0;
-            if (sw * sh > cap_elems) continue;
-            rec.x = (int)ax0;
-            rec.y = (int)cy0;
-            rec.z = (int)sw;
-            rec.w = (int)sh | ((kTcStaged | (inside ? kTcInside : 0)) << 16);
+            if (inside) rec.w = kTcInside << 16;
         }
     }
 }
 
 }  // namespace
-
-int fuse_smem_cap(int map_dtype)
-{
-    return FUSE_SMEM_BYTES / (map_dtype == PSFS_MAP_F32 ? 4 : 2);
-}
 
 void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const psfs_params &params,
                FuseArgs *out, std::vector<uint64_t> *tiles_out, std::vector<int4> *tilecam_out)
@@ -171,9 +156,8 @@ void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const
     tiles_out->resize(order.size());
     for (size_t n = 0; n < order.size(); ++n) (*tiles_out)[n] = order[n].second;
     f.n_tiles = (int)tiles_out->size();
-    f.smem_cap = fuse_smem_cap(params.map_dtype);
-    const int elem = params.map_dtype == PSFS_MAP_F32 ? 4 : 2;
-    build_tilecam(grid, cams, n_cams, f, *tiles_out, elem, f.smem_cap, *tilecam_out);
+    (void)params;
+    build_tilecam(grid, cams, n_cams, f, *tiles_out, *tilecam_out);
 }
 
 }  // namespace psfs

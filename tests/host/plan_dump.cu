@@ -1,12 +1,12 @@
 // Host-only test driver: runs the fuse planner of libpsfs (psfs_plan.cu) on a
 // grid and camera rig read from a text file and prints the projection
-// matrices and every (tile, camera) staging record, so that a test can check
-// the records against the voxel projections without a GPU.
+// matrices and every (tile, camera) record, so that a test can check the
+// records against the voxel projections without a GPU.
 //
 // input:  nx ny nz ox oy oz voxel_size n_cams map_dtype
 //         then per camera: width height K[9] R[9] t[3]
-// output: n_cams lines of 12 matrix entries, then per record
-//         "tile c x y w h_and_flags"
+// output: "WY TZ", n_cams lines of 12 matrix entries, then per record
+//         "tile c x y z w" (flags in the high half of w)
 #include <cstdio>
 #include <vector>
 
@@ -37,7 +37,7 @@ int main(int argc, char **argv)
     std::vector<uint64_t> tiles;
     std::vector<int4> rec;
     psfs::plan_fuse(g, cams.data(), n, p, &fa, &tiles, &rec);
-    std::printf("%d %d %d\n", psfs::FUSE_WY, psfs::FUSE_TZ, fa.smem_cap);
+    std::printf("%d %d\n", psfs::FUSE_WY, psfs::FUSE_TZ);
     for (int c = 0; c < n; ++c) {
         for (int q = 0; q < 12; ++q) std::printf("%.9g ", fa.cam[c].m[q]);
         std::printf("\n");
