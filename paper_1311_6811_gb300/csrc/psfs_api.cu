@@ -343,6 +343,7 @@ static psfs_status enqueue_reconstruct(psfs_handle *h, const uint8_t *images, fl
     la.sc = h->sc;
     la.out = h->maps;
     la.zero_word = count;
+    la.status = h->d_words;
     {
         ProfScope ps(h, PSFS_STAGE_LIKELIHOOD);
         PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, h->stream));
@@ -462,6 +463,7 @@ psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *sl
     la.sc = h->sc;
     la.out = slm_out;
     la.zero_word = nullptr;
+    la.status = h->d_words;
     PSFS_CK(launch_likelihood(la, PSFS_MAP_F32, true, h->stream));
     return PSFS_OK;
 }
