@@ -285,6 +285,8 @@ def run_ours(args):
         rec.set_background(torch.from_numpy(sc.mean).to(dev), torch.from_numpy(sc.var).to(dev))
     stream.synchronize()
     h = rec.handle
+    # autotuner: pick the fuse tile shape on the first frame (setup, untimed)
+    fuse_cfg = psfs.psfs_autotune(h, d_images[0], reps=3)
 
     def step():
         for f in range(F):
@@ -385,7 +387,8 @@ def run_ours(args):
                            "frames_per_s": F * args.steps * ws / (ms * 1e-3),
                            "occupied_voxels_per_frame": mean_count,
                            "l2": f"inputs larger than L2: {F * n_pix * 3 / 1e6:.0f} MB of images per step",
-                           "parallelism": f"replicas x{ws} (frames independent)"},
+                           "parallelism": f"replicas x{ws} (frames independent)",
+                           "fuse_tile": {"lanes_x": fuse_cfg[0], "warps": fuse_cfg[1], "voxels_z": fuse_cfg[2]}},
                 "stages": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(v["launches"] for v in stages.values()), "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -102,6 +102,17 @@ typedef struct {
     int32_t map_dtype;      /* psfs_map_dtype of the stored likelihood maps        */
 } psfs_params;
 
+/* Shape of the voxel tile one CTA of the fusion kernel owns: a warp covers
+ * lanes_x voxels along x by 32 / lanes_x along y, a CTA `warps` warps stacked
+ * along y, and each thread walks voxels_z voxels along z.  Supported:
+ * lanes_x in {8, 16, 32}, warps = 4, voxels_z in {8, 16}.  The shape changes
+ * speed only, never results. */
+typedef struct {
+    int32_t lanes_x;
+    int32_t warps;
+    int32_t voxels_z;
+} psfs_fuse_config;
+
 typedef struct psfs_handle psfs_handle;
 
 /* Fills `p` with P_D = 0.9, P_FA = 0.1, prior = 0.5, threshold = 0.5,
@@ -173,6 +184,21 @@ psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *sl
  * Errors: INVALID_ARG, NOT_READY, CUDA. */
 psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_occ,
                           float *d_slm, float *d_mean, float *d_var);
+
+/* Selects the tile shape of the fusion kernel (re-plans the handle; waits for
+ * its stream).  Errors: INVALID_ARG (unsupported shape), NOMEM, CUDA. */
+psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg);
+
+/* The tile shape in use.  Errors: INVALID_ARG. */
+psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
+
+/* Autotuner: times every supported tile shape on the frame `images` (device,
+ * as psfs_reconstruct) with CUDA events, `reps` launches each, keeps the
+ * fastest, writes it to *best (may be NULL) and remembers it for handles of
+ * the same grid size, camera count, image size and map type created later in
+ * the process.  Allocates and frees its own scratch; waits for the stream.
+ * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */
+psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, psfs_fuse_config *best);
 
 /* Waits for the handle's stream, then returns and clears the first problem
  * recorded on the device since the last psfs_sync (PSFS_ERR_CAPACITY), or

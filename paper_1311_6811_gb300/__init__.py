@@ -22,7 +22,11 @@ from .psfs import (  # noqa: F401
     PsfsError,
     Reconstructor,
     load,
+    FUSE_CONFIGS,
+    psfs_autotune,
     psfs_backward,
+    psfs_get_fuse_config,
+    psfs_set_fuse_config,
     psfs_create,
     psfs_destroy,
     psfs_fuse_slm,

@@ -8,8 +8,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "psfs_internal.cuh"
@@ -30,6 +33,7 @@ struct psfs_handle {
     SensorConsts sc{};
     float c0 = 0.0f;
     FuseArgs fuse{};            // per-call pointers filled in at launch
+    FuseShape shape = kDefaultFuseShape;
 
     void *maps = nullptr;       // [n_cams][H][W] of g
     float *bg_mean = nullptr;   // [n_pix][3]
@@ -194,6 +198,55 @@ psfs_status check_frame_outputs(const float *occupancy, const uint32_t *voxel_li
     return PSFS_OK;
 }
 
+// Tile shapes remembered by the autotuner, keyed by what the best shape
+// depends on: grid size, camera count, image size and map type.
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, FuseShape> g_tuned;
+
+TuneKey tune_key(const psfs_handle *h)
+{
+    return TuneKey(h->grid.nx, h->grid.ny, h->grid.nz, h->n_cams, h->W, h->H, h->params.map_dtype);
+}
+
+// (Re)plans the fuse kernel for `shape`: projection matrices, tile order and
+// per (tile, camera) records, uploaded to freshly sized device arrays.
+psfs_status replan(psfs_handle *h, const FuseShape &shape)
+{
+    std::vector<uint64_t> tiles;
+    std::vector<int4> tilecam;
+    FuseArgs f;
+    plan_fuse(h->grid, h->cams.data(), h->n_cams, h->params, shape, &f, &tiles, &tilecam);
+    uint64_t *d_tiles = nullptr;
+    int4 *d_tilecam = nullptr;
+    if (cudaMalloc(&d_tiles, tiles.size() * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&d_tilecam, tilecam.size() * sizeof(int4)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_tiles);
+        return fail(PSFS_ERR_NOMEM, "tile plan allocation");
+    }
+    cudaError_t e = cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_tilecam, tilecam.data(), tilecam.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_tiles);
+        cudaFree(d_tilecam);
+        return fail_cuda(e, "tile plan upload");
+    }
+    cudaFree(h->tiles);
+    cudaFree(h->tilecam);
+    h->tiles = d_tiles;
+    h->tilecam = d_tilecam;
+    f.maps = h->maps;
+    f.tiles = h->tiles;
+    f.tilecam = h->tilecam;
+    f.status = h->d_words;
+    h->fuse = f;
+    h->n_tiles = f.n_tiles;
+    h->shape = shape;
+    return PSFS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -278,39 +331,37 @@ psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t 
     h->sc.a_zero_const_neg = (pd == 1.0);
     h->c0 = (float)(params->log_fg_density + 1.5 * std::log(M_PI));
 
-    // projection matrices, Morton tile order and per (tile, camera) staging
-    std::vector<uint64_t> tiles;
-    std::vector<int4> tilecam;
-    plan_fuse(*grid, cams, n_cams, *params, &h->fuse, &tiles, &tilecam);
-    FuseArgs &f = h->fuse;
-    h->n_tiles = f.n_tiles;
-
     DeviceGuard guard(h->device);
     const size_t pix_bytes = (size_t)h->n_pix;
     if (cudaMalloc(&h->maps, pix_bytes * h->map_elem) != cudaSuccess ||
         cudaMalloc(&h->bg_mean, pix_bytes * 3 * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&h->bg_hinv, pix_bytes * 3 * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&h->d_words, 16 * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMallocHost(&h->h_words, 16 * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&h->tiles, tiles.size() * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc(&h->tilecam, tilecam.size() * sizeof(int4)) != cudaSuccess) {
+        cudaMallocHost(&h->h_words, 16 * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         free_handle(h);
         return fail(PSFS_ERR_NOMEM, "device scratch allocation");
     }
-    f.maps = h->maps;
-    f.tiles = h->tiles;
-    f.tilecam = h->tilecam;
-    f.status = h->d_words;
-    e = cudaMemcpy(h->tiles, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(h->tilecam, tilecam.data(), tilecam.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(h->d_words, 0, 16 * sizeof(uint32_t));
+    e = cudaMemset(h->d_words, 0, 16 * sizeof(uint32_t));
     if (e != cudaSuccess) {
         free_handle(h);
         return fail_cuda(e, "psfs_create upload");
     }
     std::memset(h->h_words, 0, 16 * sizeof(uint32_t));
+
+    // projection matrices, Morton tile order and per (tile, camera) records,
+    // for the tile shape the autotuner chose for this kind of rig if any
+    FuseShape shape = kDefaultFuseShape;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key(h));
+        if (it != g_tuned.end()) shape = it->second;
+    }
+    st = replan(h, shape);
+    if (st != PSFS_OK) {
+        free_handle(h);
+        return st;
+    }
     *out = h;
     return PSFS_OK;
 }
@@ -352,7 +403,7 @@ static psfs_status enqueue_reconstruct(psfs_handle *h, const uint8_t *images, fl
     fill_fuse_args(h, occupancy, voxel_list, capacity, count, &fa);
     {
         ProfScope ps(h, PSFS_STAGE_FUSE);
-        PSFS_CK(launch_fuse(fa, h->params.map_dtype, h->stream));
+        PSFS_CK(launch_fuse(fa, h->shape, h->params.map_dtype, h->stream));
     }
     return PSFS_OK;
 }
@@ -442,7 +493,7 @@ psfs_status psfs_fuse_slm(psfs_handle *h, const float *slm, float *occupancy, ui
     fill_fuse_args(h, occupancy, voxel_list, capacity, count, &fa);
     {
         ProfScope ps(h, PSFS_STAGE_FUSE);
-        PSFS_CK(launch_fuse(fa, h->params.map_dtype, h->stream));
+        PSFS_CK(launch_fuse(fa, h->shape, h->params.map_dtype, h->stream));
     }
     return PSFS_OK;
 }
@@ -478,6 +529,96 @@ psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_
     (void)d_var;
     if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
     return fail(PSFS_ERR_INVALID_ARG, "psfs_backward: not available in this build");
+}
+
+psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
+{
+    if (!h || !cfg) return fail(PSFS_ERR_INVALID_ARG, "NULL argument");
+    const FuseShape shape = {cfg->lanes_x, cfg->warps, cfg->voxels_z};
+    if (!fuse_shape_supported(shape)) return fail(PSFS_ERR_INVALID_ARG, "unsupported fuse tile shape");
+    DeviceGuard guard(h->device);
+    PSFS_CK(cudaStreamSynchronize(h->stream));
+    return replan(h, shape);
+}
+
+psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg)
+{
+    if (!h || !cfg) return fail(PSFS_ERR_INVALID_ARG, "NULL argument");
+    cfg->lanes_x = h->shape.lx;
+    cfg->warps = h->shape.wy;
+    cfg->voxels_z = h->shape.tz;
+    return PSFS_OK;
+}
+
+psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, psfs_fuse_config *best)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (!images || !aligned(images, 16)) return fail(PSFS_ERR_INVALID_ARG, "images NULL or not 16-byte aligned");
+    if (reps < 1) return fail(PSFS_ERR_INVALID_ARG, "reps < 1");
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    DeviceGuard guard(h->device);
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    float *occ = nullptr;
+    uint32_t *list = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&occ, n_vox * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&list, n_vox * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(occ);
+        return fail(PSFS_ERR_NOMEM, "autotune scratch");
+    }
+    psfs_status st = PSFS_OK;
+    FuseShape best_shape = h->shape;
+    float best_ms = 1e30f;
+    const int lxs[3] = {8, 16, 32}, tzs[2] = {8, 16};
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(PSFS_ERR_CUDA, "cudaEventCreate");
+    // the maps of this frame, once: only the fuse kernel depends on the shape
+    if (st == PSFS_OK) st = enqueue_reconstruct(h, images, occ, list, (uint32_t)n_vox, h->d_words + 3);
+    for (int a = 0; a < 3 && st == PSFS_OK; ++a)
+        for (int b = 0; b < 2 && st == PSFS_OK; ++b) {
+            const FuseShape shape = {lxs[a], 4, tzs[b]};
+            if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+                st = fail(PSFS_ERR_CUDA, "autotune sync");
+                break;
+            }
+            st = replan(h, shape);
+            if (st != PSFS_OK) break;
+            FuseArgs fa;
+            fill_fuse_args(h, occ, list, (uint32_t)n_vox, h->d_words + 3, &fa);
+            cudaError_t err = launch_fuse(fa, shape, h->params.map_dtype, h->stream);   // warm-up
+            if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+                err = cudaMemsetAsync(h->d_words + 3, 0, sizeof(uint32_t), h->stream);
+                if (err == cudaSuccess) err = launch_fuse(fa, shape, h->params.map_dtype, h->stream);
+            }
+            if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err != cudaSuccess) {
+                st = fail_cuda(err, "autotune timing");
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_shape = shape;
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(occ);
+    cudaFree(list);
+    cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t), h->stream);   // the scratch list never overflows
+    if (st != PSFS_OK) return st;
+    st = replan(h, best_shape);
+    if (st != PSFS_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[tune_key(h)] = best_shape;
+    }
+    if (best) psfs_get_fuse_config(h, best);
+    return PSFS_OK;
 }
 
 psfs_status psfs_sync(psfs_handle *h)

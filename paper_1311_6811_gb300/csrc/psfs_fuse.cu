@@ -3,11 +3,15 @@
 // sum over cameras (log form of the product of Eq. 4), posterior, strict
 // threshold and compaction of the occupied voxels.
 //
-// Work decomposition.  A CTA owns a tile of 32 (x) x WY (y) x TZ (z) voxels:
-// each warp is one run of 32 voxels along x (128-byte occupancy stores) and
-// each thread walks TZ voxels along z, sharing the x/y part of the
-// projection.  CTAs are issued in Morton order of their tiles, so that
-// neighbouring CTAs gather from neighbouring parts of the (L2-resident) maps.
+// Work decomposition.  A CTA owns a tile of LX (x) x (32/LX) WY (y) x TZ (z)
+// voxels: each warp is an LX x 32/LX patch of one z-slice and each thread
+// walks TZ voxels along z, sharing the x/y part of the projection.  With the
+// cameras on a ring around the grid, a z-slice maps to a band of a few image
+// rows, so a square-ish patch (LX = 8) gathers from a handful of 32-byte
+// sectors per warp where a 32-voxel row along x spans over a hundred pixels.
+// Occupancy stores stay whole sectors (LX consecutive floats per row).  CTAs
+// are issued in Morton order of their tiles, so that neighbouring CTAs gather
+// from neighbouring parts of the (L2-resident) maps.
 //
 // Gather.  The instruction stream per voxel and camera is kept minimal:
 // three fma for (u, v, w), one approximate reciprocal, two fma with
@@ -25,7 +29,7 @@ namespace psfs {
 
 namespace {
 
-template <typename MapT, int WY, int TZ>
+template <typename MapT, int LX, int WY, int TZ>
 __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ FuseArgs a)
 {
     __shared__ int s_flags[PSFS_MAX_CAMS];
@@ -41,8 +45,9 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
     const int tx = (int)(tc & 0x1FFFFFu);
     const int ty = (int)((tc >> 21) & 0x1FFFFFu);
     const int tz = (int)(tc >> 42);
-    const int i = tx * 32 + lane;
-    const int j = ty * WY + wy;
+    constexpr int LY = 32 / LX;
+    const int i = tx * LX + (lane % LX);
+    const int j = ty * (LY * WY) + wy * LY + lane / LX;
     const int k0 = tz * TZ;
     // Lanes past the grid edge (ragged tiles) project the nearest voxel of the
     // grid instead, so that the host's per-tile proofs cover them; their
@@ -141,17 +146,33 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
 
 }  // namespace
 
-cudaError_t launch_fuse(const FuseArgs &a, int map_dtype, cudaStream_t s)
+namespace {
+
+template <typename MapT, int LX, int TZ>
+cudaError_t launch_typed(const FuseArgs &a, cudaStream_t s)
+{
+    fuse_kernel<MapT, LX, 4, TZ><<<a.n_tiles, dim3(32, 4), 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename MapT>
+cudaError_t launch_shape(const FuseArgs &a, const FuseShape &sh, cudaStream_t s)
+{
+    if (sh.wy != 4) return cudaErrorInvalidValue;
+    if (sh.lx == 8) return sh.tz == 8 ? launch_typed<MapT, 8, 8>(a, s) : launch_typed<MapT, 8, 16>(a, s);
+    if (sh.lx == 16) return sh.tz == 8 ? launch_typed<MapT, 16, 8>(a, s) : launch_typed<MapT, 16, 16>(a, s);
+    if (sh.lx == 32) return sh.tz == 8 ? launch_typed<MapT, 32, 8>(a, s) : launch_typed<MapT, 32, 16>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_fuse(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s)
 {
     if (a.n_tiles <= 0) return cudaSuccess;
-    const dim3 block(32, FUSE_WY);
-    if (map_dtype == PSFS_MAP_F16)
-        fuse_kernel<__half, FUSE_WY, FUSE_TZ><<<a.n_tiles, block, 0, s>>>(a);
-    else if (map_dtype == PSFS_MAP_BF16)
-        fuse_kernel<__nv_bfloat16, FUSE_WY, FUSE_TZ><<<a.n_tiles, block, 0, s>>>(a);
-    else
-        fuse_kernel<float, FUSE_WY, FUSE_TZ><<<a.n_tiles, block, 0, s>>>(a);
-    return cudaGetLastError();
+    if (map_dtype == PSFS_MAP_F16) return launch_shape<__half>(a, shape, s);
+    if (map_dtype == PSFS_MAP_BF16) return launch_shape<__nv_bfloat16>(a, shape, s);
+    return launch_shape<float>(a, shape, s);
 }
 
 }  // namespace psfs

@@ -95,10 +95,17 @@ struct FuseArgs {
     CamMat cam[PSFS_MAX_CAMS];
 };
 
-// Tile shape of the fuse kernel: 32 voxels along x (one warp), FUSE_WY warps
-// along y, FUSE_TZ voxels along z per thread.
-constexpr int FUSE_WY = 4;
-constexpr int FUSE_TZ = 16;
+// Tile shape of the fuse kernel (see psfs_fuse_config): a warp is LX voxels
+// along x by 32 / LX along y, a CTA WY warps along y, TZ voxels per thread
+// along z.
+struct FuseShape {
+    int lx, wy, tz;
+    int tile_x() const { return lx; }
+    int tile_y() const { return (32 / lx) * wy; }
+    int tile_z() const { return tz; }
+};
+constexpr FuseShape kDefaultFuseShape = {8, 4, 16};
+bool fuse_shape_supported(const FuseShape &s);
 
 __host__ __device__ inline uint64_t pack_tile(uint32_t tx, uint32_t ty, uint32_t tz)
 {
@@ -296,11 +303,12 @@ cudaError_t launch_pack_background(const float *mean, const float *var, int64_t 
 cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_out,
                               cudaStream_t s);
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s);
-cudaError_t launch_fuse(const FuseArgs &a, int map_dtype, cudaStream_t s);
+cudaError_t launch_fuse(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 
 // Host planning (psfs_plan.cu): projection matrices, tile order and staging
 // records of the fuse kernel for one grid and camera rig.
 void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const psfs_params &params,
-               FuseArgs *out, std::vector<uint64_t> *tiles, std::vector<int4> *tilecam);
+               const FuseShape &shape, FuseArgs *out, std::vector<uint64_t> *tiles,
+               std::vector<int4> *tilecam);
 
 }  // namespace psfs

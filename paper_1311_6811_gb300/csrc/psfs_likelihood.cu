@@ -2,10 +2,10 @@
 // the per-camera log ratio of Eq. 5-9), plus the background packing kernel.
 //
 // Streaming, HBM-bound: per pixel 3 B of image + 24 B of packed background in,
-// 4 B (f32) or 2 B (f16/bf16) of map out.  A persistent grid (two CTAs per
+// 4 B (f32) or 2 B (f16/bf16) of map out.  A persistent grid (four CTAs per
 // SM) walks 512-pixel chunks; one thread per CTA streams each chunk's image
 // bytes, means and inverse variances into shared memory with bulk copies
-// (TMA) through a four-stage mbarrier ring, so that about 110 KB per SM are
+// (TMA) through a four-stage mbarrier ring, so that up to 220 KB per SM are
 // in flight independently of registers, while all threads compute from the
 // previous stages and write the map with coalesced stores.
 #include <algorithm>
@@ -66,6 +66,7 @@ constexpr int kLkImgBytes = 3 * kLkChunk;             // 1536
 constexpr int kLkBgBytes = 12 * kLkChunk;             // 6144 (3 floats per pixel)
 constexpr int kLkStageBytes = kLkImgBytes + 2 * kLkBgBytes;
 constexpr int kLkSmemBytes = kLkStages * kLkStageBytes + kLkStages * 8;
+constexpr int kLkCtasPerSm = 4;                     // 4 x 55 KB of shared memory per SM
 
 template <typename OutT, bool kSlm>
 __device__ __forceinline__ void likelihood_pixel(const LikelihoodArgs &a, OutT *out, int64_t p, float i0,
@@ -191,7 +192,7 @@ cudaError_t launch_likelihood_typed(const LikelihoodArgs &a, cudaStream_t s)
     }
     const int64_t n_tma_pix = a.n_pix / 16 * 16;
     const int64_t n_chunks = (n_tma_pix + kLkChunk - 1) / kLkChunk;
-    int64_t blocks = std::min<int64_t>(n_chunks, 2 * (int64_t)sm_count());
+    int64_t blocks = std::min<int64_t>(n_chunks, kLkCtasPerSm * (int64_t)sm_count());
     if (blocks < 1) blocks = 1;
     kern<<<(int)blocks, kLkThreads, kLkSmemBytes, s>>>(a, n_tma_pix);
     return cudaGetLastError();

@@ -34,7 +34,7 @@ uint64_t spread3(uint64_t x)
 // where a bound on the float32 projection error of the kernel stays below a
 // quarter pixel, well inside the one-pixel margin each decision keeps.
 void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, const FuseArgs &f,
-                   const std::vector<uint64_t> &tiles, std::vector<int4> &out)
+                   const FuseShape &shape, const std::vector<uint64_t> &tiles, std::vector<int4> &out)
 {
     const int W = cams[0].width, H = cams[0].height;
     const double vs = g.voxel_size;
@@ -58,9 +58,10 @@ void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, cons
     for (size_t n = 0; n < tiles.size(); ++n) {
         const uint64_t tc = tiles[n];
         const int tx = (int)(tc & 0x1FFFFF), ty = (int)((tc >> 21) & 0x1FFFFF), tz = (int)(tc >> 42);
-        const int i0 = tx * 32, i1 = std::min(g.nx, i0 + 32) - 1;
-        const int j0 = ty * FUSE_WY, j1 = std::min(g.ny, j0 + FUSE_WY) - 1;
-        const int k0 = tz * FUSE_TZ, k1 = std::min(g.nz, k0 + FUSE_TZ) - 1;
+        const int TX = shape.tile_x(), TY = shape.tile_y(), TZ = shape.tile_z();
+        const int i0 = tx * TX, i1 = std::min(g.nx, i0 + TX) - 1;
+        const int j0 = ty * TY, j1 = std::min(g.ny, j0 + TY) - 1;
+        const int k0 = tz * TZ, k1 = std::min(g.nz, k0 + TZ) - 1;
         for (int c = 0; c < n_cams; ++c) {
             const double *K = cams[c].K, *R = cams[c].R, *t = cams[c].t;
             double wmin = 1e300, wmax = -1e300, xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
@@ -108,8 +109,14 @@ void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, cons
 
 }  // namespace
 
+bool fuse_shape_supported(const FuseShape &s)
+{
+    return (s.lx == 8 || s.lx == 16 || s.lx == 32) && s.wy == 4 && (s.tz == 8 || s.tz == 16);
+}
+
 void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const psfs_params &params,
-               FuseArgs *out, std::vector<uint64_t> *tiles_out, std::vector<int4> *tilecam_out)
+               const FuseShape &shape, FuseArgs *out, std::vector<uint64_t> *tiles_out,
+               std::vector<int4> *tilecam_out)
 {
     FuseArgs &f = *out;
     std::memset(&f, 0, sizeof(f));
@@ -144,8 +151,9 @@ void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const
     f.logit_prior = (float)std::log(params.prior / (1.0 - params.prior));
     f.logit_tau = (float)std::log(params.threshold / (1.0 - params.threshold));
 
-    const int ntx = (grid.nx + 31) / 32, nty = (grid.ny + FUSE_WY - 1) / FUSE_WY,
-              ntz = (grid.nz + FUSE_TZ - 1) / FUSE_TZ;
+    const int ntx = (grid.nx + shape.tile_x() - 1) / shape.tile_x();
+    const int nty = (grid.ny + shape.tile_y() - 1) / shape.tile_y();
+    const int ntz = (grid.nz + shape.tile_z() - 1) / shape.tile_z();
     std::vector<std::pair<uint64_t, uint64_t>> order;
     order.reserve((size_t)ntx * nty * ntz);
     for (int z = 0; z < ntz; ++z)
@@ -157,7 +165,7 @@ void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const
     for (size_t n = 0; n < order.size(); ++n) (*tiles_out)[n] = order[n].second;
     f.n_tiles = (int)tiles_out->size();
     (void)params;
-    build_tilecam(grid, cams, n_cams, f, *tiles_out, *tilecam_out);
+    build_tilecam(grid, cams, n_cams, f, shape, *tiles_out, *tilecam_out);
 }
 
 }  // namespace psfs

@@ -52,6 +52,16 @@ class psfs_params(ctypes.Structure):
                 ("log_fg_density", ctypes.c_double), ("map_dtype", ctypes.c_int32)]
 
 
+class psfs_fuse_config(ctypes.Structure):
+    _fields_ = [("lanes_x", ctypes.c_int32), ("warps", ctypes.c_int32), ("voxels_z", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.lanes_x, self.warps, self.voxels_z)
+
+
+FUSE_CONFIGS = [(lx, 4, tz) for lx in (8, 16, 32) for tz in (8, 16)]
+
+
 class PsfsError(RuntimeError):
     def __init__(self, status: int, func: str, message: str):
         self.status = status
@@ -92,6 +102,9 @@ def load(build_if_missing: bool = True):
             "psfs_backward": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
             "psfs_sync": (st, [_vp]),
             "psfs_destroy": (None, [_vp]),
+            "psfs_set_fuse_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
+            "psfs_get_fuse_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
+            "psfs_autotune": (st, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(psfs_fuse_config)]),
             "psfs_profile_enable": (st, [_vp, ctypes.c_int32]),
             "psfs_profile_read": (st, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
             "psfs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -288,6 +301,26 @@ def psfs_sync(h: int) -> int:
 def psfs_destroy(h: int):
     if h:
         load().psfs_destroy(h)
+
+
+def psfs_set_fuse_config(h: int, lanes_x: int, warps: int, voxels_z: int):
+    cfg = psfs_fuse_config(lanes_x, warps, voxels_z)
+    _check(load().psfs_set_fuse_config(h, ctypes.byref(cfg)), "psfs_set_fuse_config")
+
+
+def psfs_get_fuse_config(h: int) -> tuple:
+    cfg = psfs_fuse_config()
+    _check(load().psfs_get_fuse_config(h, ctypes.byref(cfg)), "psfs_get_fuse_config")
+    return cfg.as_tuple()
+
+
+def psfs_autotune(h: int, images, reps: int = 5) -> tuple:
+    """Times every fuse tile shape on `images`, keeps and returns the fastest."""
+    import torch
+    cfg = psfs_fuse_config()
+    _check(load().psfs_autotune(h, _dev_ptr(images, "images", torch.uint8), int(reps), ctypes.byref(cfg)),
+           "psfs_autotune")
+    return cfg.as_tuple()
 
 
 PSFS_N_STAGES = 8

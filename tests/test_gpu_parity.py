@@ -238,3 +238,30 @@ def test_reduced_precision_maps_match_oracle_on_rounded_maps(dtype):
     assert rep["max_abs_err"] < (2e-3 if dtype == "f16" else 2e-2), rep
     assert rep["mean_abs_err"] < 1e-5, rep
     rec.close()
+
+
+def test_fuse_tile_shapes_give_identical_results_and_autotune():
+    """Every supported tile shape sums the same cameras in the same order, so
+    occupancy and voxel set are bit-identical; the autotuner picks one of them."""
+    sc = S.make_scene(seed=8, grid_n=48, cube_side=2.0, n_cams=5, width=200, height=150, focal=190.0)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    img = to_dev(sc.images)
+    results = []
+    for cfg in psfs.FUSE_CONFIGS:
+        psfs.psfs_set_fuse_config(rec.handle, *cfg)
+        assert psfs.psfs_get_fuse_config(rec.handle) == cfg
+        occ, lst, cnt = rec.reconstruct(img)
+        assert rec.sync() == psfs.PSFS_OK
+        results.append((occ.cpu().numpy(), psfs.voxel_list(lst, cnt, rec.capacity).numpy()))
+    for occ, lst in results[1:]:
+        np.testing.assert_array_equal(occ, results[0][0])
+        np.testing.assert_array_equal(lst, results[0][1])
+    best = psfs.psfs_autotune(rec.handle, img, reps=2)
+    assert best in psfs.FUSE_CONFIGS and psfs.psfs_get_fuse_config(rec.handle) == best
+    occ, lst, cnt = rec.reconstruct(img)
+    assert rec.sync() == psfs.PSFS_OK
+    np.testing.assert_array_equal(occ.cpu().numpy(), results[0][0])
+    with pytest.raises(psfs.PsfsError):
+        psfs.psfs_set_fuse_config(rec.handle, 12, 4, 8)
+    rec.close()

@@ -34,27 +34,28 @@ def driver(tmp_path_factory):
     return str(out)
 
 
-def _plan(driver, grid, cams, map_dtype, tmp_path):
+def _plan(driver, grid, cams, map_dtype, tmp_path, shape=(8, 4, 16)):
     inp = tmp_path / "rig.txt"
     with open(inp, "w") as f:
         f.write(f"{grid.nx} {grid.ny} {grid.nz} {grid.origin[0]!r} {grid.origin[1]!r} {grid.origin[2]!r} "
-                f"{grid.voxel_size!r} {len(cams)} {map_dtype}\n")
+                f"{grid.voxel_size!r} {len(cams)} {map_dtype} {shape[0]} {shape[1]} {shape[2]}\n")
         for c in cams:
             vals = np.concatenate([c.K.ravel(), c.R.ravel(), c.t.ravel()])
             f.write(f"{c.width} {c.height} " + " ".join(repr(float(v)) for v in vals) + "\n")
     lines = subprocess.run([driver, str(inp)], capture_output=True, text=True, check=True).stdout.splitlines()
-    wy, tz = map(int, lines[0].split())
+    tx_dim, ty_dim, tz_dim = map(int, lines[0].split())
     n = len(cams)
     M = [np.array(lines[1 + c].split(), dtype=np.float32).astype(np.float64).reshape(3, 4) for c in range(n)]
     recs = [tuple(map(int, l.split())) for l in lines[1 + n:] if l.strip()]
-    return wy, tz, M, recs
+    return (tx_dim, ty_dim, tz_dim), M, recs
 
 
-def _check(driver, grid, cams, map_dtype, tmp_path):
-    wy, tz, M, recs = _plan(driver, grid, cams, map_dtype, tmp_path)
+def _check(driver, grid, cams, map_dtype, tmp_path, shape=(8, 4, 16)):
+    (TX, TY, TZ), M, recs = _plan(driver, grid, cams, map_dtype, tmp_path, shape)
     W, H = cams[0].width, cams[0].height
     ci, cj, ck = 0.5 * (grid.nx - 1), 0.5 * (grid.ny - 1), 0.5 * (grid.nz - 1)
-    n_tiles = (-(-grid.nx // 32)) * (-(-grid.ny // wy)) * (-(-grid.nz // tz))
+    assert (TX, TY, TZ) == (shape[0], (32 // shape[0]) * shape[1], shape[2])
+    n_tiles = (-(-grid.nx // TX)) * (-(-grid.ny // TY)) * (-(-grid.nz // TZ))
     assert len(recs) == n_tiles * len(cams)
     seen_tiles = set()
     counts = {"inside": 0, "skip": 0, "checked": 0}
@@ -62,9 +63,9 @@ def _check(driver, grid, cams, map_dtype, tmp_path):
         tx, ty, tzi = tc & 0x1FFFFF, (tc >> 21) & 0x1FFFFF, tc >> 42
         seen_tiles.add(tc)
         flags = wf >> 16
-        i = np.minimum(tx * 32 + np.arange(32), grid.nx - 1)
-        j = np.minimum(ty * wy + np.arange(wy), grid.ny - 1)
-        k = np.minimum(tzi * tz + np.arange(tz), grid.nz - 1)
+        i = np.minimum(tx * TX + np.arange(TX), grid.nx - 1)
+        j = np.minimum(ty * TY + np.arange(TY), grid.ny - 1)
+        k = np.minimum(tzi * TZ + np.arange(TZ), grid.nz - 1)
         I, J, K = np.meshgrid(i, j, k, indexing="ij")
         P = np.stack([I.ravel() - ci, J.ravel() - cj, K.ravel() - ck, np.ones(I.size)], 1)
         uvw = P @ M[c].T
@@ -97,17 +98,25 @@ RIGS = {
 
 
 @pytest.mark.parametrize("rig", sorted(RIGS))
-def test_records_cover_every_voxel(driver, rig, tmp_path):
+@pytest.mark.parametrize("shape", [(8, 4, 16), (16, 4, 8), (32, 4, 8)])
+def test_records_cover_every_voxel(driver, rig, shape, tmp_path):
     sc = RIGS[rig]()
-    counts = _check(driver, sc.grid, sc.cams, 0, tmp_path)
+    counts = _check(driver, sc.grid, sc.cams, 0, tmp_path, shape)
     assert counts["inside"] > 0
 
 
-def test_records_ragged_grid(driver, tmp_path):
+@pytest.mark.parametrize("shape", [(8, 4, 16), (32, 4, 8)])
+def test_records_ragged_grid(driver, shape, tmp_path):
     """Ragged in every tile dimension."""
     cams = S.ring_cameras(np.random.default_rng(3), 3, 101, 77, 95.0, (0.0, 0.0, 1.0))
-    counts = _check(driver, S.Grid(37, 29, 23, (-0.9, -0.7, 0.1), 0.05), cams, 0, tmp_path)
+    counts = _check(driver, S.Grid(37, 29, 23, (-0.9, -0.7, 0.1), 0.05), cams, 0, tmp_path, shape)
     assert counts["inside"] > 0
+
+
+def test_unsupported_shape_is_refused(driver, tmp_path):
+    cams = S.ring_cameras(np.random.default_rng(3), 2, 64, 48, 60.0, (0.0, 0.0, 1.0))
+    with pytest.raises(subprocess.CalledProcessError):
+        _plan(driver, S.Grid(8, 8, 8, (-0.2, -0.2, 0.8), 0.05), cams, 0, tmp_path, (12, 4, 8))
 
 
 @pytest.mark.slow
