@@ -102,15 +102,18 @@ typedef struct {
     int32_t map_dtype;      /* psfs_map_dtype of the stored likelihood maps        */
 } psfs_params;
 
-/* Shape of the voxel tile one CTA of the fusion kernel owns: a warp covers
- * lanes_x voxels along x by 32 / lanes_x along y, a CTA `warps` warps stacked
- * along y, and each thread walks voxels_z voxels along z.  Supported:
- * lanes_x in {8, 16, 32}, warps = 4, voxels_z in {8, 16}.  The shape changes
- * speed only, never results. */
+/* Launch shapes (speed only, never results).  The voxel tile one CTA of the
+ * fusion kernel owns: a warp covers lanes_x voxels along x by 32 / lanes_x
+ * along y, a CTA `warps` warps stacked along y, and each thread walks
+ * voxels_z voxels along z; supported: lanes_x in {8, 16, 32}, warps = 4,
+ * voxels_z in {8, 16}.  seq_likelihood_ctas: CTAs per SM of the likelihood
+ * grid on the sequence path, 1 to 4 (0 in psfs_set_fuse_config keeps the
+ * current value). */
 typedef struct {
     int32_t lanes_x;
     int32_t warps;
     int32_t voxels_z;
+    int32_t seq_likelihood_ctas;
 } psfs_fuse_config;
 
 typedef struct psfs_handle psfs_handle;
@@ -150,6 +153,19 @@ psfs_status psfs_set_background(psfs_handle *h, const float *mean, const float *
  * PSFS_ERR_CAPACITY.  Errors: INVALID_ARG, NOT_READY, CUDA. */
 psfs_status psfs_reconstruct(psfs_handle *h, const uint8_t *images, float *occupancy,
                              uint32_t *voxel_list, uint32_t capacity, uint32_t *count);
+
+/* psfs_reconstruct over n_frames frames of this rig, one call: frame f reads
+ * images + f * (n_cams * height * width * 3) and writes
+ * occupancy + f * (nx * ny * nz), voxel_lists + f * capacity and counts[f].
+ * The likelihood stage of frame f + 1 runs on a second stream concurrently
+ * with the fusion stage of frame f (two map buffers), so that the HBM-bound
+ * and the gather-bound kernels overlap; the whole sequence is ordered after
+ * earlier work on the handle's stream and later work waits for it.  The frame
+ * size in bytes and the voxel count must be multiples of 16 and 4.
+ * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */
+psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
+                                      float *occupancy, uint32_t *voxel_lists, uint32_t capacity,
+                                      uint32_t *counts);
 
 /* psfs_reconstruct with HOST buffers: copies the images to the device, runs
  * the frame, copies the occupancy, the count and min(count, capacity) list
@@ -194,9 +210,10 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
 
 /* Autotuner: times every supported tile shape on the frame `images` (device,
  * as psfs_reconstruct) with CUDA events, `reps` launches each, keeps the
- * fastest, writes it to *best (may be NULL) and remembers it for handles of
- * the same grid size, camera count, image size and map type created later in
- * the process.  Allocates and frees its own scratch; waits for the stream.
+ * fastest and writes it to *best (may be NULL); then times the sequence path
+ * with 1 to 4 likelihood CTAs per SM and keeps the fastest.  Both choices are
+ * remembered for handles of the same grid size, camera count, image size and
+ * map type created later in the process.  Allocates and frees its own scratch; waits for the stream.
  * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */
 psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, psfs_fuse_config *best);
 

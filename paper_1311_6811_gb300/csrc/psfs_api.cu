@@ -51,6 +51,14 @@ struct psfs_handle {
     uint32_t *st_list = nullptr;
     uint32_t st_list_cap = 0;
 
+    // sequence path: likelihood and fusion of consecutive frames on two
+    // streams, maps double-buffered (created on first use)
+    cudaStream_t seq_stream[2] = {nullptr, nullptr};   // [0] likelihood, [1] fusion
+    cudaEvent_t seq_ev_in = nullptr, seq_ev_map[2] = {nullptr, nullptr}, seq_ev_fused[2] = {nullptr, nullptr};
+    cudaEvent_t seq_ev_done[2] = {nullptr, nullptr};
+    void *maps2 = nullptr;
+    int seq_lk_ctas = 2;
+
     // tracing: CUDA event pairs around each launch
     int prof_cap = 0;
     std::vector<cudaEvent_t> prof_ev;      // 2 * prof_cap events
@@ -131,6 +139,15 @@ void free_handle(psfs_handle *h)
     cudaFree(h->st_list);
     cudaFree(h->dl);
     cudaFree(h->dg);
+    cudaFree(h->maps2);
+    for (int n = 0; n < 2; ++n) {
+        if (h->seq_stream[n]) cudaStreamSynchronize(h->seq_stream[n]);
+        if (h->seq_stream[n]) cudaStreamDestroy(h->seq_stream[n]);
+        if (h->seq_ev_map[n]) cudaEventDestroy(h->seq_ev_map[n]);
+        if (h->seq_ev_fused[n]) cudaEventDestroy(h->seq_ev_fused[n]);
+        if (h->seq_ev_done[n]) cudaEventDestroy(h->seq_ev_done[n]);
+    }
+    if (h->seq_ev_in) cudaEventDestroy(h->seq_ev_in);
     prof_free(h);
     cudaSetDevice(prev);
     delete h;
@@ -148,18 +165,20 @@ void prof_free(psfs_handle *h)
 // Brackets one launch with an event pair when tracing is on.
 struct ProfScope {
     psfs_handle *h;
+    cudaStream_t st;
     int slot = -1;
-    ProfScope(psfs_handle *hh, int stage) : h(hh)
+    ProfScope(psfs_handle *hh, int stage) : ProfScope(hh, stage, hh->stream) {}
+    ProfScope(psfs_handle *hh, int stage, cudaStream_t s) : h(hh), st(s)
     {
         if (h->prof_cap > 0 && h->prof_n < h->prof_cap) {
             slot = h->prof_n++;
             h->prof_stage[slot] = stage;
-            cudaEventRecord(h->prof_ev[2 * slot], h->stream);
+            cudaEventRecord(h->prof_ev[2 * slot], st);
         }
     }
     ~ProfScope()
     {
-        if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], h->stream);
+        if (slot >= 0) cudaEventRecord(h->prof_ev[2 * slot + 1], st);
     }
 };
 
@@ -201,8 +220,12 @@ psfs_status check_frame_outputs(const float *occupancy, const uint32_t *voxel_li
 // Tile shapes remembered by the autotuner, keyed by what the best shape
 // depends on: grid size, camera count, image size and map type.
 using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+struct Tuned {
+    FuseShape shape;
+    int seq_lk_ctas;
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, FuseShape> g_tuned;
+std::map<TuneKey, Tuned> g_tuned;
 
 TuneKey tune_key(const psfs_handle *h)
 {
@@ -355,7 +378,10 @@ psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t 
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(tune_key(h));
-        if (it != g_tuned.end()) shape = it->second;
+        if (it != g_tuned.end()) {
+            shape = it->second.shape;
+            h->seq_lk_ctas = it->second.seq_lk_ctas;
+        }
     }
     st = replan(h, shape);
     if (st != PSFS_OK) {
@@ -418,6 +444,92 @@ psfs_status psfs_reconstruct(psfs_handle *h, const uint8_t *images, float *occup
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     DeviceGuard guard(h->device);
     return enqueue_reconstruct(h, images, occupancy, voxel_list, capacity, count);
+}
+
+static psfs_status seq_setup(psfs_handle *h)
+{
+    if (h->seq_stream[0]) return PSFS_OK;
+    if (cudaMalloc(&h->maps2, (size_t)h->n_pix * h->map_elem) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PSFS_ERR_NOMEM, "second map buffer");
+    }
+    for (int n = 0; n < 2; ++n) {
+        PSFS_CK(cudaStreamCreateWithFlags(&h->seq_stream[n], cudaStreamNonBlocking));
+        PSFS_CK(cudaEventCreateWithFlags(&h->seq_ev_map[n], cudaEventDisableTiming));
+        PSFS_CK(cudaEventCreateWithFlags(&h->seq_ev_fused[n], cudaEventDisableTiming));
+        PSFS_CK(cudaEventCreateWithFlags(&h->seq_ev_done[n], cudaEventDisableTiming));
+    }
+    PSFS_CK(cudaEventCreateWithFlags(&h->seq_ev_in, cudaEventDisableTiming));
+    return PSFS_OK;
+}
+
+// Enqueues n_frames frames with the given element strides between frames
+// (a stride of 0 repeats the same buffer, which only the autotuner does).
+static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images, size_t img_stride,
+                                    float *occupancy, size_t occ_stride, uint32_t *voxel_lists,
+                                    size_t list_stride, uint32_t capacity, uint32_t *counts, size_t count_stride,
+                                    int lk_ctas)
+{
+    psfs_status st = seq_setup(h);
+    if (st != PSFS_OK) return st;
+    cudaStream_t sl = h->seq_stream[0], sf = h->seq_stream[1];
+    void *bufs[2] = {h->maps, h->maps2};
+    PSFS_CK(cudaEventRecord(h->seq_ev_in, h->stream));
+    PSFS_CK(cudaStreamWaitEvent(sl, h->seq_ev_in, 0));
+    PSFS_CK(cudaStreamWaitEvent(sf, h->seq_ev_in, 0));
+    for (int f = 0; f < n_frames; ++f) {
+        const int b = f & 1;
+        if (f >= 2) PSFS_CK(cudaStreamWaitEvent(sl, h->seq_ev_fused[b], 0));   // frame f-2 done with buffer b
+        LikelihoodArgs la{};
+        la.img = images + (size_t)f * img_stride;
+        la.mean = h->bg_mean;
+        la.hinv = h->bg_hinv;
+        la.n_pix = h->n_pix;
+        la.c0 = h->c0;
+        la.sc = h->sc;
+        la.out = bufs[b];
+        la.zero_word = counts + (size_t)f * count_stride;
+        la.status = h->d_words;
+        {
+            ProfScope ps(h, PSFS_STAGE_LIKELIHOOD, sl);
+            PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, sl, lk_ctas));
+        }
+        PSFS_CK(cudaEventRecord(h->seq_ev_map[b], sl));
+        PSFS_CK(cudaStreamWaitEvent(sf, h->seq_ev_map[b], 0));
+        FuseArgs fa;
+        fill_fuse_args(h, occupancy + (size_t)f * occ_stride, voxel_lists + (size_t)f * list_stride, capacity,
+                       counts + (size_t)f * count_stride, &fa);
+        fa.maps = bufs[b];
+        {
+            ProfScope ps(h, PSFS_STAGE_FUSE, sf);
+            PSFS_CK(launch_fuse(fa, h->shape, h->params.map_dtype, sf));
+        }
+        PSFS_CK(cudaEventRecord(h->seq_ev_fused[b], sf));
+    }
+    PSFS_CK(cudaEventRecord(h->seq_ev_done[0], sl));
+    PSFS_CK(cudaEventRecord(h->seq_ev_done[1], sf));
+    PSFS_CK(cudaStreamWaitEvent(h->stream, h->seq_ev_done[0], 0));
+    PSFS_CK(cudaStreamWaitEvent(h->stream, h->seq_ev_done[1], 0));
+    return PSFS_OK;
+}
+
+psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
+                                      float *occupancy, uint32_t *voxel_lists, uint32_t capacity,
+                                      uint32_t *counts)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (n_frames < 0) return fail(PSFS_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames == 0) return PSFS_OK;
+    if (!images || !aligned(images, 16)) return fail(PSFS_ERR_INVALID_ARG, "images NULL or not 16-byte aligned");
+    if ((h->n_pix * 3) % 16 != 0) return fail(PSFS_ERR_INVALID_ARG, "frame size not a multiple of 16 bytes");
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    if (n_vox % 4 != 0) return fail(PSFS_ERR_INVALID_ARG, "voxel count not a multiple of 4");
+    psfs_status st = check_frame_outputs(occupancy, voxel_lists, capacity, counts);
+    if (st != PSFS_OK) return st;
+    DeviceGuard guard(h->device);
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    return enqueue_sequence(h, n_frames, images, (size_t)h->n_pix * 3, occupancy, n_vox, voxel_lists, capacity,
+                            capacity, counts, 1, h->seq_lk_ctas);
 }
 
 psfs_status psfs_reconstruct_host(psfs_handle *h, const uint8_t *h_images, float *h_occupancy,
@@ -536,8 +648,15 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
     if (!h || !cfg) return fail(PSFS_ERR_INVALID_ARG, "NULL argument");
     const FuseShape shape = {cfg->lanes_x, cfg->warps, cfg->voxels_z};
     if (!fuse_shape_supported(shape)) return fail(PSFS_ERR_INVALID_ARG, "unsupported fuse tile shape");
+    if (cfg->seq_likelihood_ctas < 0 || cfg->seq_likelihood_ctas > 4)
+        return fail(PSFS_ERR_INVALID_ARG, "seq_likelihood_ctas outside [0, 4]");
     DeviceGuard guard(h->device);
     PSFS_CK(cudaStreamSynchronize(h->stream));
+    if (h->seq_stream[0]) {
+        PSFS_CK(cudaStreamSynchronize(h->seq_stream[0]));
+        PSFS_CK(cudaStreamSynchronize(h->seq_stream[1]));
+    }
+    if (cfg->seq_likelihood_ctas > 0) h->seq_lk_ctas = cfg->seq_likelihood_ctas;
     return replan(h, shape);
 }
 
@@ -547,6 +666,7 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg)
     cfg->lanes_x = h->shape.lx;
     cfg->warps = h->shape.wy;
     cfg->voxels_z = h->shape.tz;
+    cfg->seq_likelihood_ctas = h->seq_lk_ctas;
     return PSFS_OK;
 }
 
@@ -604,6 +724,32 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
                 best_shape = shape;
             }
         }
+    // second stage: CTAs per SM of the likelihood grid when it shares the GPU
+    // with the fusion of the previous frame (sequence path), timed on 8
+    // repetitions of the frame
+    if (st == PSFS_OK) st = replan(h, best_shape);
+    float best_seq = 1e30f;
+    for (int lk = 1; lk <= 4 && st == PSFS_OK; ++lk) {
+        cudaError_t err = cudaStreamSynchronize(h->stream);
+        st = enqueue_sequence(h, 2, images, 0, occ, 0, list, 0, (uint32_t)n_vox, h->d_words + 3, 0, lk);
+        if (st != PSFS_OK) break;
+        if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && st == PSFS_OK; ++r)
+            st = enqueue_sequence(h, 8, images, 0, occ, 0, list, 0, (uint32_t)n_vox, h->d_words + 3, 0, lk);
+        if (st != PSFS_OK) break;
+        if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) {
+            st = fail_cuda(err, "autotune sequence timing");
+            break;
+        }
+        if (ms < best_seq) {
+            best_seq = ms;
+            h->seq_lk_ctas = lk;
+        }
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(h->stream);
@@ -615,7 +761,7 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     if (st != PSFS_OK) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[tune_key(h)] = best_shape;
+        g_tuned[tune_key(h)] = Tuned{best_shape, h->seq_lk_ctas};
     }
     if (best) psfs_get_fuse_config(h, best);
     return PSFS_OK;

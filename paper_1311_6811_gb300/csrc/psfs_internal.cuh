@@ -300,8 +300,10 @@ __device__ __forceinline__ float log_ratio_of_r(float r, const SensorConsts &c)
 cudaError_t launch_pack_background(const float *mean, const float *var, int64_t n_pix,
                                    float *mean_out, float *hinv_out, uint32_t *bad,
                                    cudaStream_t s);
-cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_out,
-                              cudaStream_t s);
+// ctas_per_sm: CTAs of the persistent likelihood grid per SM (1..4); fewer
+// leave room for fusion CTAs of another frame running concurrently.
+cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_out, cudaStream_t s,
+                              int ctas_per_sm = 4);
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 

@@ -66,7 +66,7 @@ constexpr int kLkImgBytes = 3 * kLkChunk;             // 1536
 constexpr int kLkBgBytes = 12 * kLkChunk;             // 6144 (3 floats per pixel)
 constexpr int kLkStageBytes = kLkImgBytes + 2 * kLkBgBytes;
 constexpr int kLkSmemBytes = kLkStages * kLkStageBytes + kLkStages * 8;
-constexpr int kLkCtasPerSm = 4;                     // 4 x 55 KB of shared memory per SM
+constexpr int kLkCtasPerSm = 4;                     // at most 4 x 55 KB of shared memory per SM
 
 template <typename OutT, bool kSlm>
 __device__ __forceinline__ void likelihood_pixel(const LikelihoodArgs &a, OutT *out, int64_t p, float i0,
@@ -179,7 +179,7 @@ int grid_for(int64_t work, int threads)
 }
 
 template <typename OutT, bool kSlm>
-cudaError_t launch_likelihood_typed(const LikelihoodArgs &a, cudaStream_t s)
+cudaError_t launch_likelihood_typed(const LikelihoodArgs &a, cudaStream_t s, int ctas_per_sm)
 {
     auto kern = likelihood_kernel<OutT, kSlm>;
     static bool configured[64] = {false};
@@ -192,7 +192,8 @@ cudaError_t launch_likelihood_typed(const LikelihoodArgs &a, cudaStream_t s)
     }
     const int64_t n_tma_pix = a.n_pix / 16 * 16;
     const int64_t n_chunks = (n_tma_pix + kLkChunk - 1) / kLkChunk;
-    int64_t blocks = std::min<int64_t>(n_chunks, kLkCtasPerSm * (int64_t)sm_count());
+    ctas_per_sm = std::max(1, std::min(ctas_per_sm, kLkCtasPerSm));
+    int64_t blocks = std::min<int64_t>(n_chunks, ctas_per_sm * (int64_t)sm_count());
     if (blocks < 1) blocks = 1;
     kern<<<(int)blocks, kLkThreads, kLkSmemBytes, s>>>(a, n_tma_pix);
     return cudaGetLastError();
@@ -208,12 +209,13 @@ cudaError_t launch_pack_background(const float *mean, const float *var, int64_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_out, cudaStream_t s)
+cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_out, cudaStream_t s,
+                              int ctas_per_sm)
 {
-    if (slm_out) return launch_likelihood_typed<float, true>(a, s);
-    if (map_dtype == PSFS_MAP_F16) return launch_likelihood_typed<__half, false>(a, s);
-    if (map_dtype == PSFS_MAP_BF16) return launch_likelihood_typed<__nv_bfloat16, false>(a, s);
-    return launch_likelihood_typed<float, false>(a, s);
+    if (slm_out) return launch_likelihood_typed<float, true>(a, s, ctas_per_sm);
+    if (map_dtype == PSFS_MAP_F16) return launch_likelihood_typed<__half, false>(a, s, ctas_per_sm);
+    if (map_dtype == PSFS_MAP_BF16) return launch_likelihood_typed<__nv_bfloat16, false>(a, s, ctas_per_sm);
+    return launch_likelihood_typed<float, false>(a, s, ctas_per_sm);
 }
 
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s)

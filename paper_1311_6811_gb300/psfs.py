@@ -53,7 +53,8 @@ class psfs_params(ctypes.Structure):
 
 
 class psfs_fuse_config(ctypes.Structure):
-    _fields_ = [("lanes_x", ctypes.c_int32), ("warps", ctypes.c_int32), ("voxels_z", ctypes.c_int32)]
+    _fields_ = [("lanes_x", ctypes.c_int32), ("warps", ctypes.c_int32), ("voxels_z", ctypes.c_int32),
+                ("seq_likelihood_ctas", ctypes.c_int32)]
 
     def as_tuple(self):
         return (self.lanes_x, self.warps, self.voxels_z)
@@ -97,6 +98,7 @@ def load(build_if_missing: bool = True):
             "psfs_set_background": (st, [_vp, _vp, _vp]),
             "psfs_reconstruct": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_reconstruct_host": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+            "psfs_reconstruct_sequence": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
             "psfs_backward": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -256,6 +258,15 @@ def psfs_reconstruct(h: int, images, occupancy, voxel_list, capacity: int, count
                                    _dev_ptr(count, "count")), "psfs_reconstruct")
 
 
+def psfs_reconstruct_sequence(h: int, n_frames: int, images, occupancy, voxel_lists, capacity: int, counts):
+    """n_frames frames in one call; tensors hold the frames back to back."""
+    import torch
+    _check(load().psfs_reconstruct_sequence(h, int(n_frames), _dev_ptr(images, "images", torch.uint8),
+                                            _dev_ptr(occupancy, "occupancy", torch.float32),
+                                            _dev_ptr(voxel_lists, "voxel_lists"), int(capacity),
+                                            _dev_ptr(counts, "counts")), "psfs_reconstruct_sequence")
+
+
 def psfs_reconstruct_host(h: int, images, occupancy, voxel_list, capacity: int, count) -> int:
     """Host buffers (numpy arrays or CPU tensors, pinned for speed).  Returns the
     status code: PSFS_OK or PSFS_ERR_CAPACITY (anything else raises)."""
@@ -303,15 +314,16 @@ def psfs_destroy(h: int):
         load().psfs_destroy(h)
 
 
-def psfs_set_fuse_config(h: int, lanes_x: int, warps: int, voxels_z: int):
-    cfg = psfs_fuse_config(lanes_x, warps, voxels_z)
+def psfs_set_fuse_config(h: int, lanes_x: int, warps: int, voxels_z: int, seq_likelihood_ctas: int = 0):
+    cfg = psfs_fuse_config(lanes_x, warps, voxels_z, seq_likelihood_ctas)
     _check(load().psfs_set_fuse_config(h, ctypes.byref(cfg)), "psfs_set_fuse_config")
 
 
-def psfs_get_fuse_config(h: int) -> tuple:
+def psfs_get_fuse_config(h: int, full: bool = False) -> tuple:
+    """(lanes_x, warps, voxels_z), plus seq_likelihood_ctas when `full`."""
     cfg = psfs_fuse_config()
     _check(load().psfs_get_fuse_config(h, ctypes.byref(cfg)), "psfs_get_fuse_config")
-    return cfg.as_tuple()
+    return cfg.as_tuple() + ((cfg.seq_likelihood_ctas,) if full else ())
 
 
 def psfs_autotune(h: int, images, reps: int = 5) -> tuple:

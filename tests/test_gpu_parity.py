@@ -265,3 +265,31 @@ def test_fuse_tile_shapes_give_identical_results_and_autotune():
     with pytest.raises(psfs.PsfsError):
         psfs.psfs_set_fuse_config(rec.handle, 12, 4, 8)
     rec.close()
+
+
+def test_sequence_equals_frame_by_frame():
+    """psfs_reconstruct_sequence (two streams, double-buffered maps) gives the
+    same occupancy bits and voxel sets as one psfs_reconstruct per frame."""
+    sc = S.make_scene(seed=16, grid_n=48, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0,
+                      n_frames=5, walking=True)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    F, V = imgs.shape[0], sc.grid.n_voxels
+    cap = V
+    occ = torch.empty((F, V), dtype=torch.float32, device="cuda")
+    lists = torch.empty((F, cap), dtype=torch.int32, device="cuda")
+    counts = torch.zeros((F,), dtype=torch.int32, device="cuda")
+    for lk in (1, 2, 4):
+        cfg = psfs.psfs_get_fuse_config(rec.handle)
+        psfs.psfs_set_fuse_config(rec.handle, *cfg, seq_likelihood_ctas=lk)
+        psfs.psfs_reconstruct_sequence(rec.handle, F, imgs, occ, lists, cap, counts)
+        assert rec.sync() == psfs.PSFS_OK
+        for f in range(F):
+            o1, l1, c1 = rec.reconstruct(imgs[f])
+            assert rec.sync() == psfs.PSFS_OK
+            np.testing.assert_array_equal(occ[f].cpu().numpy(), o1.cpu().numpy().ravel())
+            assert int(counts[f]) == int(c1.item())
+            np.testing.assert_array_equal(psfs.voxel_list(lists[f], counts[f:f + 1], cap).numpy(),
+                                          psfs.voxel_list(l1, c1, rec.capacity).numpy())
+    rec.close()
