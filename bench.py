@@ -390,8 +390,9 @@ def run_ours(args):
                            "occupied_voxels_per_frame": mean_count,
                            "l2": f"inputs larger than L2: {F * n_pix * 3 / 1e6:.0f} MB of images per step",
                            "parallelism": f"replicas x{ws} (frames independent)",
-                           "fuse_tile": {"lanes_x": fuse_cfg[0], "warps": fuse_cfg[1], "voxels_z": fuse_cfg[2]},
-                           "likelihood_ctas_per_sm": fuse_cfg[3],
+                           "fuse_tile": {"lanes_x": fuse_cfg[0], "warps": fuse_cfg[1], "voxels_z": fuse_cfg[2],
+                                         "staged": fuse_cfg[3]},
+                           "likelihood_ctas_per_sm": fuse_cfg[4],
                            "launch": "psfs_reconstruct_sequence (2 streams, double-buffered maps)"},
                 "stages": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(v["launches"] for v in stages.values()), "clocks": clk}

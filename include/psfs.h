@@ -106,13 +106,16 @@ typedef struct {
  * fusion kernel owns: a warp covers lanes_x voxels along x by 32 / lanes_x
  * along y, a CTA `warps` warps stacked along y, and each thread walks
  * voxels_z voxels along z; supported: lanes_x in {8, 16, 32}, warps = 4,
- * voxels_z in {8, 16}.  seq_likelihood_ctas: CTAs per SM of the likelihood
- * grid on the sequence path, 1 to 4 (0 in psfs_set_fuse_config keeps the
- * current value). */
+ * voxels_z in {8, 16}.  staged = 1 selects the persistent kernel that copies
+ * each tile's image footprint per camera into shared memory (bulk copies,
+ * double-buffered) before gathering; 0 gathers from global memory.
+ * seq_likelihood_ctas: CTAs per SM of the likelihood grid on the sequence
+ * path, 1 to 4 (0 in psfs_set_fuse_config keeps the current value). */
 typedef struct {
     int32_t lanes_x;
     int32_t warps;
     int32_t voxels_z;
+    int32_t staged;
     int32_t seq_likelihood_ctas;
 } psfs_fuse_config;
 

@@ -646,7 +646,7 @@ psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_
 psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
 {
     if (!h || !cfg) return fail(PSFS_ERR_INVALID_ARG, "NULL argument");
-    const FuseShape shape = {cfg->lanes_x, cfg->warps, cfg->voxels_z};
+    const FuseShape shape = {cfg->lanes_x, cfg->warps, cfg->voxels_z, cfg->staged};
     if (!fuse_shape_supported(shape)) return fail(PSFS_ERR_INVALID_ARG, "unsupported fuse tile shape");
     if (cfg->seq_likelihood_ctas < 0 || cfg->seq_likelihood_ctas > 4)
         return fail(PSFS_ERR_INVALID_ARG, "seq_likelihood_ctas outside [0, 4]");
@@ -666,6 +666,7 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg)
     cfg->lanes_x = h->shape.lx;
     cfg->warps = h->shape.wy;
     cfg->voxels_z = h->shape.tz;
+    cfg->staged = h->shape.staged;
     cfg->seq_likelihood_ctas = h->seq_lk_ctas;
     return PSFS_OK;
 }
@@ -694,9 +695,8 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(PSFS_ERR_CUDA, "cudaEventCreate");
     // the maps of this frame, once: only the fuse kernel depends on the shape
     if (st == PSFS_OK) st = enqueue_reconstruct(h, images, occ, list, (uint32_t)n_vox, h->d_words + 3);
-    for (int a = 0; a < 3 && st == PSFS_OK; ++a)
-        for (int b = 0; b < 2 && st == PSFS_OK; ++b) {
-            const FuseShape shape = {lxs[a], 4, tzs[b]};
+    for (int cand = 0; cand < 12 && st == PSFS_OK; ++cand) {
+            const FuseShape shape = {lxs[(cand / 2) % 3], 4, tzs[cand % 2], cand / 6};
             if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
                 st = fail(PSFS_ERR_CUDA, "autotune sync");
                 break;
@@ -723,7 +723,7 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
                 best_ms = ms;
                 best_shape = shape;
             }
-        }
+    }
     // second stage: CTAs per SM of the likelihood grid when it shares the GPU
     // with the fusion of the previous frame (sequence path), timed on 8
     // repetitions of the frame

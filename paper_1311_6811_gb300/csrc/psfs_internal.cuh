@@ -69,8 +69,12 @@ struct SlmToMapArgs {
 
 // Per (tile, camera) record prepared on the host at handle creation, in
 // double precision from the 8 corner voxel centres of the tile (int4):
-//   x, y, z   unused (reserved for a staged image box)
-//   w         flags << 16
+//   x, y   first column (rounded down to a 16-byte boundary) and row of the
+//          image box that the tile's seen voxel centres project into (1 px
+//          margin), clipped to the image
+//   z      box width in map elements (a whole number of 16-byte chunks)
+//   w      box height in rows | flags << 16
+constexpr int kTcStaged = 1;   // the staged kernel copies the box to shared memory
 constexpr int kTcInside = 2;   // every voxel centre of the tile is in front of the
                                // camera and inside the image, with margin for the
                                // float32 rounding of the kernel
@@ -98,14 +102,23 @@ struct FuseArgs {
 // Tile shape of the fuse kernel (see psfs_fuse_config): a warp is LX voxels
 // along x by 32 / LX along y, a CTA WY warps along y, TZ voxels per thread
 // along z.
+// `staged` selects the persistent kernel that copies each (tile, camera) image
+// box into shared memory with bulk copies (double-buffered across cameras)
+// and gathers from there; otherwise every CTA gathers from global memory.
 struct FuseShape {
-    int lx, wy, tz;
+    int lx, wy, tz, staged;
     int tile_x() const { return lx; }
     int tile_y() const { return (32 / lx) * wy; }
     int tile_z() const { return tz; }
 };
-constexpr FuseShape kDefaultFuseShape = {8, 4, 16};
+constexpr FuseShape kDefaultFuseShape = {8, 4, 16, 0};
 bool fuse_shape_supported(const FuseShape &s);
+
+// Shared-memory staging of the staged fusion kernel: two buffers of
+// kStageBytes, three CTAs per SM.
+constexpr int kStageBytes = 32 * 1024;
+constexpr int kStagedCtasPerSm = 3;
+inline int stage_cap_elems(int map_dtype) { return kStageBytes / (map_dtype == PSFS_MAP_F32 ? 4 : 2); }
 
 __host__ __device__ inline uint64_t pack_tile(uint32_t tx, uint32_t ty, uint32_t tz)
 {
@@ -198,6 +211,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 __device__ __forceinline__ void mbar_fence_init()
 {
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
@@ -306,6 +324,7 @@ cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_o
                               int ctas_per_sm = 4);
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
+cudaError_t launch_fuse_staged(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 
 // Host planning (psfs_plan.cu): projection matrices, tile order and staging
 // records of the fuse kernel for one grid and camera rig.

@@ -2,8 +2,8 @@
 // camera rig, done once at handle creation in double precision:
 //   * the 3x4 projection matrix of every camera in centred voxel-index space;
 //   * the voxel tiles in Morton order;
-//   * per (tile, camera) the record (skip / inside flags) that the fuse
-//     kernel reads.
+//   * per (tile, camera) the record (image box, staged / skip / inside
+//     flags) that the fusion kernels read.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -34,9 +34,14 @@ uint64_t spread3(uint64_t x)
 // where a bound on the float32 projection error of the kernel stays below a
 // quarter pixel, well inside the one-pixel margin each decision keeps.
 void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, const FuseArgs &f,
-                   const FuseShape &shape, const std::vector<uint64_t> &tiles, std::vector<int4> &out)
+                   const FuseShape &shape, int map_dtype, const std::vector<uint64_t> &tiles,
+                   std::vector<int4> &out)
 {
     const int W = cams[0].width, H = cams[0].height;
+    const int elem = map_dtype == PSFS_MAP_F32 ? 4 : 2;
+    const int chunk = 16 / elem;
+    const bool can_stage = shape.staged && ((int64_t)W * elem) % 16 == 0;
+    const int64_t cap = stage_cap_elems(map_dtype);
     const double vs = g.voxel_size;
     const double eps32 = std::ldexp(1.0, -24);
     // per camera: magnitude bounds of the float32 projection sums
@@ -102,7 +107,13 @@ void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, cons
                 rec.w = kTcSkip << 16;
                 continue;
             }
-            if (inside) rec.w = kTcInside << 16;
+            const int64_t ax0 = cx0 / chunk * chunk, ax1 = (cx1 + chunk - 1) / chunk * chunk;
+            const int64_t sw = ax1 - ax0, sh = cy1 - cy0;
+            const bool staged = can_stage && sw * sh <= cap;
+            rec.x = (int)ax0;
+            rec.y = (int)cy0;
+            rec.z = (int)sw;
+            rec.w = (int)sh | (((inside ? kTcInside : 0) | (staged ? kTcStaged : 0)) << 16);
         }
     }
 }
@@ -111,7 +122,8 @@ void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, cons
 
 bool fuse_shape_supported(const FuseShape &s)
 {
-    return (s.lx == 8 || s.lx == 16 || s.lx == 32) && s.wy == 4 && (s.tz == 8 || s.tz == 16);
+    return (s.lx == 8 || s.lx == 16 || s.lx == 32) && s.wy == 4 && (s.tz == 8 || s.tz == 16) &&
+           (s.staged == 0 || s.staged == 1);
 }
 
 void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const psfs_params &params,
@@ -164,8 +176,7 @@ void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const
     tiles_out->resize(order.size());
     for (size_t n = 0; n < order.size(); ++n) (*tiles_out)[n] = order[n].second;
     f.n_tiles = (int)tiles_out->size();
-    (void)params;
-    build_tilecam(grid, cams, n_cams, f, shape, *tiles_out, *tilecam_out);
+    build_tilecam(grid, cams, n_cams, f, shape, params.map_dtype, *tiles_out, *tilecam_out);
 }
 
 }  // namespace psfs

@@ -54,13 +54,13 @@ class psfs_params(ctypes.Structure):
 
 class psfs_fuse_config(ctypes.Structure):
     _fields_ = [("lanes_x", ctypes.c_int32), ("warps", ctypes.c_int32), ("voxels_z", ctypes.c_int32),
-                ("seq_likelihood_ctas", ctypes.c_int32)]
+                ("staged", ctypes.c_int32), ("seq_likelihood_ctas", ctypes.c_int32)]
 
     def as_tuple(self):
-        return (self.lanes_x, self.warps, self.voxels_z)
+        return (self.lanes_x, self.warps, self.voxels_z, self.staged)
 
 
-FUSE_CONFIGS = [(lx, 4, tz) for lx in (8, 16, 32) for tz in (8, 16)]
+FUSE_CONFIGS = [(lx, 4, tz, st) for st in (0, 1) for lx in (8, 16, 32) for tz in (8, 16)]
 
 
 class PsfsError(RuntimeError):
@@ -314,13 +314,14 @@ def psfs_destroy(h: int):
         load().psfs_destroy(h)
 
 
-def psfs_set_fuse_config(h: int, lanes_x: int, warps: int, voxels_z: int, seq_likelihood_ctas: int = 0):
-    cfg = psfs_fuse_config(lanes_x, warps, voxels_z, seq_likelihood_ctas)
+def psfs_set_fuse_config(h: int, lanes_x: int, warps: int, voxels_z: int, staged: int = 0,
+                         seq_likelihood_ctas: int = 0):
+    cfg = psfs_fuse_config(lanes_x, warps, voxels_z, staged, seq_likelihood_ctas)
     _check(load().psfs_set_fuse_config(h, ctypes.byref(cfg)), "psfs_set_fuse_config")
 
 
 def psfs_get_fuse_config(h: int, full: bool = False) -> tuple:
-    """(lanes_x, warps, voxels_z), plus seq_likelihood_ctas when `full`."""
+    """(lanes_x, warps, voxels_z, staged), plus seq_likelihood_ctas when `full`."""
     cfg = psfs_fuse_config()
     _check(load().psfs_get_fuse_config(h, ctypes.byref(cfg)), "psfs_get_fuse_config")
     return cfg.as_tuple() + ((cfg.seq_likelihood_ctas,) if full else ())

@@ -263,7 +263,7 @@ def test_fuse_tile_shapes_give_identical_results_and_autotune():
     assert rec.sync() == psfs.PSFS_OK
     np.testing.assert_array_equal(occ.cpu().numpy(), results[0][0])
     with pytest.raises(psfs.PsfsError):
-        psfs.psfs_set_fuse_config(rec.handle, 12, 4, 8)
+        psfs.psfs_set_fuse_config(rec.handle, 12, 4, 8, 0)
     rec.close()
 
 
