@@ -286,7 +286,8 @@ def run_ours(args):
     stream.synchronize()
     h = rec.handle
     # autotuner: pick the fuse tile shape on the first frame (setup, untimed)
-    psfs.psfs_autotune(h, d_images[0], reps=3)
+    tune_ms = {}
+    psfs.psfs_autotune(h, d_images[0], reps=3, timings=tune_ms)
     fuse_cfg = psfs.psfs_get_fuse_config(h, full=True)
 
     def step():
@@ -393,6 +394,7 @@ def run_ours(args):
                            "fuse_tile": {"lanes_x": fuse_cfg[0], "warps": fuse_cfg[1], "voxels_z": fuse_cfg[2],
                                          "staged": fuse_cfg[3]},
                            "likelihood_ctas_per_sm": fuse_cfg[4],
+                           "autotune_fuse_us": {"x".join(map(str, k)): round(1e3 * v, 2) for k, v in tune_ms.items()},
                            "launch": "psfs_reconstruct_sequence (2 streams, double-buffered maps)"},
                 "stages": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": sum(v["launches"] for v in stages.values()), "clocks": clk}

@@ -213,12 +213,16 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
 
 /* Autotuner: times every supported tile shape on the frame `images` (device,
  * as psfs_reconstruct) with CUDA events, `reps` launches each, keeps the
- * fastest and writes it to *best (may be NULL); then times the sequence path
+ * fastest and writes it to *best (may be NULL) and the mean milliseconds of
+ * each candidate to candidate_ms[PSFS_N_FUSE_CANDIDATES] (may be NULL; order:
+ * staged 0 then 1, lanes_x 8, 16, 32, voxels_z 8 then 16); then times the sequence path
  * with 1 to 4 likelihood CTAs per SM and keeps the fastest.  Both choices are
  * remembered for handles of the same grid size, camera count, image size and
  * map type created later in the process.  Allocates and frees its own scratch; waits for the stream.
  * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */
-psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, psfs_fuse_config *best);
+#define PSFS_N_FUSE_CANDIDATES 12
+psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, psfs_fuse_config *best,
+                          float *candidate_ms);
 
 /* Waits for the handle's stream, then returns and clears the first problem
  * recorded on the device since the last psfs_sync (PSFS_ERR_CAPACITY), or

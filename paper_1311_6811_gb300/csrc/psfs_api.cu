@@ -671,7 +671,8 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg)
     return PSFS_OK;
 }
 
-psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, psfs_fuse_config *best)
+psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, psfs_fuse_config *best,
+                          float *candidate_ms)
 {
     if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
     if (!images || !aligned(images, 16)) return fail(PSFS_ERR_INVALID_ARG, "images NULL or not 16-byte aligned");
@@ -719,6 +720,7 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
                 st = fail_cuda(err, "autotune timing");
                 break;
             }
+            if (candidate_ms) candidate_ms[cand] = ms / (float)reps;
             if (ms < best_ms) {
                 best_ms = ms;
                 best_shape = shape;

@@ -60,6 +60,7 @@ class psfs_fuse_config(ctypes.Structure):
         return (self.lanes_x, self.warps, self.voxels_z, self.staged)
 
 
+# candidate order of psfs_autotune's timings
 FUSE_CONFIGS = [(lx, 4, tz, st) for st in (0, 1) for lx in (8, 16, 32) for tz in (8, 16)]
 
 
@@ -106,7 +107,8 @@ def load(build_if_missing: bool = True):
             "psfs_destroy": (None, [_vp]),
             "psfs_set_fuse_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
             "psfs_get_fuse_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
-            "psfs_autotune": (st, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(psfs_fuse_config)]),
+            "psfs_autotune": (st, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(psfs_fuse_config),
+                                   ctypes.POINTER(ctypes.c_float)]),
             "psfs_profile_enable": (st, [_vp, ctypes.c_int32]),
             "psfs_profile_read": (st, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
             "psfs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -327,12 +329,17 @@ def psfs_get_fuse_config(h: int, full: bool = False) -> tuple:
     return cfg.as_tuple() + ((cfg.seq_likelihood_ctas,) if full else ())
 
 
-def psfs_autotune(h: int, images, reps: int = 5) -> tuple:
-    """Times every fuse tile shape on `images`, keeps and returns the fastest."""
+def psfs_autotune(h: int, images, reps: int = 5, timings: Optional[dict] = None) -> tuple:
+    """Times every fuse tile shape on `images`, keeps and returns the fastest;
+    fills `timings` {config tuple: mean ms} if given."""
     import torch
     cfg = psfs_fuse_config()
-    _check(load().psfs_autotune(h, _dev_ptr(images, "images", torch.uint8), int(reps), ctypes.byref(cfg)),
+    ms = (ctypes.c_float * len(FUSE_CONFIGS))()
+    _check(load().psfs_autotune(h, _dev_ptr(images, "images", torch.uint8), int(reps), ctypes.byref(cfg), ms),
            "psfs_autotune")
+    if timings is not None:
+        for c, t in zip(FUSE_CONFIGS, ms):
+            timings[c] = float(t)
     return cfg.as_tuple()
 
 
