@@ -255,6 +255,37 @@ psfs_status psfs_profile_enable(psfs_handle *h, int32_t max_launches);
  * CUDA. */
 psfs_status psfs_profile_read(psfs_handle *h, double *ms, int32_t *launches);
 
+/* Largest n_cams * height * width that psfs_reconstruct_noalloc accepts. */
+#define PSFS_NOALLOC_MAX_PIXELS (4 * 1024 * 1024)
+
+/* One frame of the reconstruction for callers that cannot allocate device
+ * memory: hosts that own every byte of device memory and hand this code fixed
+ * buffers, or latency-critical loops that must not pay the implicit
+ * synchronisation of cudaMalloc.  (The paper has no counterpart; this is a
+ * deployment form of psfs_reconstruct.)
+ *   grid, cams, n_cams, params  as psfs_create (params->map_dtype must be
+ *                               PSFS_MAP_F32); read on the host, not kept
+ *   mean, var                   device float32 [n_cams][height][width][3],
+ *                               values as psfs_set_background requires (not
+ *                               checked here)
+ *   images, occupancy, voxel_list, capacity, count
+ *                               as psfs_reconstruct (4-byte aligned device
+ *                               pointers; count > capacity signals overflow)
+ *   stream                      cudaStream_t to enqueue on (NULL = legacy)
+ * Allocates nothing: its only scratch (the frame's log-ratio maps and a status
+ * word) is a fixed __device__ array of PSFS_NOALLOC_MAX_PIXELS floats plus 256
+ * bytes that every GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's device address (set-up
+ * per device), so make it before any stream capture.  Calls share the array:
+ * calls that overlap on the GPU race and give wrong results; order them on
+ * one stream.  Same results as psfs_reconstruct.  Enqueues two kernels and
+ * returns.  Errors: INVALID_ARG (also n_cams * height * width >
+ * PSFS_NOALLOC_MAX_PIXELS), CUDA. */
+psfs_status psfs_reconstruct_noalloc(const psfs_grid *grid, const psfs_camera *cams, int32_t n_cams,
+                                     const psfs_params *params, const float *mean, const float *var,
+                                     const uint8_t *images, float *occupancy, uint32_t *voxel_list,
+                                     uint32_t capacity, uint32_t *count, void *stream);
+
 /* Static English name of a status code. */
 const char *psfs_status_string(psfs_status s);
 

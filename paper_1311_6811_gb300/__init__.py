@@ -37,6 +37,7 @@ from .psfs import (  # noqa: F401
     psfs_profile_read,
     psfs_reconstruct,
     psfs_reconstruct_host,
+    psfs_reconstruct_noalloc,
     psfs_reconstruct_sequence,
     psfs_set_background,
     psfs_status_string,

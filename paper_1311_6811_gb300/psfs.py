@@ -103,6 +103,9 @@ def load(build_if_missing: bool = True):
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
             "psfs_backward": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
+            "psfs_reconstruct_noalloc": (st, [ctypes.POINTER(psfs_grid), ctypes.POINTER(psfs_camera),
+                                              ctypes.c_int32, ctypes.POINTER(psfs_params), _vp, _vp, _vp,
+                                              _vp, _vp, ctypes.c_uint32, _vp, _vp]),
             "psfs_sync": (st, [_vp]),
             "psfs_destroy": (None, [_vp]),
             "psfs_set_fuse_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
@@ -301,6 +304,29 @@ def psfs_backward(h: int, images, d_occ, d_slm=None, d_mean=None, d_var=None):
                                 _dev_ptr(d_slm, "d_slm", torch.float32),
                                 _dev_ptr(d_mean, "d_mean", torch.float32),
                                 _dev_ptr(d_var, "d_var", torch.float32)), "psfs_backward")
+
+
+PSFS_NOALLOC_MAX_PIXELS = 4 * 1024 * 1024
+
+
+def psfs_reconstruct_noalloc(grid, cams, params, mean, var, images, occupancy, voxel_list, capacity: int, count,
+                             stream=None):
+    """One frame without any device allocation (see include/psfs.h); no handle.
+    `stream` is a torch CUDA stream, an integer cudaStream_t or None (current)."""
+    import torch
+    g = make_grid(grid) if not isinstance(grid, psfs_grid) else grid
+    c = make_cameras(cams) if not isinstance(cams, ctypes.Array) else cams
+    p = params if isinstance(params, psfs_params) else make_params(params)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _check(load().psfs_reconstruct_noalloc(ctypes.byref(g), c, len(c), ctypes.byref(p),
+                                           _dev_ptr(mean, "mean", torch.float32), _dev_ptr(var, "var", torch.float32),
+                                           _dev_ptr(images, "images", torch.uint8),
+                                           _dev_ptr(occupancy, "occupancy", torch.float32),
+                                           _dev_ptr(voxel_list, "voxel_list"), int(capacity),
+                                           _dev_ptr(count, "count"), _vp(stream)), "psfs_reconstruct_noalloc")
 
 
 def psfs_sync(h: int) -> int:
