@@ -192,9 +192,11 @@ psfs_status psfs_fuse_slm(psfs_handle *h, const float *slm, float *occupancy,
  * Errors: INVALID_ARG, NOT_READY, CUDA. */
 psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *slm_out);
 
-/* Adjoint of psfs_reconstruct.  Given d_occ = dLoss/d occupancy (device
- * float32 [nz][ny][nx]) for the frame `images`, recomputes the forward and
- * writes (each may be NULL to skip it)
+/* Adjoint of psfs_reconstruct (the paper runs the forward only; this is the
+ * gradient of a loss on the posterior of Eq. 3-4).  Given d_occ = dLoss/d
+ * occupancy (device float32 [nz][ny][nx]) for the frame `images`, recomputes
+ * the forward (maps, then the log-odds of every voxel) and writes (each may
+ * be NULL to skip it)
  *   d_slm   device float32 [n_cams][height][width]     dLoss/dSLM
  *   d_mean  device float32 [n_cams][height][width][3]  dLoss/d mean
  *   d_var   device float32 [n_cams][height][width][3]  dLoss/d var
@@ -203,6 +205,12 @@ psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *sl
  * Errors: INVALID_ARG, NOT_READY, CUDA. */
 psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_occ,
                           float *d_slm, float *d_mean, float *d_var);
+
+/* Adjoint of psfs_fuse_slm: given the SLM maps `slm` of the forward (device
+ * float32 [n_cams][height][width]) and d_occ, writes dLoss/dSLM to d_slm
+ * (device float32 [n_cams][height][width]).  Recomputes the forward.
+ * Errors: INVALID_ARG, CUDA. */
+psfs_status psfs_backward_slm(psfs_handle *h, const float *slm, const float *d_occ, float *d_slm);
 
 /* Selects the tile shape of the fusion kernel (re-plans the handle; waits for
  * its stream).  Errors: INVALID_ARG (unsupported shape), NOMEM, CUDA. */

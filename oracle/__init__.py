@@ -72,6 +72,14 @@ def _load():
             lib.oracle_backward_background.argtypes = [ctypes.c_int64, _u8p, _f32p, _f32p, _dp,
                                                        _dp, _dp, _dp]
             lib.oracle_backward_background.restype = None
+            _i64p = ctypes.POINTER(ctypes.c_int64)
+            lib.oracle_fuse_subset.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                               ctypes.c_int, _i32p, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_int64, _i64p, _dp]
+            lib.oracle_fuse_subset.restype = None
+            lib.oracle_voxel_pixels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                                ctypes.c_int, _i32p, _dp, _i32p]
+            lib.oracle_voxel_pixels.restype = None
             _lib = lib
     return _lib
 
@@ -218,3 +226,29 @@ def backward(grid, cams, images, mean, var, d_occ, params=None):
     ds = backward_slm(grid, cams, s, d_occ, params)
     dm, dv = backward_background(images, mean, var, s, ds)
     return ds, dm, dv
+
+
+def fuse_subset(grid, cams, slm_maps, voxels, params=None) -> np.ndarray:
+    """Posterior (Eq. 3-4) of the listed voxels only, FP64."""
+    lib = _load()
+    nx, ny, nz, origin, vs = _grid_args(grid)
+    wh, rec = _cam_args(cams)
+    flat = np.ascontiguousarray(np.asarray(slm_maps, np.float64).ravel())
+    idx = np.ascontiguousarray(np.asarray(voxels, np.int64))
+    out = np.empty(idx.size)
+    lib.oracle_fuse_subset(nx, ny, nz, _ptr(origin, _dp), vs, len(cams), _ptr(wh, _i32p), _ptr(rec, _dp),
+                           _ptr(flat, _dp), float(_param(params, "p_detect", 0.9)),
+                           float(_param(params, "p_false_alarm", 0.1)), float(_param(params, "prior", 0.5)),
+                           int(idx.size), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(out, _dp))
+    return out
+
+
+def voxel_pixels(grid, cams) -> np.ndarray:
+    """int32 [n_cams][n_vox]: pixel offset of each voxel centre, -1 if unseen."""
+    lib = _load()
+    nx, ny, nz, origin, vs = _grid_args(grid)
+    wh, rec = _cam_args(cams)
+    out = np.empty((len(cams), nx * ny * nz), np.int32)
+    lib.oracle_voxel_pixels(nx, ny, nz, _ptr(origin, _dp), vs, len(cams), _ptr(wh, _i32p), _ptr(rec, _dp),
+                            _ptr(out, _i32p))
+    return out

@@ -256,3 +256,62 @@ void oracle_backward_background(int64_t n_pix, const uint8_t *img, const float *
         }
     }
 }
+
+/* --------------------------------------------------------------------- */
+/* Eq. 3-4 for a list of voxels only (same arithmetic as oracle_fuse, for */
+/* finite differences on large grids, where only the voxels that project */
+/* into a perturbed pixel change).                                        */
+/* --------------------------------------------------------------------- */
+void oracle_fuse_subset(int nx, int ny, int nz, const double origin[3], double voxel_size,
+                        int n_cams, const int *wh, const double *cams, const double *slm,
+                        double pd, double pfa, double prior, int64_t n_sub, const int64_t *idx,
+                        double *occ)
+{
+    int64_t *map_off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_cams > 0 ? n_cams : 1));
+    int64_t off = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        map_off[c] = off;
+        off += (int64_t)wh[2 * c] * wh[2 * c + 1];
+    }
+    for (int64_t n = 0; n < n_sub; ++n) {
+        int64_t v = idx[n];
+        int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((int64_t)nx * ny));
+        (void)nz;
+        double X[3] = {origin[0] + (i + 0.5) * voxel_size, origin[1] + (j + 0.5) * voxel_size,
+                       origin[2] + (k + 0.5) * voxel_size};
+        double A = 1.0, B = 1.0;
+        for (int c = 0; c < n_cams; ++c) {
+            int W = wh[2 * c], px = 0, py = 0;
+            double xy[2], w;
+            if (!oracle_project(cams + ORACLE_CAM_STRIDE * c, W, wh[2 * c + 1], X, &px, &py, xy, &w)) continue;
+            double s = slm[map_off[c] + (int64_t)py * W + px];
+            double a, b;
+            sensor_terms(s, pd, pfa, &a, &b);
+            A *= a;
+            B *= b;
+        }
+        occ[n] = prior * A / (prior * A + (1.0 - prior) * B);
+    }
+    free(map_off);
+}
+
+/* Pixel offset (py * W + px) of every voxel centre in every camera, -1 where
+ * the camera does not see it: out[c * n_vox + v]. */
+void oracle_voxel_pixels(int nx, int ny, int nz, const double origin[3], double voxel_size, int n_cams,
+                         const int *wh, const double *cams, int32_t *out)
+{
+    int64_t n_vox = (int64_t)nx * ny * nz;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t v = (int64_t)i + (int64_t)nx * ((int64_t)j + (int64_t)ny * k);
+                double X[3] = {origin[0] + (i + 0.5) * voxel_size, origin[1] + (j + 0.5) * voxel_size,
+                               origin[2] + (k + 0.5) * voxel_size};
+                for (int c = 0; c < n_cams; ++c) {
+                    int px = 0, py = 0;
+                    double xy[2], w;
+                    int vis = oracle_project(cams + ORACLE_CAM_STRIDE * c, wh[2 * c], wh[2 * c + 1], X, &px, &py, xy, &w);
+                    out[(int64_t)c * n_vox + v] = vis ? py * wh[2 * c] + px : -1;
+                }
+            }
+}

@@ -25,6 +25,7 @@ from .psfs import (  # noqa: F401
     FUSE_CONFIGS,
     psfs_autotune,
     psfs_backward,
+    psfs_backward_slm,
     psfs_get_fuse_config,
     psfs_set_fuse_config,
     psfs_create,

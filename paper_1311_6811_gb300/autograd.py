@@ -1,0 +1,64 @@
+"""torch.autograd.Function wrappers over the CUDA forward and adjoint of
+libpsfs (marshalling only: both directions run in the library's kernels).
+
+  occ = psfs_occupancy(rec, images, mean, var)   # grads for mean and var
+  occ = psfs_occupancy_from_slm(rec, slm)        # grad for the SLM maps
+
+`rec` is a `Reconstructor`; the forward is recomputed in the backward (only
+the uint8 images, or the maps, are saved), so nothing of size n_voxels x
+n_cams is kept between the two passes.
+"""
+
+from __future__ import annotations
+
+import torch
+
+from . import psfs
+
+
+class _Occupancy(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rec, images, mean, var):
+        rec.set_background(mean.detach().contiguous(), var.detach().contiguous())
+        occ, _, _ = rec.reconstruct(images)
+        ctx.rec = rec
+        ctx.save_for_backward(images)
+        ctx.shapes = (mean.shape, var.shape)
+        ctx.mark_non_differentiable()
+        return occ
+
+    @staticmethod
+    def backward(ctx, grad_occ):
+        (images,) = ctx.saved_tensors
+        rec = ctx.rec
+        d_mean = torch.empty(ctx.shapes[0], dtype=torch.float32, device=images.device)
+        d_var = torch.empty(ctx.shapes[1], dtype=torch.float32, device=images.device)
+        psfs.psfs_backward(rec.handle, images, grad_occ.contiguous().float(), None, d_mean, d_var)
+        return None, None, d_mean, d_var
+
+
+class _OccupancyFromSlm(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rec, slm):
+        slm_c = slm.detach().contiguous()
+        occ, _, _ = rec.fuse_slm(slm_c)
+        ctx.rec = rec
+        ctx.save_for_backward(slm_c)
+        return occ
+
+    @staticmethod
+    def backward(ctx, grad_occ):
+        (slm,) = ctx.saved_tensors
+        d_slm = torch.empty_like(slm)
+        psfs.psfs_backward_slm(ctx.rec.handle, slm, grad_occ.contiguous().float(), d_slm)
+        return None, d_slm
+
+
+def psfs_occupancy(rec, images, mean, var):
+    """Posterior occupancy [nz][ny][nx]; differentiable in `mean` and `var`."""
+    return _Occupancy.apply(rec, images, mean, var)
+
+
+def psfs_occupancy_from_slm(rec, slm):
+    """Posterior occupancy from SLM maps [n_cams][H][W]; differentiable in `slm`."""
+    return _OccupancyFromSlm.apply(rec, slm)

@@ -631,16 +631,98 @@ psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *sl
     return PSFS_OK;
 }
 
+static psfs_status enqueue_backward(psfs_handle *h, const uint8_t *images, const float *slm, const float *d_occ,
+                                    float *d_slm, float *d_mean, float *d_var)
+{
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    if (!h->dl) {
+        if (cudaMalloc(&h->dl, n_vox * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "adjoint scratch");
+        }
+    }
+    BackwardArgs b;
+    std::memset(&b, 0, sizeof(b));
+    b.f = h->fuse;
+    b.d_occ = d_occ;
+    b.dl = h->dl;
+    b.img = images;
+    b.slm = slm;
+    b.mean = h->bg_mean;
+    b.hinv = h->bg_hinv;
+    b.c0 = h->c0;
+    b.sc = h->sc;
+    const double pd = h->params.p_detect, q = 0.5 * (h->params.p_detect + h->params.p_false_alarm);
+    b.da = (float)(2.0 * pd - 1.0);
+    b.one_minus_pd = (float)(1.0 - pd);
+    b.db = (float)(2.0 * q - 1.0);
+    b.one_minus_q = (float)(1.0 - q);
+    b.d_slm = d_slm;
+    b.d_mean = d_mean;
+    b.d_var = d_var;
+    b.n_pix = h->n_pix;
+    plan_backward_inv(h->grid, h->cams.data(), h->n_cams, h->fuse, b.inv);
+    // recompute the forward maps
+    if (images) {
+        LikelihoodArgs la{};
+        la.img = images;
+        la.mean = h->bg_mean;
+        la.hinv = h->bg_hinv;
+        la.n_pix = h->n_pix;
+        la.c0 = h->c0;
+        la.sc = h->sc;
+        la.out = h->maps;
+        la.zero_word = nullptr;
+        la.status = h->d_words;
+        ProfScope ps(h, PSFS_STAGE_LIKELIHOOD);
+        PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, h->stream));
+    } else {
+        SlmToMapArgs sa{};
+        sa.slm = slm;
+        sa.n_pix = h->n_pix;
+        sa.da = b.da;
+        sa.one_minus_pd = b.one_minus_pd;
+        sa.db = b.db;
+        sa.one_minus_q = b.one_minus_q;
+        sa.out = h->maps;
+        sa.zero_word = nullptr;
+        ProfScope ps(h, PSFS_STAGE_LIKELIHOOD);
+        PSFS_CK(launch_slm_to_map(sa, h->params.map_dtype, h->stream));
+    }
+    {
+        ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL);
+        FuseShape direct = h->shape;
+        direct.staged = 0;   // the voxel pass uses the tile plan of either kernel with direct gathers
+        PSFS_CK(launch_backward_voxel(b, direct, h->params.map_dtype, h->stream));
+    }
+    {
+        ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL);
+        PSFS_CK(launch_backward_pixel(b, h->stream));
+    }
+    return PSFS_OK;
+}
+
 psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_occ, float *d_slm,
                           float *d_mean, float *d_var)
 {
-    (void)images;
-    (void)d_occ;
-    (void)d_slm;
-    (void)d_mean;
-    (void)d_var;
     if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
-    return fail(PSFS_ERR_INVALID_ARG, "psfs_backward: not available in this build");
+    if (!images || !aligned(images, 16)) return fail(PSFS_ERR_INVALID_ARG, "images NULL or not 16-byte aligned");
+    if (!d_occ || !aligned(d_occ, 16)) return fail(PSFS_ERR_INVALID_ARG, "d_occ NULL or not 16-byte aligned");
+    if ((d_slm && !aligned(d_slm, 16)) || (d_mean && !aligned(d_mean, 16)) || (d_var && !aligned(d_var, 16)))
+        return fail(PSFS_ERR_INVALID_ARG, "gradient buffer not 16-byte aligned");
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    DeviceGuard guard(h->device);
+    return enqueue_backward(h, images, nullptr, d_occ, d_slm, d_mean, d_var);
+}
+
+psfs_status psfs_backward_slm(psfs_handle *h, const float *slm, const float *d_occ, float *d_slm)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (!slm || !aligned(slm, 16)) return fail(PSFS_ERR_INVALID_ARG, "slm NULL or not 16-byte aligned");
+    if (!d_occ || !aligned(d_occ, 16)) return fail(PSFS_ERR_INVALID_ARG, "d_occ NULL or not 16-byte aligned");
+    if (!d_slm || !aligned(d_slm, 16)) return fail(PSFS_ERR_INVALID_ARG, "d_slm NULL or not 16-byte aligned");
+    DeviceGuard guard(h->device);
+    return enqueue_backward(h, nullptr, slm, d_occ, d_slm, nullptr, nullptr);
 }
 
 psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)

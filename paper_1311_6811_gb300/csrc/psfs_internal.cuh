@@ -288,6 +288,17 @@ __device__ __forceinline__ float map_load<__nv_bfloat16>(const __nv_bfloat16 *p)
     return __bfloat162float(__ldg(p));
 }
 
+// r = log U - log N (Eq. 1) for one pixel, from its colour, mean and
+// h = 1 / (2 var):  r = c0 - 0.5 log(h0 h1 h2) + sum_c (I_c - mu_c)^2 h_c,
+// c0 = log U + 1.5 log(pi).  The forward and the adjoint both call this.
+__device__ __forceinline__ float pixel_log_odds(float i0, float i1, float i2, float m0, float m1,
+                                                float m2, float h0, float h1, float h2, float c0)
+{
+    float d0 = i0 - m0, d1 = i1 - m1, d2 = i2 - m2;
+    float quad = fmaf(d0 * d0, h0, fmaf(d1 * d1, h1, d2 * d2 * h2));
+    return (c0 - 0.5f * __logf(h0 * h1 * h2)) + quad;
+}
+
 // g(r) = log(P_D e^r + 1 - P_D) - log(q e^r + 1 - q), evaluated with
 // e^-|r| only, so it neither overflows nor loses the constant terms.  The
 // hardware approximations (ex2 / lg2 / rcp) keep the absolute error of g near
@@ -312,6 +323,24 @@ __device__ __forceinline__ float log_ratio_of_r(float r, const SensorConsts &c)
     return __logf(__fdividef(A, B));
 }
 
+// dg/dr of the function above, from the same e^-|r| terms:
+//   d/dr log(P_D e^r + 1 - P_D) = P_D e^r / (P_D e^r + 1 - P_D)
+__device__ __forceinline__ float dlog_ratio_dr(float r, const SensorConsts &c)
+{
+    const float ar = fabsf(r);
+    const float u = __expf(-ar);
+    if (r > 0.0f) {
+        const float A = fmaf(c.one_minus_pd, u, c.pd), B = fmaf(c.one_minus_q, u, c.q);
+        // A = e^-r exactly when P_D = 0: the first term is 0
+        const float t1 = c.a_zero_const_pos ? 0.0f : __fdividef(c.pd, A);
+        return t1 - __fdividef(c.q, B);
+    }
+    const float A = fmaf(c.pd, u, c.one_minus_pd), B = fmaf(c.q, u, c.one_minus_q);
+    // A = P_D u exactly when P_D = 1: the first term is 1
+    const float t1 = c.a_zero_const_neg ? 1.0f : __fdividef(c.pd * u, A);
+    return t1 - __fdividef(c.q * u, B);
+}
+
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -323,6 +352,38 @@ cudaError_t launch_pack_background(const float *mean, const float *var, int64_t 
 cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_out, cudaStream_t s,
                               int ctas_per_sm = 4);
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s);
+
+// Adjoint (psfs_backward.cu).  The voxel pass recomputes the log-odds of
+// every voxel from the maps (exactly as the forward) and writes
+// dLoss/dL = dLoss/docc occ (1 - occ); the pixel pass forms per pixel the sum
+// of dLoss/dL over the voxels whose centre projects into it, then the chain
+// rule to the SLM, mean and variance.
+struct PixelInv {
+    float qc[3];    // camera centre in continuous voxel-index coordinates (voxel centres at integers)
+    float minv[9];  // pixel (x, y, 1) -> ray direction in voxel-index coordinates, row-major
+    float margin;   // pixels: frustum widening that covers the float32 error of the forward projection
+};
+
+struct BackwardArgs {
+    FuseArgs f;                   // grid, cameras, maps (for the voxel pass), tiles
+    const float *d_occ;           // [n_vox]
+    float *dl;                    // [n_vox] dLoss/dL scratch
+    // pixel pass
+    const uint8_t *img;           // [n_pix][3] (NULL: `slm` given instead)
+    const float *slm;             // [n_pix] caller-supplied SLM (psfs_backward_slm)
+    const float *mean, *hinv;     // packed background
+    float c0;
+    SensorConsts sc;
+    float da, one_minus_pd, db, one_minus_q;   // a(s), b(s) of Eq. 5-9
+    float *d_slm, *d_mean, *d_var;             // outputs, any may be NULL
+    int64_t n_pix;
+    PixelInv inv[PSFS_MAX_CAMS];
+};
+
+cudaError_t launch_backward_voxel(const BackwardArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
+void plan_backward_inv(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const FuseArgs &f,
+                       PixelInv *inv);
+cudaError_t launch_backward_pixel(const BackwardArgs &a, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 cudaError_t launch_fuse_staged(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 

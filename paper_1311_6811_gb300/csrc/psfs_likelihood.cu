@@ -30,16 +30,6 @@ int sm_count()
     return cached[dev];
 }
 
-// r = log U - log N (Eq. 1) for one pixel, from its colour, mean and
-// h = 1 / (2 var):  r = c0 - 0.5 log(h0 h1 h2) + sum_c (I_c - mu_c)^2 h_c.
-__device__ __forceinline__ float pixel_log_odds(float i0, float i1, float i2, float m0, float m1,
-                                                float m2, float h0, float h1, float h2, float c0)
-{
-    float d0 = i0 - m0, d1 = i1 - m1, d2 = i2 - m2;
-    float quad = fmaf(d0 * d0, h0, fmaf(d1 * d1, h1, d2 * d2 * h2));
-    return (c0 - 0.5f * __logf(h0 * h1 * h2)) + quad;
-}
-
 __device__ __forceinline__ float sigmoid(float r)
 {
     if (r > 0.0f) return __fdividef(1.0f, 1.0f + __expf(-r));

@@ -179,4 +179,69 @@ void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const
     build_tilecam(grid, cams, n_cams, f, shape, params.map_dtype, *tiles_out, *tilecam_out);
 }
 
+void plan_backward_inv(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const FuseArgs &f,
+                       PixelInv *inv)
+{
+    const double vs = grid.voxel_size;
+    const double eps32 = std::ldexp(1.0, -24);
+    const double half[3] = {0.5 * grid.nx + 1, 0.5 * grid.ny + 1, 0.5 * grid.nz + 1};
+    for (int c = 0; c < n_cams; ++c) {
+        const double *K = cams[c].K, *R = cams[c].R, *t = cams[c].t;
+        // K^-1 by cofactors
+        const double det = K[0] * (K[4] * K[8] - K[5] * K[7]) - K[1] * (K[3] * K[8] - K[5] * K[6]) +
+                           K[2] * (K[3] * K[7] - K[4] * K[6]);
+        double Ki[9] = {(K[4] * K[8] - K[5] * K[7]) / det, (K[2] * K[7] - K[1] * K[8]) / det,
+                        (K[1] * K[5] - K[2] * K[4]) / det, (K[5] * K[6] - K[3] * K[8]) / det,
+                        (K[0] * K[8] - K[2] * K[6]) / det, (K[2] * K[3] - K[0] * K[5]) / det,
+                        (K[3] * K[7] - K[4] * K[6]) / det, (K[1] * K[6] - K[0] * K[7]) / det,
+                        (K[0] * K[4] - K[1] * K[3]) / det};
+        // pixel (x, y, 1) -> world direction R^T K^-1 (x, y, 1), then / voxel_size
+        for (int r = 0; r < 3; ++r)
+            for (int col = 0; col < 3; ++col) {
+                double v = 0.0;
+                for (int q = 0; q < 3; ++q) v += R[3 * q + r] * Ki[3 * q + col];
+                inv[c].minv[3 * r + col] = (float)(v / vs);
+            }
+        // camera centre C = -R^T t in voxel-index coordinates (voxel centres at integers)
+        for (int r = 0; r < 3; ++r) {
+            double C = 0.0;
+            for (int q = 0; q < 3; ++q) C -= R[3 * q + r] * t[q];
+            inv[c].qc[r] = (float)((C - grid.origin[r]) / vs - 0.5);
+        }
+        // frustum widening: a bound on the float32 error of the forward
+        // projection over the grid (as the planner bounds it per tile), x4,
+        // at least 0.05 px; 0.5 px if the grid reaches behind the camera
+        const float *m = f.cam[c].m;
+        double su = std::fabs(m[3]), sv = std::fabs(m[7]), sw = std::fabs(m[11]);
+        for (int a = 0; a < 3; ++a) {
+            su += std::fabs(m[a]) * half[a];
+            sv += std::fabs(m[4 + a]) * half[a];
+            sw += std::fabs(m[8 + a]) * half[a];
+        }
+        double wmin = 1e300, xa = 0.0, ya = 0.0;
+        for (int corner = 0; corner < 8; ++corner) {
+            const int ii = (corner & 1) ? grid.nx - 1 : 0, jj = (corner & 2) ? grid.ny - 1 : 0,
+                      kk = (corner & 4) ? grid.nz - 1 : 0;
+            const double X[3] = {grid.origin[0] + (ii + 0.5) * vs, grid.origin[1] + (jj + 0.5) * vs,
+                                 grid.origin[2] + (kk + 0.5) * vs};
+            double xc[3], uvw[3];
+            for (int r = 0; r < 3; ++r) xc[r] = R[3 * r] * X[0] + R[3 * r + 1] * X[1] + R[3 * r + 2] * X[2] + t[r];
+            for (int r = 0; r < 3; ++r) uvw[r] = K[3 * r] * xc[0] + K[3 * r + 1] * xc[1] + K[3 * r + 2] * xc[2];
+            wmin = std::min(wmin, uvw[2]);
+            if (uvw[2] > 0) {
+                xa = std::max(xa, std::fabs(uvw[0] / uvw[2]));
+                ya = std::max(ya, std::fabs(uvw[1] / uvw[2]));
+            }
+        }
+        double margin = 0.5;
+        if (wmin > 1e-3 * sw) {
+            const double dw = 8 * eps32 * sw;
+            const double ex = 2 * ((8 * eps32 * su + xa * dw) / wmin + xa * std::ldexp(1.0, -21));
+            const double ey = 2 * ((8 * eps32 * sv + ya * dw) / wmin + ya * std::ldexp(1.0, -21));
+            margin = std::min(0.5, std::max(0.05, 4 * std::max(ex, ey)));
+        }
+        inv[c].margin = (float)margin;
+    }
+}
+
 }  // namespace psfs

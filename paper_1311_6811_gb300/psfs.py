@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
             "psfs_backward": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
+            "psfs_backward_slm": (st, [_vp, _vp, _vp, _vp]),
             "psfs_reconstruct_noalloc": (st, [ctypes.POINTER(psfs_grid), ctypes.POINTER(psfs_camera),
                                               ctypes.c_int32, ctypes.POINTER(psfs_params), _vp, _vp, _vp,
                                               _vp, _vp, ctypes.c_uint32, _vp, _vp]),
@@ -327,6 +328,12 @@ def psfs_reconstruct_noalloc(grid, cams, params, mean, var, images, occupancy, v
                                            _dev_ptr(occupancy, "occupancy", torch.float32),
                                            _dev_ptr(voxel_list, "voxel_list"), int(capacity),
                                            _dev_ptr(count, "count"), _vp(stream)), "psfs_reconstruct_noalloc")
+
+
+def psfs_backward_slm(h: int, slm, d_occ, d_slm):
+    import torch
+    _check(load().psfs_backward_slm(h, _dev_ptr(slm, "slm", torch.float32), _dev_ptr(d_occ, "d_occ", torch.float32),
+                                    _dev_ptr(d_slm, "d_slm", torch.float32)), "psfs_backward_slm")
 
 
 def psfs_sync(h: int) -> int:

@@ -320,3 +320,24 @@ def test_boundary_flag_marks_pixel_edges():
     g2 = dict(g, origin=(0.0, 0.0, -0.05))
     out2 = oracle.fuse(g2, [cam], [np.full((4, 4), 0.7)])
     assert not out2["boundary"][0]
+
+
+def test_fuse_subset_and_voxel_pixels_agree_with_full_fusion():
+    """The subset evaluation is the same posterior as the full one, and the
+    voxel -> pixel table matches oracle.project."""
+    cams = _ring(4)
+    rng = np.random.default_rng(17)
+    maps = _random_maps(cams, rng)
+    full = oracle.fuse(SMALL_GRID, cams, maps)
+    idx = rng.choice(full["occ"].size, 50, replace=False)
+    sub = oracle.fuse_subset(SMALL_GRID, cams, np.concatenate([m.ravel() for m in maps]), idx)
+    np.testing.assert_array_equal(sub, full["occ"][idx])
+    pix = oracle.voxel_pixels(SMALL_GRID, cams)
+    g = SMALL_GRID
+    for v in idx[:10]:
+        i, j, k = v % g["nx"], (v // g["nx"]) % g["ny"], v // (g["nx"] * g["ny"])
+        X = [g["origin"][0] + (i + .5) * g["voxel_size"], g["origin"][1] + (j + .5) * g["voxel_size"],
+             g["origin"][2] + (k + .5) * g["voxel_size"]]
+        for c, cam in enumerate(cams):
+            vis, (px, py), _, _ = oracle.project(cam, X)
+            assert pix[c, v] == (py * cam.width + px if vis else -1)
