@@ -55,6 +55,11 @@ def parse_args(argv=None):
                     help="frames the CPU oracle baseline times (bounded sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fuse-config", default=None,
+                    help="lanes_x,warps,voxels_z,staged[,likelihood_ctas]: skip the autotuner")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the per-frame FP32/FP16 forward and forward+backward timings")
+    ap.add_argument("--forms-frames", type=int, default=20)
     ap.add_argument("--workers", type=int, default=min(8, os.cpu_count() or 1),
                     help="processes rendering the synthetic frames")
     return ap.parse_args(argv)
@@ -287,7 +292,11 @@ def run_ours(args):
     h = rec.handle
     # autotuner: pick the fuse tile shape on the first frame (setup, untimed)
     tune_ms = {}
-    psfs.psfs_autotune(h, d_images[0], reps=3, timings=tune_ms)
+    if args.fuse_config:
+        cfg = [int(x) for x in args.fuse_config.split(",")]
+        psfs.psfs_set_fuse_config(h, *cfg)
+    else:
+        psfs.psfs_autotune(h, d_images[0], reps=3, timings=tune_ms)
     fuse_cfg = psfs.psfs_get_fuse_config(h, full=True)
 
     def step():
@@ -375,6 +384,10 @@ def run_ours(args):
                "h2d_bytes_per_step": F * n_pix * 3, "d2h_bytes_per_step": int(d2h / e2e_steps),
                "steps": e2e_steps, "path": "psfs_reconstruct_host per frame (pinned host buffers)"}
 
+    forms = None
+    if not args.no_forms:
+        forms = time_forms(args, sc, d_images, occ, dev, psfs, fuse_cfg)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(sc, min(args.cpu_sample_frames, F))
@@ -396,10 +409,65 @@ def run_ours(args):
                            "likelihood_ctas_per_sm": fuse_cfg[4],
                            "autotune_fuse_us": {"x".join(map(str, k)): round(1e3 * v, 2) for k, v in tune_ms.items()},
                            "launch": "psfs_reconstruct_sequence (2 streams, double-buffered maps)"},
-                "stages": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "stages": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
                 "gpu_launches": sum(v["launches"] for v in stages.values()), "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
+
+
+def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg):
+    """Per-frame device time of the plain FP32 forward, and of forward +
+    adjoint with FP32 and with FP16 maps (the loss is sum (occ - target)^2 with
+    the previous frame's FP32 occupancy as target), CUDA events on the
+    handle's stream.  Also the FP16 forward's occupancy error against FP32."""
+    import torch
+    F = min(args.forms_frames, d_images.shape[0])
+    V = sc.grid.n_voxels
+    n_pix = d_images[0].numel() // 3
+    out = {"frames": F}
+    stream = torch.cuda.Stream(device=dev)
+    for dtype in ("f32", "f16"):
+        with torch.cuda.stream(stream):
+            rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=dtype, stream=stream, device=dev)
+            rec.set_background(torch.from_numpy(sc.mean).to(dev), torch.from_numpy(sc.var).to(dev))
+            psfs.psfs_set_fuse_config(rec.handle, *fuse_cfg[:4])
+            o, lst, cnt = rec.alloc_outputs()
+            d_occ = torch.empty(V, dtype=torch.float32, device=dev)
+            d_slm = torch.empty(n_pix, dtype=torch.float32, device=dev)
+            d_mean = torch.empty(n_pix * 3, dtype=torch.float32, device=dev)
+            d_var = torch.empty(n_pix * 3, dtype=torch.float32, device=dev)
+            err = 0.0
+            for f in range(2):   # warm-up (the torch ops of the loss too: their first launch loads them)
+                rec.reconstruct(d_images[f], (o, lst, cnt))
+                torch.sub(o.view(-1), occ_f32[f], out=d_occ)
+                d_occ.mul_(2.0)
+                psfs.psfs_backward(rec.handle, d_images[f], d_occ, d_slm, d_mean, d_var)
+                err = max(err, float((o.view(-1) - occ_f32[f]).abs().max()))
+            err = 0.0
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            for f in range(F):
+                rec.reconstruct(d_images[f], (o, lst, cnt))
+            e[1].record(stream)
+            for f in range(F):
+                rec.reconstruct(d_images[f], (o, lst, cnt))
+                torch.sub(o.view(-1), occ_f32[max(f - 1, 0)], out=d_occ)
+                d_occ.mul_(2.0)
+                psfs.psfs_backward(rec.handle, d_images[f], d_occ, d_slm, d_mean, d_var)
+            e[2].record(stream)
+            for f in range(min(F, 4)):
+                rec.reconstruct(d_images[f], (o, lst, cnt))
+                err = max(err, float((o.view(-1) - occ_f32[f]).abs().max()))
+        stream.synchronize()
+        assert rec.sync() == psfs.PSFS_OK
+        out[f"{dtype}_forward_us"] = 1e3 * e[0].elapsed_time(e[1]) / F
+        out[f"{dtype}_forward_backward_us"] = 1e3 * e[1].elapsed_time(e[2]) / F
+        if dtype != "f32":
+            out[f"{dtype}_max_abs_occ_diff_vs_f32"] = err
+        rec.close()
+    out["note"] = ("one frame per call (no stream overlap); backward = recomputed maps + voxel pass + "
+                   "per-pixel owner pass + chain rule to SLM, mean, var")
+    return out
 
 
 def main(argv=None):
