@@ -263,6 +263,51 @@ psfs_status psfs_profile_enable(psfs_handle *h, int32_t max_launches);
  * CUDA. */
 psfs_status psfs_profile_read(psfs_handle *h, double *ms, int32_t *launches);
 
+/* ---- Batched persistent launch (no counterpart in the paper, which runs one
+ * frame at a time): many frames, each with its own rig (grid size, camera
+ * count, image size, background: its handle), in one persistent kernel
+ * captured in a CUDA graph.  The kernel interleaves the likelihood chunks of
+ * frame f with the fusion tiles of frame f - 1, so that HBM-bound and
+ * gather-bound work share the SMs; a fusion tile waits (bounded, 1 s, then
+ * PSFS_ERR_TIMEOUT from psfs_batch_sync) for its frame's maps.  Results are
+ * those of psfs_reconstruct on each frame. */
+typedef struct {
+    psfs_handle *handle;     /* the frame's rig; its background must be set;
+                                must outlive the batch                        */
+    const uint8_t *images;   /* device, as psfs_reconstruct                   */
+    float *occupancy;        /* device outputs, as psfs_reconstruct           */
+    uint32_t *voxel_list;
+    uint32_t capacity;
+    uint32_t *count;
+} psfs_frame;
+
+typedef struct psfs_batch psfs_batch;
+
+/* Plans every frame, allocates one map buffer per frame, builds the work
+ * list and captures the graph.  The buffers named in `frames` are fixed: a
+ * run reads whatever they hold when it executes.  All handles must share the
+ * map type and device.  `stream` is where psfs_batch_run enqueues.
+ * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */
+psfs_status psfs_batch_create(const psfs_frame *frames, int32_t n_frames, void *stream, psfs_batch **out);
+
+/* Launches the captured graph (all frames) on the batch's stream. */
+psfs_status psfs_batch_run(psfs_batch *b);
+
+/* Waits for the batch's stream; returns and clears the first device-side
+ * problem (PSFS_ERR_TIMEOUT, PSFS_ERR_CAPACITY) or PSFS_OK. */
+psfs_status psfs_batch_sync(psfs_batch *b);
+
+/* Tile shape of the batch's fusion items (staged must be 0); re-plans and
+ * re-captures. */
+psfs_status psfs_batch_set_config(psfs_batch *b, const psfs_fuse_config *cfg);
+
+/* Autotuner of the batch: times the whole graph for each of the 6 direct
+ * tile shapes (candidate order lanes_x 8, 16, 32 x voxels_z 8, 16; times in
+ * candidate_ms[6] if not NULL), keeps the fastest. */
+psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *best, float *candidate_ms);
+
+void psfs_batch_destroy(psfs_batch *b);
+
 /* Largest n_cams * height * width that psfs_reconstruct_noalloc accepts. */
 #define PSFS_NOALLOC_MAX_PIXELS (4 * 1024 * 1024)
 

@@ -24,6 +24,13 @@ from .psfs import (  # noqa: F401
     load,
     FUSE_CONFIGS,
     psfs_autotune,
+    BATCH_CONFIGS,
+    psfs_batch_autotune,
+    psfs_batch_create,
+    psfs_batch_destroy,
+    psfs_batch_run,
+    psfs_batch_set_config,
+    psfs_batch_sync,
     psfs_backward,
     psfs_backward_slm,
     psfs_get_fuse_config,

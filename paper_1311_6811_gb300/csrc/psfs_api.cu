@@ -907,3 +907,296 @@ psfs_status psfs_profile_read(psfs_handle *h, double *ms, int32_t *launches)
 void psfs_destroy(psfs_handle *h) { free_handle(h); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched persistent launch over many frames (form of the hot path with no
+// counterpart in the paper, which runs one frame at a time)
+// ---------------------------------------------------------------------------
+struct psfs_batch {
+    int device = 0;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int map_dtype = PSFS_MAP_F32;
+    std::vector<psfs_frame> frames;
+    FuseShape shape = kDefaultFuseShape;
+    BatchFrame *d_frames = nullptr;
+    uint64_t *d_items = nullptr;
+    int64_t n_items = 0;
+    uint32_t *d_words = nullptr;   // [0] status, [16 ...] per-frame done counters
+    uint32_t *h_words = nullptr;
+    std::vector<void *> maps;
+    std::vector<uint64_t *> tiles;
+    std::vector<int4 *> tilecam;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int blocks = 0;
+};
+
+namespace {
+
+void batch_free_plan(psfs_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    for (auto p : b->tiles) cudaFree(p);
+    for (auto p : b->tilecam) cudaFree(p);
+    b->tiles.clear();
+    b->tilecam.clear();
+    cudaFree(b->d_frames);
+    cudaFree(b->d_items);
+    b->d_frames = nullptr;
+    b->d_items = nullptr;
+}
+
+void batch_free(psfs_batch *b)
+{
+    if (!b) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
+    cudaStreamSynchronize(b->user_stream);
+    batch_free_plan(b);
+    for (auto p : b->maps) cudaFree(p);
+    cudaFree(b->d_words);
+    cudaFreeHost(b->h_words);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaSetDevice(prev);
+    delete b;
+}
+
+// Plans every frame for `shape`, builds the interleaved work list, uploads the
+// descriptors and captures [zero the counters, batched kernel] in a graph.
+psfs_status batch_build(psfs_batch *b, const FuseShape &shape)
+{
+    batch_free_plan(b);
+    const int F = (int)b->frames.size();
+    std::vector<BatchFrame> hf(F);
+    std::vector<uint32_t> n_chunks(F), n_tiles(F);
+    for (int f = 0; f < F; ++f) {
+        const psfs_frame &fr = b->frames[f];
+        psfs_handle *h = fr.handle;
+        std::vector<uint64_t> tiles;
+        std::vector<int4> tilecam;
+        FuseArgs fa;
+        plan_fuse(h->grid, h->cams.data(), h->n_cams, h->params, shape, &fa, &tiles, &tilecam);
+        uint64_t *dt = nullptr;
+        int4 *dtc = nullptr;
+        if (cudaMalloc(&dt, tiles.size() * sizeof(uint64_t)) != cudaSuccess ||
+            cudaMalloc(&dtc, tilecam.size() * sizeof(int4)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(dt);
+            return fail(PSFS_ERR_NOMEM, "batch plan allocation");
+        }
+        b->tiles.push_back(dt);
+        b->tilecam.push_back(dtc);
+        PSFS_CK(cudaMemcpy(dt, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+        PSFS_CK(cudaMemcpy(dtc, tilecam.data(), tilecam.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        fa.maps = b->maps[f];
+        fa.tiles = dt;
+        fa.tilecam = dtc;
+        fa.occ = fr.occupancy;
+        fa.list = fr.voxel_list;
+        fa.capacity = fr.capacity;
+        fa.count = fr.count;
+        fa.status = b->d_words;
+        BatchFrame &bf = hf[f];
+        std::memset(&bf, 0, sizeof(bf));
+        bf.fa = fa;
+        bf.img = fr.images;
+        bf.mean = h->bg_mean;
+        bf.hinv = h->bg_hinv;
+        bf.n_pix = h->n_pix;
+        bf.n_chunks = (uint32_t)((h->n_pix + kBatchChunk - 1) / kBatchChunk);
+        bf.c0 = h->c0;
+        bf.sc = h->sc;
+        n_chunks[f] = bf.n_chunks;
+        n_tiles[f] = (uint32_t)fa.n_tiles;
+    }
+    // work list: chunks of frame f interleaved with tiles of frame f - 1
+    std::vector<uint64_t> items;
+    for (int f = 0; f <= F; ++f) {
+        const uint64_t nc = f < F ? n_chunks[f] : 0, nt = f > 0 ? n_tiles[f - 1] : 0;
+        uint64_t ci = 0, ti = 0;
+        while (ci < nc || ti < nt) {
+            // take a chunk while chunks are ahead of tiles in proportion
+            const bool take_chunk = ti >= nt || (ci < nc && ci * nt <= ti * nc);
+            if (take_chunk) items.push_back(pack_item((uint32_t)f, 0, ci++));
+            else items.push_back(pack_item((uint32_t)(f - 1), 1, ti++));
+        }
+    }
+    b->n_items = (int64_t)items.size();
+    if (cudaMalloc(&b->d_frames, hf.size() * sizeof(BatchFrame)) != cudaSuccess ||
+        cudaMalloc(&b->d_items, std::max<size_t>(1, items.size()) * sizeof(uint64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PSFS_ERR_NOMEM, "batch descriptor allocation");
+    }
+    PSFS_CK(cudaMemcpy(b->d_frames, hf.data(), hf.size() * sizeof(BatchFrame), cudaMemcpyHostToDevice));
+    if (!items.empty())
+        PSFS_CK(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    BatchLaunch bl;
+    bl.frames = b->d_frames;
+    bl.items = b->d_items;
+    bl.n_items = b->n_items;
+    bl.done = b->d_words + 16;
+    bl.status = b->d_words;
+    bl.blocks = b->blocks;
+    PSFS_CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(b->d_words + 16, 0, sizeof(uint32_t) * (size_t)F, b->cap_stream);
+    if (e == cudaSuccess) e = launch_batch(bl, shape, b->map_dtype, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail_cuda(e, "batch capture");
+    }
+    if (e2 != cudaSuccess) return fail_cuda(e2, "cudaStreamEndCapture");
+    b->graph = g;
+    PSFS_CK(cudaGraphInstantiate(&b->exec, g, 0));
+    b->shape = shape;
+    return PSFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+psfs_status psfs_batch_create(const psfs_frame *frames, int32_t n_frames, void *stream, psfs_batch **out)
+{
+    if (!out) return fail(PSFS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!frames || n_frames < 1 || n_frames > (1 << 23)) return fail(PSFS_ERR_INVALID_ARG, "frames / n_frames");
+    const int dtype = frames[0].handle ? frames[0].handle->params.map_dtype : -1;
+    for (int f = 0; f < n_frames; ++f) {
+        const psfs_frame &fr = frames[f];
+        if (!fr.handle) return fail(PSFS_ERR_INVALID_ARG, "frame without a handle");
+        if (!fr.handle->bg_ready) return fail(PSFS_ERR_NOT_READY, "a frame's handle has no background");
+        if (fr.handle->params.map_dtype != dtype) return fail(PSFS_ERR_INVALID_ARG, "frames differ in map_dtype");
+        if (!fr.images || !aligned(fr.images, 16)) return fail(PSFS_ERR_INVALID_ARG, "frame images NULL or unaligned");
+        psfs_status st = check_frame_outputs(fr.occupancy, fr.voxel_list, fr.capacity, fr.count);
+        if (st != PSFS_OK) return st;
+        if (fr.handle->device != frames[0].handle->device) return fail(PSFS_ERR_INVALID_ARG, "frames on different devices");
+    }
+    psfs_batch *b = new (std::nothrow) psfs_batch();
+    if (!b) return fail(PSFS_ERR_NOMEM, "host allocation");
+    b->device = frames[0].handle->device;
+    b->user_stream = (cudaStream_t)stream;
+    b->map_dtype = dtype;
+    b->frames.assign(frames, frames + n_frames);
+    DeviceGuard guard(b->device);
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&b->d_words, sizeof(uint32_t) * (16 + (size_t)n_frames)) != cudaSuccess ||
+        cudaMallocHost(&b->h_words, sizeof(uint32_t) * 16) != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return fail(PSFS_ERR_NOMEM, "batch allocation");
+    }
+    cudaMemset(b->d_words, 0, sizeof(uint32_t) * (16 + (size_t)n_frames));
+    const size_t elem = dtype == PSFS_MAP_F32 ? 4 : 2;
+    for (int f = 0; f < n_frames; ++f) {
+        void *m = nullptr;
+        if (cudaMalloc(&m, (size_t)frames[f].handle->n_pix * elem) != cudaSuccess) {
+            cudaGetLastError();
+            batch_free(b);
+            return fail(PSFS_ERR_NOMEM, "batch map buffers");
+        }
+        b->maps.push_back(m);
+    }
+    psfs_status st = batch_build(b, frames[0].handle->shape.staged ? kDefaultFuseShape : frames[0].handle->shape);
+    if (st != PSFS_OK) {
+        batch_free(b);
+        return st;
+    }
+    *out = b;
+    return PSFS_OK;
+}
+
+psfs_status psfs_batch_run(psfs_batch *b)
+{
+    if (!b) return fail(PSFS_ERR_INVALID_ARG, "batch is NULL");
+    DeviceGuard guard(b->device);
+    PSFS_CK(cudaGraphLaunch(b->exec, b->user_stream));
+    return PSFS_OK;
+}
+
+psfs_status psfs_batch_sync(psfs_batch *b)
+{
+    if (!b) return fail(PSFS_ERR_INVALID_ARG, "batch is NULL");
+    DeviceGuard guard(b->device);
+    PSFS_CK(cudaMemcpyAsync(b->h_words, b->d_words, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->user_stream));
+    PSFS_CK(cudaMemsetAsync(b->d_words, 0, sizeof(uint32_t), b->user_stream));
+    PSFS_CK(cudaStreamSynchronize(b->user_stream));
+    const uint32_t w = b->h_words[0];
+    if (w & kStatusTimeout) return fail(PSFS_ERR_TIMEOUT, "a batched work item timed out waiting for its frame");
+    if (w & kStatusCapacity) return fail(PSFS_ERR_CAPACITY, "voxel list capacity exceeded");
+    return PSFS_OK;
+}
+
+psfs_status psfs_batch_set_config(psfs_batch *b, const psfs_fuse_config *cfg)
+{
+    if (!b || !cfg) return fail(PSFS_ERR_INVALID_ARG, "NULL argument");
+    const FuseShape shape = {cfg->lanes_x, cfg->warps, cfg->voxels_z, 0};
+    if (!fuse_shape_supported(shape) || cfg->staged != 0)
+        return fail(PSFS_ERR_INVALID_ARG, "unsupported batch tile shape (staged is not available in a batch)");
+    DeviceGuard guard(b->device);
+    PSFS_CK(cudaStreamSynchronize(b->user_stream));
+    return batch_build(b, shape);
+}
+
+psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *best, float *candidate_ms)
+{
+    if (!b || reps < 1) return fail(PSFS_ERR_INVALID_ARG, "batch NULL or reps < 1");
+    DeviceGuard guard(b->device);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PSFS_CK(cudaEventCreate(&e0));
+    PSFS_CK(cudaEventCreate(&e1));
+    const int lxs[3] = {8, 16, 32}, tzs[2] = {8, 16};
+    FuseShape best_shape = b->shape;
+    float best_ms = 1e30f;
+    psfs_status st = PSFS_OK;
+    for (int cand = 0; cand < 6 && st == PSFS_OK; ++cand) {
+        const FuseShape shape = {lxs[cand / 2], 4, tzs[cand % 2], 0};
+        if (cudaStreamSynchronize(b->user_stream) != cudaSuccess) {
+            st = fail(PSFS_ERR_CUDA, "batch autotune sync");
+            break;
+        }
+        st = batch_build(b, shape);
+        if (st != PSFS_OK) break;
+        cudaError_t err = cudaGraphLaunch(b->exec, b->user_stream);   // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(e0, b->user_stream);
+        for (int r = 0; r < reps && err == cudaSuccess; ++r) err = cudaGraphLaunch(b->exec, b->user_stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, b->user_stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) {
+            st = fail_cuda(err, "batch autotune timing");
+            break;
+        }
+        if (candidate_ms) candidate_ms[cand] = ms / (float)reps;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_shape = shape;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PSFS_OK) return st;
+    st = batch_build(b, best_shape);
+    if (st != PSFS_OK) return st;
+    cudaMemsetAsync(b->d_words, 0, sizeof(uint32_t), b->user_stream);
+    if (best) {
+        best->lanes_x = best_shape.lx;
+        best->warps = best_shape.wy;
+        best->voxels_z = best_shape.tz;
+        best->staged = 0;
+        best->seq_likelihood_ctas = 0;
+    }
+    return PSFS_OK;
+}
+
+void psfs_batch_destroy(psfs_batch *b) { batch_free(b); }
+
+}  // extern "C"

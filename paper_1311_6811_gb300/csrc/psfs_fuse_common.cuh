@@ -95,7 +95,16 @@ __device__ __forceinline__ void tile_epilogue(const FuseArgs &a, int i, int j, i
 // One camera's contribution to the TZ voxels of a thread, gathering from
 // global memory.  `inside`: the host proved every voxel centre of the tile is
 // in front of the camera and inside the image, so no test is made.
-template <typename MapT, int TZ>
+// kCoherent: load the maps through the coherent path (maps written by other
+// CTAs of the same kernel).
+template <typename MapT, int TZ, bool kCoherent = false>
+__device__ __forceinline__ float gather_load(const MapT *p)
+{
+    if (kCoherent) return map_load_coherent(p);
+    return map_load<MapT>(p);
+}
+
+template <typename MapT, int TZ, bool kCoherent = false>
 __device__ __forceinline__ void gather_global(const float *m, float bu, float bv, float bw, const float *fk,
                                               const MapT *map, uint32_t W, uint32_t H, bool inside, float *L)
 {
@@ -107,13 +116,14 @@ __device__ __forceinline__ void gather_global(const float *m, float bu, float bv
         for (int t = 0; t < TZ; ++t) {
             const Proj p = project_biased(m, bu, bv, bw, fk[t]);
             // the host proved the pixel lies in the image; min() only guards the buffer
-            L[t] += map_load<MapT>(map + min(p.by * W + p.bx + bias_off, last_pix));
+            L[t] += gather_load<MapT, TZ, kCoherent>(map + min(p.by * W + p.bx + bias_off, last_pix));
         }
     } else {
 #pragma unroll
         for (int t = 0; t < TZ; ++t) {
             int pix;
-            if (proj_pixel(project_biased(m, bu, bv, bw, fk[t]), W, H, &pix)) L[t] += map_load<MapT>(map + pix);
+            if (proj_pixel(project_biased(m, bu, bv, bw, fk[t]), W, H, &pix))
+                L[t] += gather_load<MapT, TZ, kCoherent>(map + pix);
         }
     }
 }

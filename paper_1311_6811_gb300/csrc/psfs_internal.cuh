@@ -276,6 +276,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Map loads through the coherent path, for maps written earlier in the same
+// kernel by other CTAs (the batched kernel); map_load below uses the
+// read-only path, valid when the maps come from an earlier kernel.
+__device__ __forceinline__ float map_load_coherent(const float *p) { return *p; }
+__device__ __forceinline__ float map_load_coherent(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ float map_load_coherent(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
 template <typename T>
 __device__ __forceinline__ float map_load(const T *p);
 template <>
@@ -381,6 +388,41 @@ struct BackwardArgs {
 };
 
 cudaError_t launch_backward_voxel(const BackwardArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
+
+// Batched persistent launch (psfs_batch.cu).  One kernel walks a list of work
+// items over many frames, each frame with its own grid, cameras and
+// background: likelihood chunks (kind 0) and fusion tiles (kind 1).  A fusion
+// tile of frame f waits until every chunk of frame f is done (per-frame
+// counter); items are ordered so that every item depends only on items with
+// smaller indices, so the persistent grid always makes progress.
+struct BatchFrame {
+    FuseArgs fa;            // grid, cameras, tile plan, maps (batch-owned), outputs
+    const uint8_t *img;     // [n_pix][3]
+    const float *mean;      // packed background of the frame's handle
+    const float *hinv;
+    int64_t n_pix;
+    uint32_t n_chunks;
+    float c0;
+    SensorConsts sc;
+};
+
+constexpr int kBatchChunk = 512;   // pixels per likelihood item
+
+__host__ __device__ inline uint64_t pack_item(uint32_t frame, uint32_t kind, uint64_t index)
+{
+    return ((uint64_t)frame << 40) | ((uint64_t)kind << 39) | index;
+}
+
+struct BatchLaunch {
+    const BatchFrame *frames;   // device
+    const uint64_t *items;      // device
+    int64_t n_items;
+    uint32_t *done;             // device, [n_frames] completed chunks (zeroed before the launch)
+    uint32_t *status;
+    int blocks;
+};
+
+cudaError_t launch_batch(const BatchLaunch &b, const FuseShape &shape, int map_dtype, cudaStream_t s);
 void plan_backward_inv(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const FuseArgs &f,
                        PixelInv *inv);
 cudaError_t launch_backward_pixel(const BackwardArgs &a, cudaStream_t s);

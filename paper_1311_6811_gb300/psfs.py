@@ -64,6 +64,11 @@ class psfs_fuse_config(ctypes.Structure):
 FUSE_CONFIGS = [(lx, 4, tz, st) for st in (0, 1) for lx in (8, 16, 32) for tz in (8, 16)]
 
 
+class psfs_frame(ctypes.Structure):
+    _fields_ = [("handle", ctypes.c_void_p), ("images", ctypes.c_void_p), ("occupancy", ctypes.c_void_p),
+                ("voxel_list", ctypes.c_void_p), ("capacity", ctypes.c_uint32), ("count", ctypes.c_void_p)]
+
+
 class PsfsError(RuntimeError):
     def __init__(self, status: int, func: str, message: str):
         self.status = status
@@ -113,6 +118,13 @@ def load(build_if_missing: bool = True):
             "psfs_get_fuse_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
             "psfs_autotune": (st, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(psfs_fuse_config),
                                    ctypes.POINTER(ctypes.c_float)]),
+            "psfs_batch_create": (st, [ctypes.POINTER(psfs_frame), ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
+            "psfs_batch_run": (st, [_vp]),
+            "psfs_batch_sync": (st, [_vp]),
+            "psfs_batch_set_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
+            "psfs_batch_autotune": (st, [_vp, ctypes.c_int32, ctypes.POINTER(psfs_fuse_config),
+                                         ctypes.POINTER(ctypes.c_float)]),
+            "psfs_batch_destroy": (None, [_vp]),
             "psfs_profile_enable": (st, [_vp, ctypes.c_int32]),
             "psfs_profile_read": (st, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
             "psfs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -374,6 +386,64 @@ def psfs_autotune(h: int, images, reps: int = 5, timings: Optional[dict] = None)
         for c, t in zip(FUSE_CONFIGS, ms):
             timings[c] = float(t)
     return cfg.as_tuple()
+
+
+def psfs_batch_create(frames, stream=None) -> int:
+    """`frames`: list of dicts/tuples (handle, images, occupancy, voxel_list,
+    capacity, count) with CUDA tensors; returns the batch (an int pointer)."""
+    import torch
+    arr = (psfs_frame * len(frames))()
+    for n, fr in enumerate(frames):
+        if isinstance(fr, dict):
+            fr = (fr["handle"], fr["images"], fr["occupancy"], fr["voxel_list"], fr["capacity"], fr["count"])
+        h, img, occ, lst, cap, cnt = fr
+        arr[n].handle = h
+        arr[n].images = _dev_ptr(img, "images", torch.uint8)
+        arr[n].occupancy = _dev_ptr(occ, "occupancy", torch.float32)
+        arr[n].voxel_list = _dev_ptr(lst, "voxel_list")
+        arr[n].capacity = int(cap)
+        arr[n].count = _dev_ptr(cnt, "count")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    out = _vp()
+    _check(load().psfs_batch_create(arr, len(frames), _vp(stream), ctypes.byref(out)), "psfs_batch_create")
+    return out.value
+
+
+def psfs_batch_run(b: int):
+    _check(load().psfs_batch_run(b), "psfs_batch_run")
+
+
+def psfs_batch_sync(b: int) -> int:
+    st = load().psfs_batch_sync(b)
+    if st not in (PSFS_OK, PSFS_ERR_CAPACITY):
+        _check(st, "psfs_batch_sync")
+    return st
+
+
+BATCH_CONFIGS = [(lx, 4, tz, 0) for lx in (8, 16, 32) for tz in (8, 16)]
+
+
+def psfs_batch_set_config(b: int, lanes_x: int, warps: int, voxels_z: int):
+    cfg = psfs_fuse_config(lanes_x, warps, voxels_z, 0, 0)
+    _check(load().psfs_batch_set_config(b, ctypes.byref(cfg)), "psfs_batch_set_config")
+
+
+def psfs_batch_autotune(b: int, reps: int = 3, timings: Optional[dict] = None) -> tuple:
+    cfg = psfs_fuse_config()
+    ms = (ctypes.c_float * len(BATCH_CONFIGS))()
+    _check(load().psfs_batch_autotune(b, int(reps), ctypes.byref(cfg), ms), "psfs_batch_autotune")
+    if timings is not None:
+        for c, t in zip(BATCH_CONFIGS, ms):
+            timings[c] = float(t)
+    return cfg.as_tuple()
+
+
+def psfs_batch_destroy(b: int):
+    if b:
+        load().psfs_batch_destroy(b)
 
 
 PSFS_N_STAGES = 8
