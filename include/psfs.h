@@ -170,6 +170,16 @@ psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const ui
                                       float *occupancy, uint32_t *voxel_lists, uint32_t capacity,
                                       uint32_t *counts);
 
+/* Keeps the packed background (24 bytes per pixel) resident in L2 for the
+ * likelihood stage of psfs_reconstruct_sequence (enable = 1), through an L2
+ * access-policy window on the sequence path's own likelihood stream; frames
+ * after the first then read it from L2 instead of HBM.  Raises the
+ * process's persisting-L2 limit (cudaLimitPersistingL2CacheSize) to the
+ * background size if it is lower (capped by the device maximum); the limit
+ * belongs to this process's CUDA context and ends with it.  enable = 0
+ * removes the window.  Errors: INVALID_ARG, NOMEM, CUDA. */
+psfs_status psfs_set_background_l2(psfs_handle *h, int32_t enable);
+
 /* psfs_reconstruct with HOST buffers: copies the images to the device, runs
  * the frame, copies the occupancy, the count and min(count, capacity) list
  * entries back, and synchronises.  Host buffers have the shapes of

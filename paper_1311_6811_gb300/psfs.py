@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
             "psfs_reconstruct": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_reconstruct_host": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_reconstruct_sequence": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+            "psfs_set_background_l2": (st, [_vp, ctypes.c_int32]),
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
             "psfs_backward": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -283,6 +284,10 @@ def psfs_reconstruct_sequence(h: int, n_frames: int, images, occupancy, voxel_li
                                             _dev_ptr(occupancy, "occupancy", torch.float32),
                                             _dev_ptr(voxel_lists, "voxel_lists"), int(capacity),
                                             _dev_ptr(counts, "counts")), "psfs_reconstruct_sequence")
+
+
+def psfs_set_background_l2(h: int, enable: bool = True):
+    _check(load().psfs_set_background_l2(h, int(bool(enable))), "psfs_set_background_l2")
 
 
 def psfs_reconstruct_host(h: int, images, occupancy, voxel_list, capacity: int, count) -> int:

@@ -280,7 +280,8 @@ def test_sequence_equals_frame_by_frame():
     occ = torch.empty((F, V), dtype=torch.float32, device="cuda")
     lists = torch.empty((F, cap), dtype=torch.int32, device="cuda")
     counts = torch.zeros((F,), dtype=torch.int32, device="cuda")
-    for lk in (1, 2, 4):
+    for lk, l2 in ((1, False), (2, True), (4, False)):
+        psfs.psfs_set_background_l2(rec.handle, l2)
         cfg = psfs.psfs_get_fuse_config(rec.handle)
         psfs.psfs_set_fuse_config(rec.handle, *cfg, seq_likelihood_ctas=lk)
         psfs.psfs_reconstruct_sequence(rec.handle, F, imgs, occ, lists, cap, counts)
