@@ -102,6 +102,11 @@ bool finite_all(const double *v, int n)
     return true;
 }
 
+// Floats of each half (mean, then 1 / (2 var)) of the background
+// allocation: 3 per pixel rounded up to 256 bytes, so that the second half
+// starts on a boundary the bulk copies accept (16 bytes) with room to spare.
+size_t bg_half_floats(size_t n_pix) { return (n_pix * 3 + 63) / 64 * 64; }
+
 psfs_status check_params(const psfs_params *p)
 {
     if (!p) return fail(PSFS_ERR_INVALID_ARG, "params is NULL");
@@ -357,14 +362,14 @@ psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t 
     DeviceGuard guard(h->device);
     const size_t pix_bytes = (size_t)h->n_pix;
     if (cudaMalloc(&h->maps, pix_bytes * h->map_elem) != cudaSuccess ||
-        cudaMalloc(&h->bg_mean, pix_bytes * 6 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&h->bg_mean, (bg_half_floats(pix_bytes) * 2) * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&h->d_words, 16 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&h->h_words, 16 * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         free_handle(h);
         return fail(PSFS_ERR_NOMEM, "device scratch allocation");
     }
-    h->bg_hinv = h->bg_mean + pix_bytes * 3;
+    h->bg_hinv = h->bg_mean + bg_half_floats(pix_bytes);
     e = cudaMemset(h->d_words, 0, 16 * sizeof(uint32_t));
     if (e != cudaSuccess) {
         free_handle(h);
@@ -459,7 +464,7 @@ static psfs_status apply_l2_window(psfs_handle *h)
         int max_win = 0, max_persist = 0;
         PSFS_CK(cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, h->device));
         PSFS_CK(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, h->device));
-        const size_t bytes = (size_t)h->n_pix * 6 * sizeof(float);
+        const size_t bytes = bg_half_floats((size_t)h->n_pix) * 2 * sizeof(float);
         size_t limit = 0;
         PSFS_CK(cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize));
         const size_t want = std::min(bytes, (size_t)max_persist);

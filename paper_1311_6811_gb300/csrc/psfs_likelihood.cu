@@ -180,6 +180,8 @@ cudaError_t launch_likelihood_typed(const LikelihoodArgs &a, cudaStream_t s, int
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
+    // bulk copies need 16-byte aligned sources: refuse rather than fault
+    if (((uintptr_t)a.img | (uintptr_t)a.mean | (uintptr_t)a.hinv) & 15u) return cudaErrorMisalignedAddress;
     const int64_t n_tma_pix = a.n_pix / 16 * 16;
     const int64_t n_chunks = (n_tma_pix + kLkChunk - 1) / kLkChunk;
     ctas_per_sm = std::max(1, std::min(ctas_per_sm, kLkCtasPerSm));
