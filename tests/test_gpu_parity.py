@@ -294,3 +294,21 @@ def test_sequence_equals_frame_by_frame():
             np.testing.assert_array_equal(psfs.voxel_list(lists[f], counts[f:f + 1], cap).numpy(),
                                           psfs.voxel_list(l1, c1, rec.capacity).numpy())
     rec.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_256cube_16cam_1280x720_two_bodies(dtype):
+    """Full-size 256^3 x 16 cameras x 1280x720, two bodies (one partly
+    occluding the other): FP32 maps meet the parity tolerances; FP16 / BF16
+    maps report their error against FP64 (max, mean |docc| and the
+    occupied-set Hamming distance) under loose sanity bounds."""
+    sc = S.scene_256cube_16cam(seed=2)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    got = gpu_reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params, map_dtype=dtype)
+    rep = compare(got, ref, exact=(dtype == "f32"))
+    print(dtype, rep)
+    assert ref["list"].size > 50000
+    if dtype != "f32":
+        assert rep["max_abs_err"] < (5e-3 if dtype == "f16" else 5e-2)
+        assert rep["set_diff"] < 0.01 * ref["list"].size
