@@ -50,13 +50,15 @@ __device__ __forceinline__ void store1<__nv_bfloat16>(__nv_bfloat16 *out, int64_
 }
 
 constexpr int kLkChunk = 512;                       // pixels per chunk (multiple of 16)
-constexpr int kLkStages = 4;
-constexpr int kLkThreads = 256;
 constexpr int kLkImgBytes = 3 * kLkChunk;             // 1536
 constexpr int kLkBgBytes = 12 * kLkChunk;             // 6144 (3 floats per pixel)
 constexpr int kLkStageBytes = kLkImgBytes + 2 * kLkBgBytes;
-constexpr int kLkSmemBytes = kLkStages * kLkStageBytes + kLkStages * 8;
 constexpr int kLkCtasPerSm = 4;                     // at most 4 x 55 KB of shared memory per SM
+// Two shapes: 256 threads with a 4-stage ring (2 to 4 CTAs per SM), or one
+// CTA per SM of 512 threads with a 6-stage ring (83 KB in flight), which
+// leaves most of the SM to fusion CTAs of another frame on the sequence path.
+template <int kStages>
+constexpr int lk_smem_bytes() { return kStages * kLkStageBytes + kStages * 8; }
 
 template <typename OutT, bool kSlm>
 __device__ __forceinline__ void likelihood_pixel(const LikelihoodArgs &a, OutT *out, int64_t p, float i0,
@@ -69,7 +71,7 @@ __device__ __forceinline__ void likelihood_pixel(const LikelihoodArgs &a, OutT *
 // n_tma_pix = n_pix rounded down to 16 pixels (48 image bytes), so every
 // bulk copy has a size and offsets that are multiples of 16 bytes; the last
 // < 16 pixels are read with plain loads by CTA 0.
-template <typename OutT, bool kSlm>
+template <typename OutT, bool kSlm, int kLkThreads, int kLkStages>
 __global__ void __launch_bounds__(kLkThreads) likelihood_kernel(const LikelihoodArgs a, int64_t n_tma_pix)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -168,27 +170,35 @@ int grid_for(int64_t work, int threads)
     return (int)blocks;
 }
 
-template <typename OutT, bool kSlm>
-cudaError_t launch_likelihood_typed(const LikelihoodArgs &a, cudaStream_t s, int ctas_per_sm)
+template <typename OutT, bool kSlm, int kThreads, int kStages>
+cudaError_t launch_likelihood_shape(const LikelihoodArgs &a, cudaStream_t s, int ctas_per_sm)
 {
-    auto kern = likelihood_kernel<OutT, kSlm>;
+    auto kern = likelihood_kernel<OutT, kSlm, kThreads, kStages>;
+    constexpr int smem = lk_smem_bytes<kStages>();
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !configured[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kLkSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
-    // bulk copies need 16-byte aligned sources: refuse rather than fault
-    if (((uintptr_t)a.img | (uintptr_t)a.mean | (uintptr_t)a.hinv) & 15u) return cudaErrorMisalignedAddress;
     const int64_t n_tma_pix = a.n_pix / 16 * 16;
     const int64_t n_chunks = (n_tma_pix + kLkChunk - 1) / kLkChunk;
-    ctas_per_sm = std::max(1, std::min(ctas_per_sm, kLkCtasPerSm));
     int64_t blocks = std::min<int64_t>(n_chunks, ctas_per_sm * (int64_t)sm_count());
     if (blocks < 1) blocks = 1;
-    kern<<<(int)blocks, kLkThreads, kLkSmemBytes, s>>>(a, n_tma_pix);
+    kern<<<(int)blocks, kThreads, smem, s>>>(a, n_tma_pix);
     return cudaGetLastError();
+}
+
+template <typename OutT, bool kSlm>
+cudaError_t launch_likelihood_typed(const LikelihoodArgs &a, cudaStream_t s, int ctas_per_sm)
+{
+    // bulk copies need 16-byte aligned sources: refuse rather than fault
+    if (((uintptr_t)a.img | (uintptr_t)a.mean | (uintptr_t)a.hinv) & 15u) return cudaErrorMisalignedAddress;
+    ctas_per_sm = std::max(1, std::min(ctas_per_sm, kLkCtasPerSm));
+    if (ctas_per_sm == 1) return launch_likelihood_shape<OutT, kSlm, 512, 6>(a, s, 1);
+    return launch_likelihood_shape<OutT, kSlm, 256, 4>(a, s, ctas_per_sm);
 }
 
 }  // namespace
