@@ -50,16 +50,49 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
     __syncthreads();
 
     const MapT *maps = reinterpret_cast<const MapT *>(a.maps);
-    for (int c = 0; c < a.n_cams; ++c) {
+    const uint32_t last_pix = W * H - 1u;
+    const uint32_t bias_off = 0u - (kFloorBias * W + kFloorBias);
+    int c = 0;
+    while (c < a.n_cams) {
         const int flags = s_flags[c];
-        if (flags & kTcSkip) continue;
-        float m[12];
+        const int flags1 = c + 1 < a.n_cams ? s_flags[c + 1] : kTcSkip;
+        if ((flags & kTcInside) && (flags1 & kTcInside)) {
+            // two proven cameras at once: all 2 TZ gathers in flight before
+            // any add; the adds keep the camera order of the sequential sum
+            float m0[12], m1[12];
 #pragma unroll
-        for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
-        float bu, bv, bw;
-        project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
-        gather_global<MapT, TZ>(m, bu, bv, bw, tc.fk, maps + (int64_t)c * a.map_stride, W, H,
-                                (flags & kTcInside) != 0, L);
+            for (int q = 0; q < 12; ++q) {
+                m0[q] = a.cam[c].m[q];
+                m1[q] = a.cam[c + 1].m[q];
+            }
+            float bu0, bv0, bw0, bu1, bv1, bw1;
+            project_base(m0, tc.fi, tc.fj, &bu0, &bv0, &bw0);
+            project_base(m1, tc.fi, tc.fj, &bu1, &bv1, &bw1);
+            const MapT *map0 = maps + (int64_t)c * a.map_stride, *map1 = map0 + a.map_stride;
+            float g0[TZ], g1[TZ];
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) {
+                const Proj p0 = project_biased(m0, bu0, bv0, bw0, tc.fk[t]);
+                const Proj p1 = project_biased(m1, bu1, bv1, bw1, tc.fk[t]);
+                // the host proved both pixels lie in the image; min() only guards the buffer
+                g0[t] = map_load<MapT>(map0 + min(p0.by * W + p0.bx + bias_off, last_pix));
+                g1[t] = map_load<MapT>(map1 + min(p1.by * W + p1.bx + bias_off, last_pix));
+            }
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) L[t] = (L[t] + g0[t]) + g1[t];
+            c += 2;
+            continue;
+        }
+        if (!(flags & kTcSkip)) {
+            float m[12];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
+            float bu, bv, bw;
+            project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
+            gather_global<MapT, TZ>(m, bu, bv, bw, tc.fk, maps + (int64_t)c * a.map_stride, W, H,
+                                    (flags & kTcInside) != 0, L);
+        }
+        ++c;
     }
     tile_epilogue<WY, TZ>(a, tc.i, tc.j, tc.k0, L, lane, wy, s_warp_off, &s_base);
 }
