@@ -36,6 +36,9 @@ struct psfs_handle {
     FuseShape shape = kDefaultFuseShape;
 
     void *maps = nullptr;       // [n_cams][H][W] of g
+    CUtensorMap tm_main[kBoxClasses];   // tensor maps of `maps` (staged kernel)
+    CUtensorMap tm_alt[kBoxClasses];    // tensor maps of `maps2` (sequence path)
+    bool tm_main_ok = false, tm_alt_ok = false;
     float *bg_mean = nullptr;   // [n_pix][3]  } one allocation, so that one L2
     float *bg_hinv = nullptr;   // [n_pix][3]  } access window covers both
     bool bg_l2 = false;         // keep the background resident in L2 (sequence path)
@@ -269,6 +272,8 @@ psfs_status replan(psfs_handle *h, const FuseShape &shape)
     f.tiles = h->tiles;
     f.tilecam = h->tilecam;
     f.status = h->d_words;
+    f.tmap_ok = h->tm_main_ok ? 1 : 0;
+    for (int k = 0; k < kBoxClasses; ++k) f.tmap[k] = h->tm_main[k];
     h->fuse = f;
     h->n_tiles = f.n_tiles;
     h->shape = shape;
@@ -370,6 +375,7 @@ psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t 
         return fail(PSFS_ERR_NOMEM, "device scratch allocation");
     }
     h->bg_hinv = h->bg_mean + bg_half_floats(pix_bytes);
+    h->tm_main_ok = encode_map_tensors(h->maps, params->map_dtype, W, H, n_cams, h->tm_main);
     e = cudaMemset(h->d_words, 0, 16 * sizeof(uint32_t));
     if (e != cudaSuccess) {
         free_handle(h);
@@ -486,6 +492,7 @@ static psfs_status seq_setup(psfs_handle *h)
         cudaGetLastError();
         return fail(PSFS_ERR_NOMEM, "second map buffer");
     }
+    h->tm_alt_ok = encode_map_tensors(h->maps2, h->params.map_dtype, h->W, h->H, h->n_cams, h->tm_alt);
     for (int n = 0; n < 2; ++n) {
         PSFS_CK(cudaStreamCreateWithFlags(&h->seq_stream[n], cudaStreamNonBlocking));
         PSFS_CK(cudaEventCreateWithFlags(&h->seq_ev_map[n], cudaEventDisableTiming));
@@ -533,6 +540,10 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
         fill_fuse_args(h, occupancy + (size_t)f * occ_stride, voxel_lists + (size_t)f * list_stride, capacity,
                        counts + (size_t)f * count_stride, &fa);
         fa.maps = bufs[b];
+        if (b == 1) {
+            fa.tmap_ok = h->tm_alt_ok ? 1 : 0;
+            for (int k = 0; k < kBoxClasses; ++k) fa.tmap[k] = h->tm_alt[k];
+        }
         {
             ProfScope ps(h, PSFS_STAGE_FUSE, sf);
             PSFS_CK(launch_fuse(fa, h->shape, h->params.map_dtype, sf));
@@ -1038,6 +1049,7 @@ psfs_status batch_build(psfs_batch *b, const FuseShape &shape)
         PSFS_CK(cudaMemcpy(dt, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
         PSFS_CK(cudaMemcpy(dtc, tilecam.data(), tilecam.size() * sizeof(int4), cudaMemcpyHostToDevice));
         fa.maps = b->maps[f];
+        fa.tmap_ok = 0;   // batched items gather from global memory
         fa.tiles = dt;
         fa.tilecam = dtc;
         fa.occ = fr.occupancy;

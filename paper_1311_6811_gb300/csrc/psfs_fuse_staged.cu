@@ -4,14 +4,15 @@
 // A persistent grid (three CTAs per SM) walks its tiles round-robin; for each
 // tile it visits the cameras in order.  Every (tile, camera) step has an
 // image box planned on the host (the pixels its voxel centres project into,
-// 16-byte aligned rows).  One thread copies the box of step s + 2 into one of
-// two shared-memory buffers with one bulk copy (TMA) per row, signalled on an
-// mbarrier, while all threads gather step s from the other buffer.  A warp's
-// 32 gathers then cost a shared-memory wavefront or two instead of the dozen
-// 32-byte L1 sectors that the same gathers touch in global memory.  Steps whose
-// box does not fit a buffer, or whose camera straddles the image border
-// without a proof, gather from global memory within the same pipeline; steps
-// whose camera sees nothing of the tile do nothing.
+// 16-byte aligned origin).  One thread copies the box of step s + 2 into one
+// of two shared-memory buffers as a few tensor-map boxes (TMA: 16 rows of 32,
+// 64 or 128 elements each, stacked so that the buffer is a dense
+// [rows][box width] array), signalled on an mbarrier, while all threads
+// gather step s from the other buffer.  A warp's 32 gathers then cost a
+// shared-memory wavefront or two instead of the dozen 32-byte L1 sectors that
+// the same gathers touch in global memory.  Steps whose box is too wide or
+// too tall for a buffer gather from global memory within the same pipeline;
+// steps whose camera sees nothing of the tile do nothing.
 #include <algorithm>
 
 #include "psfs_fuse_common.cuh"
@@ -32,7 +33,9 @@ __device__ __forceinline__ float smem_load<__nv_bfloat16>(const __nv_bfloat16 *p
 template <typename MapT, int LX, int WY, int TZ>
 __global__ void __launch_bounds__(32 * WY) fuse_staged_kernel(const __grid_constant__ FuseArgs a)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // tensor copies land on 128-byte boundaries: round the dynamic window up
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     auto buf = [&](int b) { return reinterpret_cast<MapT *>(smem + b * kStageBytes); };
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * kStageBytes);
     __shared__ uint32_t s_warp_off[WY];
@@ -57,18 +60,20 @@ __global__ void __launch_bounds__(32 * WY) fuse_staged_kernel(const __grid_const
     const int64_t n_steps = my_tiles * K;
 
     // step s: tile blockIdx.x + (s / K) * gridDim.x, camera s % K, buffer s & 1
+    const bool use_tma = a.tmap_ok != 0;
     auto issue = [&](int64_t s) {
         const int b = (int)(s & 1);
         const int64_t tile = (int64_t)blockIdx.x + (s / K) * gridDim.x;
         const int c = (int)(s % K);
         const int4 rec = __ldg(&a.tilecam[tile * K + c]);
         const int flags = rec.w >> 16;
-        if (flags & kTcStaged) {
-            const uint32_t sw = (uint32_t)rec.z, sh = (uint32_t)(rec.w & 0xFFFF);
-            const uint32_t row_bytes = sw * (uint32_t)sizeof(MapT);
-            mbar_arrive_expect_tx(&bars[b], row_bytes * sh);
-            const MapT *src = maps + (int64_t)c * a.map_stride + (int64_t)rec.y * W + rec.x;
-            for (uint32_t r = 0; r < sh; ++r) bulk_g2s(buf(b) + r * sw, src + (int64_t)r * W, row_bytes, &bars[b]);
+        if (use_tma && (flags & kTcStaged)) {
+            const int cls = (rec.z >> 16) & 3, nby = rec.z >> 18;
+            const uint32_t box_bytes = (uint32_t)((32 << cls) * kBoxRows * (int)sizeof(MapT));
+            mbar_arrive_expect_tx(&bars[b], box_bytes * (uint32_t)nby);
+            for (int q = 0; q < nby; ++q)
+                tma_load_3d(reinterpret_cast<unsigned char *>(buf(b)) + (size_t)q * box_bytes, &a.tmap[cls], rec.x,
+                            rec.y + q * kBoxRows, c, &bars[b]);
         } else {
             mbar_arrive(&bars[b]);   // nothing to copy: complete the phase at once
         }
@@ -96,17 +101,19 @@ __global__ void __launch_bounds__(32 * WY) fuse_staged_kernel(const __grid_const
             for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
             float bu, bv, bw;
             project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
-            if (flags & kTcStaged) {
+            if (use_tma && (flags & kTcStaged)) {
                 const MapT *sb = buf(b);
-                const uint32_t sw = (uint32_t)rec.z, sh = (uint32_t)(rec.w & 0xFFFF);
+                // clipped extents; the buffer is [nby * 16 rows][32 << cls]
+                const uint32_t sw = (uint32_t)(rec.z & 0xFFFF), sh = (uint32_t)(rec.w & 0xFFFF);
+                const uint32_t pitch = 32u << ((rec.z >> 16) & 3);
                 const uint32_t ox = kFloorBias + (uint32_t)rec.x, oy = kFloorBias + (uint32_t)rec.y;
                 if (flags & kTcInside) {
                     // the host proved every centre lands in the box; min() only guards the buffer
-                    const uint32_t last = sw * sh - 1u;
+                    const uint32_t last = (uint32_t)(rec.z >> 18) * kBoxRows * pitch - 1u;
 #pragma unroll
                     for (int t = 0; t < TZ; ++t) {
                         const Proj p = project_biased(m, bu, bv, bw, tc.fk[t]);
-                        L[t] += smem_load<MapT>(sb + min((p.by - oy) * sw + (p.bx - ox), last));
+                        L[t] += smem_load<MapT>(sb + min((p.by - oy) * pitch + (p.bx - ox), last));
                     }
                 } else {
                     // the box is the seen part of the tile's footprint, clipped to the image
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(32 * WY) fuse_staged_kernel(const __grid_const
                     for (int t = 0; t < TZ; ++t) {
                         const Proj p = project_biased(m, bu, bv, bw, tc.fk[t]);
                         const uint32_t sx = p.bx - ox, sy = p.by - oy;
-                        if ((sx < sw) & (sy < sh)) L[t] += smem_load<MapT>(sb + sy * sw + sx);
+                        if ((sx < sw) & (sy < sh)) L[t] += smem_load<MapT>(sb + sy * pitch + sx);
                     }
                 }
             } else {
@@ -132,7 +139,7 @@ template <typename MapT, int LX, int TZ>
 cudaError_t launch_typed(const FuseArgs &a, cudaStream_t s)
 {
     auto kern = fuse_staged_kernel<MapT, LX, 4, TZ>;
-    constexpr int smem = 2 * kStageBytes + 16;
+    constexpr int smem = 2 * kStageBytes + 16 + 128;
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);

@@ -17,6 +17,7 @@
 //             L_v > logit(threshold).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (type only; the encoder is fetched through the runtime)
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -71,9 +72,11 @@ struct SlmToMapArgs {
 // double precision from the 8 corner voxel centres of the tile (int4):
 //   x, y   first column (rounded down to a 16-byte boundary) and row of the
 //          image box that the tile's seen voxel centres project into (1 px
-//          margin), clipped to the image
-//   z      box width in map elements (a whole number of 16-byte chunks)
-//   w      box height in rows | flags << 16
+//          margin)
+//   z      width of that box clipped to the image, in map elements
+//          | width class << 16 (tensor-map box width 32 << class)
+//          | number of 16-row boxes << 18
+//   w      height of the box clipped to the image, in rows | flags << 16
 constexpr int kTcStaged = 1;   // the staged kernel copies the box to shared memory
 constexpr int kTcInside = 2;   // every voxel centre of the tile is in front of the
                                // camera and inside the image, with margin for the
@@ -96,8 +99,20 @@ struct FuseArgs {
     uint32_t capacity;
     uint32_t *count;
     uint32_t *status;
+    int tmap_ok;              // the tensor maps below describe `maps`
     CamMat cam[PSFS_MAX_CAMS];
+    // 3-D tensor maps {W, H, n_cams} of `maps` with boxes of (32 << class) x 16
+    // x 1 elements, for the staged kernel
+    CUtensorMap tmap[3];
 };
+
+// Height of one staged box (rows) and the widths of the three box classes.
+constexpr int kBoxRows = 16;
+constexpr int kBoxClasses = 3;
+
+// Encodes the three tensor maps of a [n_cams][H][W] map buffer; false when
+// the rows are not 16-byte aligned or the encoder is unavailable.
+bool encode_map_tensors(void *maps, int map_dtype, int W, int H, int n_cams, CUtensorMap *out);
 
 // Tile shape of the fuse kernel (see psfs_fuse_config): a warp is LX voxels
 // along x by 32 / LX along y, a CTA WY warps along y, TZ voxels per thread
@@ -115,7 +130,8 @@ constexpr FuseShape kDefaultFuseShape = {8, 4, 16, 0};
 bool fuse_shape_supported(const FuseShape &s);
 
 // Shared-memory staging of the staged fusion kernel: two buffers of
-// kStageBytes, three CTAs per SM.
+// kStageBytes (each holds the boxes of one (tile, camera) step), three CTAs
+// per SM.
 constexpr int kStageBytes = 32 * 1024;
 constexpr int kStagedCtasPerSm = 3;
 inline int stage_cap_elems(int map_dtype) { return kStageBytes / (map_dtype == PSFS_MAP_F32 ? 4 : 2); }
@@ -222,6 +238,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+
+// One box of a 3-D tensor map, global -> shared (TMA), completion counted on
+// `bar`.  x must be a multiple of 16 bytes / element size; rows and cameras
+// outside the tensor are filled with zeros.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tmap, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // One bulk copy global -> shared, completion counted on `bar` (bytes and both

@@ -41,7 +41,6 @@ void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, cons
     const int elem = map_dtype == PSFS_MAP_F32 ? 4 : 2;
     const int chunk = 16 / elem;
     const bool can_stage = shape.staged && ((int64_t)W * elem) % 16 == 0;
-    const int64_t cap = stage_cap_elems(map_dtype);
     const double vs = g.voxel_size;
     const double eps32 = std::ldexp(1.0, -24);
     // per camera: magnitude bounds of the float32 projection sums
@@ -107,18 +106,68 @@ void build_tilecam(const psfs_grid &g, const psfs_camera *cams, int n_cams, cons
                 rec.w = kTcSkip << 16;
                 continue;
             }
-            const int64_t ax0 = cx0 / chunk * chunk, ax1 = (cx1 + chunk - 1) / chunk * chunk;
-            const int64_t sw = ax1 - ax0, sh = cy1 - cy0;
-            const bool staged = can_stage && sw * sh <= cap;
+            const int64_t ax0 = cx0 / chunk * chunk;
+            const int64_t sw = cx1 - ax0, sh = cy1 - cy0;   // clipped extents from the box origin
+            int cls = 0;
+            while (cls < kBoxClasses && (32 << cls) < sw) ++cls;
+            const int64_t nby = (sh + kBoxRows - 1) / kBoxRows;
+            const bool staged = can_stage && cls < kBoxClasses &&
+                                (int64_t)(32 << cls) * nby * kBoxRows * elem <= (int64_t)kStageBytes;
             rec.x = (int)ax0;
             rec.y = (int)cy0;
-            rec.z = (int)sw;
+            rec.z = (int)sw | (staged ? (cls << 16) | ((int)nby << 18) : 0);
             rec.w = (int)sh | (((inside ? kTcInside : 0) | (staged ? kTcStaged : 0)) << 16);
         }
     }
 }
 
 }  // namespace
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+bool encode_map_tensors(void *maps, int map_dtype, int W, int H, int n_cams, CUtensorMap *out)
+{
+    const int elem = map_dtype == PSFS_MAP_F32 ? 4 : 2;
+    if (((int64_t)W * elem) % 16 != 0 || ((uintptr_t)maps & 15u)) return false;
+    EncodeTiledFn fn = encoder();
+    if (!fn) return false;
+    const CUtensorMapDataType dt = map_dtype == PSFS_MAP_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : map_dtype == PSFS_MAP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n_cams};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * elem, (cuuint64_t)W * H * elem};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int cls = 0; cls < kBoxClasses; ++cls) {
+        const cuuint32_t box[3] = {(cuuint32_t)(32 << cls), (cuuint32_t)kBoxRows, 1};
+        if (fn(&out[cls], dt, 3, maps, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
 
 bool fuse_shape_supported(const FuseShape &s)
 {

@@ -61,10 +61,11 @@ def _check(driver, grid, cams, map_dtype, tmp_path, shape=(8, 4, 16, 1)):
     assert len(recs) == n_tiles * len(cams)
     seen_tiles = set()
     counts = {"inside": 0, "skip": 0, "checked": 0, "staged": 0}
-    for tc, c, x0, y0, sw, wf in recs:
+    for tc, c, x0, y0, zf, wf in recs:
         tx, ty, tzi = tc & 0x1FFFFF, (tc >> 21) & 0x1FFFFF, tc >> 42
         seen_tiles.add(tc)
         flags, sh = wf >> 16, wf & 0xFFFF
+        sw, cls, nby = zf & 0xFFFF, (zf >> 16) & 3, zf >> 18
         i = np.minimum(tx * TX + np.arange(TX), grid.nx - 1)
         j = np.minimum(ty * TY + np.arange(TY), grid.ny - 1)
         k = np.minimum(tzi * TZ + np.arange(TZ), grid.nz - 1)
@@ -74,6 +75,8 @@ def _check(driver, grid, cams, map_dtype, tmp_path, shape=(8, 4, 16, 1)):
         w = uvw[:, 2]
         with np.errstate(all="ignore"):
             x, y = uvw[:, 0] / w, uvw[:, 1] / w
+        if not flags & STAGED:
+            assert zf >> 16 == 0, (tc, c)
         if flags & SKIP:
             counts["skip"] += 1
             assert not flags & (STAGED | INSIDE)
@@ -84,8 +87,12 @@ def _check(driver, grid, cams, map_dtype, tmp_path, shape=(8, 4, 16, 1)):
         if flags & STAGED:
             counts["staged"] += 1
             assert shape[3] == 1
-            assert x0 >= 0 and y0 >= 0 and x0 % chunk == 0 and sw % chunk == 0, (tc, c)
-            assert x0 + sw <= W and y0 + sh <= H and sw * sh <= cap, (tc, c)
+            # tensor boxes of (32 << cls) x 16 pixels, nby of them stacked, from a
+            # 16-byte aligned column; the clipped extent fits the smallest class
+            assert x0 >= 0 and y0 >= 0 and x0 % chunk == 0, (tc, c)
+            assert x0 + sw <= W and y0 + sh <= H, (tc, c)
+            assert cls < 3 and (32 << cls) >= sw and (cls == 0 or (16 << cls) < sw), (tc, c, sw, cls)
+            assert nby * 16 >= sh > (nby - 1) * 16 and (32 << cls) * nby * 16 <= cap, (tc, c)
             assert np.all(w > 0), (tc, c)
             seen = (x >= 0) & (x < W) & (y >= 0) & (y < H)
             # every seen centre lies at least half a pixel inside the box
