@@ -56,7 +56,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fuse-config", default=None,
-                    help="lanes_x,warps,voxels_z,staged[,likelihood_ctas]: skip the autotuner")
+                    help="lanes_x,warps,voxels_z,staged[,likelihood_ctas[,frames_per_group]]: skip the autotuner")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the per-frame FP32/FP16 forward and forward+backward timings")
     ap.add_argument("--forms-frames", type=int, default=20)
@@ -360,18 +360,28 @@ def run_ours(args):
     ms_per_step = ms / max(args.steps, 1)
     mean_count = float(counts.double().mean().item())
 
-    # roofline of the dominant kernel (algorithmic bytes / average launch time)
+    # roofline of the dominant kernel (algorithmic bytes / average launch time).
+    # The sequence runs in units of G frames (frame groups) plus F mod G single
+    # frames; per unit of nf frames the likelihood reads the background once
+    # (24 B/px), nf images (3 B/px) and writes nf maps, the fusion reads nf maps
+    # and writes nf occupancy grids and lists.
     map_elem = 4 if args.map_dtype == "f32" else 2
-    alg_bytes = {"likelihood": n_pix * (3 + 24 + map_elem),
-                 "fuse": n_pix * map_elem + V * 4 + mean_count * 4}
-    alg_bytes["batch"] = F * (alg_bytes["likelihood"] + alg_bytes["fuse"])
-    kern_names = {"likelihood": "likelihood_kernel", "fuse": "fuse_kernel", "batch": "batch_kernel"}
+    G = fuse_cfg[5] if batch is None else 1
+    units = [G] * (F // G) + [1] * (F % G) if G > 1 else [1] * F
+    fuse_frame_bytes = n_pix * map_elem + V * 4 + mean_count * 4
+    step_bytes = {"likelihood": sum(n_pix * (24 + nf * (3 + map_elem)) for nf in units),
+                  "fuse": F * fuse_frame_bytes,
+                  "batch": F * (n_pix * (3 + 24 + map_elem) + fuse_frame_bytes)}
+    grouped = G > 1
+    kern_names = {"likelihood": "likelihood_group_kernel" if grouped else "likelihood_kernel",
+                  "fuse": "fuse_group_kernel" if grouped else "fuse_kernel", "batch": "batch_kernel"}
     stages = {}
     for name, (t_ms, n) in prof.items():
         avg = t_ms / n
+        per_launch = step_bytes[name] * args.steps / n if name in step_bytes else None
         stages[name] = {"launches": n, "avg_us": 1e3 * avg, "share": None,
-                        "alg_bytes_per_launch": alg_bytes.get(name),
-                        "achieved_gbs": alg_bytes[name] / (avg * 1e-3) / 1e9 if name in alg_bytes else None}
+                        "alg_bytes_per_launch": per_launch,
+                        "achieved_gbs": per_launch / (avg * 1e-3) / 1e9 if per_launch else None}
     tot = sum(v["avg_us"] * v["launches"] for v in stages.values())
     for v in stages.values():
         v["share"] = v["avg_us"] * v["launches"] / tot if tot else None
@@ -432,9 +442,11 @@ def run_ours(args):
                            "fuse_tile": {"lanes_x": fuse_cfg[0], "warps": fuse_cfg[1], "voxels_z": fuse_cfg[2],
                                          "staged": fuse_cfg[3]},
                            "likelihood_ctas_per_sm": fuse_cfg[4],
+                           "frames_per_group": G,
                            "autotune_fuse_us": {"x".join(map(str, k)): round(1e3 * v, 2) for k, v in tune_ms.items()},
                            "launch": ("psfs_batch_run (one persistent kernel, CUDA graph)" if batch is not None
-                                      else "psfs_reconstruct_sequence (2 streams, double-buffered maps)"),
+                                      else f"psfs_reconstruct_sequence (frame groups of {G}: one background pass "
+                                      "and one projection per group; 2 streams, double-buffered maps)"),
                            "background_l2_resident": not args.no_l2_background},
                 "stages": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
                 "gpu_launches": sum(v["launches"] for v in stages.values()), "clocks": clk}

@@ -110,13 +110,24 @@ typedef struct {
  * each tile's image footprint per camera into shared memory (bulk copies,
  * double-buffered) before gathering; 0 gathers from global memory.
  * seq_likelihood_ctas: CTAs per SM of the likelihood grid on the sequence
- * path, 1 to 4 (0 in psfs_set_fuse_config keeps the current value). */
+ * path, 1 to 4 (0 in psfs_set_fuse_config keeps the current value).
+ * frames_per_group: frames per launch on the sequence path: 1 = one frame
+ * per likelihood and fusion launch; 2, 4 or 8 = frame groups, where one
+ * likelihood launch reads the background once for the whole group and writes
+ * the group's maps interleaved per pixel, and one fusion launch projects each
+ * voxel once and gathers all frames of the group with one vector load (each
+ * frame's results are bit-identical to one frame per launch).  Groups need
+ * staged = 0, lanes_x 8 or 16, and voxels_z 8 for 8 frames; with another
+ * shape the sequence path runs one frame per launch.  Trailing frames that do
+ * not fill a group run one per launch.  0 in psfs_set_fuse_config keeps the
+ * current value.  The batch entry points ignore this field. */
 typedef struct {
     int32_t lanes_x;
     int32_t warps;
     int32_t voxels_z;
     int32_t staged;
     int32_t seq_likelihood_ctas;
+    int32_t frames_per_group;
 } psfs_fuse_config;
 
 typedef struct psfs_handle psfs_handle;
@@ -160,12 +171,15 @@ psfs_status psfs_reconstruct(psfs_handle *h, const uint8_t *images, float *occup
 /* psfs_reconstruct over n_frames frames of this rig, one call: frame f reads
  * images + f * (n_cams * height * width * 3) and writes
  * occupancy + f * (nx * ny * nz), voxel_lists + f * capacity and counts[f].
- * The likelihood stage of frame f + 1 runs on a second stream concurrently
- * with the fusion stage of frame f (two map buffers), so that the HBM-bound
- * and the gather-bound kernels overlap; the whole sequence is ordered after
- * earlier work on the handle's stream and later work waits for it.  The frame
- * size in bytes and the voxel count must be multiples of 16 and 4.
- * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */
+ * Frames run in units of frames_per_group frames (psfs_fuse_config; one
+ * likelihood and one fusion launch per unit).  The likelihood stage of unit
+ * u + 1 runs on a second stream concurrently with the fusion stage of unit u
+ * (two map buffers), so that the HBM-bound and the gather-bound kernels
+ * overlap; the whole sequence is ordered after earlier work on the handle's
+ * stream and later work waits for it.  The frame size in bytes and the voxel
+ * count must be multiples of 16 and 4.  The first call with frame groups
+ * allocates two group map buffers (n_cams * height * width * frames_per_group
+ * map elements each).  Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */
 psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
                                       float *occupancy, uint32_t *voxel_lists, uint32_t capacity,
                                       uint32_t *counts);
@@ -233,8 +247,11 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
  * as psfs_reconstruct) with CUDA events, `reps` launches each, keeps the
  * fastest and writes it to *best (may be NULL) and the mean milliseconds of
  * each candidate to candidate_ms[PSFS_N_FUSE_CANDIDATES] (may be NULL; order:
- * staged 0 then 1, lanes_x 8, 16, 32, voxels_z 8 then 16); then times the sequence path
- * with 1 to 4 likelihood CTAs per SM and keeps the fastest.  Both choices are
+ * staged 0 then 1, lanes_x 8, 16, 32, voxels_z 8 then 16); then times the
+ * sequence path on 8 frames with 1 to 4 likelihood CTAs per SM at one frame
+ * per launch, and frame groups of 2, 4 and 8 frames (direct tile shapes,
+ * voxels_z 8 and 16, 1 to 3 likelihood CTAs per SM), and keeps the fastest
+ * sequence configuration (which may change the tile shape).  The choices are
  * remembered for handles of the same grid size, camera count, image size and
  * map type created later in the process.  Allocates and frees its own scratch; waits for the stream.
  * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */

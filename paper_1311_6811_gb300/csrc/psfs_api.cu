@@ -62,6 +62,11 @@ struct psfs_handle {
     cudaEvent_t seq_ev_done[2] = {nullptr, nullptr};
     void *maps2 = nullptr;
     int seq_lk_ctas = 2;
+    // frame groups: frames per group on the sequence path (1 = one frame per
+    // launch) and the two group map buffers [n_pix][group_cap] (first use)
+    int seq_group = 1;
+    void *gmaps[2] = {nullptr, nullptr};
+    int group_cap = 0;
 
     // tracing: CUDA event pairs around each launch
     int prof_cap = 0;
@@ -148,6 +153,8 @@ void free_handle(psfs_handle *h)
     cudaFree(h->dl);
     cudaFree(h->dg);
     cudaFree(h->maps2);
+    cudaFree(h->gmaps[0]);
+    cudaFree(h->gmaps[1]);
     for (int n = 0; n < 2; ++n) {
         if (h->seq_stream[n]) cudaStreamSynchronize(h->seq_stream[n]);
         if (h->seq_stream[n]) cudaStreamDestroy(h->seq_stream[n]);
@@ -212,6 +219,7 @@ psfs_status fill_fuse_args(psfs_handle *h, float *occ, uint32_t *list, uint32_t 
     a->list = list;
     a->capacity = capacity;
     a->count = count;
+    a->occ_fstride = a->list_fstride = a->count_fstride = 0;
     return PSFS_OK;
 }
 
@@ -231,6 +239,7 @@ using TuneKey = std::tuple<int, int, int, int, int, int, int>;
 struct Tuned {
     FuseShape shape;
     int seq_lk_ctas;
+    int seq_group;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, Tuned> g_tuned;
@@ -392,6 +401,7 @@ psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t 
         if (it != g_tuned.end()) {
             shape = it->second.shape;
             h->seq_lk_ctas = it->second.seq_lk_ctas;
+            h->seq_group = it->second.seq_group;
         }
     }
     st = replan(h, shape);
@@ -503,23 +513,57 @@ static psfs_status seq_setup(psfs_handle *h)
     return apply_l2_window(h);
 }
 
+// Group map buffers for `frames` frames per group (waits for the sequence
+// streams before it replaces smaller ones).
+static psfs_status ensure_group_maps(psfs_handle *h, int frames)
+{
+    if (frames <= h->group_cap) return PSFS_OK;
+    PSFS_CK(cudaStreamSynchronize(h->seq_stream[0]));
+    PSFS_CK(cudaStreamSynchronize(h->seq_stream[1]));
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->gmaps[b]);
+        h->gmaps[b] = nullptr;
+    }
+    h->group_cap = 0;
+    for (int b = 0; b < 2; ++b) {
+        if (cudaMalloc(&h->gmaps[b], (size_t)h->n_pix * frames * h->map_elem) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "frame-group map buffers");
+        }
+    }
+    h->group_cap = frames;
+    return PSFS_OK;
+}
+
 // Enqueues n_frames frames with the given element strides between frames
 // (a stride of 0 repeats the same buffer, which only the autotuner does).
+// Frames go in units: groups of `group` frames (likelihood and fusion of the
+// whole group in one launch each) while whole groups remain, then single
+// frames.  Unit u's likelihood (stream 0) writes map buffer u & 1 while the
+// fusion of unit u - 1 (stream 1) reads the other one.
 static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images, size_t img_stride,
                                     float *occupancy, size_t occ_stride, uint32_t *voxel_lists,
                                     size_t list_stride, uint32_t capacity, uint32_t *counts, size_t count_stride,
-                                    int lk_ctas)
+                                    int lk_ctas, int group)
 {
     psfs_status st = seq_setup(h);
     if (st != PSFS_OK) return st;
+    if (group > 1 && !group_shape_supported(h->shape, group)) group = 1;
+    if (group > 1 && n_frames >= group) {
+        st = ensure_group_maps(h, group);
+        if (st != PSFS_OK) return st;
+    }
     cudaStream_t sl = h->seq_stream[0], sf = h->seq_stream[1];
     void *bufs[2] = {h->maps, h->maps2};
     PSFS_CK(cudaEventRecord(h->seq_ev_in, h->stream));
     PSFS_CK(cudaStreamWaitEvent(sl, h->seq_ev_in, 0));
     PSFS_CK(cudaStreamWaitEvent(sf, h->seq_ev_in, 0));
-    for (int f = 0; f < n_frames; ++f) {
-        const int b = f & 1;
-        if (f >= 2) PSFS_CK(cudaStreamWaitEvent(sl, h->seq_ev_fused[b], 0));   // frame f-2 done with buffer b
+    int f = 0;
+    for (int u = 0; f < n_frames; ++u) {
+        const int nf = (group > 1 && n_frames - f >= group) ? group : 1;
+        const int b = u & 1;
+        if (u >= 2) PSFS_CK(cudaStreamWaitEvent(sl, h->seq_ev_fused[b], 0));   // unit u-2 done with buffer b
+        void *buf = nf > 1 ? h->gmaps[b] : bufs[b];
         LikelihoodArgs la{};
         la.img = images + (size_t)f * img_stride;
         la.mean = h->bg_mean;
@@ -527,28 +571,42 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
         la.n_pix = h->n_pix;
         la.c0 = h->c0;
         la.sc = h->sc;
-        la.out = bufs[b];
+        la.out = buf;
         la.zero_word = counts + (size_t)f * count_stride;
         la.status = h->d_words;
+        la.img_fstride = (int64_t)img_stride;
+        la.zero_fstride = (int64_t)count_stride;
         {
             ProfScope ps(h, PSFS_STAGE_LIKELIHOOD, sl);
-            PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, sl, lk_ctas));
+            if (nf > 1)
+                PSFS_CK(launch_likelihood_group(la, nf, h->params.map_dtype, sl, lk_ctas));
+            else
+                PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, sl, lk_ctas));
         }
         PSFS_CK(cudaEventRecord(h->seq_ev_map[b], sl));
         PSFS_CK(cudaStreamWaitEvent(sf, h->seq_ev_map[b], 0));
         FuseArgs fa;
         fill_fuse_args(h, occupancy + (size_t)f * occ_stride, voxel_lists + (size_t)f * list_stride, capacity,
                        counts + (size_t)f * count_stride, &fa);
-        fa.maps = bufs[b];
-        if (b == 1) {
+        fa.maps = buf;
+        if (nf > 1) {
+            fa.tmap_ok = 0;
+            fa.occ_fstride = (int64_t)occ_stride;
+            fa.list_fstride = (int64_t)list_stride;
+            fa.count_fstride = (int64_t)count_stride;
+        } else if (b == 1) {
             fa.tmap_ok = h->tm_alt_ok ? 1 : 0;
             for (int k = 0; k < kBoxClasses; ++k) fa.tmap[k] = h->tm_alt[k];
         }
         {
             ProfScope ps(h, PSFS_STAGE_FUSE, sf);
-            PSFS_CK(launch_fuse(fa, h->shape, h->params.map_dtype, sf));
+            if (nf > 1)
+                PSFS_CK(launch_fuse_group(fa, h->shape, nf, h->params.map_dtype, sf));
+            else
+                PSFS_CK(launch_fuse(fa, h->shape, h->params.map_dtype, sf));
         }
         PSFS_CK(cudaEventRecord(h->seq_ev_fused[b], sf));
+        f += nf;
     }
     PSFS_CK(cudaEventRecord(h->seq_ev_done[0], sl));
     PSFS_CK(cudaEventRecord(h->seq_ev_done[1], sf));
@@ -583,7 +641,7 @@ psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const ui
     DeviceGuard guard(h->device);
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     return enqueue_sequence(h, n_frames, images, (size_t)h->n_pix * 3, occupancy, n_vox, voxel_lists, capacity,
-                            capacity, counts, 1, h->seq_lk_ctas);
+                            capacity, counts, 1, h->seq_lk_ctas, h->seq_group);
 }
 
 psfs_status psfs_reconstruct_host(psfs_handle *h, const uint8_t *h_images, float *h_occupancy,
@@ -786,6 +844,9 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
     if (!fuse_shape_supported(shape)) return fail(PSFS_ERR_INVALID_ARG, "unsupported fuse tile shape");
     if (cfg->seq_likelihood_ctas < 0 || cfg->seq_likelihood_ctas > 4)
         return fail(PSFS_ERR_INVALID_ARG, "seq_likelihood_ctas outside [0, 4]");
+    if (cfg->frames_per_group < 0 || (cfg->frames_per_group > 1 && !group_shape_supported(shape, cfg->frames_per_group)))
+        return fail(PSFS_ERR_INVALID_ARG,
+                    "frames_per_group: 0, 1, or 2 / 4 / 8 with staged 0, lanes_x 8 or 16 (voxels_z 8 for 8 frames)");
     DeviceGuard guard(h->device);
     PSFS_CK(cudaStreamSynchronize(h->stream));
     if (h->seq_stream[0]) {
@@ -793,6 +854,7 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
         PSFS_CK(cudaStreamSynchronize(h->seq_stream[1]));
     }
     if (cfg->seq_likelihood_ctas > 0) h->seq_lk_ctas = cfg->seq_likelihood_ctas;
+    if (cfg->frames_per_group > 0) h->seq_group = cfg->frames_per_group;
     return replan(h, shape);
 }
 
@@ -804,6 +866,7 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg)
     cfg->voxels_z = h->shape.tz;
     cfg->staged = h->shape.staged;
     cfg->seq_likelihood_ctas = h->seq_lk_ctas;
+    cfg->frames_per_group = h->seq_group;
     return PSFS_OK;
 }
 
@@ -816,13 +879,20 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     DeviceGuard guard(h->device);
     const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    // scratch: occupancy of 8 frames, 8 lists of n_vox / 8 entries (the
+    // sequence timings; a frame with more occupied voxels only sets the
+    // capacity bit, cleared below) and 8 counts
+    constexpr int kTuneFrames = 8;
+    const uint32_t seq_cap = (uint32_t)std::max<uint64_t>(1, n_vox / kTuneFrames);
     float *occ = nullptr;
-    uint32_t *list = nullptr;
+    uint32_t *list = nullptr, *tcounts = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaMalloc(&occ, n_vox * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&list, n_vox * sizeof(uint32_t)) != cudaSuccess) {
+    if (cudaMalloc(&occ, kTuneFrames * n_vox * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&list, n_vox * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&tcounts, kTuneFrames * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(occ);
+        cudaFree(list);
         return fail(PSFS_ERR_NOMEM, "autotune scratch");
     }
     psfs_status st = PSFS_OK;
@@ -862,44 +932,72 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
                 best_shape = shape;
             }
     }
-    // second stage: CTAs per SM of the likelihood grid when it shares the GPU
-    // with the fusion of the previous frame (sequence path), timed on 8
-    // repetitions of the frame
-    if (st == PSFS_OK) st = replan(h, best_shape);
-    float best_seq = 1e30f;
-    for (int lk = 1; lk <= 4 && st == PSFS_OK; ++lk) {
-        cudaError_t err = cudaStreamSynchronize(h->stream);
-        st = enqueue_sequence(h, 2, images, 0, occ, 0, list, 0, (uint32_t)n_vox, h->d_words + 3, 0, lk);
-        if (st != PSFS_OK) break;
-        if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
-        for (int r = 0; r < reps && st == PSFS_OK; ++r)
-            st = enqueue_sequence(h, 8, images, 0, occ, 0, list, 0, (uint32_t)n_vox, h->d_words + 3, 0, lk);
-        if (st != PSFS_OK) break;
+    // second stage: the sequence path, timed on 8 frames (distinct outputs,
+    // the same images) per repetition: CTAs per SM of the likelihood grid
+    // (1 to 4) with one frame per launch, then frame groups of 2, 4 and 8
+    // frames with the direct tile shapes that support them
+    auto time_sequence = [&](int lk, int group, float *ms_out) -> psfs_status {
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(PSFS_ERR_CUDA, "autotune sync");
+        psfs_status s2 = enqueue_sequence(h, kTuneFrames, images, 0, occ, n_vox, list, seq_cap, seq_cap, tcounts,
+                                          1, lk, group);   // warm-up (allocates group buffers)
+        if (s2 != PSFS_OK) return s2;
+        cudaError_t err = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && s2 == PSFS_OK && err == cudaSuccess; ++r)
+            s2 = enqueue_sequence(h, kTuneFrames, images, 0, occ, n_vox, list, seq_cap, seq_cap, tcounts, 1, lk,
+                                  group);
+        if (s2 != PSFS_OK) return s2;
         if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
         if (err == cudaSuccess) err = cudaEventSynchronize(e1);
         float ms = 0.0f;
         if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-        if (err != cudaSuccess) {
-            st = fail_cuda(err, "autotune sequence timing");
-            break;
-        }
-        if (ms < best_seq) {
+        if (err != cudaSuccess) return fail_cuda(err, "autotune sequence timing");
+        *ms_out = ms;
+        return PSFS_OK;
+    };
+    if (st == PSFS_OK) st = replan(h, best_shape);
+    float best_seq = 1e30f;
+    int best_group = 1;
+    for (int lk = 1; lk <= 4 && st == PSFS_OK; ++lk) {
+        float ms = 0.0f;
+        st = time_sequence(lk, 1, &ms);
+        if (st == PSFS_OK && ms < best_seq) {
             best_seq = ms;
             h->seq_lk_ctas = lk;
         }
     }
+    const int group_lx = (best_shape.lx == 16) ? 16 : 8;
+    const int groups[3] = {2, 4, 8};
+    for (int gi = 0; gi < 3 && st == PSFS_OK; ++gi) {
+        for (int tz = 8; tz <= 16 && st == PSFS_OK; tz += 8) {
+            const FuseShape gshape = {group_lx, 4, tz, 0};
+            if (!group_shape_supported(gshape, groups[gi])) continue;
+            st = replan(h, gshape);
+            for (int lk = 1; lk <= 3 && st == PSFS_OK; ++lk) {
+                float ms = 0.0f;
+                st = time_sequence(lk, groups[gi], &ms);
+                if (st == PSFS_OK && ms < best_seq) {
+                    best_seq = ms;
+                    best_group = groups[gi];
+                    best_shape = gshape;
+                    h->seq_lk_ctas = lk;
+                }
+            }
+        }
+    }
+    h->seq_group = best_group;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(h->stream);
     cudaFree(occ);
     cudaFree(list);
+    cudaFree(tcounts);
     cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t), h->stream);   // the scratch list never overflows
     if (st != PSFS_OK) return st;
     st = replan(h, best_shape);
     if (st != PSFS_OK) return st;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[tune_key(h)] = Tuned{best_shape, h->seq_lk_ctas};
+        g_tuned[tune_key(h)] = Tuned{best_shape, h->seq_lk_ctas, h->seq_group};
     }
     if (best) psfs_get_fuse_config(h, best);
     return PSFS_OK;

@@ -40,8 +40,9 @@ struct TileCoords {
 // warp, one atomicAdd per CTA on the global count, then each warp writes its
 // indices at its prefix offset.  Contains two __syncthreads.
 template <int WY, int TZ>
-__device__ __forceinline__ void tile_epilogue(const FuseArgs &a, int i, int j, int k0, const float *L, int lane,
-                                              int wy, uint32_t *s_warp_off, uint32_t *s_base)
+__device__ __forceinline__ void tile_epilogue_to(const FuseArgs &a, float *occ, uint32_t *list, uint32_t *count,
+                                                 int i, int j, int k0, const float *L, int lane, int wy,
+                                                 uint32_t *s_warp_off, uint32_t *s_base)
 {
     const bool in_xy = (i < a.nx) && (j < a.ny);
     uint32_t ballots[TZ];
@@ -53,7 +54,7 @@ __device__ __forceinline__ void tile_epilogue(const FuseArgs &a, int i, int j, i
         const float lo = L[t] + a.logit_prior;
         if (valid) {
             const uint32_t lin = (uint32_t)i + (uint32_t)a.nx * ((uint32_t)j + (uint32_t)a.ny * (uint32_t)k);
-            __stcs(a.occ + lin, __fdividef(1.0f, 1.0f + __expf(-lo)));
+            __stcs(occ + lin, __fdividef(1.0f, 1.0f + __expf(-lo)));
         }
         ballots[t] = __ballot_sync(0xFFFFFFFFu, valid && (lo > a.logit_tau));
         warp_count += __popc(ballots[t]);
@@ -70,7 +71,7 @@ __device__ __forceinline__ void tile_epilogue(const FuseArgs &a, int i, int j, i
         }
         uint32_t base = 0;
         if (total) {
-            base = atomicAdd(a.count, total);
+            base = atomicAdd(count, total);
             if ((uint64_t)base + total > (uint64_t)a.capacity) atomicOr(a.status, kStatusCapacity);
         }
         *s_base = base;
@@ -85,11 +86,19 @@ __device__ __forceinline__ void tile_epilogue(const FuseArgs &a, int i, int j, i
             const uint32_t p = pos + __popc(b & lt_mask);
             if (p < a.capacity) {
                 const int k = k0 + t;
-                a.list[p] = (uint32_t)i + (uint32_t)a.nx * ((uint32_t)j + (uint32_t)a.ny * (uint32_t)k);
+                list[p] = (uint32_t)i + (uint32_t)a.nx * ((uint32_t)j + (uint32_t)a.ny * (uint32_t)k);
             }
         }
         pos += __popc(b);
     }
+}
+
+// The epilogue into the frame's own outputs a.occ, a.list, a.count.
+template <int WY, int TZ>
+__device__ __forceinline__ void tile_epilogue(const FuseArgs &a, int i, int j, int k0, const float *L, int lane,
+                                              int wy, uint32_t *s_warp_off, uint32_t *s_base)
+{
+    tile_epilogue_to<WY, TZ>(a, a.occ, a.list, a.count, i, j, k0, L, lane, wy, s_warp_off, s_base);
 }
 
 // One camera's contribution to the TZ voxels of a thread, gathering from

@@ -1,0 +1,407 @@
+// psfs_group.cu -- frame groups of the sequence path.
+//
+// The rig, grid and background are fixed across the frames of a sequence, so
+// F consecutive frames can share the work that does not depend on the image:
+//
+//   * likelihood: one pass over the packed background (24 B per pixel, the
+//     largest input) computes the log ratio g of Eq. 5-9 for all F frames of
+//     the group.  The F maps are written interleaved per pixel,
+//     [n_cams][H][W][F], one F-wide vector store per pixel.
+//   * fusion: each voxel centre is projected into each camera once (Eq. 3)
+//     and one F-wide vector load gathers g of that pixel for all F frames;
+//     every frame keeps its own log-odds accumulator, output grid and list.
+//
+// Per frame and per pixel / voxel the arithmetic is exactly that of the
+// single-frame kernels (the same helper functions, the same camera order of
+// the sum), so each frame's occupancy, list and count are bit-identical to a
+// single-frame reconstruction; the group only removes repeated background
+// reads, projections and load instructions.
+#include <algorithm>
+
+#include "psfs_fuse_common.cuh"
+
+namespace psfs {
+
+namespace {
+
+int group_sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 152;
+    }
+    return cached[dev];
+}
+
+// ---------------------------------------------------------------------------
+// F-wide map vectors
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T to_map(float g);
+template <>
+__device__ __forceinline__ float to_map<float>(float g) { return g; }
+template <>
+__device__ __forceinline__ __half to_map<__half>(float g) { return __float2half_rn(g); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_map<__nv_bfloat16>(float g) { return __float2bfloat16_rn(g); }
+
+template <typename T>
+__device__ __forceinline__ uint32_t map_bits(T v);
+template <>
+__device__ __forceinline__ uint32_t map_bits<float>(float v) { return __float_as_uint(v); }
+template <>
+__device__ __forceinline__ uint32_t map_bits<__half>(__half v) { return __half_as_ushort(v); }
+template <>
+__device__ __forceinline__ uint32_t map_bits<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+
+template <typename T>
+__device__ __forceinline__ float map_value(uint32_t bits);
+template <>
+__device__ __forceinline__ float map_value<float>(uint32_t bits) { return __uint_as_float(bits); }
+template <>
+__device__ __forceinline__ float map_value<__half>(uint32_t bits)
+{
+    return __half2float(__ushort_as_half((unsigned short)bits));
+}
+template <>
+__device__ __forceinline__ float map_value<__nv_bfloat16>(uint32_t bits)
+{
+    return __bfloat162float(__ushort_as_bfloat16((unsigned short)bits));
+}
+
+// Packs F map values into 32-bit words (element e in the low half first for
+// 16-bit types, the little-endian order of a [F] array).
+template <typename T, int F>
+struct GroupWords {
+    static constexpr int kWords = (F * (int)sizeof(T) + 3) / 4;
+    uint32_t w[kWords];
+
+    __device__ __forceinline__ void set(int e, T v)
+    {
+        if (sizeof(T) == 4) {
+            w[e] = map_bits<T>(v);
+        } else {
+            const uint32_t b = map_bits<T>(v) & 0xFFFFu;
+            w[e >> 1] = (e & 1) ? (w[e >> 1] | (b << 16)) : b;
+        }
+    }
+    __device__ __forceinline__ float get(int e) const
+    {
+        if (sizeof(T) == 4) return map_value<T>(w[e]);
+        return map_value<T>((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
+    }
+};
+
+// Vector store / read-only vector load of the F * sizeof(T) bytes of one
+// pixel (4, 8, 16 or 32 bytes; the address is a multiple of that size).
+template <int kWords>
+__device__ __forceinline__ void store_words(uint32_t *dst, const uint32_t *w)
+{
+    if constexpr (kWords == 1) {
+        *dst = w[0];
+    } else if constexpr (kWords == 2) {
+        *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
+    } else {
+        static_assert(kWords % 4 == 0, "group vector of 16-byte words");
+#pragma unroll
+        for (int q = 0; q < kWords; q += 4)
+            *reinterpret_cast<uint4 *>(dst + q) = make_uint4(w[q], w[q + 1], w[q + 2], w[q + 3]);
+    }
+}
+
+template <int kWords>
+__device__ __forceinline__ void load_words(const uint32_t *src, uint32_t *w)
+{
+    if constexpr (kWords == 1) {
+        w[0] = __ldg(src);
+    } else if constexpr (kWords == 2) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(src));
+        w[0] = v.x;
+        w[1] = v.y;
+    } else {
+        static_assert(kWords % 4 == 0, "group vector of 16-byte words");
+#pragma unroll
+        for (int q = 0; q < kWords; q += 4) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(src + q));
+            w[q] = v.x;
+            w[q + 1] = v.y;
+            w[q + 2] = v.z;
+            w[q + 3] = v.w;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Likelihood of a frame group
+// ---------------------------------------------------------------------------
+constexpr int kGChunk = 512;                 // pixels per chunk (multiple of 16)
+constexpr int kGImgBytes = 3 * kGChunk;      // 1536 per frame
+constexpr int kGBgBytes = 12 * kGChunk;      // 6144 (3 floats per pixel)
+constexpr int kGThreads = 256;
+constexpr int kGStages = 4;
+
+template <int F>
+struct GLayout {
+    static constexpr int kStage = F * kGImgBytes + 2 * kGBgBytes;   // bytes per ring stage
+    static constexpr int kSmem = kGStages * kStage + kGStages * 8;  // + mbarriers
+};
+
+template <typename OutT, int F>
+__device__ __forceinline__ void group_pixel(const LikelihoodArgs &a, OutT *out, int64_t p, const unsigned char *im,
+                                            int64_t im_stride, const float *m, const float *h)
+{
+    GroupWords<OutT, F> pk;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const unsigned char *q = im + f * im_stride;
+        const float r = pixel_log_odds((float)q[0], (float)q[1], (float)q[2], m[0], m[1], m[2], h[0], h[1], h[2],
+                                       a.c0);
+        pk.set(f, to_map<OutT>(log_ratio_of_r(r, a.sc)));
+    }
+    store_words<GroupWords<OutT, F>::kWords>(reinterpret_cast<uint32_t *>(out + p * F), pk.w);
+}
+
+// Persistent grid over 512-pixel chunks; one thread per CTA streams each
+// chunk's F image slices, means and inverse variances into shared memory
+// with bulk copies through a 4-stage mbarrier ring.  n_tma_pix = n_pix
+// rounded down to 16 pixels; CTA 0 computes the last < 16 pixels with plain
+// loads.
+template <typename OutT, int F>
+__global__ void __launch_bounds__(kGThreads) likelihood_group_kernel(const LikelihoodArgs a, int64_t n_tma_pix)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kGStages * GLayout<F>::kStage);
+    OutT *out = reinterpret_cast<OutT *>(a.out);
+    const int tid = threadIdx.x;
+    if (a.zero_word && blockIdx.x == 0 && tid < F) a.zero_word[(int64_t)tid * a.zero_fstride] = 0u;
+    if (tid == 0) {
+        for (int s = 0; s < kGStages; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    const int64_t n_chunks = (n_tma_pix + kGChunk - 1) / kGChunk;
+    const int64_t my_chunks =
+        (int64_t)blockIdx.x < n_chunks ? (n_chunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto stage_img = [&](int s) { return smem + s * GLayout<F>::kStage; };
+    auto stage_mean = [&](int s) {
+        return reinterpret_cast<float *>(smem + s * GLayout<F>::kStage + F * kGImgBytes);
+    };
+    auto stage_hinv = [&](int s) {
+        return reinterpret_cast<float *>(smem + s * GLayout<F>::kStage + F * kGImgBytes + kGBgBytes);
+    };
+    auto issue = [&](int64_t k) {
+        const int s = (int)(k % kGStages);
+        const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kGChunk;
+        const uint32_t np = (uint32_t)min((int64_t)kGChunk, n_tma_pix - p0);
+        mbar_arrive_expect_tx(&bars[s], (3u * F + 24u) * np);
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+            bulk_g2s(stage_img(s) + f * kGImgBytes, a.img + f * a.img_fstride + 3 * p0, 3u * np, &bars[s]);
+        bulk_g2s(stage_mean(s), a.mean + 3 * p0, 12u * np, &bars[s]);
+        bulk_g2s(stage_hinv(s), a.hinv + 3 * p0, 12u * np, &bars[s]);
+    };
+    if (tid == 0)
+        for (int64_t k = 0; k < my_chunks && k < kGStages; ++k) issue(k);
+
+    for (int64_t k = 0; k < my_chunks; ++k) {
+        const int s = (int)(k % kGStages);
+        mbar_wait_bounded(&bars[s], (uint32_t)((k / kGStages) & 1), a.status);
+        const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kGChunk;
+        const int np = (int)min((int64_t)kGChunk, n_tma_pix - p0);
+        const unsigned char *im = stage_img(s);
+        const float *mu = stage_mean(s);
+        const float *hv = stage_hinv(s);
+        for (int q = tid; q < np; q += kGThreads)
+            group_pixel<OutT, F>(a, out, p0 + q, im + 3 * q, kGImgBytes, mu + 3 * q, hv + 3 * q);
+        __syncthreads();   // every thread is done with stage s before it is refilled
+        if (tid == 0 && k + kGStages < my_chunks) issue(k + kGStages);
+    }
+
+    if (blockIdx.x == 0) {
+        for (int64_t p = n_tma_pix + tid; p < a.n_pix; p += kGThreads)
+            group_pixel<OutT, F>(a, out, p, a.img + 3 * p, a.img_fstride, a.mean + 3 * p, a.hinv + 3 * p);
+    }
+}
+
+template <typename OutT, int F>
+cudaError_t launch_lk_group(const LikelihoodArgs &a, cudaStream_t s, int ctas_per_sm)
+{
+    auto kern = likelihood_group_kernel<OutT, F>;
+    constexpr int smem = GLayout<F>::kSmem;
+    static bool configured[64] = {false};
+    static int max_ctas[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kGThreads, smem);
+        if (e != cudaSuccess) return e;
+        max_ctas[dev] = std::max(1, n);
+        configured[dev] = true;
+    }
+    const int per_sm = std::max(1, std::min(ctas_per_sm, max_ctas[dev]));
+    const int64_t n_tma_pix = a.n_pix / 16 * 16;
+    const int64_t n_chunks = (n_tma_pix + kGChunk - 1) / kGChunk;
+    int64_t blocks = std::min<int64_t>(n_chunks, (int64_t)per_sm * group_sm_count());
+    if (blocks < 1) blocks = 1;
+    kern<<<(int)blocks, kGThreads, smem, s>>>(a, n_tma_pix);
+    return cudaGetLastError();
+}
+
+template <typename OutT>
+cudaError_t launch_lk_group_typed(const LikelihoodArgs &a, int frames, cudaStream_t s, int ctas_per_sm)
+{
+    // bulk copies need 16-byte aligned sources and sizes: refuse rather than fault
+    if (((uintptr_t)a.img | (uintptr_t)a.mean | (uintptr_t)a.hinv | (uintptr_t)a.img_fstride) & 15u)
+        return cudaErrorMisalignedAddress;
+    if (((uintptr_t)a.out) & (uintptr_t)(frames * sizeof(OutT) - 1)) return cudaErrorMisalignedAddress;
+    if (frames == 2) return launch_lk_group<OutT, 2>(a, s, ctas_per_sm);
+    if (frames == 4) return launch_lk_group<OutT, 4>(a, s, ctas_per_sm);
+    if (frames == 8) return launch_lk_group<OutT, 8>(a, s, ctas_per_sm);
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Fusion of a frame group
+// ---------------------------------------------------------------------------
+// The tile decomposition, per-tile camera records and projection are those of
+// the direct fuse kernel; a thread holds F x TZ log-odds accumulators.
+template <typename MapT, int LX, int WY, int TZ, int F>
+__global__ void __launch_bounds__(32 * WY) fuse_group_kernel(const __grid_constant__ FuseArgs a)
+{
+    using Words = GroupWords<MapT, F>;
+    __shared__ int s_flags[PSFS_MAX_CAMS];
+    __shared__ uint32_t s_warp_off[WY];
+    __shared__ uint32_t s_base;
+
+    const int lane = threadIdx.x;
+    const int wy = threadIdx.y;
+    const int tid = wy * 32 + lane;
+    if (tid < a.n_cams) s_flags[tid] = __ldg(&a.tilecam[(int64_t)blockIdx.x * a.n_cams + tid].w) >> 16;
+
+    TileCoords<LX, WY, TZ> tc;
+    tc.init(a, a.tiles[blockIdx.x], lane, wy);
+    const uint32_t W = (uint32_t)a.W, H = (uint32_t)a.H;
+    float L[F][TZ];
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int t = 0; t < TZ; ++t) L[f][t] = 0.0f;
+    __syncthreads();
+
+    const uint32_t *maps = reinterpret_cast<const uint32_t *>(a.maps);
+    const uint32_t last_pix = W * H - 1u;
+    const uint32_t bias_off = 0u - (kFloorBias * W + kFloorBias);
+    for (int c = 0; c < a.n_cams; ++c) {
+        const int flags = s_flags[c];
+        if (flags & kTcSkip) continue;
+        float m[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
+        float bu, bv, bw;
+        project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
+        const uint32_t *map = maps + (int64_t)c * a.map_stride * Words::kWords;
+        if (flags & kTcInside) {
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) {
+                const Proj p = project_biased(m, bu, bv, bw, tc.fk[t]);
+                // the host proved the pixel lies in the image; min() only guards the buffer
+                const uint32_t pix = min(p.by * W + p.bx + bias_off, last_pix);
+                Words g;
+                load_words<Words::kWords>(map + (size_t)pix * Words::kWords, g.w);
+#pragma unroll
+                for (int f = 0; f < F; ++f) L[f][t] += g.get(f);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) {
+                int pix;
+                if (proj_pixel(project_biased(m, bu, bv, bw, tc.fk[t]), W, H, &pix)) {
+                    Words g;
+                    load_words<Words::kWords>(map + (size_t)pix * Words::kWords, g.w);
+#pragma unroll
+                    for (int f = 0; f < F; ++f) L[f][t] += g.get(f);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+        tile_epilogue_to<WY, TZ>(a, a.occ + f * a.occ_fstride, a.list + f * a.list_fstride,
+                                 a.count + f * a.count_fstride, tc.i, tc.j, tc.k0, L[f], lane, wy, s_warp_off,
+                                 &s_base);
+}
+
+template <typename MapT, int LX, int TZ, int F>
+cudaError_t launch_fg(const FuseArgs &a, cudaStream_t s)
+{
+    fuse_group_kernel<MapT, LX, 4, TZ, F><<<a.n_tiles, dim3(32, 4), 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename MapT, int LX, int F>
+cudaError_t launch_fg_tz(const FuseArgs &a, int tz, cudaStream_t s)
+{
+    if (tz == 8) return launch_fg<MapT, LX, 8, F>(a, s);
+    if constexpr (F <= 4) {
+        if (tz == 16) return launch_fg<MapT, LX, 16, F>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename MapT, int F>
+cudaError_t launch_fg_shape(const FuseArgs &a, const FuseShape &sh, cudaStream_t s)
+{
+    if (sh.wy != 4 || sh.staged) return cudaErrorInvalidValue;
+    if (sh.lx == 8) return launch_fg_tz<MapT, 8, F>(a, sh.tz, s);
+    if (sh.lx == 16) return launch_fg_tz<MapT, 16, F>(a, sh.tz, s);
+    return cudaErrorInvalidValue;
+}
+
+template <typename MapT>
+cudaError_t launch_fg_typed(const FuseArgs &a, const FuseShape &sh, int frames, cudaStream_t s)
+{
+    if (((uintptr_t)a.maps) & (uintptr_t)(frames * sizeof(MapT) - 1)) return cudaErrorMisalignedAddress;
+    if (frames == 2) return launch_fg_shape<MapT, 2>(a, sh, s);
+    if (frames == 4) return launch_fg_shape<MapT, 4>(a, sh, s);
+    if (frames == 8) return launch_fg_shape<MapT, 8>(a, sh, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool group_size_supported(int frames) { return frames == 2 || frames == 4 || frames == 8; }
+
+bool group_shape_supported(const FuseShape &s, int frames)
+{
+    return group_size_supported(frames) && s.wy == 4 && s.staged == 0 && (s.lx == 8 || s.lx == 16) &&
+           (s.tz == 8 || (s.tz == 16 && frames <= 4));
+}
+
+cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map_dtype, cudaStream_t s,
+                                    int ctas_per_sm)
+{
+    if (map_dtype == PSFS_MAP_F16) return launch_lk_group_typed<__half>(a, frames, s, ctas_per_sm);
+    if (map_dtype == PSFS_MAP_BF16) return launch_lk_group_typed<__nv_bfloat16>(a, frames, s, ctas_per_sm);
+    return launch_lk_group_typed<float>(a, frames, s, ctas_per_sm);
+}
+
+cudaError_t launch_fuse_group(const FuseArgs &a, const FuseShape &shape, int frames, int map_dtype,
+                              cudaStream_t s)
+{
+    if (a.n_tiles <= 0) return cudaSuccess;
+    if (map_dtype == PSFS_MAP_F16) return launch_fg_typed<__half>(a, shape, frames, s);
+    if (map_dtype == PSFS_MAP_BF16) return launch_fg_typed<__nv_bfloat16>(a, shape, frames, s);
+    return launch_fg_typed<float>(a, shape, frames, s);
+}
+
+}  // namespace psfs

@@ -57,6 +57,11 @@ struct LikelihoodArgs {
     void *out;                // [n_pix] map of g (f32 / f16 / bf16) or of s (f32)
     uint32_t *zero_word;      // if non-null, set to 0 by one thread
     uint32_t *status;         // device status word (bounded-wait timeouts)
+    // frame groups (sequence path): img is frame 0 of the group, frame f at
+    // img + f * img_fstride bytes; out is [n_pix][F]; the F words
+    // zero_word + f * zero_fstride are set to 0
+    int64_t img_fstride;
+    int64_t zero_fstride;
 };
 
 struct SlmToMapArgs {
@@ -100,6 +105,10 @@ struct FuseArgs {
     uint32_t *count;
     uint32_t *status;
     int tmap_ok;              // the tensor maps below describe `maps`
+    // frame groups (sequence path): maps are [n_cams][H][W][F]; the outputs of
+    // frame f are occ + f * occ_fstride, list + f * list_fstride and
+    // count + f * count_fstride
+    int64_t occ_fstride, list_fstride, count_fstride;
     CamMat cam[PSFS_MAX_CAMS];
     // 3-D tensor maps {W, H, n_cams} of `maps` with boxes of (32 << class) x 16
     // x 1 elements, for the staged kernel
@@ -456,6 +465,17 @@ void plan_backward_inv(const psfs_grid &grid, const psfs_camera *cams, int n_cam
 cudaError_t launch_backward_pixel(const BackwardArgs &a, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 cudaError_t launch_fuse_staged(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
+
+// Frame groups of the sequence path (psfs_group.cu): F frames share one pass
+// over the background (likelihood) and one projection per voxel and camera
+// (fusion), with the maps of the group interleaved per pixel.  Each frame's
+// arithmetic is that of the single-frame kernels.
+bool group_size_supported(int frames);
+bool group_shape_supported(const FuseShape &s, int frames);
+cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map_dtype, cudaStream_t s,
+                                    int ctas_per_sm);
+cudaError_t launch_fuse_group(const FuseArgs &a, const FuseShape &shape, int frames, int map_dtype,
+                              cudaStream_t s);
 
 // Host planning (psfs_plan.cu): projection matrices, tile order and staging
 // records of the fuse kernel for one grid and camera rig.

@@ -1,0 +1,169 @@
+"""Frame groups of the sequence path: F frames per likelihood launch (one
+pass over the background) and per fusion launch (one projection per voxel
+and camera, one vector gather for all F frames).  Each frame's occupancy,
+count and voxel set must be bit-identical to one psfs_reconstruct per frame
+with the same tile shape, for every group size, map type and a frame count
+that leaves trailing frames outside the last group; one group's frame is also
+checked against the FP64 oracle directly."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1311_6811_gb300 import psfs  # noqa: E402
+from synth import scene as S  # noqa: E402
+from tests.gpu_helpers import compare, to_dev  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    psfs.load()
+
+
+def _scene(n_frames):
+    return S.make_scene(seed=21, grid_n=48, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0,
+                        n_frames=n_frames, walking=True)
+
+
+def _run_sequence(rec, imgs, cap):
+    F, V = imgs.shape[0], rec.n_voxels
+    occ = torch.full((F, V), -1.0, dtype=torch.float32, device="cuda")
+    lists = torch.empty((F, cap), dtype=torch.int32, device="cuda")
+    counts = torch.full((F,), 12345, dtype=torch.int32, device="cuda")
+    psfs.psfs_reconstruct_sequence(rec.handle, F, imgs, occ, lists, cap, counts)
+    assert rec.sync() == psfs.PSFS_OK
+    return occ, lists, counts
+
+
+def _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap):
+    for f in range(imgs.shape[0]):
+        o1, l1, c1 = rec.reconstruct(imgs[f])
+        assert rec.sync() == psfs.PSFS_OK
+        np.testing.assert_array_equal(occ[f].cpu().numpy(), o1.cpu().numpy().ravel(), err_msg=f"frame {f}")
+        assert int(counts[f]) == int(c1.item()), f
+        np.testing.assert_array_equal(psfs.voxel_list(lists[f], counts[f:f + 1], cap).numpy(),
+                                      psfs.voxel_list(l1, c1, rec.capacity).numpy())
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("group,tz", [(2, 16), (4, 8), (4, 16), (8, 8)])
+def test_groups_equal_frame_by_frame(group, tz, dtype):
+    """11 frames: whole groups, then 11 mod F trailing frames one per launch."""
+    sc = _scene(11)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=dtype)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    cap = rec.n_voxels
+    for lx in (8, 16):
+        psfs.psfs_set_fuse_config(rec.handle, lx, 4, tz, 0, 2, group)
+        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, group)
+        occ, lists, counts = _run_sequence(rec, imgs, cap)
+        _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap)
+    rec.close()
+
+
+@pytest.mark.parametrize("lk", [1, 2, 3, 4])
+def test_group_likelihood_grid_sizes(lk):
+    """Every likelihood grid size (CTAs per SM, clamped by shared memory)."""
+    sc = _scene(8)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, lk, 4)
+    occ, lists, counts = _run_sequence(rec, imgs, rec.n_voxels)
+    _assert_frame_by_frame(rec, imgs, occ, lists, counts, rec.n_voxels)
+    rec.close()
+
+
+def test_group_ragged_grid():
+    """Grid 37 x 29 x 24 (ragged along x and y for every tile shape, along z
+    for voxels_z = 16), 3 cameras of 104 x 80 (some voxels outside some
+    views), 6 frames in groups of 4 plus 2 single frames."""
+    grid = S.Grid(37, 29, 24, (-0.9, -0.7, 0.1), 0.05)
+    sc = S.make_scene(seed=22, grid_n=48, cube_side=2.0, n_cams=3, width=104, height=80, focal=95.0,
+                      n_frames=6, walking=True)
+    rec = psfs.Reconstructor(grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    for tz in (8, 16):
+        psfs.psfs_set_fuse_config(rec.handle, 8, 4, tz, 0, 2, 4)
+        occ, lists, counts = _run_sequence(rec, imgs, rec.n_voxels)
+        _assert_frame_by_frame(rec, imgs, occ, lists, counts, rec.n_voxels)
+    rec.close()
+
+
+def test_group_frame_matches_oracle():
+    """Frame 2 of a group of 4, against the FP64 oracle at the FP32 tolerances."""
+    sc = _scene(4)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 2, 4)
+    occ, lists, counts = _run_sequence(rec, imgs, rec.n_voxels)
+    f = 2
+    got = {"occ": occ[f].cpu().numpy().astype(np.float64), "count": int(counts[f]) & 0xFFFFFFFF,
+           "list": psfs.voxel_list(lists[f], counts[f:f + 1], rec.n_voxels).numpy(), "status": psfs.PSFS_OK}
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images[f], sc.mean, sc.var, sc.params)
+    rep = compare(got, ref)
+    assert ref["list"].size > 500
+    print(rep)
+    rec.close()
+
+
+def test_group_capacity_overflow_per_frame():
+    """A capacity below the occupied count: every frame's count is still the
+    full count, only `capacity` entries are written, and the overflow is
+    reported by psfs_sync."""
+    sc = _scene(4)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    full = []
+    for f in range(4):
+        _, _, c1 = rec.reconstruct(imgs[f])
+        assert rec.sync() == psfs.PSFS_OK
+        full.append(int(c1.item()))
+    cap = min(full) // 2
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 2, 4)
+    V = rec.n_voxels
+    occ = torch.empty((4, V), dtype=torch.float32, device="cuda")
+    counts = torch.zeros((4,), dtype=torch.int32, device="cuda")
+    lists_flat = torch.full((4 * cap,), -1, dtype=torch.int32, device="cuda")
+    psfs.psfs_reconstruct_sequence(rec.handle, 4, imgs, occ, lists_flat, cap, counts)
+    assert rec.sync() == psfs.PSFS_ERR_CAPACITY
+    assert [int(c) for c in counts] == full
+    lf = lists_flat.view(4, cap).cpu().numpy()
+    assert (lf >= 0).all() and (lf < V).all()
+    rec.close()
+
+
+def test_group_config_validation():
+    sc = _scene(2)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    for bad in [(8, 4, 8, 0, 0, 3), (8, 4, 16, 0, 0, 8), (8, 4, 8, 1, 0, 4), (32, 4, 8, 0, 0, 2),
+                (8, 4, 8, 0, 0, -1)]:
+        with pytest.raises(psfs.PsfsError):
+            psfs.psfs_set_fuse_config(rec.handle, *bad)
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 0, 4)
+    assert psfs.psfs_get_fuse_config(rec.handle, full=True)[5] == 4
+    # 0 keeps the current group size
+    psfs.psfs_set_fuse_config(rec.handle, 16, 4, 8, 0, 0, 0)
+    assert psfs.psfs_get_fuse_config(rec.handle, full=True)[5] == 4
+    rec.close()
+
+
+def test_autotune_picks_a_sequence_configuration():
+    sc = _scene(2)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    psfs.psfs_autotune(rec.handle, to_dev(sc.images[0]), reps=1)
+    cfg = psfs.psfs_get_fuse_config(rec.handle, full=True)
+    assert cfg[5] in (1, 2, 4, 8) and 1 <= cfg[4] <= 4
+    assert rec.sync() == psfs.PSFS_OK
+    rec.close()
