@@ -106,7 +106,8 @@ typedef struct {
  * fusion kernel owns: a warp covers lanes_x voxels along x by 32 / lanes_x
  * along y, a CTA `warps` warps stacked along y, and each thread walks
  * voxels_z voxels along z; supported: lanes_x in {8, 16, 32}, warps = 4,
- * voxels_z in {8, 16}.  staged = 1 selects the persistent kernel that copies
+ * voxels_z in {4, 8, 16} (8 or 16 when staged).  staged = 1 selects the
+ * persistent kernel that copies
  * each tile's image footprint per camera into shared memory (bulk copies,
  * double-buffered) before gathering; 0 gathers from global memory.
  * seq_likelihood_ctas: CTAs per SM of the likelihood grid on the sequence
@@ -117,7 +118,7 @@ typedef struct {
  * the group's maps interleaved per pixel, and one fusion launch projects each
  * voxel once and gathers all frames of the group with one vector load (each
  * frame's results are bit-identical to one frame per launch).  Groups need
- * staged = 0, lanes_x 8 or 16, and voxels_z 8 for 8 frames; with another
+ * staged = 0, lanes_x 8 or 16, and voxels_z 4 or 8 for 8 frames; with another
  * shape the sequence path runs one frame per launch.  Trailing frames that do
  * not fill a group run one per launch.  0 in psfs_set_fuse_config keeps the
  * current value.  The batch entry points ignore this field. */
@@ -250,7 +251,7 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
  * staged 0 then 1, lanes_x 8, 16, 32, voxels_z 8 then 16); then times the
  * sequence path on 8 frames with 1 to 4 likelihood CTAs per SM at one frame
  * per launch, and frame groups of 2, 4 and 8 frames (direct tile shapes,
- * voxels_z 8 and 16, 1 to 3 likelihood CTAs per SM), and keeps the fastest
+ * voxels_z 4, 8 and 16, 1 to 3 likelihood CTAs per SM), and keeps the fastest
  * sequence configuration (which may change the tile shape).  The choices are
  * remembered for handles of the same grid size, camera count, image size and
  * map type created later in the process.  Allocates and frees its own scratch; waits for the stream.

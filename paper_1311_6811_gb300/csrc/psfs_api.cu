@@ -846,7 +846,7 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
         return fail(PSFS_ERR_INVALID_ARG, "seq_likelihood_ctas outside [0, 4]");
     if (cfg->frames_per_group < 0 || (cfg->frames_per_group > 1 && !group_shape_supported(shape, cfg->frames_per_group)))
         return fail(PSFS_ERR_INVALID_ARG,
-                    "frames_per_group: 0, 1, or 2 / 4 / 8 with staged 0, lanes_x 8 or 16 (voxels_z 8 for 8 frames)");
+                    "frames_per_group: 0, 1, or 2 / 4 / 8 with staged 0, lanes_x 8 or 16 (voxels_z 4 or 8 for 8 frames)");
     DeviceGuard guard(h->device);
     PSFS_CK(cudaStreamSynchronize(h->stream));
     if (h->seq_stream[0]) {
@@ -968,7 +968,8 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     const int group_lx = (best_shape.lx == 16) ? 16 : 8;
     const int groups[3] = {2, 4, 8};
     for (int gi = 0; gi < 3 && st == PSFS_OK; ++gi) {
-        for (int tz = 8; tz <= 16 && st == PSFS_OK; tz += 8) {
+        for (int tz : {4, 8, 16}) {
+            if (st != PSFS_OK) break;
             const FuseShape gshape = {group_lx, 4, tz, 0};
             if (!group_shape_supported(gshape, groups[gi])) continue;
             st = replan(h, gshape);

@@ -134,9 +134,24 @@ template <typename MapT>
 cudaError_t launch_shape(const BatchLaunch &b, const FuseShape &sh, cudaStream_t s)
 {
     if (sh.wy != 4) return cudaErrorInvalidValue;
-    if (sh.lx == 8) return sh.tz == 8 ? launch_typed<MapT, 8, 8>(b, s) : launch_typed<MapT, 8, 16>(b, s);
-    if (sh.lx == 16) return sh.tz == 8 ? launch_typed<MapT, 16, 8>(b, s) : launch_typed<MapT, 16, 16>(b, s);
-    if (sh.lx == 32) return sh.tz == 8 ? launch_typed<MapT, 32, 8>(b, s) : launch_typed<MapT, 32, 16>(b, s);
+    if (sh.lx == 8) {
+        if (sh.tz == 4) return launch_typed<MapT, 8, 4>(b, s);
+        if (sh.tz == 8) return launch_typed<MapT, 8, 8>(b, s);
+        if (sh.tz == 16) return launch_typed<MapT, 8, 16>(b, s);
+        return cudaErrorInvalidValue;
+    }
+    if (sh.lx == 16) {
+        if (sh.tz == 4) return launch_typed<MapT, 16, 4>(b, s);
+        if (sh.tz == 8) return launch_typed<MapT, 16, 8>(b, s);
+        if (sh.tz == 16) return launch_typed<MapT, 16, 16>(b, s);
+        return cudaErrorInvalidValue;
+    }
+    if (sh.lx == 32) {
+        if (sh.tz == 4) return launch_typed<MapT, 32, 4>(b, s);
+        if (sh.tz == 8) return launch_typed<MapT, 32, 8>(b, s);
+        if (sh.tz == 16) return launch_typed<MapT, 32, 16>(b, s);
+        return cudaErrorInvalidValue;
+    }
     return cudaErrorInvalidValue;
 }
 

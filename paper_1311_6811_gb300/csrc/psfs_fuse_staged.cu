@@ -159,9 +159,12 @@ template <typename MapT>
 cudaError_t launch_shape(const FuseArgs &a, const FuseShape &sh, cudaStream_t s)
 {
     if (sh.wy != 4) return cudaErrorInvalidValue;
-    if (sh.lx == 8) return sh.tz == 8 ? launch_typed<MapT, 8, 8>(a, s) : launch_typed<MapT, 8, 16>(a, s);
-    if (sh.lx == 16) return sh.tz == 8 ? launch_typed<MapT, 16, 8>(a, s) : launch_typed<MapT, 16, 16>(a, s);
-    if (sh.lx == 32) return sh.tz == 8 ? launch_typed<MapT, 32, 8>(a, s) : launch_typed<MapT, 32, 16>(a, s);
+    if (sh.lx == 8 && (sh.tz == 8 || sh.tz == 16))
+        return sh.tz == 8 ? launch_typed<MapT, 8, 8>(a, s) : launch_typed<MapT, 8, 16>(a, s);
+    if (sh.lx == 16 && (sh.tz == 8 || sh.tz == 16))
+        return sh.tz == 8 ? launch_typed<MapT, 16, 8>(a, s) : launch_typed<MapT, 16, 16>(a, s);
+    if (sh.lx == 32 && (sh.tz == 8 || sh.tz == 16))
+        return sh.tz == 8 ? launch_typed<MapT, 32, 8>(a, s) : launch_typed<MapT, 32, 16>(a, s);
     return cudaErrorInvalidValue;
 }
 

@@ -351,6 +351,7 @@ cudaError_t launch_fg(const FuseArgs &a, cudaStream_t s)
 template <typename MapT, int LX, int F>
 cudaError_t launch_fg_tz(const FuseArgs &a, int tz, cudaStream_t s)
 {
+    if (tz == 4) return launch_fg<MapT, LX, 4, F>(a, s);
     if (tz == 8) return launch_fg<MapT, LX, 8, F>(a, s);
     if constexpr (F <= 4) {
         if (tz == 16) return launch_fg<MapT, LX, 16, F>(a, s);
@@ -384,7 +385,7 @@ bool group_size_supported(int frames) { return frames == 2 || frames == 4 || fra
 bool group_shape_supported(const FuseShape &s, int frames)
 {
     return group_size_supported(frames) && s.wy == 4 && s.staged == 0 && (s.lx == 8 || s.lx == 16) &&
-           (s.tz == 8 || (s.tz == 16 && frames <= 4));
+           (s.tz == 4 || s.tz == 8 || (s.tz == 16 && frames <= 4));
 }
 
 cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map_dtype, cudaStream_t s,

@@ -171,8 +171,9 @@ bool encode_map_tensors(void *maps, int map_dtype, int W, int H, int n_cams, CUt
 
 bool fuse_shape_supported(const FuseShape &s)
 {
-    return (s.lx == 8 || s.lx == 16 || s.lx == 32) && s.wy == 4 && (s.tz == 8 || s.tz == 16) &&
-           (s.staged == 0 || s.staged == 1);
+    return (s.lx == 8 || s.lx == 16 || s.lx == 32) && s.wy == 4 &&
+           ((s.staged == 0 && (s.tz == 4 || s.tz == 8 || s.tz == 16)) ||
+            (s.staged == 1 && (s.tz == 8 || s.tz == 16)));
 }
 
 void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const psfs_params &params,

@@ -52,7 +52,7 @@ def _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("group,tz", [(2, 16), (4, 8), (4, 16), (8, 8)])
+@pytest.mark.parametrize("group,tz", [(2, 16), (4, 4), (4, 8), (4, 16), (8, 4), (8, 8)])
 def test_groups_equal_frame_by_frame(group, tz, dtype):
     """11 frames: whole groups, then 11 mod F trailing frames one per launch."""
     sc = _scene(11)
@@ -143,11 +143,37 @@ def test_group_capacity_overflow_per_frame():
     rec.close()
 
 
+def test_backward_tile_shapes_identical():
+    """The adjoint's voxel pass runs with the handle's tile shape, voxels_z = 4
+    included: gradients are bit-identical across shapes."""
+    sc = _scene(2)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    img = to_dev(sc.images[0])
+    V = rec.n_voxels
+    n_pix = img.numel() // 3
+    g = torch.Generator().manual_seed(5)
+    d_occ = torch.randn(V, generator=g).cuda()
+    outs = []
+    for cfg in [(8, 4, 16, 0), (8, 4, 4, 0), (16, 4, 4, 0), (32, 4, 4, 0)]:
+        psfs.psfs_set_fuse_config(rec.handle, *cfg)
+        d_slm = torch.empty(n_pix, device="cuda")
+        d_mean = torch.empty(n_pix * 3, device="cuda")
+        d_var = torch.empty(n_pix * 3, device="cuda")
+        psfs.psfs_backward(rec.handle, img, d_occ, d_slm, d_mean, d_var)
+        assert rec.sync() == psfs.PSFS_OK
+        outs.append([t.cpu().numpy() for t in (d_slm, d_mean, d_var)])
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            np.testing.assert_array_equal(a, b)
+    rec.close()
+
+
 def test_group_config_validation():
     sc = _scene(2)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
     for bad in [(8, 4, 8, 0, 0, 3), (8, 4, 16, 0, 0, 8), (8, 4, 8, 1, 0, 4), (32, 4, 8, 0, 0, 2),
-                (8, 4, 8, 0, 0, -1)]:
+                (8, 4, 8, 0, 0, -1), (32, 4, 4, 0, 0, 4)]:
         with pytest.raises(psfs.PsfsError):
             psfs.psfs_set_fuse_config(rec.handle, *bad)
     psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 0, 4)

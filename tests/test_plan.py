@@ -120,7 +120,7 @@ RIGS = {
 
 
 @pytest.mark.parametrize("rig", sorted(RIGS))
-@pytest.mark.parametrize("shape", [(8, 4, 16, 1), (16, 4, 8, 1), (32, 4, 8, 0)])
+@pytest.mark.parametrize("shape", [(8, 4, 16, 1), (16, 4, 8, 1), (32, 4, 8, 0), (8, 4, 4, 0)])
 def test_records_cover_every_voxel(driver, rig, shape, tmp_path):
     sc = RIGS[rig]()
     counts = _check(driver, sc.grid, sc.cams, 0, tmp_path, shape)
