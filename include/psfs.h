@@ -185,6 +185,21 @@ psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const ui
                                       float *occupancy, uint32_t *voxel_lists, uint32_t capacity,
                                       uint32_t *counts);
 
+/* psfs_reconstruct_sequence from and to host memory, synchronous: frame f
+ * reads h_images + f * (n_cams * height * width * 3) and writes
+ * h_occupancy + f * (nx * ny * nz) (h_occupancy may be NULL: no occupancy
+ * copy), h_counts[f] and the first min(h_counts[f], capacity) entries of
+ * h_lists + f * capacity.  Frames go through two device staging slots of a
+ * few frame groups each (allocated on first use, grown on demand): the copy
+ * in of one slot and the copy out of the other overlap the kernels.  Pinned
+ * host buffers (cudaHostAlloc / cudaHostRegister) let the copies run
+ * asynchronously; pageable ones work but serialise them.  Returns after the
+ * last copy.  Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA, CAPACITY (some
+ * frame had more occupied voxels than `capacity`; its count is still exact). */
+psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, const uint8_t *h_images,
+                                           float *h_occupancy, uint32_t *h_lists, uint32_t capacity,
+                                           uint32_t *h_counts);
+
 /* Keeps the packed background (24 bytes per pixel) resident in L2 for the
  * likelihood stage of psfs_reconstruct_sequence (enable = 1), through an L2
  * access-policy window on the sequence path's own likelihood stream; frames

@@ -68,6 +68,18 @@ struct psfs_handle {
     void *gmaps[2] = {nullptr, nullptr};
     int group_cap = 0;
 
+    // host-buffer sequence path (first use): two chunk slots of device
+    // staging, copies in and out on two streams of their own
+    cudaStream_t io_stream[2] = {nullptr, nullptr};   // [0] host to device, [1] device to host
+    cudaEvent_t io_ev_in[2] = {nullptr, nullptr}, io_ev_comp[2] = {nullptr, nullptr};
+    cudaEvent_t io_ev_cnt[2] = {nullptr, nullptr}, io_ev_out[2] = {nullptr, nullptr};
+    uint8_t *io_img[2] = {nullptr, nullptr};
+    float *io_occ[2] = {nullptr, nullptr};
+    uint32_t *io_list[2] = {nullptr, nullptr};
+    uint32_t *io_cnt[2] = {nullptr, nullptr};
+    int io_frames = 0;          // frames per slot
+    uint32_t io_cap = 0;        // list entries per frame
+
     // tracing: CUDA event pairs around each launch
     int prof_cap = 0;
     std::vector<cudaEvent_t> prof_ev;      // 2 * prof_cap events
@@ -155,6 +167,16 @@ void free_handle(psfs_handle *h)
     cudaFree(h->maps2);
     cudaFree(h->gmaps[0]);
     cudaFree(h->gmaps[1]);
+    for (int n = 0; n < 2; ++n) {
+        if (h->io_stream[n]) cudaStreamSynchronize(h->io_stream[n]);
+        if (h->io_stream[n]) cudaStreamDestroy(h->io_stream[n]);
+        for (cudaEvent_t e : {h->io_ev_in[n], h->io_ev_comp[n], h->io_ev_cnt[n], h->io_ev_out[n]})
+            if (e) cudaEventDestroy(e);
+        cudaFree(h->io_img[n]);
+        cudaFree(h->io_occ[n]);
+        cudaFree(h->io_list[n]);
+        cudaFree(h->io_cnt[n]);
+    }
     for (int n = 0; n < 2; ++n) {
         if (h->seq_stream[n]) cudaStreamSynchronize(h->seq_stream[n]);
         if (h->seq_stream[n]) cudaStreamDestroy(h->seq_stream[n]);
@@ -642,6 +664,138 @@ psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const ui
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     return enqueue_sequence(h, n_frames, images, (size_t)h->n_pix * 3, occupancy, n_vox, voxel_lists, capacity,
                             capacity, counts, 1, h->seq_lk_ctas, h->seq_group);
+}
+
+// Staging of the host-buffer sequence path: two slots of `frames` frames.
+static psfs_status io_setup(psfs_handle *h, int frames, uint32_t capacity)
+{
+    if (!h->io_stream[0]) {
+        for (int n = 0; n < 2; ++n) {
+            PSFS_CK(cudaStreamCreateWithFlags(&h->io_stream[n], cudaStreamNonBlocking));
+            PSFS_CK(cudaEventCreateWithFlags(&h->io_ev_in[n], cudaEventDisableTiming));
+            PSFS_CK(cudaEventCreateWithFlags(&h->io_ev_comp[n], cudaEventDisableTiming));
+            PSFS_CK(cudaEventCreateWithFlags(&h->io_ev_cnt[n], cudaEventDisableTiming));
+            PSFS_CK(cudaEventCreateWithFlags(&h->io_ev_out[n], cudaEventDisableTiming));
+        }
+    }
+    if (frames <= h->io_frames && capacity <= h->io_cap) return PSFS_OK;
+    PSFS_CK(cudaStreamSynchronize(h->io_stream[0]));
+    PSFS_CK(cudaStreamSynchronize(h->io_stream[1]));
+    PSFS_CK(cudaStreamSynchronize(h->stream));
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    frames = std::max(frames, h->io_frames);
+    capacity = std::max(capacity, h->io_cap);
+    h->io_frames = 0;
+    h->io_cap = 0;
+    for (int n = 0; n < 2; ++n) {
+        cudaFree(h->io_img[n]);
+        cudaFree(h->io_occ[n]);
+        cudaFree(h->io_list[n]);
+        cudaFree(h->io_cnt[n]);
+        h->io_img[n] = nullptr;
+        h->io_occ[n] = nullptr;
+        h->io_list[n] = nullptr;
+        h->io_cnt[n] = nullptr;
+    }
+    for (int n = 0; n < 2; ++n) {
+        if (cudaMalloc(&h->io_img[n], (size_t)frames * h->n_pix * 3) != cudaSuccess ||
+            cudaMalloc(&h->io_occ[n], (size_t)frames * n_vox * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&h->io_list[n], (size_t)frames * std::max<uint32_t>(capacity, 1) * sizeof(uint32_t)) !=
+                cudaSuccess ||
+            cudaMalloc(&h->io_cnt[n], (size_t)frames * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "host-buffer sequence staging");
+        }
+    }
+    h->io_frames = frames;
+    h->io_cap = capacity;
+    return PSFS_OK;
+}
+
+psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, const uint8_t *h_images,
+                                           float *h_occupancy, uint32_t *h_lists, uint32_t capacity,
+                                           uint32_t *h_counts)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (n_frames < 0) return fail(PSFS_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames == 0) return PSFS_OK;
+    if (!h_images) return fail(PSFS_ERR_INVALID_ARG, "h_images is NULL");
+    if (capacity > 0 && !h_lists) return fail(PSFS_ERR_INVALID_ARG, "h_lists is NULL");
+    if (!h_counts) return fail(PSFS_ERR_INVALID_ARG, "h_counts is NULL");
+    if ((h->n_pix * 3) % 16 != 0) return fail(PSFS_ERR_INVALID_ARG, "frame size not a multiple of 16 bytes");
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    if (n_vox % 4 != 0) return fail(PSFS_ERR_INVALID_ARG, "voxel count not a multiple of 4");
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    DeviceGuard guard(h->device);
+    // chunks of four frame groups (at least 8 frames) per slot: the copies of
+    // one chunk overlap the kernels of the next
+    const int group = std::max(1, h->seq_group);
+    const int chunk = std::min<int>(n_frames, std::max(8, 4 * group));
+    psfs_status st = io_setup(h, chunk, capacity);
+    if (st != PSFS_OK) return st;
+    const size_t frame_bytes = (size_t)h->n_pix * 3;
+    const uint32_t lcap = std::max<uint32_t>(capacity, 1);
+    cudaStream_t cin = h->io_stream[0], cout = h->io_stream[1];
+    PSFS_CK(cudaEventRecord(h->io_ev_in[0], h->stream));   // after earlier work on the handle
+    PSFS_CK(cudaStreamWaitEvent(cin, h->io_ev_in[0], 0));
+    const int n_chunks = (n_frames + chunk - 1) / chunk;
+    bool overflow = false;
+    // list entries of chunk p go out once its counts are on the host
+    auto drain_lists = [&](int p) -> psfs_status {
+        const int q = p & 1, f0 = p * chunk, nf = std::min(chunk, n_frames - f0);
+        PSFS_CK(cudaEventSynchronize(h->io_ev_cnt[q]));
+        for (int f = 0; f < nf; ++f) {
+            const uint32_t n = h_counts[f0 + f];
+            overflow |= n > capacity;
+            const uint32_t m = std::min(n, capacity);
+            if (m)
+                PSFS_CK(cudaMemcpyAsync(h_lists + (size_t)(f0 + f) * capacity, h->io_list[q] + (size_t)f * lcap,
+                                        (size_t)m * sizeof(uint32_t), cudaMemcpyDeviceToHost, cout));
+        }
+        PSFS_CK(cudaEventRecord(h->io_ev_out[q], cout));
+        return PSFS_OK;
+    };
+    // slot q = k & 1: the copy in of chunk k waits until chunk k - 2's
+    // kernels have read the images of slot q; chunk k's kernels wait until
+    // chunk k - 2's results have been copied out of slot q.  The list copies
+    // of chunk k - 1 are enqueued (once its counts are on the host) before
+    // the copies out of chunk k, so copies in, kernels and copies out of
+    // consecutive chunks overlap.
+    for (int k = 0; k < n_chunks && st == PSFS_OK; ++k) {
+        const int q = k & 1, f0 = k * chunk, nf = std::min(chunk, n_frames - f0);
+        if (k >= 2) PSFS_CK(cudaStreamWaitEvent(cin, h->io_ev_comp[q], 0));
+        PSFS_CK(cudaMemcpyAsync(h->io_img[q], h_images + (size_t)f0 * frame_bytes, (size_t)nf * frame_bytes,
+                                cudaMemcpyHostToDevice, cin));
+        PSFS_CK(cudaEventRecord(h->io_ev_in[q], cin));
+        PSFS_CK(cudaStreamWaitEvent(h->stream, h->io_ev_in[q], 0));
+        if (k >= 2) PSFS_CK(cudaStreamWaitEvent(h->stream, h->io_ev_out[q], 0));
+        st = enqueue_sequence(h, nf, h->io_img[q], frame_bytes, h->io_occ[q], n_vox, h->io_list[q], lcap, capacity,
+                              h->io_cnt[q], 1, h->seq_lk_ctas, h->seq_group);
+        if (st != PSFS_OK) break;
+        PSFS_CK(cudaEventRecord(h->io_ev_comp[q], h->stream));
+        if (k >= 1) {
+            st = drain_lists(k - 1);
+            if (st != PSFS_OK) break;
+        }
+        PSFS_CK(cudaStreamWaitEvent(cout, h->io_ev_comp[q], 0));
+        PSFS_CK(cudaMemcpyAsync(h_counts + f0, h->io_cnt[q], (size_t)nf * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                cout));
+        PSFS_CK(cudaEventRecord(h->io_ev_cnt[q], cout));
+        if (h_occupancy)
+            PSFS_CK(cudaMemcpyAsync(h_occupancy + (size_t)f0 * n_vox, h->io_occ[q], (size_t)nf * n_vox * sizeof(float),
+                                    cudaMemcpyDeviceToHost, cout));
+    }
+    if (st == PSFS_OK) st = drain_lists(n_chunks - 1);
+    PSFS_CK(cudaStreamSynchronize(cout));
+    PSFS_CK(cudaStreamSynchronize(h->stream));
+    if (st != PSFS_OK) return st;
+    if (overflow) {
+        // the capacity bit was set by these frames: clear it here
+        PSFS_CK(cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t), h->stream));
+        PSFS_CK(cudaStreamSynchronize(h->stream));
+        return fail(PSFS_ERR_CAPACITY, "voxel list capacity exceeded");
+    }
+    return PSFS_OK;
 }
 
 psfs_status psfs_reconstruct_host(psfs_handle *h, const uint8_t *h_images, float *h_occupancy,

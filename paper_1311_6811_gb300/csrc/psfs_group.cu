@@ -98,11 +98,16 @@ struct GroupWords {
 };
 
 // Vector store / read-only vector load of the F * sizeof(T) bytes of one
-// pixel (4, 8, 16 or 32 bytes; the address is a multiple of that size).
+// pixel (4, 8, 16 or 32 bytes; the address is a multiple of that size, the
+// buffers are 256-byte aligned).
 template <int kWords>
 __device__ __forceinline__ void store_words(uint32_t *dst, const uint32_t *w)
 {
-    if constexpr (kWords == 1) {
+    if constexpr (kWords == 8) {
+        asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(w[0]), "r"(w[1]),
+                     "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                     : "memory");
+    } else if constexpr (kWords == 1) {
         *dst = w[0];
     } else if constexpr (kWords == 2) {
         *reinterpret_cast<uint2 *>(dst) = make_uint2(w[0], w[1]);
@@ -117,7 +122,13 @@ __device__ __forceinline__ void store_words(uint32_t *dst, const uint32_t *w)
 template <int kWords>
 __device__ __forceinline__ void load_words(const uint32_t *src, uint32_t *w)
 {
-    if constexpr (kWords == 1) {
+    if constexpr (kWords == 8) {
+        // one 256-bit read-only load per lane (sm_100+): a lane's whole
+        // 32-byte group vector, one L1 sector, in one request
+        asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+            : "l"(src));
+    } else if constexpr (kWords == 1) {
         w[0] = __ldg(src);
     } else if constexpr (kWords == 2) {
         const uint2 v = __ldg(reinterpret_cast<const uint2 *>(src));
@@ -156,11 +167,12 @@ __device__ __forceinline__ void group_pixel(const LikelihoodArgs &a, OutT *out, 
                                             int64_t im_stride, const float *m, const float *h)
 {
     GroupWords<OutT, F> pk;
+    const float m0 = m[0], m1 = m[1], m2 = m[2], h0 = h[0], h1 = h[1], h2 = h[2];
+    const float base = pixel_log_base(h0, h1, h2, a.c0);   // r = base + quad, as pixel_log_odds
 #pragma unroll
     for (int f = 0; f < F; ++f) {
         const unsigned char *q = im + f * im_stride;
-        const float r = pixel_log_odds((float)q[0], (float)q[1], (float)q[2], m[0], m[1], m[2], h[0], h[1], h[2],
-                                       a.c0);
+        const float r = base + pixel_quad((float)q[0], (float)q[1], (float)q[2], m0, m1, m2, h0, h1, h2);
         pk.set(f, to_map<OutT>(log_ratio_of_r(r, a.sc)));
     }
     store_words<GroupWords<OutT, F>::kWords>(reinterpret_cast<uint32_t *>(out + p * F), pk.w);
@@ -273,6 +285,67 @@ cudaError_t launch_lk_group_typed(const LikelihoodArgs &a, int frames, cudaStrea
 // ---------------------------------------------------------------------------
 // Fusion of a frame group
 // ---------------------------------------------------------------------------
+// Epilogue of a frame group: per frame the posterior, threshold and
+// compaction of tile_epilogue (the same per-voxel arithmetic), with the F
+// frames' counts taken together: two barriers per tile, and F threads each
+// reserve one frame's list range with one atomicAdd.
+template <int WY, int TZ, int F>
+__device__ __forceinline__ void group_epilogue(const FuseArgs &a, int i, int j, int k0, const float (&L)[F][TZ],
+                                               int lane, int wy, uint32_t (*s_off)[WY], uint32_t *s_base)
+{
+    const bool in_xy = (i < a.nx) && (j < a.ny);
+    const uint32_t zstride = (uint32_t)a.nx * (uint32_t)a.ny;
+    const uint32_t lin0 = (uint32_t)i + (uint32_t)a.nx * ((uint32_t)j + (uint32_t)a.ny * (uint32_t)k0);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        float *occ = a.occ + f * a.occ_fstride;
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int t = 0; t < TZ; ++t) {
+            const bool valid = in_xy && (k0 + t < a.nz);
+            const float lo = L[f][t] + a.logit_prior;
+            if (valid) __stcs(occ + lin0 + (uint32_t)t * zstride, __fdividef(1.0f, 1.0f + __expf(-lo)));
+            cnt += __popc(__ballot_sync(0xFFFFFFFFu, valid && (lo > a.logit_tau)));
+        }
+        if (lane == 0) s_off[f][wy] = cnt;
+    }
+    __syncthreads();
+    const int tid = wy * 32 + lane;
+    if (tid < F) {
+        uint32_t total = 0;
+#pragma unroll
+        for (int w = 0; w < WY; ++w) {
+            const uint32_t c = s_off[tid][w];
+            s_off[tid][w] = total;
+            total += c;
+        }
+        uint32_t base = 0;
+        if (total) {
+            base = atomicAdd(a.count + tid * a.count_fstride, total);
+            if ((uint64_t)base + total > (uint64_t)a.capacity) atomicOr(a.status, kStatusCapacity);
+        }
+        s_base[tid] = base;
+    }
+    __syncthreads();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        uint32_t *list = a.list + f * a.list_fstride;
+        uint32_t pos = s_base[f] + s_off[f][wy];
+#pragma unroll
+        for (int t = 0; t < TZ; ++t) {
+            const bool valid = in_xy && (k0 + t < a.nz);
+            const float lo = L[f][t] + a.logit_prior;
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, valid && (lo > a.logit_tau));
+            if ((b >> lane) & 1u) {
+                const uint32_t p = pos + __popc(b & lt_mask);
+                if (p < a.capacity) list[p] = lin0 + (uint32_t)t * zstride;
+            }
+            pos += __popc(b);
+        }
+    }
+}
+
 // The tile decomposition, per-tile camera records and projection are those of
 // the direct fuse kernel; a thread holds F x TZ log-odds accumulators.
 template <typename MapT, int LX, int WY, int TZ, int F>
@@ -280,8 +353,8 @@ __global__ void __launch_bounds__(32 * WY) fuse_group_kernel(const __grid_consta
 {
     using Words = GroupWords<MapT, F>;
     __shared__ int s_flags[PSFS_MAX_CAMS];
-    __shared__ uint32_t s_warp_off[WY];
-    __shared__ uint32_t s_base;
+    __shared__ uint32_t s_off[F][WY];
+    __shared__ uint32_t s_base[F];
 
     const int lane = threadIdx.x;
     const int wy = threadIdx.y;
@@ -334,11 +407,7 @@ __global__ void __launch_bounds__(32 * WY) fuse_group_kernel(const __grid_consta
             }
         }
     }
-#pragma unroll
-    for (int f = 0; f < F; ++f)
-        tile_epilogue_to<WY, TZ>(a, a.occ + f * a.occ_fstride, a.list + f * a.list_fstride,
-                                 a.count + f * a.count_fstride, tc.i, tc.j, tc.k0, L[f], lane, wy, s_warp_off,
-                                 &s_base);
+    group_epilogue<WY, TZ, F>(a, tc.i, tc.j, tc.k0, L, lane, wy, s_off, s_base);
 }
 
 template <typename MapT, int LX, int TZ, int F>

@@ -335,12 +335,25 @@ __device__ __forceinline__ float map_load<__nv_bfloat16>(const __nv_bfloat16 *p)
 // r = log U - log N (Eq. 1) for one pixel, from its colour, mean and
 // h = 1 / (2 var):  r = c0 - 0.5 log(h0 h1 h2) + sum_c (I_c - mu_c)^2 h_c,
 // c0 = log U + 1.5 log(pi).  The forward and the adjoint both call this.
+// The pixel's colour-independent part c0 - log(det)/2 and the quadratic form
+// sum (I - mu)^2 h; r is their sum.  Kernels that evaluate one pixel for
+// several frames compute the first part once and add it the same way.
+__device__ __forceinline__ float pixel_log_base(float h0, float h1, float h2, float c0)
+{
+    return c0 - 0.5f * __logf(h0 * h1 * h2);
+}
+
+__device__ __forceinline__ float pixel_quad(float i0, float i1, float i2, float m0, float m1, float m2, float h0,
+                                            float h1, float h2)
+{
+    const float d0 = i0 - m0, d1 = i1 - m1, d2 = i2 - m2;
+    return fmaf(d0 * d0, h0, fmaf(d1 * d1, h1, d2 * d2 * h2));
+}
+
 __device__ __forceinline__ float pixel_log_odds(float i0, float i1, float i2, float m0, float m1,
                                                 float m2, float h0, float h1, float h2, float c0)
 {
-    float d0 = i0 - m0, d1 = i1 - m1, d2 = i2 - m2;
-    float quad = fmaf(d0 * d0, h0, fmaf(d1 * d1, h1, d2 * d2 * h2));
-    return (c0 - 0.5f * __logf(h0 * h1 * h2)) + quad;
+    return pixel_log_base(h0, h1, h2, c0) + pixel_quad(i0, i1, i2, m0, m1, m2, h0, h1, h2);
 }
 
 // g(r) = log(P_D e^r + 1 - P_D) - log(q e^r + 1 - q), evaluated with
@@ -350,20 +363,15 @@ __device__ __forceinline__ float pixel_log_odds(float i0, float i1, float i2, fl
 // is 0 or 1, which takes the branch without the ratio.
 __device__ __forceinline__ float log_ratio_of_r(float r, const SensorConsts &c)
 {
-    float ar = fabsf(r);
-    float u = __expf(-ar);
-    float A, B;
-    bool deg;
-    if (r > 0.0f) {   // divide both by e^r
-        A = fmaf(c.one_minus_pd, u, c.pd);
-        B = fmaf(c.one_minus_q, u, c.q);
-        deg = c.a_zero_const_pos;
-    } else {
-        A = fmaf(c.pd, u, c.one_minus_pd);
-        B = fmaf(c.q, u, c.one_minus_q);
-        deg = c.a_zero_const_neg;
+    const float ar = fabsf(r);
+    const float u = __expf(-ar);
+    // r > 0: both terms divided by e^r.  Operand selects, not branches.
+    const bool pos = r > 0.0f;
+    const float A = fmaf(pos ? c.one_minus_pd : c.pd, u, pos ? c.pd : c.one_minus_pd);
+    const float B = fmaf(pos ? c.one_minus_q : c.q, u, pos ? c.q : c.one_minus_q);
+    if (c.a_zero_const_pos | c.a_zero_const_neg) {   // P_D in {0, 1} (uniform across the launch)
+        if (pos ? c.a_zero_const_pos : c.a_zero_const_neg) return -ar - __logf(B);   // A = e^-|r| exactly
     }
-    if (deg) return -ar - __logf(B);   // A = e^-|r| exactly
     return __logf(__fdividef(A, B));
 }
 

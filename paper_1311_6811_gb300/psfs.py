@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
             "psfs_reconstruct": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_reconstruct_host": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_reconstruct_sequence": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+            "psfs_reconstruct_sequence_host": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_set_background_l2": (st, [_vp, ctypes.c_int32]),
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
@@ -299,6 +300,20 @@ def psfs_reconstruct_host(h: int, images, occupancy, voxel_list, capacity: int, 
                                       _host_ptr(count, "count"))
     if st not in (PSFS_OK, PSFS_ERR_CAPACITY):
         _check(st, "psfs_reconstruct_host")
+    return st
+
+
+def psfs_reconstruct_sequence_host(h: int, n_frames: int, images, occupancy, voxel_lists, capacity: int,
+                                   counts) -> int:
+    """n_frames frames from and to host buffers (numpy arrays or CPU tensors,
+    pinned for speed; occupancy may be None).  Returns PSFS_OK or
+    PSFS_ERR_CAPACITY (anything else raises)."""
+    st = load().psfs_reconstruct_sequence_host(h, int(n_frames), _host_ptr(images, "images"),
+                                               _host_ptr(occupancy, "occupancy") if occupancy is not None else None,
+                                               _host_ptr(voxel_lists, "voxel_lists"), int(capacity),
+                                               _host_ptr(counts, "counts"))
+    if st not in (PSFS_OK, PSFS_ERR_CAPACITY):
+        _check(st, "psfs_reconstruct_sequence_host")
     return st
 
 

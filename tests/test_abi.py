@@ -139,6 +139,7 @@ def test_calls_reject_null_handle(lib):
     assert lib.psfs_set_background(None, None, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_reconstruct(None, None, None, None, 0, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_reconstruct_host(None, None, None, None, 0, None) == psfs.PSFS_ERR_INVALID_ARG
+    assert lib.psfs_reconstruct_sequence_host(None, 1, None, None, None, 0, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_fuse_slm(None, None, None, None, 0, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_get_likelihood(None, None, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_backward(None, None, None, None, None, None) == psfs.PSFS_ERR_INVALID_ARG

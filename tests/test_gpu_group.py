@@ -193,3 +193,44 @@ def test_autotune_picks_a_sequence_configuration():
     assert cfg[5] in (1, 2, 4, 8) and 1 <= cfg[4] <= 4
     assert rec.sync() == psfs.PSFS_OK
     rec.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_sequence_host_equals_device(pinned):
+    """psfs_reconstruct_sequence_host (copies in and out overlapping the
+    kernels, two staging slots reused across 5 chunks) gives the device
+    sequence's occupancy, counts and voxel sets."""
+    n = 37
+    sc = _scene(n)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 2, 2)   # groups of 2: chunks of 8 frames
+    V, cap = rec.n_voxels, rec.n_voxels // 4
+    occ_d, lists_d, counts_d = _run_sequence(rec, to_dev(sc.images), cap)
+
+    def host(shape, dtype):
+        t = torch.full(shape, -7, dtype=dtype)
+        return t.pin_memory() if pinned else t
+
+    imgs_h = torch.from_numpy(np.ascontiguousarray(sc.images))
+    imgs_h = imgs_h.pin_memory() if pinned else imgs_h
+    occ_h, lists_h, counts_h = host((n, V), torch.float32), host((n, cap), torch.int32), host((n,), torch.int32)
+    assert psfs.psfs_reconstruct_sequence_host(rec.handle, n, imgs_h, occ_h, lists_h, cap, counts_h) == psfs.PSFS_OK
+    np.testing.assert_array_equal(occ_h.numpy(), occ_d.cpu().numpy())
+    np.testing.assert_array_equal(counts_h.numpy(), counts_d.cpu().numpy())
+    for f in range(n):
+        c = int(counts_h[f])
+        np.testing.assert_array_equal(np.sort(lists_h[f, :c].numpy()),
+                                      psfs.voxel_list(lists_d[f], counts_d[f:f + 1], cap).numpy())
+        assert (lists_h[f, c:] == -7).all()   # nothing past the count is written
+    # without the occupancy copy, and with a capacity below the counts
+    small = int(counts_h.min()) // 2
+    lists2 = host((n, small), torch.int32)
+    counts2 = host((n,), torch.int32)
+    st = psfs.psfs_reconstruct_sequence_host(rec.handle, n, imgs_h, None, lists2, small, counts2)
+    assert st == psfs.PSFS_ERR_CAPACITY
+    np.testing.assert_array_equal(counts2.numpy(), counts_h.numpy())
+    l2 = lists2.numpy()
+    assert ((l2 >= 0) & (l2 < V)).all()
+    assert rec.sync() == psfs.PSFS_OK   # the capacity bit was cleared by the host call
+    rec.close()
