@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(32 * WY) backward_voxel_kernel(const __grid_co
         const int k = tc.k0 + t;
         if (k >= a.nz) break;
         const uint32_t lin = (uint32_t)tc.i + (uint32_t)a.nx * ((uint32_t)tc.j + (uint32_t)a.ny * (uint32_t)k);
-        const float occ = __fdividef(1.0f, 1.0f + __expf(-(L[t] + a.logit_prior)));
+        const float occ = posterior_of_logodds(L[t] + a.logit_prior);
         b.dl[lin] = __ldg(b.d_occ + lin) * occ * (1.0f - occ);
     }
 }
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) backward_pixel_kernel(const __grid_consta
                 }
                 r = pixel_log_odds((float)im[0], (float)im[1], (float)im[2], mu[0], mu[1], mu[2], hh[0], hh[1], hh[2],
                                    b.c0);
-                s_val = r > 0.0f ? __fdividef(1.0f, 1.0f + __expf(-r)) : __fdividef(__expf(r), 1.0f + __expf(r));
+                s_val = sigmoid_fast(r);
             } else {
                 s_val = __ldg(b.slm + p);
             }

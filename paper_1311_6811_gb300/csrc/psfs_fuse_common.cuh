@@ -54,7 +54,7 @@ __device__ __forceinline__ void tile_epilogue_to(const FuseArgs &a, float *occ, 
         const float lo = L[t] + a.logit_prior;
         if (valid) {
             const uint32_t lin = (uint32_t)i + (uint32_t)a.nx * ((uint32_t)j + (uint32_t)a.ny * (uint32_t)k);
-            __stcs(occ + lin, __fdividef(1.0f, 1.0f + __expf(-lo)));
+            __stcs(occ + lin, posterior_of_logodds(lo));
         }
         ballots[t] = __ballot_sync(0xFFFFFFFFu, valid && (lo > a.logit_tau));
         warp_count += __popc(ballots[t]);

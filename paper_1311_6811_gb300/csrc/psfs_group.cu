@@ -304,7 +304,7 @@ __device__ __forceinline__ void group_epilogue(const FuseArgs &a, int i, int j, 
         for (int t = 0; t < TZ; ++t) {
             const bool valid = in_xy && (k0 + t < a.nz);
             const float lo = L[f][t] + a.logit_prior;
-            if (valid) __stcs(occ + lin0 + (uint32_t)t * zstride, __fdividef(1.0f, 1.0f + __expf(-lo)));
+            if (valid) __stcs(occ + lin0 + (uint32_t)t * zstride, posterior_of_logodds(lo));
             cnt += __popc(__ballot_sync(0xFFFFFFFFu, valid && (lo > a.logit_tau)));
         }
         if (lane == 0) s_off[f][wy] = cnt;

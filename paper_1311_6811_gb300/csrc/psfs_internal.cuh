@@ -160,6 +160,44 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// The hardware approximations of 2^x and log2(x) with denormals flushed
+// (PTX ex2 / lg2 .approx.ftz), and e^x, log(x), a / b and the logistic
+// function built from them: e^x = 2^(x log2 e), log x = ln 2 log2 x,
+// a / b = a (1 / b).  Every kernel that evaluates these quantities (forward,
+// frame groups, adjoint) goes through these functions, so their results agree
+// bit for bit.
+constexpr float kLog2e = 1.44269504088896341f;
+constexpr float kLn2 = 0.693147180559945309f;
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float exp_fast(float x) { return ex2_approx(x * kLog2e); }
+__device__ __forceinline__ float log_fast(float x) { return lg2_approx(x) * kLn2; }
+__device__ __forceinline__ float div_fast(float a, float b) { return a * rcp_approx(b); }
+
+// posterior 1 / (1 + e^-lo) of log-odds lo (Eq. 3-4 in log form)
+__device__ __forceinline__ float posterior_of_logodds(float lo) { return rcp_approx(1.0f + exp_fast(-lo)); }
+
+// the silhouette likelihood s = 1 / (1 + e^-r) of Eq. 2, without overflow
+__device__ __forceinline__ float sigmoid_fast(float r)
+{
+    if (r > 0.0f) return rcp_approx(1.0f + exp_fast(-r));
+    const float e = exp_fast(r);
+    return div_fast(e, 1.0f + e);
+}
+
 // Pixel coordinate with a bias: fma with round-down of u * rw + 1.5 * 2^23
 // leaves floor(u * rw) in the low mantissa bits, so the bit pattern minus
 // kFloorBias is floor(u / w) for |u / w| < 2^22.  Outside that range, and for
@@ -340,7 +378,7 @@ __device__ __forceinline__ float map_load<__nv_bfloat16>(const __nv_bfloat16 *p)
 // several frames compute the first part once and add it the same way.
 __device__ __forceinline__ float pixel_log_base(float h0, float h1, float h2, float c0)
 {
-    return c0 - 0.5f * __logf(h0 * h1 * h2);
+    return c0 - 0.5f * log_fast(h0 * h1 * h2);
 }
 
 __device__ __forceinline__ float pixel_quad(float i0, float i1, float i2, float m0, float m1, float m2, float h0,
@@ -364,15 +402,15 @@ __device__ __forceinline__ float pixel_log_odds(float i0, float i1, float i2, fl
 __device__ __forceinline__ float log_ratio_of_r(float r, const SensorConsts &c)
 {
     const float ar = fabsf(r);
-    const float u = __expf(-ar);
+    const float u = exp_fast(-ar);
     // r > 0: both terms divided by e^r.  Operand selects, not branches.
     const bool pos = r > 0.0f;
     const float A = fmaf(pos ? c.one_minus_pd : c.pd, u, pos ? c.pd : c.one_minus_pd);
     const float B = fmaf(pos ? c.one_minus_q : c.q, u, pos ? c.q : c.one_minus_q);
     if (c.a_zero_const_pos | c.a_zero_const_neg) {   // P_D in {0, 1} (uniform across the launch)
-        if (pos ? c.a_zero_const_pos : c.a_zero_const_neg) return -ar - __logf(B);   // A = e^-|r| exactly
+        if (pos ? c.a_zero_const_pos : c.a_zero_const_neg) return -ar - log_fast(B);   // A = e^-|r| exactly
     }
-    return __logf(__fdividef(A, B));
+    return log_fast(div_fast(A, B));
 }
 
 // dg/dr of the function above, from the same e^-|r| terms:
@@ -380,17 +418,17 @@ __device__ __forceinline__ float log_ratio_of_r(float r, const SensorConsts &c)
 __device__ __forceinline__ float dlog_ratio_dr(float r, const SensorConsts &c)
 {
     const float ar = fabsf(r);
-    const float u = __expf(-ar);
+    const float u = exp_fast(-ar);
     if (r > 0.0f) {
         const float A = fmaf(c.one_minus_pd, u, c.pd), B = fmaf(c.one_minus_q, u, c.q);
         // A = e^-r exactly when P_D = 0: the first term is 0
-        const float t1 = c.a_zero_const_pos ? 0.0f : __fdividef(c.pd, A);
-        return t1 - __fdividef(c.q, B);
+        const float t1 = c.a_zero_const_pos ? 0.0f : div_fast(c.pd, A);
+        return t1 - div_fast(c.q, B);
     }
     const float A = fmaf(c.pd, u, c.one_minus_pd), B = fmaf(c.q, u, c.one_minus_q);
     // A = P_D u exactly when P_D = 1: the first term is 1
-    const float t1 = c.a_zero_const_neg ? 1.0f : __fdividef(c.pd * u, A);
-    return t1 - __fdividef(c.q * u, B);
+    const float t1 = c.a_zero_const_neg ? 1.0f : div_fast(c.pd * u, A);
+    return t1 - div_fast(c.q * u, B);
 }
 
 // ---------------------------------------------------------------------------

@@ -30,12 +30,6 @@ int sm_count()
     return cached[dev];
 }
 
-__device__ __forceinline__ float sigmoid(float r)
-{
-    if (r > 0.0f) return __fdividef(1.0f, 1.0f + __expf(-r));
-    const float e = __expf(r);
-    return __fdividef(e, 1.0f + e);
-}
 
 template <typename OutT>
 __device__ __forceinline__ void store1(OutT *out, int64_t p, float a);
@@ -65,7 +59,7 @@ __device__ __forceinline__ void likelihood_pixel(const LikelihoodArgs &a, OutT *
                                                  float i1, float i2, const float *m, const float *h)
 {
     const float r = pixel_log_odds(i0, i1, i2, m[0], m[1], m[2], h[0], h[1], h[2], a.c0);
-    store1<OutT>(out, p, kSlm ? sigmoid(r) : log_ratio_of_r(r, a.sc));
+    store1<OutT>(out, p, kSlm ? sigmoid_fast(r) : log_ratio_of_r(r, a.sc));
 }
 
 // n_tma_pix = n_pix rounded down to 16 pixels (48 image bytes), so every

@@ -52,11 +52,8 @@ __global__ void __launch_bounds__(256) noalloc_likelihood_kernel(const uint8_t *
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pix; p += stride) {
         const float h0 = 0.5f / var[3 * p], h1 = 0.5f / var[3 * p + 1], h2 = 0.5f / var[3 * p + 2];
-        const float d0 = (float)img[3 * p] - mean[3 * p];
-        const float d1 = (float)img[3 * p + 1] - mean[3 * p + 1];
-        const float d2 = (float)img[3 * p + 2] - mean[3 * p + 2];
-        const float quad = fmaf(d0 * d0, h0, fmaf(d1 * d1, h1, d2 * d2 * h2));
-        const float r = (c0 - 0.5f * __logf(h0 * h1 * h2)) + quad;
+        const float r = pixel_log_odds((float)img[3 * p], (float)img[3 * p + 1], (float)img[3 * p + 2], mean[3 * p],
+                                       mean[3 * p + 1], mean[3 * p + 2], h0, h1, h2, c0);
         maps[p] = log_ratio_of_r(r, sc);
     }
 }
