@@ -107,20 +107,66 @@ __global__ void __launch_bounds__(256) backward_pixel_kernel(const __grid_consta
             rb = fmaxf(rb, fabsf(e[bx] * ia - Bb));
             rc = fmaxf(rc, fabsf(e[cx] * ia - Bc));
         }
-        // slices in front of the camera: sign(s - q_a) = sign(d_ax)
+        // slices in front of the camera: sign(s - q_a) = sign(d_ax) = sg
         int s_lo = 0, s_hi = nn[ax] - 1;
+        const float sg = d[ax] > 0.0f ? 1.0f : -1.0f;
         if (d[ax] > 0.0f) s_lo = max(s_lo, floor_i(qa) + 1);
         else s_hi = min(s_hi, ceil_i(qa) - 1);
+        // Slices whose widened window can hold a lattice point of the grid:
+        // with |s - q_a| = sg (s - q_a) the window edges are linear in s, and
+        // lo_edge(s) <= n - 1, hi_edge(s) >= 0 are linear constraints on s.
+        // The range is widened by one slice each way against rounding (it
+        // only skips slices; every candidate is still tested exactly).
+        {
+            const float nbx = (float)(nn[bx] - 1), ncx = (float)(nn[cx] - 1);
+            float s_min = (float)s_lo, s_max = (float)s_hi;
+            // edge(s) = A + s B +- (sg (s - q_a) r + 1e-3) = k0 + k1 s
+            auto clip = [&](float A, float B, float r, float hi_bound) {
+                // hi edge >= 0:  (A - sg q_a r + 1e-3) + s (B + sg r) >= 0
+                const float k0h = A - sg * qa * r + 1e-3f, k1h = B + sg * r;
+                // lo edge <= hi_bound:  (A + sg q_a r - 1e-3) + s (B - sg r) <= hi_bound
+                const float k0l = A + sg * qa * r - 1e-3f, k1l = B - sg * r;
+                if (fabsf(k1h) > 1e-6f) {
+                    const float t = -k0h / k1h;
+                    if (k1h > 0.0f) s_min = fmaxf(s_min, floorf(t) - 1.0f);
+                    else s_max = fminf(s_max, ceilf(t) + 1.0f);
+                } else if (k0h < -1.0f) {
+                    s_max = -1.0f;   // never reaches the grid
+                }
+                if (fabsf(k1l) > 1e-6f) {
+                    const float t = (hi_bound - k0l) / k1l;
+                    if (k1l > 0.0f) s_max = fminf(s_max, ceilf(t) + 1.0f);
+                    else s_min = fmaxf(s_min, floorf(t) - 1.0f);
+                } else if (k0l > hi_bound + 1.0f) {
+                    s_max = -1.0f;
+                }
+            };
+            clip(Ab, Bb, rb, nbx);
+            clip(Ac, Bc, rc, ncx);
+            if (!(s_min <= s_max)) {   // also NaN: the ray misses the grid
+                s_lo = 1;
+                s_hi = 0;
+            } else {
+                const float top = (float)nn[ax];
+                s_lo = max(s_lo, (int)fminf(fmaxf(s_min, -1.0f), top));
+                s_hi = min(s_hi, (int)fminf(fmaxf(s_max, -1.0f), top));
+            }
+        }
         const float* m = a.cam[cam].m;
         const float *dl = b.dl;
+        const float nb1 = (float)(nn[bx] - 1), nc1 = (float)(nn[cx] - 1);
         float acc = 0.0f;
         for (int s = s_lo; s <= s_hi; ++s) {
             const float fs = (float)s;
             const float b0 = fmaf(fs, Bb, Ab), c0 = fmaf(fs, Bc, Ac);
             const float ds = fabsf(fs - qa);
             const float eb = fmaf(ds, rb, 1e-3f), ec = fmaf(ds, rc, 1e-3f);
-            const int b_lo = max(0, ceil_i(b0 - eb)), b_hi = min(nn[bx] - 1, floor_i(b0 + eb));
-            const int c_lo = max(0, ceil_i(c0 - ec)), c_hi = min(nn[cx] - 1, floor_i(c0 + ec));
+            // lattice points of the window, as floats: most slices hold none
+            const float fb_lo = fmaxf(ceilf(b0 - eb), 0.0f), fb_hi = fminf(floorf(b0 + eb), nb1);
+            if (!(fb_lo <= fb_hi)) continue;
+            const float fc_lo = fmaxf(ceilf(c0 - ec), 0.0f), fc_hi = fminf(floorf(c0 + ec), nc1);
+            if (!(fc_lo <= fc_hi)) continue;
+            const int b_lo = (int)fb_lo, b_hi = (int)fb_hi, c_lo = (int)fc_lo, c_hi = (int)fc_hi;
             for (int ib = b_lo; ib <= b_hi; ++ib)
                 for (int ic = c_lo; ic <= c_hi; ++ic) {
                     int idx[3];
