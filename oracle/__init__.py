@@ -53,6 +53,8 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_slm.argtypes = [ctypes.c_int64, _u8p, _f32p, _f32p, ctypes.c_double, _dp]
             lib.oracle_slm.restype = None
+            lib.oracle_surface.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _u8p, _u32p]
+            lib.oracle_surface.restype = ctypes.c_int64
             lib.oracle_project.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _i32p, _i32p,
                                            _dp, _dp]
             lib.oracle_project.restype = ctypes.c_int
@@ -175,6 +177,20 @@ def fuse(grid, cams, slm_maps: np.ndarray, params=None, edge_eps: float = 1e-3) 
     assert n == lst.size
     return {"occ": occ, "logodds": lo, "occupied": occupied.astype(bool),
             "boundary": boundary.astype(bool), "n_seen": n_seen, "list": lst}
+
+
+def surface(shape, occupied) -> np.ndarray:
+    """Inner-voxel removal: ascending linear indices of the occupied voxels
+    with a face neighbour that is not occupied (outside the grid counts as not
+    occupied).  `shape` = (nx, ny, nz); `occupied` has nx*ny*nz entries in
+    linear order i + nx (j + ny k)."""
+    lib = _load()
+    nx, ny, nz = (int(x) for x in shape)
+    occ = np.ascontiguousarray(np.asarray(occupied).ravel() != 0, dtype=np.uint8)
+    assert occ.size == nx * ny * nz
+    out = np.empty(max(int(occ.sum()), 1), np.uint32)
+    n = lib.oracle_surface(nx, ny, nz, _ptr(occ, _u8p), _ptr(out, _u32p))
+    return out[:n].copy()
 
 
 def reconstruct(grid, cams, images, mean, var, params=None, edge_eps: float = 1e-3) -> dict:

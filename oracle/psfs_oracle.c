@@ -177,6 +177,36 @@ int64_t oracle_compact(int64_t n_vox, const uint8_t *occupied, uint32_t *list)
 }
 
 /* --------------------------------------------------------------------- */
+/* Inner-voxel removal (end of Sec. 2.2.2; Sec. 3.3.3 step (e)): the      */
+/* surface voxels are the occupied voxels with at least one of their six  */
+/* face neighbours not occupied; a neighbour outside the grid counts as   */
+/* not occupied.  Ascending linear indices; returns the count.            */
+/* --------------------------------------------------------------------- */
+static int occupied_at(int nx, int ny, int nz, const uint8_t *occupied, int i, int j, int k)
+{
+    if (i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) return 0;
+    return occupied[(int64_t)i + (int64_t)nx * ((int64_t)j + (int64_t)ny * k)] != 0;
+}
+
+int64_t oracle_surface(int nx, int ny, int nz, const uint8_t *occupied, uint32_t *list)
+{
+    int64_t n = 0;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                if (!occupied_at(nx, ny, nz, occupied, i, j, k)) continue;
+                int inner = occupied_at(nx, ny, nz, occupied, i - 1, j, k) &&
+                            occupied_at(nx, ny, nz, occupied, i + 1, j, k) &&
+                            occupied_at(nx, ny, nz, occupied, i, j - 1, k) &&
+                            occupied_at(nx, ny, nz, occupied, i, j + 1, k) &&
+                            occupied_at(nx, ny, nz, occupied, i, j, k - 1) &&
+                            occupied_at(nx, ny, nz, occupied, i, j, k + 1);
+                if (!inner) list[n++] = (uint32_t)((int64_t)i + (int64_t)nx * ((int64_t)j + (int64_t)ny * k));
+            }
+    return n;
+}
+
+/* --------------------------------------------------------------------- */
 /* Adjoint of Eq. 3-4 with respect to the maps.                           */
 /* Given dLoss/docc per voxel:                                            */
 /*   dLoss/dlogodds_v = docc_v occ_v (1 - occ_v)                          */
