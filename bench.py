@@ -476,6 +476,39 @@ def run_ours(args):
                 "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": traffic,
                 "alg_bytes_per_launch": stages[dom]["alg_bytes_per_launch"]}
 
+    # inner-voxel removal on the step's lists (all frames in one call), timed
+    # with events on the handle's stream; not part of the headline value
+    nxt = None
+    if batch is None:
+        scap = cap
+        s_lists = torch.empty((F, scap), dtype=torch.int32, device=dev)
+        s_counts = torch.zeros((F,), dtype=torch.int32, device=dev)
+        with torch.cuda.stream(stream):
+            psfs.psfs_surface(h, F, lists, cap, counts, s_lists, scap, s_counts)   # warm-up (scratch)
+            reps = 10
+            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0e.record(stream)
+            for _ in range(reps):
+                psfs.psfs_surface(h, F, lists, cap, counts, s_lists, scap, s_counts)
+            t1e.record(stream)
+        torch.cuda.synchronize(dev)
+        st_s = psfs.psfs_sync(h)
+        if st_s != psfs.PSFS_OK:
+            raise RuntimeError(f"surface pass failed: {psfs.psfs_status_string(st_s)}")
+        us_call = 1e3 * t0e.elapsed_time(t1e) / reps
+        n_surf = float(s_counts.double().mean().item())
+        # per frame: the list read twice, the bitmask zeroed (n_vox / 8 B), six
+        # neighbour words read per listed voxel, the surface list written
+        surf_bytes = mean_count * 4 * 2 + V / 8 + mean_count * 6 * 4 + n_surf * 4
+        peak_s, _ = measured_peaks()
+        nxt = {"surface": {"us_per_frame": us_call / F, "frames_per_call": F, "launches_per_call": 3,
+                           "occupied_per_frame": mean_count, "surface_voxels_per_frame": n_surf,
+                           "alg_bytes_per_frame": surf_bytes,
+                           "achieved_gbs": surf_bytes / (us_call / F * 1e-6) / 1e9,
+                           "hbm_frac": surf_bytes / (us_call / F * 1e-6) / 1e9 / peak_s,
+                           "note": "psfs_surface over the step's 100 lists in one call (memset + 2 kernels); "
+                                   "latency-bound: ~30 K listed voxels per frame"}}
+
     # end to end through the C ABI with host buffers (pinned): the whole
     # sequence per step through psfs_reconstruct_sequence_host, which copies
     # the images in and the occupancy grids, counts and voxel lists out,
@@ -537,6 +570,7 @@ def run_ours(args):
                                       "and one projection per group; 2 streams, double-buffered maps)"),
                            "background_l2_resident": not args.no_l2_background},
                 "stages": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
+                "next": nxt,
                 "gpu_launches": sum(v["launches"] for v in stages.values()), "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0

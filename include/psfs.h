@@ -200,6 +200,30 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
                                            float *h_occupancy, uint32_t *h_lists, uint32_t capacity,
                                            uint32_t *h_counts);
 
+/* Inner-voxel removal (end of Section 2.2.2 and step (e) of Section 3.3.3 of
+ * the paper, which removes the voxels inside the body and keeps the surface
+ * voxels): for each of n_frames frames of this handle's grid, the surface
+ * voxels are the listed (occupied) voxels with at least one of their six face
+ * neighbours not listed; a neighbour outside the grid counts as not listed.
+ *   voxel_lists      device uint32, frame f's occupied voxels (linear indices,
+ *                    any order, as psfs_reconstruct* write them) at
+ *                    voxel_lists + f * list_stride
+ *   counts           device uint32 [n_frames]; counts[f] > list_stride (an
+ *                    overflowed list) makes the frame's result incomplete and
+ *                    is reported by psfs_sync as PSFS_ERR_CAPACITY
+ *   surface_lists    device uint32, frame f's surface voxels at
+ *                    surface_lists + f * surface_capacity (order unspecified;
+ *                    only the first surface_capacity are written)
+ *   surface_counts   device uint32 [n_frames], the surface voxel counts (even
+ *                    beyond surface_capacity; overflow is reported by psfs_sync)
+ * Work is proportional to the listed voxels: one occupancy bitmask per frame
+ * (n_vox / 8 bytes of handle scratch per frame, grown on demand) is built
+ * from the lists and probed for the six neighbours.  Enqueued on the
+ * handle's stream after earlier work.  Errors: INVALID_ARG, NOMEM, CUDA. */
+psfs_status psfs_surface(psfs_handle *h, int32_t n_frames, const uint32_t *voxel_lists, uint32_t list_stride,
+                         const uint32_t *counts, uint32_t *surface_lists, uint32_t surface_capacity,
+                         uint32_t *surface_counts);
+
 /* Keeps the packed background (24 bytes per pixel) resident in L2 for the
  * likelihood stage of psfs_reconstruct_sequence (enable = 1), through an L2
  * access-policy window on the sequence path's own likelihood stream; frames
@@ -291,6 +315,7 @@ typedef enum {
     PSFS_STAGE_BACKWARD_VOXEL = 2,  /* adjoint: recomputed log-odds -> dLoss/dL     */
     PSFS_STAGE_BACKWARD_PIXEL = 3,  /* adjoint: per-pixel owner pass + chain rule   */
     PSFS_STAGE_BATCH = 4,        /* batched persistent launch                       */
+    PSFS_STAGE_SURFACE = 5,      /* inner-voxel removal (psfs_surface)              */
     PSFS_N_STAGES = 8
 } psfs_stage;
 

@@ -80,6 +80,10 @@ struct psfs_handle {
     int io_frames = 0;          // frames per slot
     uint32_t io_cap = 0;        // list entries per frame
 
+    // inner-voxel removal: per-frame occupancy bitmasks (first use)
+    uint32_t *surf_masks = nullptr;
+    int surf_frames = 0;
+
     // tracing: CUDA event pairs around each launch
     int prof_cap = 0;
     std::vector<cudaEvent_t> prof_ev;      // 2 * prof_cap events
@@ -167,6 +171,7 @@ void free_handle(psfs_handle *h)
     cudaFree(h->maps2);
     cudaFree(h->gmaps[0]);
     cudaFree(h->gmaps[1]);
+    cudaFree(h->surf_masks);
     for (int n = 0; n < 2; ++n) {
         if (h->io_stream[n]) cudaStreamSynchronize(h->io_stream[n]);
         if (h->io_stream[n]) cudaStreamDestroy(h->io_stream[n]);
@@ -795,6 +800,53 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
         PSFS_CK(cudaStreamSynchronize(h->stream));
         return fail(PSFS_ERR_CAPACITY, "voxel list capacity exceeded");
     }
+    return PSFS_OK;
+}
+
+psfs_status psfs_surface(psfs_handle *h, int32_t n_frames, const uint32_t *voxel_lists, uint32_t list_stride,
+                         const uint32_t *counts, uint32_t *surface_lists, uint32_t surface_capacity,
+                         uint32_t *surface_counts)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (n_frames < 0) return fail(PSFS_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames == 0) return PSFS_OK;
+    if (list_stride > 0 && (!voxel_lists || !aligned(voxel_lists, 4)))
+        return fail(PSFS_ERR_INVALID_ARG, "voxel_lists NULL or not 4-byte aligned");
+    if (!counts || !aligned(counts, 4)) return fail(PSFS_ERR_INVALID_ARG, "counts NULL or not 4-byte aligned");
+    if (surface_capacity > 0 && (!surface_lists || !aligned(surface_lists, 4)))
+        return fail(PSFS_ERR_INVALID_ARG, "surface_lists NULL or not 4-byte aligned");
+    if (!surface_counts || !aligned(surface_counts, 4))
+        return fail(PSFS_ERR_INVALID_ARG, "surface_counts NULL or not 4-byte aligned");
+    DeviceGuard guard(h->device);
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    const uint32_t words = (uint32_t)((n_vox + 31) / 32);
+    if (n_frames > h->surf_frames) {
+        PSFS_CK(cudaStreamSynchronize(h->stream));
+        cudaFree(h->surf_masks);
+        h->surf_masks = nullptr;
+        h->surf_frames = 0;
+        if (cudaMalloc(&h->surf_masks, (size_t)n_frames * words * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "surface bitmasks");
+        }
+        h->surf_frames = n_frames;
+    }
+    SurfaceArgs a{};
+    a.lists = voxel_lists;
+    a.list_stride = list_stride;
+    a.counts = counts;
+    a.surface_lists = surface_lists;
+    a.surface_capacity = surface_capacity;
+    a.surface_counts = surface_counts;
+    a.masks = h->surf_masks;
+    a.mask_words = words;
+    a.n_vox = (uint32_t)n_vox;
+    a.nx = h->grid.nx;
+    a.ny = h->grid.ny;
+    a.nz = h->grid.nz;
+    a.status = h->d_words;
+    ProfScope ps(h, PSFS_STAGE_SURFACE);
+    PSFS_CK(launch_surface(a, n_frames, h->stream));
     return PSFS_OK;
 }
 

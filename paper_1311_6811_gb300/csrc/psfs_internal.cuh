@@ -512,6 +512,26 @@ cudaError_t launch_backward_pixel(const BackwardArgs &a, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 cudaError_t launch_fuse_staged(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 
+// Inner-voxel removal over the occupied-voxel lists of n frames
+// (psfs_surface.cu): frame f's list at lists + f * list_stride with counts[f]
+// entries, its occupancy bitmask at masks + f * mask_words (mask_words =
+// ceil(n_vox / 32), zeroed by the launcher), its surface voxels appended at
+// surface_lists + f * surface_capacity, counted in surface_counts[f].
+struct SurfaceArgs {
+    const uint32_t *lists;
+    uint32_t list_stride;
+    const uint32_t *counts;
+    uint32_t *surface_lists;
+    uint32_t surface_capacity;
+    uint32_t *surface_counts;
+    uint32_t *masks;
+    uint32_t mask_words;
+    uint32_t n_vox;
+    int nx, ny, nz;
+    uint32_t *status;
+};
+cudaError_t launch_surface(const SurfaceArgs &a, int n_frames, cudaStream_t s);
+
 // Frame groups of the sequence path (psfs_group.cu): F frames share one pass
 // over the background (likelihood) and one projection per voxel and camera
 // (fusion), with the maps of the group interleaved per pixel.  Each frame's

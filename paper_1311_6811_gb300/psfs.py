@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
             "psfs_reconstruct_host": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_reconstruct_sequence": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_reconstruct_sequence_host": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+            "psfs_surface": (st, [_vp, ctypes.c_int32, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_set_background_l2": (st, [_vp, ctypes.c_int32]),
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
@@ -317,6 +318,15 @@ def psfs_reconstruct_sequence_host(h: int, n_frames: int, images, occupancy, vox
     return st
 
 
+def psfs_surface(h: int, n_frames: int, voxel_lists, list_stride: int, counts, surface_lists,
+                 surface_capacity: int, surface_counts):
+    """Inner-voxel removal on the device: frame f's surface voxels (listed
+    voxels with a face neighbour not listed) from its occupied-voxel list."""
+    _check(load().psfs_surface(h, int(n_frames), _dev_ptr(voxel_lists, "voxel_lists"), int(list_stride),
+                               _dev_ptr(counts, "counts"), _dev_ptr(surface_lists, "surface_lists"),
+                               int(surface_capacity), _dev_ptr(surface_counts, "surface_counts")), "psfs_surface")
+
+
 def psfs_fuse_slm(h: int, slm, occupancy, voxel_list, capacity: int, count):
     import torch
     _check(load().psfs_fuse_slm(h, _dev_ptr(slm, "slm", torch.float32),
@@ -469,7 +479,7 @@ def psfs_batch_destroy(b: int):
 
 
 PSFS_N_STAGES = 8
-STAGE_NAMES = ["likelihood", "fuse", "backward_voxel", "backward_pixel", "batch"]
+STAGE_NAMES = ["likelihood", "fuse", "backward_voxel", "backward_pixel", "batch", "surface"]
 
 
 def psfs_profile_enable(h: int, max_launches: int):
