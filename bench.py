@@ -532,9 +532,21 @@ def run_ours(args):
             d2h += F * V * 4 + F * 4 + 4 * int(torch.clamp(h_cnt.long(), max=cap_e2e).sum())
         dt = max_over_ranks(time.perf_counter() - t0, dev)
         barrier()
+        # the host link alone, same pinned buffers: one copy each way
+        d_img_tmp = torch.empty(images.shape, dtype=torch.uint8, device=dev)
+        link = {}
+        for name, dst, src in (("h2d_gbs", d_img_tmp, h_images), ("d2h_gbs", h_occ, occ)):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            link[name] = src.numel() * src.element_size() / (time.perf_counter() - t0) / 1e9
+        del d_img_tmp
         e2e = {"value": sum_over_ranks(float(F * V * K * e2e_steps), dev) / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": F * n_pix * 3, "d2h_bytes_per_step": int(d2h / e2e_steps),
                "steps": e2e_steps, "ms_per_step": 1e3 * dt / e2e_steps,
+               "link_alone": {k: round(v, 1) for k, v in link.items()},
                "path": "psfs_reconstruct_sequence_host over the step's frames (pinned host buffers; "
                        "copies in and out overlap the kernels)"}
 

@@ -53,6 +53,9 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_slm.argtypes = [ctypes.c_int64, _u8p, _f32p, _f32p, ctypes.c_double, _dp]
             lib.oracle_slm.restype = None
+            lib.oracle_smooth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, _dp,
+                                          _u8p]
+            lib.oracle_smooth.restype = None
             lib.oracle_surface.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _u8p, _u32p]
             lib.oracle_surface.restype = ctypes.c_int64
             lib.oracle_project.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _i32p, _i32p,
@@ -177,6 +180,21 @@ def fuse(grid, cams, slm_maps: np.ndarray, params=None, edge_eps: float = 1e-3) 
     assert n == lst.size
     return {"occ": occ, "logodds": lo, "occupied": occupied.astype(bool),
             "boundary": boundary.astype(bool), "n_seen": n_seen, "list": lst}
+
+
+def smooth(shape, prob, threshold: float = 0.5) -> dict:
+    """3 x 3 x 3 box mean of the voxel probabilities over the neighbours
+    inside the grid, then the strict threshold: {"smoothed", "occupied",
+    "list"} (ascending linear indices).  `prob` has nx*ny*nz entries in linear
+    order i + nx (j + ny k)."""
+    lib = _load()
+    nx, ny, nz = (int(x) for x in shape)
+    p = np.ascontiguousarray(np.asarray(prob, np.float64).ravel())
+    assert p.size == nx * ny * nz
+    sm = np.empty_like(p)
+    occ = np.empty(p.size, np.uint8)
+    lib.oracle_smooth(nx, ny, nz, _ptr(p, _dp), float(threshold), _ptr(sm, _dp), _ptr(occ, _u8p))
+    return {"smoothed": sm, "occupied": occ.astype(bool), "list": np.flatnonzero(occ).astype(np.uint32)}
 
 
 def surface(shape, occupied) -> np.ndarray:

@@ -177,6 +177,35 @@ int64_t oracle_compact(int64_t n_vox, const uint8_t *occupied, uint32_t *list)
 }
 
 /* --------------------------------------------------------------------- */
+/* Spatial smoothing of the voxel probabilities before the threshold      */
+/* (end of Sec. 2.2.2; Sec. 3.3.3 step (d)).  The paper does not give the */
+/* filter; this is the 3 x 3 x 3 box mean over the neighbours inside the  */
+/* grid (each voxel's own 27-neighbourhood clipped to the grid, divided   */
+/* by the number of voxels in it).  occupied <=> smoothed > threshold.    */
+/* --------------------------------------------------------------------- */
+void oracle_smooth(int nx, int ny, int nz, const double *prob, double threshold, double *smoothed,
+                   uint8_t *occupied)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double sum = 0.0;
+                int n = 0;
+                for (int dk = -1; dk <= 1; ++dk)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        for (int di = -1; di <= 1; ++di) {
+                            int a = i + di, b = j + dj, c = k + dk;
+                            if (a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) continue;
+                            sum += prob[(int64_t)a + (int64_t)nx * ((int64_t)b + (int64_t)ny * c)];
+                            ++n;
+                        }
+                int64_t v = (int64_t)i + (int64_t)nx * ((int64_t)j + (int64_t)ny * k);
+                smoothed[v] = sum / n;
+                occupied[v] = smoothed[v] > threshold;
+            }
+}
+
+/* --------------------------------------------------------------------- */
 /* Inner-voxel removal (end of Sec. 2.2.2; Sec. 3.3.3 step (e)): the      */
 /* surface voxels are the occupied voxels with at least one of their six  */
 /* face neighbours not occupied; a neighbour outside the grid counts as   */
