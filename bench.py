@@ -508,6 +508,29 @@ def run_ours(args):
                            "hbm_frac": surf_bytes / (us_call / F * 1e-6) / 1e9 / peak_s,
                            "note": "psfs_surface over the step's 100 lists in one call (memset + 2 kernels); "
                                    "latency-bound: ~30 K listed voxels per frame"}}
+        # smoothing + threshold + compaction over the step's occupancy grids
+        sm_grid = torch.empty((F, V), dtype=torch.float32, device=dev)
+        sm_counts = torch.zeros((F,), dtype=torch.int32, device=dev)
+        with torch.cuda.stream(stream):
+            psfs.psfs_smooth(h, F, occ, sm_grid, s_lists, scap, sm_counts)   # warm-up
+            t0e.record(stream)
+            for _ in range(reps):
+                psfs.psfs_smooth(h, F, occ, sm_grid, s_lists, scap, sm_counts)
+            t1e.record(stream)
+        torch.cuda.synchronize(dev)
+        st_s = psfs.psfs_sync(h)
+        if st_s != psfs.PSFS_OK:
+            raise RuntimeError(f"smoothing pass failed: {psfs.psfs_status_string(st_s)}")
+        us_sm = 1e3 * t0e.elapsed_time(t1e) / reps / F
+        n_sm = float(sm_counts.double().mean().item())
+        sm_bytes = V * 4 * 2 + n_sm * 4
+        nxt["smooth"] = {"us_per_frame": us_sm, "frames_per_call": F, "launches_per_call": 2,
+                         "voxels_above_threshold_per_frame": n_sm, "alg_bytes_per_frame": sm_bytes,
+                         "achieved_gbs": sm_bytes / (us_sm * 1e-6) / 1e9,
+                         "hbm_frac": sm_bytes / (us_sm * 1e-6) / 1e9 / peak_s,
+                         "note": "psfs_smooth over the step's 100 occupancy grids in one call: read the "
+                                 "probabilities, write the smoothed grid and the list (memset + 1 kernel)"}
+        del sm_grid
 
     # end to end through the C ABI with host buffers (pinned): the whole
     # sequence per step through psfs_reconstruct_sequence_host, which copies

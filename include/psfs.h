@@ -200,6 +200,29 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
                                            float *h_occupancy, uint32_t *h_lists, uint32_t capacity,
                                            uint32_t *h_counts);
 
+/* Smoothing of the voxel probabilities before the threshold (end of Section
+ * 2.2.2, which filters the probabilities and then thresholds them; step (d)
+ * of Section 3.3.3).  The paper does not give the filter; this is the
+ * 3 x 3 x 3 box mean over the neighbours inside the grid (a voxel's
+ * 27-neighbourhood clipped to the grid, divided by the number of voxels in
+ * it, summed along x, then y, then z in FP32), followed by the strict
+ * threshold smoothed > params.threshold and the compaction.  For n_frames
+ * frames of this handle's grid:
+ *   occupancy      device f32, frame f's posterior grid [nz][ny][nx] (as
+ *                  psfs_reconstruct* write it) at occupancy + f * n_vox
+ *   smoothed       device f32 or NULL, frame f's smoothed grid at
+ *                  smoothed + f * n_vox
+ *   voxel_lists    device uint32, frame f's voxels above the threshold at
+ *                  voxel_lists + f * capacity (order unspecified; only the
+ *                  first `capacity` are written)
+ *   counts         device uint32 [n_frames], set to the full counts; overflow
+ *                  is reported by psfs_sync as PSFS_ERR_CAPACITY
+ * One launch for all frames; each probability is read once from memory.
+ * Errors: INVALID_ARG (NULL or misaligned pointers, more than 65535 / (nz / 8)
+ * frames), CUDA. */
+psfs_status psfs_smooth(psfs_handle *h, int32_t n_frames, const float *occupancy, float *smoothed,
+                        uint32_t *voxel_lists, uint32_t capacity, uint32_t *counts);
+
 /* Inner-voxel removal (end of Section 2.2.2 and step (e) of Section 3.3.3 of
  * the paper, which removes the voxels inside the body and keeps the surface
  * voxels): for each of n_frames frames of this handle's grid, the surface
@@ -316,6 +339,7 @@ typedef enum {
     PSFS_STAGE_BACKWARD_PIXEL = 3,  /* adjoint: per-pixel owner pass + chain rule   */
     PSFS_STAGE_BATCH = 4,        /* batched persistent launch                       */
     PSFS_STAGE_SURFACE = 5,      /* inner-voxel removal (psfs_surface)              */
+    PSFS_STAGE_SMOOTH = 6,       /* smoothing + threshold (psfs_smooth)             */
     PSFS_N_STAGES = 8
 } psfs_stage;
 

@@ -803,6 +803,36 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
     return PSFS_OK;
 }
 
+psfs_status psfs_smooth(psfs_handle *h, int32_t n_frames, const float *occupancy, float *smoothed,
+                        uint32_t *voxel_lists, uint32_t capacity, uint32_t *counts)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (n_frames < 0) return fail(PSFS_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames == 0) return PSFS_OK;
+    if (!occupancy || !aligned(occupancy, 4)) return fail(PSFS_ERR_INVALID_ARG, "occupancy NULL or not 4-byte aligned");
+    if (smoothed && !aligned(smoothed, 4)) return fail(PSFS_ERR_INVALID_ARG, "smoothed not 4-byte aligned");
+    if (capacity > 0 && (!voxel_lists || !aligned(voxel_lists, 4)))
+        return fail(PSFS_ERR_INVALID_ARG, "voxel_lists NULL or not 4-byte aligned");
+    if (!counts || !aligned(counts, 4)) return fail(PSFS_ERR_INVALID_ARG, "counts NULL or not 4-byte aligned");
+    const int tz = (h->grid.nz + 7) / 8;
+    if ((int64_t)tz * n_frames > 65535) return fail(PSFS_ERR_INVALID_ARG, "too many frames for one call");
+    DeviceGuard guard(h->device);
+    SmoothArgs a{};
+    a.prob = occupancy;
+    a.smoothed = smoothed;
+    a.lists = voxel_lists;
+    a.capacity = capacity;
+    a.counts = counts;
+    a.nx = h->grid.nx;
+    a.ny = h->grid.ny;
+    a.nz = h->grid.nz;
+    a.threshold = (float)h->params.threshold;
+    a.status = h->d_words;
+    ProfScope ps(h, PSFS_STAGE_SMOOTH);
+    PSFS_CK(launch_smooth(a, n_frames, h->stream));
+    return PSFS_OK;
+}
+
 psfs_status psfs_surface(psfs_handle *h, int32_t n_frames, const uint32_t *voxel_lists, uint32_t list_stride,
                          const uint32_t *counts, uint32_t *surface_lists, uint32_t surface_capacity,
                          uint32_t *surface_counts)

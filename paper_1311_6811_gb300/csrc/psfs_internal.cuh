@@ -532,6 +532,22 @@ struct SurfaceArgs {
 };
 cudaError_t launch_surface(const SurfaceArgs &a, int n_frames, cudaStream_t s);
 
+// Smoothing before the threshold (psfs_smooth.cu): frame f's probabilities at
+// prob + f * n_vox, its smoothed grid (if not null) at smoothed + f * n_vox,
+// its list at lists + f * capacity, its count at counts[f] (zeroed by the
+// launcher).
+struct SmoothArgs {
+    const float *prob;
+    float *smoothed;
+    uint32_t *lists;
+    uint32_t capacity;
+    uint32_t *counts;
+    int nx, ny, nz;
+    float threshold;
+    uint32_t *status;
+};
+cudaError_t launch_smooth(const SmoothArgs &a, int n_frames, cudaStream_t s);
+
 // Frame groups of the sequence path (psfs_group.cu): F frames share one pass
 // over the background (likelihood) and one projection per voxel and camera
 // (fusion), with the maps of the group interleaved per pixel.  Each frame's

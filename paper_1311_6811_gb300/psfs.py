@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
             "psfs_reconstruct_sequence": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_reconstruct_sequence_host": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_surface": (st, [_vp, ctypes.c_int32, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp]),
+            "psfs_smooth": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_set_background_l2": (st, [_vp, ctypes.c_int32]),
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
@@ -318,6 +319,16 @@ def psfs_reconstruct_sequence_host(h: int, n_frames: int, images, occupancy, vox
     return st
 
 
+def psfs_smooth(h: int, n_frames: int, occupancy, smoothed, voxel_lists, capacity: int, counts):
+    """Smoothing (3 x 3 x 3 box mean over in-grid neighbours) of n_frames
+    posterior grids, strict threshold and compaction; `smoothed` may be None."""
+    import torch
+    _check(load().psfs_smooth(h, int(n_frames), _dev_ptr(occupancy, "occupancy", torch.float32),
+                              _dev_ptr(smoothed, "smoothed", torch.float32) if smoothed is not None else None,
+                              _dev_ptr(voxel_lists, "voxel_lists"), int(capacity), _dev_ptr(counts, "counts")),
+           "psfs_smooth")
+
+
 def psfs_surface(h: int, n_frames: int, voxel_lists, list_stride: int, counts, surface_lists,
                  surface_capacity: int, surface_counts):
     """Inner-voxel removal on the device: frame f's surface voxels (listed
@@ -479,7 +490,7 @@ def psfs_batch_destroy(b: int):
 
 
 PSFS_N_STAGES = 8
-STAGE_NAMES = ["likelihood", "fuse", "backward_voxel", "backward_pixel", "batch", "surface"]
+STAGE_NAMES = ["likelihood", "fuse", "backward_voxel", "backward_pixel", "batch", "surface", "smooth"]
 
 
 def psfs_profile_enable(h: int, max_launches: int):
