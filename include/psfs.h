@@ -218,8 +218,8 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
  *   counts         device uint32 [n_frames], set to the full counts; overflow
  *                  is reported by psfs_sync as PSFS_ERR_CAPACITY
  * One launch for all frames; each probability is read once from memory.
- * Errors: INVALID_ARG (NULL or misaligned pointers, more than 65535 / (nz / 8)
- * frames), CUDA. */
+ * Errors: INVALID_ARG (NULL or misaligned pointers, more than
+ * 65535 / ceil(nz / 32) frames), CUDA. */
 psfs_status psfs_smooth(psfs_handle *h, int32_t n_frames, const float *occupancy, float *smoothed,
                         uint32_t *voxel_lists, uint32_t capacity, uint32_t *counts);
 

@@ -814,7 +814,7 @@ psfs_status psfs_smooth(psfs_handle *h, int32_t n_frames, const float *occupancy
     if (capacity > 0 && (!voxel_lists || !aligned(voxel_lists, 4)))
         return fail(PSFS_ERR_INVALID_ARG, "voxel_lists NULL or not 4-byte aligned");
     if (!counts || !aligned(counts, 4)) return fail(PSFS_ERR_INVALID_ARG, "counts NULL or not 4-byte aligned");
-    const int tz = (h->grid.nz + 7) / 8;
+    const int tz = (h->grid.nz + 31) / 32;   // z-tiles of 32 planes per frame
     if ((int64_t)tz * n_frames > 65535) return fail(PSFS_ERR_INVALID_ARG, "too many frames for one call");
     DeviceGuard guard(h->device);
     SmoothArgs a{};

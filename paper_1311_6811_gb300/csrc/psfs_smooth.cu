@@ -6,12 +6,13 @@
 // grid, divided by the number of voxels in it), then the strict threshold
 // smoothed > tau and the compaction of the voxels above it.
 //
-// One CTA owns a 32 (x) x 8 (y) x 8 (z) block of one frame.  It loads the
-// block and a one-voxel halo (34 x 10 x 10, zeros outside the grid) into
-// shared memory with row-coalesced loads and forms the 3-sums along x there;
-// each thread then takes its (x, y) column, forms the 3-sums along y of the
-// ten halo planes and the 3-sums along z in registers: ((x-sums) y-sums)
-// z-sums, the same order for every voxel.  The scaling by the reciprocal of
+// One CTA owns 32 (x) x 8 (y) columns over 32 planes (z) of one frame.  The
+// planes, each with its one-voxel halo (34 x 10, zeros outside the grid),
+// stream through shared memory in z order, the next plane's loads in flight
+// while the current one is summed: the 3-sums along x in shared memory, the
+// 3-sums along y per thread, and the 3-sums along z from the y-sums of the
+// last three planes kept in registers: ((x-sums) y-sums) z-sums, the same
+// order for every voxel.  The scaling by the reciprocal of
 // the clipped count (the FP32 reciprocal of an integer: one rounding more
 // than a division), the optional store of
 // the smoothed value, the threshold and the warp-aggregated compaction (one
@@ -23,14 +24,17 @@ namespace psfs {
 
 namespace {
 
-constexpr int kSX = 32, kSY = 8, kSZ = 8;                     // outputs per CTA
-constexpr int kHX = kSX + 2, kHY = kSY + 2, kHZ = kSZ + 2;    // with the halo
+constexpr int kSX = 32, kSY = 8, kSZ = 32;   // outputs per CTA: 32 x 8 columns, 32 planes
+constexpr int kHX = kSX + 2, kHY = kSY + 2;   // one plane with its halo: 34 x 10
+constexpr int kPlane = kHX * kHY;             // 340 floats
+constexpr int kThreads = kSX * kSY;
+constexpr int kPerThread = (kPlane + kThreads - 1) / kThreads;   // 2
 
-__global__ void __launch_bounds__(kSX * kSY) smooth_kernel(const SmoothArgs a, int tiles_z)
+__global__ void __launch_bounds__(kThreads) smooth_kernel(const SmoothArgs a, int tiles_z)
 {
-    constexpr int kRows = kHZ * kHY;   // halo rows (z, y), row r = z * kHY + y
-    __shared__ float v[kRows][kHX];
-    __shared__ float sx[kRows][kSX];
+    __shared__ float v[kPlane];
+    __shared__ float sx[kHY][kSX];
+    __shared__ uint32_t s_bal[kSZ][kSY];   // each warp's ballot per output plane
     __shared__ uint32_t s_off[kSY];
     __shared__ uint32_t s_base;
 
@@ -41,69 +45,77 @@ __global__ void __launch_bounds__(kSX * kSY) smooth_kernel(const SmoothArgs a, i
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const size_t n_vox = (size_t)nx * ny * nz;
     const float *prob = a.prob + (size_t)f * n_vox;
-
-    // halo rows of 34 floats: warp w takes rows w, w + 8, ...; lane l loads
-    // x = l and lanes 0, 1 also x = 32, 33.  All loads of a thread are issued
-    // before the first shared-memory store.
-    {
-        constexpr int kPerWarp = (kRows + kSY - 1) / kSY;
-        const int gxa = x0 - 1 + lx, gxb = x0 + 31 + lx;
-        const bool oka = gxa >= 0 && gxa < nx, okb = lx < 2 && gxb < nx;
-        float va[kPerWarp], vb[kPerWarp];
-#pragma unroll
-        for (int q = 0; q < kPerWarp; ++q) {
-            const int row = ly + q * kSY;
-            const int z = row / kHY, y = row - z * kHY;
-            const int gy = y0 - 1 + y, gz = z0 - 1 + z;
-            const bool okr = row < kRows && gy >= 0 && gz >= 0 && gy < ny && gz < nz;
-            const size_t rbase = okr ? (size_t)nx * ((size_t)gy + (size_t)ny * gz) : 0;
-            va[q] = (okr && oka) ? __ldg(prob + rbase + gxa) : 0.0f;
-            vb[q] = (okr && okb) ? __ldg(prob + rbase + gxb) : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < kPerWarp; ++q) {
-            const int row = ly + q * kSY;
-            if (row < kRows) {
-                v[row][lx] = va[q];
-                if (lx < 2) v[row][32 + lx] = vb[q];
-            }
-        }
-    }
-    __syncthreads();
-    // 3-sums along x of every halo row
-#pragma unroll
-    for (int q = 0; q < (kRows + kSY - 1) / kSY; ++q) {
-        const int row = ly + q * kSY;
-        if (row < kRows) sx[row][lx] = (v[row][lx] + v[row][lx + 1]) + v[row][lx + 2];
-    }
-    __syncthreads();
-    // this thread's column (x0 + lx, y0 + ly): 3-sums along y for the kHZ
-    // halo planes, then along z
-    float ys[kHZ];
-#pragma unroll
-    for (int z = 0; z < kHZ; ++z)
-        ys[z] = (sx[z * kHY + ly][lx] + sx[z * kHY + ly + 1][lx]) + sx[z * kHY + ly + 2][lx];
-
     const int gx = x0 + lx, gy = y0 + ly;
     const bool in_xy = gx < nx && gy < ny;
     // 1 / (number of in-grid voxels of the clipped neighbourhood), per z case
     const int cxy = (1 + (gx > 0) + (gx + 1 < nx)) * (1 + (gy > 0) + (gy + 1 < ny));
     const float inv1 = 1.0f / (float)cxy, inv2 = 1.0f / (float)(2 * cxy), inv3 = 1.0f / (float)(3 * cxy);
     float *out = a.smoothed ? a.smoothed + (size_t)f * n_vox : nullptr;
-    uint32_t ballots[kSZ];
-    uint32_t warp_count = 0;
+    const size_t col = (size_t)gx + (size_t)nx * gy;   // this thread's column
+
+    // This thread's halo elements e = tid + k * 256 of every plane (row
+    // e / 34, column e % 34): their in-plane offset and in-grid test are the
+    // same for all planes.
+    const size_t nxy = (size_t)nx * ny;
+    size_t off[kPerThread];
+    bool ok[kPerThread];
 #pragma unroll
-    for (int t = 0; t < kSZ; ++t) {
-        const int gz = z0 + t;
-        const bool valid = in_xy && gz < nz;
-        const float sum = (ys[t] + ys[t + 1]) + ys[t + 2];
-        const int cz = 1 + (gz > 0) + (gz + 1 < nz);
-        const float sm = sum * (cz == 3 ? inv3 : cz == 2 ? inv2 : inv1);
-        const size_t lin = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * gz);
-        if (valid && out) __stcs(out + lin, sm);
-        ballots[t] = __ballot_sync(0xFFFFFFFFu, valid && sm > a.threshold);
-        warp_count += __popc(ballots[t]);
+    for (int k = 0; k < kPerThread; ++k) {
+        const int e = tid + k * kThreads;
+        const int y = e / kHX, x = e - y * kHX;
+        const int ex = x0 - 1 + x, ey = y0 - 1 + y;
+        ok[k] = e < kPlane && ex >= 0 && ey >= 0 && ex < nx && ey < ny;
+        off[k] = ok[k] ? (size_t)ex + (size_t)nx * ey : 0;
     }
+    auto load_plane = [&](int gz, float (&r)[kPerThread]) {
+        const bool okz = gz >= 0 && gz < nz;
+        const float *pl = prob + (okz ? (size_t)gz * nxy : 0);
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) r[k] = (okz && ok[k]) ? __ldg(pl + off[k]) : 0.0f;
+    };
+    // Planes z0 - 1 .. z0 + kSZ stream through shared memory; the next
+    // plane's loads are in flight while the current one is summed.  A thread
+    // keeps the y-sums of the last three planes: output plane z = p - 1 is
+    // (ys[z - 1] + ys[z]) + ys[z + 1].
+    float cur[kPerThread], nxt[kPerThread];
+    load_plane(z0 - 1, cur);
+    float y_a = 0.0f, y_b = 0.0f;   // y-sums of planes p - 2, p - 1
+    uint32_t warp_count = 0;
+#pragma unroll 1
+    for (int q = 0; q < kSZ + 2; ++q) {
+        const int p = z0 - 1 + q;
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k)
+            if (tid + k * kThreads < kPlane) v[tid + k * kThreads] = cur[k];
+        if (q + 1 < kSZ + 2) load_plane(p + 1, nxt);
+        __syncthreads();
+        // 3-sums along x of the plane's ten halo rows
+        for (int e = tid; e < kHY * kSX; e += kThreads) {
+            const int y = e >> 5, x = e & 31;
+            sx[y][x] = (v[y * kHX + x] + v[y * kHX + x + 1]) + v[y * kHX + x + 2];
+        }
+        __syncthreads();
+        const float y_c = (sx[ly][lx] + sx[ly + 1][lx]) + sx[ly + 2][lx];
+        if (q >= 2) {
+            const int t = q - 2, gz = z0 + t;
+            const bool valid = in_xy && gz < nz;
+            const float sum = (y_a + y_b) + y_c;
+            const int cz = 1 + (gz > 0) + (gz + 1 < nz);
+            const float sm = sum * (cz == 3 ? inv3 : cz == 2 ? inv2 : inv1);
+            if (valid && out) __stcs(out + col + (size_t)gz * nxy, sm);
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, valid && sm > a.threshold);
+            if (lx == 0) s_bal[t][ly] = b;
+            warp_count += __popc(b);
+        }
+        y_a = y_b;
+        y_b = y_c;
+#pragma unroll
+        for (int k = 0; k < kPerThread; ++k) cur[k] = nxt[k];
+        // the next plane overwrites v only after every thread has left the x-sums
+        // (ordered by the barrier above); sx is rewritten after the next barrier
+    }
+
+    // compaction of the CTA's voxels above the threshold: one atomicAdd
     if (lx == 0) s_off[ly] = warp_count;
     __syncthreads();
     if (tid == 0) {
@@ -126,11 +138,11 @@ __global__ void __launch_bounds__(kSX * kSY) smooth_kernel(const SmoothArgs a, i
     uint32_t *list = a.lists + (size_t)f * a.capacity;
 #pragma unroll
     for (int t = 0; t < kSZ; ++t) {
-        const uint32_t b = ballots[t];
+        const uint32_t b = s_bal[t][ly];
         if ((b >> lx) & 1u) {
-            const uint32_t p = pos + __popc(b & ((1u << lx) - 1u));
-            if (p < a.capacity)
-                list[p] = (uint32_t)gx + (uint32_t)nx * ((uint32_t)gy + (uint32_t)ny * (uint32_t)(z0 + t));
+            const uint32_t pp = pos + __popc(b & ((1u << lx) - 1u));
+            if (pp < a.capacity)
+                list[pp] = (uint32_t)gx + (uint32_t)nx * ((uint32_t)gy + (uint32_t)ny * (uint32_t)(z0 + t));
         }
         pos += __popc(b);
     }
