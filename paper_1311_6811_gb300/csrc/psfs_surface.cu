@@ -86,9 +86,14 @@ cudaError_t launch_surface(const SurfaceArgs &a, int n_frames, cudaStream_t s)
     if (n_frames <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(a.masks, 0, (size_t)n_frames * a.mask_words * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    // blocks per frame: enough for a few per SM over all frames, at most the
-    // list's length
-    const uint32_t per_frame = std::max<uint32_t>(1, std::min<uint32_t>(16, (a.list_stride + kSurfThreads - 1) / kSurfThreads));
+    // blocks per frame: about four per SM in total (a handful of frames
+    // still fills the GPU), at most one per 256 list entries
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t want = (uint32_t)std::max(1, 4 * std::max(sms, 1) / n_frames);
+    const uint32_t per_frame =
+        std::max<uint32_t>(1, std::min<uint32_t>(std::min<uint32_t>(want, 64), (a.list_stride + kSurfThreads - 1) / kSurfThreads));
     const dim3 grid(per_frame, (unsigned)n_frames);
     surface_mark_kernel<<<grid, kSurfThreads, 0, s>>>(a);
     e = cudaGetLastError();
