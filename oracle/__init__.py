@@ -53,6 +53,10 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_slm.argtypes = [ctypes.c_int64, _u8p, _f32p, _f32p, ctypes.c_double, _dp]
             lib.oracle_slm.restype = None
+            lib.oracle_reproject.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                             ctypes.c_int, _i32p, _dp, ctypes.c_int64, _u32p, ctypes.c_double,
+                                             _u8p]
+            lib.oracle_reproject.restype = None
             lib.oracle_smooth.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, _dp,
                                           _u8p]
             lib.oracle_smooth.restype = None
@@ -180,6 +184,21 @@ def fuse(grid, cams, slm_maps: np.ndarray, params=None, edge_eps: float = 1e-3) 
     assert n == lst.size
     return {"occ": occ, "logodds": lo, "occupied": occupied.astype(bool),
             "boundary": boundary.astype(bool), "n_seen": n_seen, "list": lst}
+
+
+def reproject(grid, cams, voxel_list, grow: float = 0.0) -> np.ndarray:
+    """Silhouettes of the listed voxels: uint8 masks [n_cams][H][W], pixel set
+    iff its centre ray meets a listed voxel's cube (grown by `grow` voxel
+    sizes) in front of the camera.  Brute force: small cases only."""
+    lib = _load()
+    nx, ny, nz, origin, vs = _grid_args(grid)
+    wh, rec = _cam_args(cams)
+    lst = np.ascontiguousarray(np.asarray(voxel_list, np.uint32).ravel())
+    H, W = int(wh[1]), int(wh[0])
+    masks = np.zeros((len(cams), H, W), np.uint8)
+    lib.oracle_reproject(nx, ny, nz, _ptr(origin, _dp), vs, len(cams), _ptr(wh, _i32p), _ptr(rec, _dp),
+                         lst.size, _ptr(lst, _u32p) if lst.size else None, float(grow), _ptr(masks, _u8p))
+    return masks
 
 
 def smooth(shape, prob, threshold: float = 0.5) -> dict:

@@ -177,6 +177,88 @@ int64_t oracle_compact(int64_t n_vox, const uint8_t *occupied, uint32_t *list)
 }
 
 /* --------------------------------------------------------------------- */
+/* Silhouettes of a voxel set (Sec. 2.3: the projection of the voxels in  */
+/* each camera is the tracker's prior knowledge, matched against the      */
+/* particles' projected models).  Pixel (x, y) of camera c is set iff the */
+/* ray from the camera centre C = -R^T t through the pixel centre         */
+/* (x + 1/2, y + 1/2) meets, at a positive ray parameter, the cube of a   */
+/* listed voxel: origin + [i, i+1] x [j, j+1] x [k, k+1] * voxel_size,    */
+/* grown by `grow` voxel sizes on every side (grow = 0: the cube itself). */
+/* Brute force: every pixel against every listed voxel, slab test.        */
+/* masks: [n_cams][H][W] bytes.                                           */
+/* --------------------------------------------------------------------- */
+static void inverse3(const double *A, double *Ai)
+{
+    double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                 A[2] * (A[3] * A[7] - A[4] * A[6]);
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+    Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    Ai[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+    Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+}
+
+/* does C + t d, t > 0, meet the box [lo, hi]? */
+static int ray_hits_box(const double C[3], const double d[3], const double lo[3], const double hi[3])
+{
+    double t_in = 0.0, t_out = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            if (C[a] < lo[a] || C[a] > hi[a]) return 0;
+            continue;
+        }
+        double t1 = (lo[a] - C[a]) / d[a], t2 = (hi[a] - C[a]) / d[a];
+        if (t1 > t2) {
+            double tmp = t1;
+            t1 = t2;
+            t2 = tmp;
+        }
+        if (t1 > t_in) t_in = t1;
+        if (t2 < t_out) t_out = t2;
+    }
+    return t_in <= t_out;
+}
+
+void oracle_reproject(int nx, int ny, int nz, const double origin[3], double voxel_size, int n_cams,
+                      const int *wh, const double *cams, int64_t n_list, const uint32_t *list, double grow,
+                      uint8_t *masks)
+{
+    int64_t off = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        const int W = wh[2 * c], H = wh[2 * c + 1];
+        const double *K = cams + ORACLE_CAM_STRIDE * c, *R = K + 9, *t = K + 18;
+        double Ki[9], C[3];
+        inverse3(K, Ki);
+        for (int r = 0; r < 3; ++r) C[r] = -(R[r] * t[0] + R[3 + r] * t[1] + R[6 + r] * t[2]);
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const double p[3] = {x + 0.5, y + 0.5, 1.0};
+                double q[3], d[3];
+                for (int r = 0; r < 3; ++r) q[r] = Ki[3 * r] * p[0] + Ki[3 * r + 1] * p[1] + Ki[3 * r + 2] * p[2];
+                for (int r = 0; r < 3; ++r) d[r] = R[r] * q[0] + R[3 + r] * q[1] + R[6 + r] * q[2];
+                uint8_t hit = 0;
+                for (int64_t e = 0; e < n_list && !hit; ++e) {
+                    const int64_t v = list[e];
+                    const int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((int64_t)nx * ny));
+                    if (k >= nz) continue;
+                    const double lo[3] = {origin[0] + (i - grow) * voxel_size, origin[1] + (j - grow) * voxel_size,
+                                          origin[2] + (k - grow) * voxel_size};
+                    const double hi[3] = {origin[0] + (i + 1 + grow) * voxel_size,
+                                          origin[1] + (j + 1 + grow) * voxel_size,
+                                          origin[2] + (k + 1 + grow) * voxel_size};
+                    hit = (uint8_t)ray_hits_box(C, d, lo, hi);
+                }
+                masks[off + (int64_t)y * W + x] = hit;
+            }
+        off += (int64_t)W * H;
+    }
+}
+
+/* --------------------------------------------------------------------- */
 /* Spatial smoothing of the voxel probabilities before the threshold      */
 /* (end of Sec. 2.2.2; Sec. 3.3.3 step (d)).  The paper does not give the */
 /* filter; this is the 3 x 3 x 3 box mean over the neighbours inside the  */
