@@ -200,6 +200,26 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
                                            float *h_occupancy, uint32_t *h_lists, uint32_t capacity,
                                            uint32_t *h_counts);
 
+/* Silhouettes of the reconstructed voxels in every camera (Section 2.3: the
+ * projection of the voxels is the tracker's prior knowledge; Section 3.3.3,
+ * voxel projection): pixel (x, y) of camera c is set iff the ray from the
+ * camera centre through the pixel centre (x + 1/2, y + 1/2) meets, in front
+ * of the camera, the cube of a listed voxel (origin + [i, i+1] x [j, j+1] x
+ * [k, k+1] * voxel_size).  For n_frames frames of this handle's rig:
+ *   voxel_lists   device uint32, frame f's voxels (linear indices, any order;
+ *                 the surface list of psfs_surface gives the same silhouette
+ *                 as the occupied list, with less work) at voxel_lists +
+ *                 f * list_stride
+ *   counts        device uint32 [n_frames] (entries beyond list_stride are
+ *                 not read)
+ *   masks         device uint8 [n_frames][n_cams][height][width], written
+ *                 completely (0 or 1)
+ * Rays are tested in float32: pixels whose centre ray passes within about
+ * 1e-3 voxel of a cube's edge may differ from an exact evaluation.
+ * Errors: INVALID_ARG, CUDA. */
+psfs_status psfs_reproject(psfs_handle *h, int32_t n_frames, const uint32_t *voxel_lists, uint32_t list_stride,
+                           const uint32_t *counts, uint8_t *masks);
+
 /* Smoothing of the voxel probabilities before the threshold (end of Section
  * 2.2.2, which filters the probabilities and then thresholds them; step (d)
  * of Section 3.3.3).  The paper does not give the filter; this is the
@@ -340,6 +360,7 @@ typedef enum {
     PSFS_STAGE_BATCH = 4,        /* batched persistent launch                       */
     PSFS_STAGE_SURFACE = 5,      /* inner-voxel removal (psfs_surface)              */
     PSFS_STAGE_SMOOTH = 6,       /* smoothing + threshold (psfs_smooth)             */
+    PSFS_STAGE_REPROJECT = 7,    /* voxel silhouettes (psfs_reproject)              */
     PSFS_N_STAGES = 8
 } psfs_stage;
 

@@ -803,6 +803,40 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
     return PSFS_OK;
 }
 
+psfs_status psfs_reproject(psfs_handle *h, int32_t n_frames, const uint32_t *voxel_lists, uint32_t list_stride,
+                           const uint32_t *counts, uint8_t *masks)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (n_frames < 0) return fail(PSFS_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames == 0) return PSFS_OK;
+    if (list_stride > 0 && (!voxel_lists || !aligned(voxel_lists, 4)))
+        return fail(PSFS_ERR_INVALID_ARG, "voxel_lists NULL or not 4-byte aligned");
+    if (!counts || !aligned(counts, 4)) return fail(PSFS_ERR_INVALID_ARG, "counts NULL or not 4-byte aligned");
+    if (!masks) return fail(PSFS_ERR_INVALID_ARG, "masks is NULL");
+    if (n_frames > 65535) return fail(PSFS_ERR_INVALID_ARG, "more than 65535 frames in one call");
+    DeviceGuard guard(h->device);
+    ReprojectArgs a{};
+    for (int c = 0; c < h->n_cams; ++c) a.cam[c] = h->fuse.cam[c];
+    plan_backward_inv(h->grid, h->cams.data(), h->n_cams, h->fuse, a.inv);
+    a.lists = voxel_lists;
+    a.list_stride = list_stride;
+    a.counts = counts;
+    a.masks = masks;
+    a.n_cams = h->n_cams;
+    a.W = h->W;
+    a.H = h->H;
+    a.nx = h->grid.nx;
+    a.ny = h->grid.ny;
+    a.nz = h->grid.nz;
+    a.ci = h->fuse.ci;
+    a.cj = h->fuse.cj;
+    a.ck = h->fuse.ck;
+    a.n_vox = (uint32_t)((uint64_t)h->grid.nx * h->grid.ny * h->grid.nz);
+    ProfScope ps(h, PSFS_STAGE_REPROJECT);
+    PSFS_CK(launch_reproject(a, n_frames, h->stream));
+    return PSFS_OK;
+}
+
 psfs_status psfs_smooth(psfs_handle *h, int32_t n_frames, const float *occupancy, float *smoothed,
                         uint32_t *voxel_lists, uint32_t capacity, uint32_t *counts)
 {

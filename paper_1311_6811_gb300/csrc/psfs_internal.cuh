@@ -454,6 +454,22 @@ struct PixelInv {
     float margin;   // pixels: frustum widening that covers the float32 error of the forward projection
 };
 
+// Silhouettes of listed voxels (psfs_reproject.cu): frame f's list at lists +
+// f * list_stride with counts[f] entries; masks [n_frames][n_cams][H][W]
+// bytes (zeroed by the launcher).
+struct ReprojectArgs {
+    CamMat cam[PSFS_MAX_CAMS];
+    PixelInv inv[PSFS_MAX_CAMS];
+    const uint32_t *lists;
+    uint32_t list_stride;
+    const uint32_t *counts;
+    uint8_t *masks;
+    int n_cams, W, H, nx, ny, nz;
+    float ci, cj, ck;
+    uint32_t n_vox;
+};
+cudaError_t launch_reproject(const ReprojectArgs &a, int n_frames, cudaStream_t s);
+
 struct BackwardArgs {
     FuseArgs f;                   // grid, cameras, maps (for the voxel pass), tiles
     const float *d_occ;           // [n_vox]

@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
             "psfs_reconstruct_sequence_host": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_surface": (st, [_vp, ctypes.c_int32, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_smooth": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+            "psfs_reproject": (st, [_vp, ctypes.c_int32, _vp, ctypes.c_uint32, _vp, _vp]),
             "psfs_set_background_l2": (st, [_vp, ctypes.c_int32]),
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
@@ -319,6 +320,14 @@ def psfs_reconstruct_sequence_host(h: int, n_frames: int, images, occupancy, vox
     return st
 
 
+def psfs_reproject(h: int, n_frames: int, voxel_lists, list_stride: int, counts, masks):
+    """Silhouettes of the listed voxels: masks uint8 [n_frames][n_cams][H][W]."""
+    import torch
+    _check(load().psfs_reproject(h, int(n_frames), _dev_ptr(voxel_lists, "voxel_lists"), int(list_stride),
+                                 _dev_ptr(counts, "counts"), _dev_ptr(masks, "masks", torch.uint8)),
+           "psfs_reproject")
+
+
 def psfs_smooth(h: int, n_frames: int, occupancy, smoothed, voxel_lists, capacity: int, counts):
     """Smoothing (3 x 3 x 3 box mean over in-grid neighbours) of n_frames
     posterior grids, strict threshold and compaction; `smoothed` may be None."""
@@ -490,7 +499,8 @@ def psfs_batch_destroy(b: int):
 
 
 PSFS_N_STAGES = 8
-STAGE_NAMES = ["likelihood", "fuse", "backward_voxel", "backward_pixel", "batch", "surface", "smooth"]
+STAGE_NAMES = ["likelihood", "fuse", "backward_voxel", "backward_pixel", "batch", "surface", "smooth",
+               "reproject"]
 
 
 def psfs_profile_enable(h: int, max_launches: int):
