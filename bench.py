@@ -684,9 +684,32 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg):
         out[f"{dtype}_forward_backward_us"] = 1e3 * e[1].elapsed_time(e[2]) / F
         if dtype != "f32":
             out[f"{dtype}_max_abs_occ_diff_vs_f32"] = err
+        # batched forward: the sequence path with frame groups (16 frames per
+        # group for 16-bit maps, the tuned group size for FP32)
+        nseq = min(32, d_images.shape[0])
+        G = 16 if dtype != "f32" else max(int(fuse_cfg[5]), 1)
+        lx = fuse_cfg[0] if fuse_cfg[0] in (8, 16) else 8
+        psfs.psfs_set_fuse_config(rec.handle, lx, 4, 4, 0, fuse_cfg[4], G)
+        cap_s = 1 << 17
+        occ_s = torch.empty((nseq, V), dtype=torch.float32, device=dev)
+        lst_s = torch.empty((nseq, cap_s), dtype=torch.int32, device=dev)
+        cnt_s = torch.zeros((nseq,), dtype=torch.int32, device=dev)
+        with torch.cuda.stream(stream):
+            psfs.psfs_reconstruct_sequence(rec.handle, nseq, d_images[:nseq], occ_s, lst_s, cap_s, cnt_s)
+            e[0].record(stream)
+            for _ in range(3):
+                psfs.psfs_reconstruct_sequence(rec.handle, nseq, d_images[:nseq], occ_s, lst_s, cap_s, cnt_s)
+            e[3].record(stream)
+        stream.synchronize()
+        assert rec.sync() == psfs.PSFS_OK
+        out[f"{dtype}_batched_forward_us"] = 1e3 * e[0].elapsed_time(e[3]) / (3 * nseq)
+        out[f"{dtype}_batched_frames_per_group"] = G
+        if dtype != "f32":
+            out[f"{dtype}_batched_max_abs_occ_diff_vs_f32"] = float((occ_s - occ_f32[:nseq]).abs().max())
         rec.close()
-    out["note"] = ("one frame per call (no stream overlap); backward = recomputed maps + voxel pass + "
-                   "per-pixel owner pass + chain rule to SLM, mean, var")
+    out["note"] = ("*_forward_us / *_forward_backward_us: one frame per call (no stream overlap); backward = "
+                   "recomputed maps + voxel pass + per-pixel owner pass + chain rule to SLM, mean, var.  "
+                   "*_batched_forward_us: psfs_reconstruct_sequence over 32 frames in frame groups")
     return out
 
 

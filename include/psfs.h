@@ -113,12 +113,13 @@ typedef struct {
  * seq_likelihood_ctas: CTAs per SM of the likelihood grid on the sequence
  * path, 1 to 4 (0 in psfs_set_fuse_config keeps the current value).
  * frames_per_group: frames per launch on the sequence path: 1 = one frame
- * per likelihood and fusion launch; 2, 4 or 8 = frame groups, where one
+ * per likelihood and fusion launch; 2, 4, 8 or 16 = frame groups, where one
  * likelihood launch reads the background once for the whole group and writes
  * the group's maps interleaved per pixel, and one fusion launch projects each
  * voxel once and gathers all frames of the group with one vector load (each
  * frame's results are bit-identical to one frame per launch).  Groups need
- * staged = 0, lanes_x 8 or 16, and voxels_z 4 or 8 for 8 frames; with another
+ * staged = 0, lanes_x 8 or 16, voxels_z 4 or 8 for 8 frames and 4 for 16
+ * frames; with another
  * shape the sequence path runs one frame per launch.  Trailing frames that do
  * not fill a group run one per launch.  0 in psfs_set_fuse_config keeps the
  * current value.  The batch entry points ignore this field. */
@@ -331,8 +332,8 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
  * fastest and writes it to *best (may be NULL) and the mean milliseconds of
  * each candidate to candidate_ms[PSFS_N_FUSE_CANDIDATES] (may be NULL; order:
  * staged 0 then 1, lanes_x 8, 16, 32, voxels_z 8 then 16); then times the
- * sequence path on 8 frames with 1 to 4 likelihood CTAs per SM at one frame
- * per launch, and frame groups of 2, 4 and 8 frames (direct tile shapes,
+ * sequence path on 16 frames with 1 to 4 likelihood CTAs per SM at one frame
+ * per launch, and frame groups of 2, 4, 8 and 16 frames (direct tile shapes,
  * voxels_z 4, 8 and 16, 1 to 3 likelihood CTAs per SM), and keeps the fastest
  * sequence configuration (which may change the tile shape).  The choices are
  * remembered for handles of the same grid size, camera count, image size and

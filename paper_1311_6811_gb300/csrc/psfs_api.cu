@@ -732,10 +732,10 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
     if (n_vox % 4 != 0) return fail(PSFS_ERR_INVALID_ARG, "voxel count not a multiple of 4");
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     DeviceGuard guard(h->device);
-    // chunks of four frame groups (at least 8 frames) per slot: the copies of
+    // chunks of two frame groups (at least 8 frames) per slot: the copies of
     // one chunk overlap the kernels of the next
     const int group = std::max(1, h->seq_group);
-    const int chunk = std::min<int>(n_frames, std::max(8, 4 * group));
+    const int chunk = std::min<int>(n_frames, std::max(8, 2 * group));
     psfs_status st = io_setup(h, chunk, capacity);
     if (st != PSFS_OK) return st;
     const size_t frame_bytes = (size_t)h->n_pix * 3;
@@ -1116,7 +1116,7 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
         return fail(PSFS_ERR_INVALID_ARG, "seq_likelihood_ctas outside [0, 4]");
     if (cfg->frames_per_group < 0 || (cfg->frames_per_group > 1 && !group_shape_supported(shape, cfg->frames_per_group)))
         return fail(PSFS_ERR_INVALID_ARG,
-                    "frames_per_group: 0, 1, or 2 / 4 / 8 with staged 0, lanes_x 8 or 16 (voxels_z 4 or 8 for 8 frames)");
+                    "frames_per_group: 0, 1, or 2 / 4 / 8 / 16 with staged 0, lanes_x 8 or 16 (voxels_z 4 or 8 for 8 frames, 4 for 16)");
     DeviceGuard guard(h->device);
     PSFS_CK(cudaStreamSynchronize(h->stream));
     if (h->seq_stream[0]) {
@@ -1149,10 +1149,10 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     DeviceGuard guard(h->device);
     const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
-    // scratch: occupancy of 8 frames, 8 lists of n_vox / 8 entries (the
+    // scratch: occupancy of 16 frames, 16 lists of n_vox / 16 entries (the
     // sequence timings; a frame with more occupied voxels only sets the
-    // capacity bit, cleared below) and 8 counts
-    constexpr int kTuneFrames = 8;
+    // capacity bit, cleared below) and 16 counts
+    constexpr int kTuneFrames = 16;
     const uint32_t seq_cap = (uint32_t)std::max<uint64_t>(1, n_vox / kTuneFrames);
     float *occ = nullptr;
     uint32_t *list = nullptr, *tcounts = nullptr;
@@ -1202,10 +1202,10 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
                 best_shape = shape;
             }
     }
-    // second stage: the sequence path, timed on 8 frames (distinct outputs,
+    // second stage: the sequence path, timed on 16 frames (distinct outputs,
     // the same images) per repetition: CTAs per SM of the likelihood grid
-    // (1 to 4) with one frame per launch, then frame groups of 2, 4 and 8
-    // frames with the direct tile shapes that support them
+    // (1 to 4) with one frame per launch, then frame groups of 2, 4, 8 and
+    // 16 frames with the direct tile shapes that support them
     auto time_sequence = [&](int lk, int group, float *ms_out) -> psfs_status {
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(PSFS_ERR_CUDA, "autotune sync");
         psfs_status s2 = enqueue_sequence(h, kTuneFrames, images, 0, occ, n_vox, list, seq_cap, seq_cap, tcounts,
@@ -1236,8 +1236,8 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
         }
     }
     const int group_lx = (best_shape.lx == 16) ? 16 : 8;
-    const int groups[3] = {2, 4, 8};
-    for (int gi = 0; gi < 3 && st == PSFS_OK; ++gi) {
+    const int groups[4] = {2, 4, 8, 16};
+    for (int gi = 0; gi < 4 && st == PSFS_OK; ++gi) {
         for (int tz : {4, 8, 16}) {
             if (st != PSFS_OK) break;
             const FuseShape gshape = {group_lx, 4, tz, 0};

@@ -103,10 +103,13 @@ struct GroupWords {
 template <int kWords>
 __device__ __forceinline__ void store_words(uint32_t *dst, const uint32_t *w)
 {
-    if constexpr (kWords == 8) {
-        asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(w[0]), "r"(w[1]),
-                     "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
-                     : "memory");
+    if constexpr (kWords % 8 == 0) {
+#pragma unroll
+        for (int q = 0; q < kWords; q += 8)
+            asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst + q), "r"(w[q]),
+                         "r"(w[q + 1]), "r"(w[q + 2]), "r"(w[q + 3]), "r"(w[q + 4]), "r"(w[q + 5]), "r"(w[q + 6]),
+                         "r"(w[q + 7])
+                         : "memory");
     } else if constexpr (kWords == 1) {
         *dst = w[0];
     } else if constexpr (kWords == 2) {
@@ -122,12 +125,15 @@ __device__ __forceinline__ void store_words(uint32_t *dst, const uint32_t *w)
 template <int kWords>
 __device__ __forceinline__ void load_words(const uint32_t *src, uint32_t *w)
 {
-    if constexpr (kWords == 8) {
-        // one 256-bit read-only load per lane (sm_100+): a lane's whole
-        // 32-byte group vector, one L1 sector, in one request
-        asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
-            : "l"(src));
+    if constexpr (kWords % 8 == 0) {
+        // 256-bit read-only loads (sm_100+): each a whole 32-byte sector of
+        // the lane's group vector in one request
+#pragma unroll
+        for (int q = 0; q < kWords; q += 8)
+            asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(w[q]), "=r"(w[q + 1]), "=r"(w[q + 2]), "=r"(w[q + 3]), "=r"(w[q + 4]), "=r"(w[q + 5]),
+                  "=r"(w[q + 6]), "=r"(w[q + 7])
+                : "l"(src + q));
     } else if constexpr (kWords == 1) {
         w[0] = __ldg(src);
     } else if constexpr (kWords == 2) {
@@ -154,12 +160,11 @@ constexpr int kGChunk = 512;                 // pixels per chunk (multiple of 16
 constexpr int kGImgBytes = 3 * kGChunk;      // 1536 per frame
 constexpr int kGBgBytes = 12 * kGChunk;      // 6144 (3 floats per pixel)
 constexpr int kGThreads = 256;
-constexpr int kGStages = 4;
-
 template <int F>
 struct GLayout {
+    static constexpr int kStages = F >= 16 ? 2 : 4;                 // ring depth (16 frames: 74 KB)
     static constexpr int kStage = F * kGImgBytes + 2 * kGBgBytes;   // bytes per ring stage
-    static constexpr int kSmem = kGStages * kStage + kGStages * 8;  // + mbarriers
+    static constexpr int kSmem = kStages * kStage + kStages * 8;    // + mbarriers
 };
 
 template <typename OutT, int F>
@@ -187,12 +192,12 @@ template <typename OutT, int F>
 __global__ void __launch_bounds__(kGThreads) likelihood_group_kernel(const LikelihoodArgs a, int64_t n_tma_pix)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kGStages * GLayout<F>::kStage);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + GLayout<F>::kStages * GLayout<F>::kStage);
     OutT *out = reinterpret_cast<OutT *>(a.out);
     const int tid = threadIdx.x;
     if (a.zero_word && blockIdx.x == 0 && tid < F) a.zero_word[(int64_t)tid * a.zero_fstride] = 0u;
     if (tid == 0) {
-        for (int s = 0; s < kGStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < GLayout<F>::kStages; ++s) mbar_init(&bars[s], 1);
         mbar_fence_init();
     }
     __syncthreads();
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(kGThreads) likelihood_group_kernel(const Likel
         return reinterpret_cast<float *>(smem + s * GLayout<F>::kStage + F * kGImgBytes + kGBgBytes);
     };
     auto issue = [&](int64_t k) {
-        const int s = (int)(k % kGStages);
+        const int s = (int)(k % GLayout<F>::kStages);
         const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kGChunk;
         const uint32_t np = (uint32_t)min((int64_t)kGChunk, n_tma_pix - p0);
         mbar_arrive_expect_tx(&bars[s], (3u * F + 24u) * np);
@@ -219,11 +224,11 @@ __global__ void __launch_bounds__(kGThreads) likelihood_group_kernel(const Likel
         bulk_g2s(stage_hinv(s), a.hinv + 3 * p0, 12u * np, &bars[s]);
     };
     if (tid == 0)
-        for (int64_t k = 0; k < my_chunks && k < kGStages; ++k) issue(k);
+        for (int64_t k = 0; k < my_chunks && k < GLayout<F>::kStages; ++k) issue(k);
 
     for (int64_t k = 0; k < my_chunks; ++k) {
-        const int s = (int)(k % kGStages);
-        mbar_wait_bounded(&bars[s], (uint32_t)((k / kGStages) & 1), a.status);
+        const int s = (int)(k % GLayout<F>::kStages);
+        mbar_wait_bounded(&bars[s], (uint32_t)((k / GLayout<F>::kStages) & 1), a.status);
         const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kGChunk;
         const int np = (int)min((int64_t)kGChunk, n_tma_pix - p0);
         const unsigned char *im = stage_img(s);
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(kGThreads) likelihood_group_kernel(const Likel
         for (int q = tid; q < np; q += kGThreads)
             group_pixel<OutT, F>(a, out, p0 + q, im + 3 * q, kGImgBytes, mu + 3 * q, hv + 3 * q);
         __syncthreads();   // every thread is done with stage s before it is refilled
-        if (tid == 0 && k + kGStages < my_chunks) issue(k + kGStages);
+        if (tid == 0 && k + GLayout<F>::kStages < my_chunks) issue(k + GLayout<F>::kStages);
     }
 
     if (blockIdx.x == 0) {
@@ -279,6 +284,7 @@ cudaError_t launch_lk_group_typed(const LikelihoodArgs &a, int frames, cudaStrea
     if (frames == 2) return launch_lk_group<OutT, 2>(a, s, ctas_per_sm);
     if (frames == 4) return launch_lk_group<OutT, 4>(a, s, ctas_per_sm);
     if (frames == 8) return launch_lk_group<OutT, 8>(a, s, ctas_per_sm);
+    if (frames == 16) return launch_lk_group<OutT, 16>(a, s, ctas_per_sm);
     return cudaErrorInvalidValue;
 }
 
@@ -420,8 +426,11 @@ cudaError_t launch_fg(const FuseArgs &a, cudaStream_t s)
 template <typename MapT, int LX, int F>
 cudaError_t launch_fg_tz(const FuseArgs &a, int tz, cudaStream_t s)
 {
+    // F x TZ accumulators per thread: at most 64
     if (tz == 4) return launch_fg<MapT, LX, 4, F>(a, s);
-    if (tz == 8) return launch_fg<MapT, LX, 8, F>(a, s);
+    if constexpr (F <= 8) {
+        if (tz == 8) return launch_fg<MapT, LX, 8, F>(a, s);
+    }
     if constexpr (F <= 4) {
         if (tz == 16) return launch_fg<MapT, LX, 16, F>(a, s);
     }
@@ -444,17 +453,18 @@ cudaError_t launch_fg_typed(const FuseArgs &a, const FuseShape &sh, int frames, 
     if (frames == 2) return launch_fg_shape<MapT, 2>(a, sh, s);
     if (frames == 4) return launch_fg_shape<MapT, 4>(a, sh, s);
     if (frames == 8) return launch_fg_shape<MapT, 8>(a, sh, s);
+    if (frames == 16) return launch_fg_shape<MapT, 16>(a, sh, s);
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-bool group_size_supported(int frames) { return frames == 2 || frames == 4 || frames == 8; }
+bool group_size_supported(int frames) { return frames == 2 || frames == 4 || frames == 8 || frames == 16; }
 
 bool group_shape_supported(const FuseShape &s, int frames)
 {
     return group_size_supported(frames) && s.wy == 4 && s.staged == 0 && (s.lx == 8 || s.lx == 16) &&
-           (s.tz == 4 || s.tz == 8 || (s.tz == 16 && frames <= 4));
+           (s.tz == 4 || (s.tz == 8 && frames <= 8) || (s.tz == 16 && frames <= 4));
 }
 
 cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map_dtype, cudaStream_t s,

@@ -52,10 +52,10 @@ def _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("group,tz", [(2, 16), (4, 4), (4, 8), (4, 16), (8, 4), (8, 8)])
+@pytest.mark.parametrize("group,tz", [(2, 16), (4, 4), (4, 8), (4, 16), (8, 4), (8, 8), (16, 4)])
 def test_groups_equal_frame_by_frame(group, tz, dtype):
-    """11 frames: whole groups, then 11 mod F trailing frames one per launch."""
-    sc = _scene(11)
+    """19 frames: whole groups, then 19 mod F trailing frames one per launch."""
+    sc = _scene(19)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=dtype)
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
     imgs = to_dev(sc.images)
@@ -173,7 +173,7 @@ def test_group_config_validation():
     sc = _scene(2)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
     for bad in [(8, 4, 8, 0, 0, 3), (8, 4, 16, 0, 0, 8), (8, 4, 8, 1, 0, 4), (32, 4, 8, 0, 0, 2),
-                (8, 4, 8, 0, 0, -1), (32, 4, 4, 0, 0, 4)]:
+                (8, 4, 8, 0, 0, -1), (32, 4, 4, 0, 0, 4), (8, 4, 8, 0, 0, 16), (8, 4, 4, 0, 0, 32)]:
         with pytest.raises(psfs.PsfsError):
             psfs.psfs_set_fuse_config(rec.handle, *bad)
     psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 0, 4)
@@ -190,7 +190,7 @@ def test_autotune_picks_a_sequence_configuration():
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
     psfs.psfs_autotune(rec.handle, to_dev(sc.images[0]), reps=1)
     cfg = psfs.psfs_get_fuse_config(rec.handle, full=True)
-    assert cfg[5] in (1, 2, 4, 8) and 1 <= cfg[4] <= 4
+    assert cfg[5] in (1, 2, 4, 8, 16) and 1 <= cfg[4] <= 4
     assert rec.sync() == psfs.PSFS_OK
     rec.close()
 
