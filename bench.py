@@ -476,7 +476,7 @@ def run_ours(args):
                 "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": traffic,
                 "alg_bytes_per_launch": stages[dom]["alg_bytes_per_launch"],
                 "note": ("the fusion kernels are bound by L1 gather throughput (ncu: 79 % of L1 peak for "
-                         "fuse_group_kernel, profiles/fuse_group_kernel_128cube_8cam.md), not by HBM")
+                         "fuse_group_kernel), not by HBM")
                         if dom == "fuse" else None}
     # the whole step against the per-frame algorithmic bytes of the single-frame
     # method (images 3 + background 24 + maps 2 x map bytes per pixel,
