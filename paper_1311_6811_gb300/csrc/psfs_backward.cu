@@ -18,7 +18,10 @@
 // them it walks the slices of the grid across the pixel's ray along the grid
 // axis closest to the ray, and in each slice tests the lattice points inside
 // the pixel's (slightly widened) frustum with the exact projection arithmetic
-// of the forward kernels, so the ownership is the forward's bit for bit.
+// of the forward kernels, so the ownership is the forward's bit for bit.  The
+// walk marks the slices with candidates in a 64-bit mask per block of 64
+// slices (one branch-free pass the whole warp runs in step) and then visits
+// only the marked slices.
 #include "psfs_fuse_common.cuh"
 
 namespace psfs {
@@ -156,32 +159,55 @@ __global__ void __launch_bounds__(256) backward_pixel_kernel(const __grid_consta
         const float *dl = b.dl;
         const float nb1 = (float)(nn[bx] - 1), nc1 = (float)(nn[cx] - 1);
         float acc = 0.0f;
-        for (int s = s_lo; s <= s_hi; ++s) {
+        // The window of slice s: centre (b0, c0), half-widths (eb, ec).
+        auto window = [&](int s, float &b0, float &c0, float &eb, float &ec) {
             const float fs = (float)s;
-            const float b0 = fmaf(fs, Bb, Ab), c0 = fmaf(fs, Bc, Ac);
+            b0 = fmaf(fs, Bb, Ab);
+            c0 = fmaf(fs, Bc, Ac);
             const float ds = fabsf(fs - qa);
-            const float eb = fmaf(ds, rb, 1e-3f), ec = fmaf(ds, rc, 1e-3f);
-            // lattice points of the window, as floats: most slices hold none
-            const float fb_lo = fmaxf(ceilf(b0 - eb), 0.0f), fb_hi = fminf(floorf(b0 + eb), nb1);
-            if (!(fb_lo <= fb_hi)) continue;
-            const float fc_lo = fmaxf(ceilf(c0 - ec), 0.0f), fc_hi = fminf(floorf(c0 + ec), nc1);
-            if (!(fc_lo <= fc_hi)) continue;
-            const int b_lo = (int)fb_lo, b_hi = (int)fb_hi, c_lo = (int)fc_lo, c_hi = (int)fc_hi;
-            for (int ib = b_lo; ib <= b_hi; ++ib)
-                for (int ic = c_lo; ic <= c_hi; ++ic) {
-                    int idx[3];
-                    idx[ax] = s;
-                    idx[bx] = ib;
-                    idx[cx] = ic;
-                    int pix2;
-                    if (project_voxel(m, (float)idx[0] - cc[0], (float)idx[1] - cc[1], (float)idx[2] - cc[2],
-                                      (uint32_t)a.W, (uint32_t)a.H, &pix2) &&
-                        pix2 == pix) {
-                        const uint32_t lin =
-                            (uint32_t)idx[0] + (uint32_t)a.nx * ((uint32_t)idx[1] + (uint32_t)a.ny * (uint32_t)idx[2]);
-                        acc += __ldg(dl + lin);
+            eb = fmaf(ds, rb, 1e-3f);
+            ec = fmaf(ds, rc, 1e-3f);
+        };
+        // Slices go in blocks of 64: a branch-free pass marks, in a 64-bit mask,
+        // the slices whose windows hold a lattice point of the grid; a second
+        // pass visits only the marked slices, in ascending order, and tests
+        // their lattice points exactly.  The whole warp runs the first pass
+        // in step, and the second only as often as its busiest lane needs.
+        for (int s0 = s_lo; s0 <= s_hi; s0 += 64) {
+            const int n_s = min(64, s_hi - s0 + 1);
+            uint64_t mask = 0;
+            for (int q = 0; q < n_s; ++q) {
+                float b0, c0, eb, ec;
+                window(s0 + q, b0, c0, eb, ec);
+                // an integer in [lo, hi] clipped to the grid <=> floor(min(hi, n - 1)) >= max(lo, 0)
+                const bool hit = fminf(floorf(b0 + eb), nb1) >= fmaxf(b0 - eb, 0.0f) &&
+                                 fminf(floorf(c0 + ec), nc1) >= fmaxf(c0 - ec, 0.0f);
+                mask |= (uint64_t)hit << q;
+            }
+            while (mask) {
+                const int q = __ffsll((long long)mask) - 1;
+                mask &= mask - 1;
+                const int s = s0 + q;
+                float b0, c0, eb, ec;
+                window(s, b0, c0, eb, ec);
+                const int b_lo = (int)fmaxf(ceilf(b0 - eb), 0.0f), b_hi = (int)fminf(floorf(b0 + eb), nb1);
+                const int c_lo = (int)fmaxf(ceilf(c0 - ec), 0.0f), c_hi = (int)fminf(floorf(c0 + ec), nc1);
+                for (int ib = b_lo; ib <= b_hi; ++ib)
+                    for (int ic = c_lo; ic <= c_hi; ++ic) {
+                        int idx[3];
+                        idx[ax] = s;
+                        idx[bx] = ib;
+                        idx[cx] = ic;
+                        int pix2;
+                        if (project_voxel(m, (float)idx[0] - cc[0], (float)idx[1] - cc[1], (float)idx[2] - cc[2],
+                                          (uint32_t)a.W, (uint32_t)a.H, &pix2) &&
+                            pix2 == pix) {
+                            const uint32_t lin = (uint32_t)idx[0] +
+                                                 (uint32_t)a.nx * ((uint32_t)idx[1] + (uint32_t)a.ny * (uint32_t)idx[2]);
+                            acc += __ldg(dl + lin);
+                        }
                     }
-                }
+            }
         }
         // chain rule to the SLM and to the background model
         float dslm = 0.0f, dm[3] = {0.0f, 0.0f, 0.0f}, dv[3] = {0.0f, 0.0f, 0.0f};
