@@ -53,6 +53,12 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_slm.argtypes = [ctypes.c_int64, _u8p, _f32p, _f32p, ctypes.c_double, _dp]
             lib.oracle_slm.restype = None
+            lib.oracle_edges.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _u8p, _u8p]
+            lib.oracle_edges.restype = None
+            lib.oracle_particle_weights.argtypes = [ctypes.c_int, _i32p, _dp, _u8p, ctypes.c_int64, ctypes.c_int,
+                                                    _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp,
+                                                    _i32p]
+            lib.oracle_particle_weights.restype = None
             lib.oracle_reproject.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
                                              ctypes.c_int, _i32p, _dp, ctypes.c_int64, _u32p, ctypes.c_double,
                                              _u8p]
@@ -184,6 +190,34 @@ def fuse(grid, cams, slm_maps: np.ndarray, params=None, edge_eps: float = 1e-3) 
     assert n == lst.size
     return {"occ": occ, "logodds": lo, "occupied": occupied.astype(bool),
             "boundary": boundary.astype(bool), "n_seen": n_seen, "list": lst}
+
+
+def edges(masks) -> np.ndarray:
+    """Edge maps of silhouettes [n_cams][H][W]: set pixels with a 4-neighbour
+    inside the image that is not set."""
+    lib = _load()
+    m = np.ascontiguousarray(np.asarray(masks) != 0, dtype=np.uint8)
+    out = np.empty_like(m)
+    lib.oracle_edges(m.shape[0], m.shape[2], m.shape[1], _ptr(m, _u8p), _ptr(out, _u8p))
+    return out
+
+
+def particle_weights(cams, masks, cylinders, kt: int = 8, kw: int = 4, edge_eps: float = 1e-3) -> dict:
+    """Tracker weights (Eq. 14-16) of particles = cylinders [P][n_cyl][7]
+    (a xyz, b xyz, r) against silhouettes [n_cams][H][W]: {"weights" [P],
+    "terms" [P][n_cams][2] (S_e, S_r), "ambiguous" [P][n_cams]}."""
+    lib = _load()
+    wh, rec = _cam_args(cams)
+    m = np.ascontiguousarray(np.asarray(masks) != 0, dtype=np.uint8)
+    cy = np.ascontiguousarray(np.asarray(cylinders, np.float64))
+    P, n_cyl = cy.shape[0], cy.shape[1]
+    w = np.empty(P)
+    terms = np.empty((P, len(cams), 2))
+    amb = np.empty((P, len(cams)), np.int32)
+    lib.oracle_particle_weights(len(cams), _ptr(wh, _i32p), _ptr(rec, _dp), _ptr(m, _u8p), P, n_cyl,
+                                _ptr(cy, _dp), int(kt), int(kw), float(edge_eps), _ptr(w, _dp), _ptr(terms, _dp),
+                                _ptr(amb, _i32p))
+    return {"weights": w, "terms": terms, "ambiguous": amb}
 
 
 def reproject(grid, cams, voxel_list, grow: float = 0.0) -> np.ndarray:

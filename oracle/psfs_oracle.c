@@ -177,6 +177,112 @@ int64_t oracle_compact(int64_t n_vox, const uint8_t *occupied, uint32_t *list)
 }
 
 /* --------------------------------------------------------------------- */
+/* Particle weights of the tracker (Sec. 2.3.2, Eq. 14-16): the match of  */
+/* each particle's projected body model with the voxel silhouettes and    */
+/* their edges in every camera.                                            */
+/*   Edge map: a pixel is an edge iff it is set in the silhouette and one  */
+/*   of its 4 neighbours inside the image is not.                          */
+/*   A particle is n_cyl cylinders (a[3], b[3], r), 7 values each.  For a  */
+/*   cylinder and camera centre C = -R^T t: u = (b - a) / |b - a|, n =     */
+/*   unit(u x (m - C)) with m = (a + b) / 2 (the direction of the outline  */
+/*   seen from C).  Silhouette samples: a + t (b - a) + w r n with         */
+/*   t = (k + 1/2) / kt, w = (2 l + 1) / kw - 1; edge samples: the same t, */
+/*   w = -1 and +1.  A sample is looked up in the pixel containing its     */
+/*   projection; behind the camera or outside the image its value is 0.    */
+/*   S_r = (1 / N_r) sum (1 - p_r), S_e = (1 / N_e) sum (1 - p_e) per      */
+/*   camera (Eq. 14-15), weight = exp(-sum_c (S_e + S_r)) (Eq. 16).        */
+/*   ambiguous[p * n_cams + c] counts the samples whose projection is      */
+/*   within edge_eps px of a pixel edge (the looked-up pixel may differ in */
+/*   another precision).                                                   */
+/* --------------------------------------------------------------------- */
+void oracle_edges(int n_cams, int W, int H, const uint8_t *masks, uint8_t *edges)
+{
+    for (int c = 0; c < n_cams; ++c) {
+        const uint8_t *m = masks + (int64_t)c * W * H;
+        uint8_t *e = edges + (int64_t)c * W * H;
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                int edge = 0;
+                if (m[(int64_t)y * W + x]) {
+                    if (x > 0 && !m[(int64_t)y * W + x - 1]) edge = 1;
+                    if (x + 1 < W && !m[(int64_t)y * W + x + 1]) edge = 1;
+                    if (y > 0 && !m[(int64_t)(y - 1) * W + x]) edge = 1;
+                    if (y + 1 < H && !m[(int64_t)(y + 1) * W + x]) edge = 1;
+                }
+                e[(int64_t)y * W + x] = (uint8_t)edge;
+            }
+    }
+}
+
+static int sample_value(const double *cam, int W, int H, const uint8_t *map, const double X[3], double edge_eps,
+                        int *ambiguous)
+{
+    int px, py;
+    double xy[2], w;
+    int vis = oracle_project(cam, W, H, X, &px, &py, xy, &w);
+    if (w > 0.0 && (dist_to_integer(xy[0]) < edge_eps || dist_to_integer(xy[1]) < edge_eps)) ++*ambiguous;
+    if (!vis) return 0;
+    return map[(int64_t)py * W + px] != 0;
+}
+
+void oracle_particle_weights(int n_cams, const int *wh, const double *cams, const uint8_t *masks,
+                             int64_t n_particles, int n_cyl, const double *cyl, int kt, int kw, double edge_eps,
+                             double *weights, double *terms, int *ambiguous)
+{
+    const int W = wh[0], H = wh[1];
+    uint8_t *edges = (uint8_t *)malloc((size_t)n_cams * W * H);
+    oracle_edges(n_cams, W, H, masks, edges);
+    for (int64_t p = 0; p < n_particles; ++p) {
+        double total = 0.0;
+        for (int c = 0; c < n_cams; ++c) {
+            const double *cam = cams + ORACLE_CAM_STRIDE * c, *R = cam + 9, *t = cam + 18;
+            const uint8_t *mask = masks + (int64_t)c * W * H, *edge = edges + (int64_t)c * W * H;
+            double C[3];
+            for (int r = 0; r < 3; ++r) C[r] = -(R[r] * t[0] + R[3 + r] * t[1] + R[6 + r] * t[2]);
+            int miss_r = 0, miss_e = 0, amb = 0;
+            for (int q = 0; q < n_cyl; ++q) {
+                const double *cy = cyl + ((size_t)p * n_cyl + q) * 7;
+                const double *A = cy, *B = cy + 3, rad = cy[6];
+                double u[3], mid[3], view[3], n[3];
+                for (int r = 0; r < 3; ++r) {
+                    u[r] = B[r] - A[r];
+                    mid[r] = 0.5 * (A[r] + B[r]);
+                    view[r] = mid[r] - C[r];
+                }
+                n[0] = u[1] * view[2] - u[2] * view[1];
+                n[1] = u[2] * view[0] - u[0] * view[2];
+                n[2] = u[0] * view[1] - u[1] * view[0];
+                double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                for (int r = 0; r < 3; ++r) n[r] = nn > 0.0 ? n[r] / nn : 0.0;
+                for (int k = 0; k < kt; ++k) {
+                    const double tt = (k + 0.5) / kt;
+                    for (int l = 0; l < kw; ++l) {
+                        const double ww = (2.0 * l + 1.0) / kw - 1.0;
+                        double X[3];
+                        for (int r = 0; r < 3; ++r) X[r] = A[r] + tt * u[r] + ww * rad * n[r];
+                        miss_r += 1 - sample_value(cam, W, H, mask, X, edge_eps, &amb);
+                    }
+                    for (int side = -1; side <= 1; side += 2) {
+                        double X[3];
+                        for (int r = 0; r < 3; ++r) X[r] = A[r] + tt * u[r] + side * rad * n[r];
+                        miss_e += 1 - sample_value(cam, W, H, edge, X, edge_eps, &amb);
+                    }
+                }
+            }
+            const double s_r = (double)miss_r / (n_cyl * kt * kw), s_e = (double)miss_e / (n_cyl * kt * 2);
+            if (terms) {
+                terms[(p * n_cams + c) * 2 + 0] = s_e;
+                terms[(p * n_cams + c) * 2 + 1] = s_r;
+            }
+            if (ambiguous) ambiguous[p * n_cams + c] = amb;
+            total += s_e + s_r;
+        }
+        weights[p] = exp(-total);
+    }
+    free(edges);
+}
+
+/* --------------------------------------------------------------------- */
 /* Silhouettes of a voxel set (Sec. 2.3: the projection of the voxels in  */
 /* each camera is the tracker's prior knowledge, matched against the      */
 /* particles' projected models).  Pixel (x, y) of camera c is set iff the */
