@@ -544,6 +544,32 @@ def run_ours(args):
                             "note": "psfs_reproject of the step's 100 surface lists in one call (mask memset + "
                                     "1 kernel): one thread per (surface voxel, camera), exact centre-ray tests "
                                     "over the cube's projected box"}
+        # tracker weights of 200 particles (10 cylinders each, around frame 0's
+        # body) against frame 0's silhouettes
+        caps0 = sc.capsules[0]
+        base = np.array([[*c_.a, *c_.b, c_.radius] for c_ in caps0], dtype=np.float32)
+        prng = np.random.default_rng(args.seed + 17)
+        n_part = 200
+        parts = np.repeat(base[None], n_part, axis=0)
+        jit = prng.normal(0, 0.03, size=parts.shape).astype(np.float32)
+        jit[..., 6] = 0.0
+        parts = torch.from_numpy(parts + jit).to(dev)
+        pw = torch.empty(n_part, device=dev)
+        pt = torch.empty((n_part, K, 2), device=dev)
+        m0 = masks[0].contiguous()
+        with torch.cuda.stream(stream):
+            psfs.psfs_particle_weights(h, parts, m0, pw, pt)   # warm-up
+            t0e.record(stream)
+            for _ in range(reps):
+                psfs.psfs_particle_weights(h, parts, m0, pw, pt)
+            t1e.record(stream)
+        torch.cuda.synchronize(dev)
+        us_w = 1e3 * t0e.elapsed_time(t1e) / reps
+        n_samples = n_part * K * len(caps0) * (8 * 4 + 2 * 8)
+        nxt["particle_weights"] = {"us_per_call": us_w, "particles": n_part, "cylinders": len(caps0),
+                                   "samples_per_call": n_samples, "gsamples_per_s": n_samples / (us_w * 1e-6) / 1e9,
+                                   "note": "psfs_particle_weights (Eq. 14-16), one launch, one CTA per particle; "
+                                           "sample lookups in the L2-resident silhouettes"}
         del masks
         # smoothing + threshold + compaction over the step's occupancy grids
         sm_grid = torch.empty((F, V), dtype=torch.float32, device=dev)

@@ -201,6 +201,34 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
                                            float *h_occupancy, uint32_t *h_lists, uint32_t capacity,
                                            uint32_t *h_counts);
 
+/* Particle weights of the tracker (Section 2.3.2, Eq. 14-16; Section 3.3.3,
+ * the sum-squared-difference steps b-d): how well each particle's projected
+ * body matches the voxel silhouettes (psfs_reproject) and their edges in
+ * every camera of this handle's rig.  The paper gives the weights but not
+ * the sample points; here:
+ *   cylinders  device f32 [n_particles][n_cyl][7]: endpoints a, b (world
+ *              xyz) and radius r of each body cylinder
+ *   samples    per cylinder and camera, with C the camera centre, u = b - a,
+ *              n = unit(u x ((a + b) / 2 - C)): silhouette samples a + t u +
+ *              w r n at t = (k + 1/2) / kt, w = (2 l + 1) / kw - 1 (k < kt,
+ *              l < kw); edge samples at the same t with w = -1 and +1
+ *   value      the bit of the pixel a sample projects into: the silhouette
+ *              bit, or for edge samples the edge bit (a set pixel with a
+ *              4-neighbour inside the image that is not set); 0 behind the
+ *              camera or outside the image
+ *   masks      device uint8 [n_cams][height][width] silhouettes (0 / 1)
+ *   terms      device f32 [n_particles][n_cams][2] or NULL: S_e, S_r of
+ *              Eq. 14-15, the mean of (1 - value) over the edge / silhouette
+ *              samples of all cylinders
+ *   weights    device f32 [n_particles]: exp(-sum over cameras of
+ *              (S_e + S_r)) (Eq. 16)
+ * Samples are projected in float32: one whose projection lies within about
+ * 1e-3 px of a pixel edge may read the neighbouring pixel.
+ * Errors: INVALID_ARG (n_cyl, kt or kw outside [1, 64], NULL pointers),
+ * CUDA. */
+psfs_status psfs_particle_weights(psfs_handle *h, int32_t n_particles, int32_t n_cyl, const float *cylinders,
+                                  int32_t kt, int32_t kw, const uint8_t *masks, float *weights, float *terms);
+
 /* Silhouettes of the reconstructed voxels in every camera (Section 2.3: the
  * projection of the voxels is the tracker's prior knowledge; Section 3.3.3,
  * voxel projection): pixel (x, y) of camera c is set iff the ray from the

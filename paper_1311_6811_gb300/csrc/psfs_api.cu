@@ -803,6 +803,50 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
     return PSFS_OK;
 }
 
+psfs_status psfs_particle_weights(psfs_handle *h, int32_t n_particles, int32_t n_cyl, const float *cylinders,
+                                  int32_t kt, int32_t kw, const uint8_t *masks, float *weights, float *terms)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (n_particles < 0) return fail(PSFS_ERR_INVALID_ARG, "n_particles < 0");
+    if (n_particles == 0) return PSFS_OK;
+    if (n_cyl < 1 || n_cyl > 64) return fail(PSFS_ERR_INVALID_ARG, "n_cyl outside [1, 64]");
+    if (kt < 1 || kt > 64 || kw < 1 || kw > 64) return fail(PSFS_ERR_INVALID_ARG, "kt or kw outside [1, 64]");
+    if (!cylinders || !aligned(cylinders, 4)) return fail(PSFS_ERR_INVALID_ARG, "cylinders NULL or misaligned");
+    if (!masks) return fail(PSFS_ERR_INVALID_ARG, "masks is NULL");
+    if (!weights || !aligned(weights, 4)) return fail(PSFS_ERR_INVALID_ARG, "weights NULL or misaligned");
+    if (terms && !aligned(terms, 4)) return fail(PSFS_ERR_INVALID_ARG, "terms misaligned");
+    DeviceGuard guard(h->device);
+    WeightArgs a{};
+    for (int c = 0; c < h->n_cams; ++c) {
+        const psfs_camera &cam = h->cams[c];
+        for (int r = 0; r < 3; ++r) {
+            for (int col = 0; col < 3; ++col) {
+                double v = 0.0;
+                for (int q = 0; q < 3; ++q) v += cam.K[3 * r + q] * cam.R[3 * q + col];
+                a.P[c][4 * r + col] = (float)v;
+            }
+            double v = 0.0;
+            for (int q = 0; q < 3; ++q) v += cam.K[3 * r + q] * cam.t[q];
+            a.P[c][4 * r + 3] = (float)v;
+            double C = 0.0;
+            for (int q = 0; q < 3; ++q) C -= cam.R[3 * q + r] * cam.t[q];
+            a.C[c][r] = (float)C;
+        }
+    }
+    a.n_cams = h->n_cams;
+    a.W = h->W;
+    a.H = h->H;
+    a.n_cyl = n_cyl;
+    a.kt = kt;
+    a.kw = kw;
+    a.cyl = cylinders;
+    a.masks = masks;
+    a.weights = weights;
+    a.terms = terms;
+    PSFS_CK(launch_weights(a, n_particles, h->stream));
+    return PSFS_OK;
+}
+
 psfs_status psfs_reproject(psfs_handle *h, int32_t n_frames, const uint32_t *voxel_lists, uint32_t list_stride,
                            const uint32_t *counts, uint8_t *masks)
 {

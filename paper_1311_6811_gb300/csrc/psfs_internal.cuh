@@ -470,6 +470,22 @@ struct ReprojectArgs {
 };
 cudaError_t launch_reproject(const ReprojectArgs &a, int n_frames, cudaStream_t s);
 
+// Particle weights of the tracker (psfs_weights.cu): world -> pixel
+// matrices P = K [R | t] and camera centres per camera; particle p's
+// cylinders at cyl + p * n_cyl * 7 (a xyz, b xyz, r); silhouettes
+// [n_cams][H][W]; weights [P]; terms [P][n_cams][2] (S_e, S_r) or null.
+struct WeightArgs {
+    float P[PSFS_MAX_CAMS][12];
+    float C[PSFS_MAX_CAMS][3];
+    int n_cams, W, H;
+    int n_cyl, kt, kw;
+    const float *cyl;
+    const uint8_t *masks;
+    float *weights;
+    float *terms;
+};
+cudaError_t launch_weights(const WeightArgs &a, int n_particles, cudaStream_t s);
+
 struct BackwardArgs {
     FuseArgs f;                   // grid, cameras, maps (for the voxel pass), tiles
     const float *d_occ;           // [n_vox]

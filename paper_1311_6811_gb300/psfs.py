@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
             "psfs_surface": (st, [_vp, ctypes.c_int32, _vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_smooth": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_reproject": (st, [_vp, ctypes.c_int32, _vp, ctypes.c_uint32, _vp, _vp]),
+            "psfs_particle_weights": (st, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32,
+                                           _vp, _vp, _vp]),
             "psfs_set_background_l2": (st, [_vp, ctypes.c_int32]),
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
@@ -318,6 +320,19 @@ def psfs_reconstruct_sequence_host(h: int, n_frames: int, images, occupancy, vox
     if st not in (PSFS_OK, PSFS_ERR_CAPACITY):
         _check(st, "psfs_reconstruct_sequence_host")
     return st
+
+
+def psfs_particle_weights(h: int, cylinders, masks, weights, terms=None, kt: int = 8, kw: int = 4):
+    """Tracker weights (Eq. 14-16) of particles `cylinders` f32 [P][n_cyl][7]
+    against silhouettes `masks` uint8 [n_cams][H][W]; writes `weights` [P]
+    and, if given, `terms` [P][n_cams][2] (S_e, S_r)."""
+    import torch
+    P, n_cyl = int(cylinders.shape[0]), int(cylinders.shape[1])
+    _check(load().psfs_particle_weights(h, P, n_cyl, _dev_ptr(cylinders, "cylinders", torch.float32), int(kt),
+                                        int(kw), _dev_ptr(masks, "masks", torch.uint8),
+                                        _dev_ptr(weights, "weights", torch.float32),
+                                        _dev_ptr(terms, "terms", torch.float32) if terms is not None else None),
+           "psfs_particle_weights")
 
 
 def psfs_reproject(h: int, n_frames: int, voxel_lists, list_stride: int, counts, masks):

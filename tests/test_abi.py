@@ -143,6 +143,7 @@ def test_calls_reject_null_handle(lib):
     assert lib.psfs_surface(None, 1, None, 0, None, None, 0, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_smooth(None, 1, None, None, None, 0, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_reproject(None, 1, None, 0, None, None) == psfs.PSFS_ERR_INVALID_ARG
+    assert lib.psfs_particle_weights(None, 1, 10, None, 8, 4, None, None, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_fuse_slm(None, None, None, None, 0, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_get_likelihood(None, None, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_backward(None, None, None, None, None, None) == psfs.PSFS_ERR_INVALID_ARG
