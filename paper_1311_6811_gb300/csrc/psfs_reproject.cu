@@ -39,7 +39,9 @@ __global__ void __launch_bounds__(kRpThreads) reproject_kernel(const __grid_cons
         const uint32_t v = __ldg(list + e);
         if (v >= a.n_vox) continue;
         const uint32_t kz = v / nxy, r = v - kz * nxy, jy = r / nx, ix = r - jy * nx;
-        const float *m = a.cam[c].m;
+        float m[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
         // projected corners (centred index coordinates)
         const float x0 = (float)ix - a.ci, y0 = (float)jy - a.cj, z0 = (float)kz - a.ck;
         float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
@@ -70,8 +72,14 @@ __global__ void __launch_bounds__(kRpThreads) reproject_kernel(const __grid_cons
             ya = max(ya, (int)fmaxf(ceilf(vmin - 0.5f - dv), -1.0f));
             yb = min(yb, (int)fminf(floorf(vmax - 0.5f + dv), (float)H));
         }
-        const PixelInv &iv = a.inv[c];
-        const float lo[3] = {(float)ix - 0.5f, (float)jy - 0.5f, (float)kz - 0.5f};
+        // this camera's inverse projection and the cube's slab offsets from the
+        // camera centre, in registers for the pixel loop
+        float mi[9], o1[3];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) mi[q] = a.inv[c].minv[q];
+        o1[0] = (float)ix - 0.5f - a.inv[c].qc[0];
+        o1[1] = (float)jy - 0.5f - a.inv[c].qc[1];
+        o1[2] = (float)kz - 0.5f - a.inv[c].qc[2];
         uint8_t *mask = masks + (size_t)c * W * H;
         for (int y = ya; y <= yb; ++y) {
             const float py = (float)y + 0.5f;
@@ -80,9 +88,9 @@ __global__ void __launch_bounds__(kRpThreads) reproject_kernel(const __grid_cons
                 float t_in = 0.0f, t_out = INFINITY;
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
-                    const float d = fmaf(iv.minv[3 * ax], px, fmaf(iv.minv[3 * ax + 1], py, iv.minv[3 * ax + 2]));
+                    const float d = fmaf(mi[3 * ax], px, fmaf(mi[3 * ax + 1], py, mi[3 * ax + 2]));
                     const float id = 1.0f / d;
-                    const float t1 = (lo[ax] - iv.qc[ax]) * id, t2 = (lo[ax] + 1.0f - iv.qc[ax]) * id;
+                    const float t1 = o1[ax] * id, t2 = (o1[ax] + 1.0f) * id;
                     t_in = fmaxf(t_in, fminf(t1, t2));
                     t_out = fminf(t_out, fmaxf(t1, t2));
                 }
