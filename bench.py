@@ -190,9 +190,10 @@ def csrc_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
+def ncu_traffic(kernel: str, config: dict):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+    was taken on the current sources of that kernel and the same launch
+    configuration; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -200,7 +201,16 @@ def ncu_traffic(kernel: str):
         with open(path) as f:
             d = json.load(f)
         rec = d.get("kernels", {}).get(kernel)
-        if not rec or rec.get("csrc_sha") != csrc_digest():
+        if not rec:
+            return None
+        h = hashlib.sha256()
+        for name in rec["sources"]:
+            with open(os.path.join(ROOT, "paper_1311_6811_gb300", "csrc", name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+        if h.hexdigest()[:16] != rec["sources_sha"]:
+            return None
+        if any(config.get(k_) != v for k_, v in rec.get("config", {}).items()):
             return None
         return float(rec["dram_bytes_per_launch"])
     except (ValueError, KeyError, OSError):
@@ -470,7 +480,8 @@ def run_ours(args):
     dom = max(stages, key=lambda k: stages[k]["avg_us"] * stages[k]["launches"])
     peak, peak_kind = measured_peaks()
     ach = stages[dom]["achieved_gbs"]
-    traffic = ncu_traffic(kern_names.get(dom, dom))
+    traffic = ncu_traffic(kern_names.get(dom, dom),
+                          {"lanes_x": fuse_cfg[0], "voxels_z": fuse_cfg[2], "frames_per_group": G})
     roofline = {"bound": "hbm", "kernel": kern_names.get(dom, dom), "achieved": ach, "peak": peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": traffic,
