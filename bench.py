@@ -170,6 +170,27 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # helpers
 # --------------------------------------------------------------------------- #
+def sequence_units(n_frames, group, voxels_z=4, map_elem=4):
+    """Frames per unit of psfs_reconstruct_sequence: groups of `group` frames
+    while they fill, then the largest smaller power-of-two groups that fit and
+    whose 32-byte pixel records (P = min(g, 32 / map_elem) frames) the tile
+    height supports (voxels_z 4; 8 when P <= 8; 16 when P <= 4), else single
+    frames."""
+    def ok(g):
+        p = min(g, 32 // map_elem)
+        return voxels_z == 4 or (voxels_z == 8 and p <= 8) or (voxels_z == 16 and p <= 4)
+
+    units, left = [], n_frames
+    while left > 0:
+        g = group
+        while g > 1 and (g > left or not ok(g)):
+            g //= 2
+        g = max(g, 1)
+        units.append(g)
+        left -= g
+    return units
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -453,25 +474,39 @@ def run_ours(args):
     mean_count = float(counts.double().mean().item())
 
     # roofline of the dominant kernel (algorithmic bytes / average launch time).
-    # The sequence runs in units of G frames (frame groups) plus F mod G single
-    # frames; per unit of nf frames the likelihood reads the background once
-    # (24 B/px), nf images (3 B/px) and writes nf maps, the fusion reads nf maps
-    # and writes nf occupancy grids and lists.
+    # The sequence runs in units of G frames (frame groups), then the largest
+    # smaller groups that fit the remaining frames, then single frames; per
+    # unit of nf frames the likelihood reads the background once (24 B/px), nf
+    # images (3 B/px) and writes nf maps, the fusion reads nf maps and writes
+    # nf occupancy grids and lists.
     map_elem = 4 if args.map_dtype == "f32" else 2
     G = fuse_cfg[5] if batch is None else 1
-    units = [G] * (F // G) + [1] * (F % G) if G > 1 else [1] * F
+    units = sequence_units(F, G, fuse_cfg[2], map_elem)
     fuse_frame_bytes = n_pix * map_elem + V * 4 + mean_count * 4
     step_bytes = {"likelihood": sum(n_pix * (24 + nf * (3 + map_elem)) for nf in units),
                   "fuse": F * fuse_frame_bytes,
                   "batch": F * (n_pix * (3 + 24 + map_elem) + fuse_frame_bytes)}
     grouped = G > 1
     kern_names = {"likelihood": "likelihood_group_kernel" if grouped else "likelihood_kernel",
-                  "fuse": "fuse_group_kernel" if grouped else "fuse_kernel", "batch": "batch_kernel"}
+                  "fuse": "fuse_group_kernel" if grouped else "fuse_kernel",
+                  "batch": "batch_kernel"}
+    # kernel launches: one likelihood launch per unit, one fusion launch per
+    # plane of 32-byte pixel records (a unit's stage events span its planes)
+    plane = 32 // map_elem
+    fuse_launches = sum(-(-nf // plane) if nf > 1 else 1 for nf in units)
+    if batch is None:
+        gpu_launches = args.steps * (len(units) + fuse_launches)
+    else:
+        gpu_launches = sum(n for _, n in prof.values())
+    # the profile has one event per unit and stage; a fusion event spans the
+    # unit's plane launches, back to back on one stream
+    per_unit = {"likelihood": 1.0, "fuse": fuse_launches / len(units)} if batch is None else {}
     stages = {}
     for name, (t_ms, n) in prof.items():
-        avg = t_ms / n
-        per_launch = step_bytes[name] * args.steps / n if name in step_bytes else None
-        stages[name] = {"launches": n, "avg_us": 1e3 * avg, "share": None,
+        n_launch = int(round(n * per_unit.get(name, 1.0)))
+        avg = t_ms / n_launch
+        per_launch = step_bytes[name] * args.steps / n_launch if name in step_bytes else None
+        stages[name] = {"launches": n_launch, "events": n, "avg_us": 1e3 * avg, "share": None,
                         "alg_bytes_per_launch": per_launch,
                         "achieved_gbs": per_launch / (avg * 1e-3) / 1e9 if per_launch else None}
     tot = sum(v["avg_us"] * v["launches"] for v in stages.values())
@@ -480,12 +515,16 @@ def run_ours(args):
     dom = max(stages, key=lambda k: stages[k]["avg_us"] * stages[k]["launches"])
     peak, peak_kind = measured_peaks()
     ach = stages[dom]["achieved_gbs"]
+    # the fusion kernel of a group runs per plane of 32-byte records: its
+    # launch depends on the frames per record, the likelihood's on G
     traffic = ncu_traffic(kern_names.get(dom, dom),
-                          {"lanes_x": fuse_cfg[0], "voxels_z": fuse_cfg[2], "frames_per_group": G})
+                          {"lanes_x": fuse_cfg[0], "voxels_z": fuse_cfg[2],
+                           "frames_per_group": min(G, plane) if dom == "fuse" else G})
     roofline = {"bound": "hbm", "kernel": kern_names.get(dom, dom), "achieved": ach, "peak": peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                 "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": traffic,
                 "alg_bytes_per_launch": stages[dom]["alg_bytes_per_launch"],
+                "units_per_step": units,
                 "note": ("the fusion kernels are bound by L1 gather throughput (ncu: 79 % of L1 peak for "
                          "fuse_group_kernel), not by HBM")
                         if dom == "fuse" else None}
@@ -681,7 +720,7 @@ def run_ours(args):
                 "stages": stages, "roofline": roofline, "roofline_sequence": roofline_sequence,
                 "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
                 "next": nxt,
-                "gpu_launches": sum(v["launches"] for v in stages.values()), "clocks": clk}
+                "gpu_launches": gpu_launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -735,10 +774,10 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg):
         out[f"{dtype}_forward_backward_us"] = 1e3 * e[1].elapsed_time(e[2]) / F
         if dtype != "f32":
             out[f"{dtype}_max_abs_occ_diff_vs_f32"] = err
-        # batched forward: the sequence path with frame groups (16 frames per
-        # group for 16-bit maps, the tuned group size for FP32)
+        # batched forward: the sequence path with frame groups (the tuned group
+        # size, at least 16 frames for 16-bit maps)
         nseq = min(32, d_images.shape[0])
-        G = 16 if dtype != "f32" else max(int(fuse_cfg[5]), 1)
+        G = max(int(fuse_cfg[5]), 16) if dtype != "f32" else max(int(fuse_cfg[5]), 1)
         lx = fuse_cfg[0] if fuse_cfg[0] in (8, 16) else 8
         psfs.psfs_set_fuse_config(rec.handle, lx, 4, 4, 0, fuse_cfg[4], G)
         cap_s = 1 << 17

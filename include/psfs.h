@@ -113,15 +113,17 @@ typedef struct {
  * seq_likelihood_ctas: CTAs per SM of the likelihood grid on the sequence
  * path, 1 to 4 (0 in psfs_set_fuse_config keeps the current value).
  * frames_per_group: frames per launch on the sequence path: 1 = one frame
- * per likelihood and fusion launch; 2, 4, 8 or 16 = frame groups, where one
- * likelihood launch reads the background once for the whole group and writes
- * the group's maps interleaved per pixel, and one fusion launch projects each
- * voxel once and gathers all frames of the group with one vector load (each
+ * per likelihood and fusion launch; 2, 4, 8, 16 or 32 = frame groups, where
+ * one likelihood launch reads the background once for the whole group and
+ * writes the group's maps as 32-byte pixel records of P frames (P = 8 for
+ * FP32 maps, 16 for 16-bit maps, the group size when smaller), one plane of
+ * records per P frames; one fusion launch per plane projects each voxel once
+ * per camera and gathers the plane's P frames with one vector load (each
  * frame's results are bit-identical to one frame per launch).  Groups need
- * staged = 0, lanes_x 8 or 16, voxels_z 4 or 8 for 8 frames and 4 for 16
- * frames; with another
- * shape the sequence path runs one frame per launch.  Trailing frames that do
- * not fill a group run one per launch.  0 in psfs_set_fuse_config keeps the
+ * staged = 0, lanes_x 8 or 16, and voxels_z 4, or 8 when P <= 8, or 16 when
+ * P <= 4; with another shape the sequence path runs one frame per launch.
+ * Trailing frames that do not fill a group run in the largest smaller groups
+ * that fit, the last odd frame alone.  0 in psfs_set_fuse_config keeps the
  * current value.  The batch entry points ignore this field. */
 typedef struct {
     int32_t lanes_x;

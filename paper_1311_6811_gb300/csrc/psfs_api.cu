@@ -282,7 +282,7 @@ psfs_status replan(psfs_handle *h, const FuseShape &shape)
 {
     std::vector<uint64_t> tiles;
     std::vector<int4> tilecam;
-    FuseArgs f;
+    FuseArgs f{};
     plan_fuse(h->grid, h->cams.data(), h->n_cams, h->params, shape, &f, &tiles, &tilecam);
     uint64_t *d_tiles = nullptr;
     int4 *d_tilecam = nullptr;
@@ -562,12 +562,23 @@ static psfs_status ensure_group_maps(psfs_handle *h, int frames)
     return PSFS_OK;
 }
 
+// Frames in the next unit of a sequence: the largest group size that fits the
+// remaining frames (group, group / 2, ... down to 2 frames, each with the
+// tile shape), else one frame.
+static int unit_frames(const psfs_handle *h, int group, int remaining)
+{
+    for (int g = group; g >= 2; g >>= 1)
+        if (g <= remaining && group_shape_supported(h->shape, g, (int)h->map_elem)) return g;
+    return 1;
+}
+
 // Enqueues n_frames frames with the given element strides between frames
 // (a stride of 0 repeats the same buffer, which only the autotuner does).
 // Frames go in units: groups of `group` frames (likelihood and fusion of the
-// whole group in one launch each) while whole groups remain, then single
-// frames.  Unit u's likelihood (stream 0) writes map buffer u & 1 while the
-// fusion of unit u - 1 (stream 1) reads the other one.
+// whole group in one launch each) while whole groups remain, then the largest
+// smaller groups that fit, then single frames.  Unit u's likelihood (stream 0)
+// writes map buffer u & 1 while the fusion of unit u - 1 (stream 1) reads the
+// other one.
 static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images, size_t img_stride,
                                     float *occupancy, size_t occ_stride, uint32_t *voxel_lists,
                                     size_t list_stride, uint32_t capacity, uint32_t *counts, size_t count_stride,
@@ -575,9 +586,10 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
 {
     psfs_status st = seq_setup(h);
     if (st != PSFS_OK) return st;
-    if (group > 1 && !group_shape_supported(h->shape, group)) group = 1;
-    if (group > 1 && n_frames >= group) {
-        st = ensure_group_maps(h, group);
+    if (group > 1 && !group_shape_supported(h->shape, group, (int)h->map_elem)) group = 1;
+    const int first_unit = unit_frames(h, group, n_frames);
+    if (first_unit > 1) {
+        st = ensure_group_maps(h, first_unit);
         if (st != PSFS_OK) return st;
     }
     cudaStream_t sl = h->seq_stream[0], sf = h->seq_stream[1];
@@ -587,7 +599,7 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
     PSFS_CK(cudaStreamWaitEvent(sf, h->seq_ev_in, 0));
     int f = 0;
     for (int u = 0; f < n_frames; ++u) {
-        const int nf = (group > 1 && n_frames - f >= group) ? group : 1;
+        const int nf = unit_frames(h, group, n_frames - f);
         const int b = u & 1;
         if (u >= 2) PSFS_CK(cudaStreamWaitEvent(sl, h->seq_ev_fused[b], 0));   // unit u-2 done with buffer b
         void *buf = nf > 1 ? h->gmaps[b] : bufs[b];
@@ -627,10 +639,11 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
         }
         {
             ProfScope ps(h, PSFS_STAGE_FUSE, sf);
-            if (nf > 1)
+            if (nf > 1) {
                 PSFS_CK(launch_fuse_group(fa, h->shape, nf, h->params.map_dtype, sf));
-            else
+            } else {
                 PSFS_CK(launch_fuse(fa, h->shape, h->params.map_dtype, sf));
+            }
         }
         PSFS_CK(cudaEventRecord(h->seq_ev_fused[b], sf));
         f += nf;
@@ -1158,9 +1171,11 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
     if (!fuse_shape_supported(shape)) return fail(PSFS_ERR_INVALID_ARG, "unsupported fuse tile shape");
     if (cfg->seq_likelihood_ctas < 0 || cfg->seq_likelihood_ctas > 4)
         return fail(PSFS_ERR_INVALID_ARG, "seq_likelihood_ctas outside [0, 4]");
-    if (cfg->frames_per_group < 0 || (cfg->frames_per_group > 1 && !group_shape_supported(shape, cfg->frames_per_group)))
+    if (cfg->frames_per_group < 0 ||
+        (cfg->frames_per_group > 1 && !group_shape_supported(shape, cfg->frames_per_group, (int)h->map_elem)))
         return fail(PSFS_ERR_INVALID_ARG,
-                    "frames_per_group: 0, 1, or 2 / 4 / 8 / 16 with staged 0, lanes_x 8 or 16 (voxels_z 4 or 8 for 8 frames, 4 for 16)");
+                    "frames_per_group: 0, 1, or 2 / 4 / 8 / 16 / 32 with staged 0, lanes_x 8 or 16, voxels_z 4 "
+                    "(8 when a 32-byte pixel record holds at most 8 frames, 16 when at most 4)");
     DeviceGuard guard(h->device);
     PSFS_CK(cudaStreamSynchronize(h->stream));
     if (h->seq_stream[0]) {
@@ -1193,10 +1208,11 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     DeviceGuard guard(h->device);
     const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
-    // scratch: occupancy of 16 frames, 16 lists of n_vox / 16 entries (the
-    // sequence timings; a frame with more occupied voxels only sets the
-    // capacity bit, cleared below) and 16 counts
-    constexpr int kTuneFrames = 16;
+    // scratch: occupancy of kTuneFrames frames, kTuneFrames lists of
+    // n_vox / kTuneFrames entries (the sequence timings; a frame with more
+    // occupied voxels only sets the capacity bit, cleared below) and the
+    // counts; two groups of 32 frames for grids up to 2^23 voxels, one above
+    const int kTuneFrames = n_vox <= (1ull << 23) ? 2 * kMaxGroup : kMaxGroup;
     const uint32_t seq_cap = (uint32_t)std::max<uint64_t>(1, n_vox / kTuneFrames);
     float *occ = nullptr;
     uint32_t *list = nullptr, *tcounts = nullptr;
@@ -1246,10 +1262,10 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
                 best_shape = shape;
             }
     }
-    // second stage: the sequence path, timed on 16 frames (distinct outputs,
-    // the same images) per repetition: CTAs per SM of the likelihood grid
-    // (1 to 4) with one frame per launch, then frame groups of 2, 4, 8 and
-    // 16 frames with the direct tile shapes that support them
+    // second stage: the sequence path, timed on kTuneFrames frames (distinct
+    // outputs, the same images) per repetition: CTAs per SM of the likelihood
+    // grid (1 to 4) with one frame per launch, then frame groups of 2, 4, 8,
+    // 16 and 32 frames with the direct tile shapes that support them
     auto time_sequence = [&](int lk, int group, float *ms_out) -> psfs_status {
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(PSFS_ERR_CUDA, "autotune sync");
         psfs_status s2 = enqueue_sequence(h, kTuneFrames, images, 0, occ, n_vox, list, seq_cap, seq_cap, tcounts,
@@ -1280,12 +1296,12 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
         }
     }
     const int group_lx = (best_shape.lx == 16) ? 16 : 8;
-    const int groups[4] = {2, 4, 8, 16};
-    for (int gi = 0; gi < 4 && st == PSFS_OK; ++gi) {
+    const int groups[5] = {2, 4, 8, 16, kMaxGroup};
+    for (int gi = 0; gi < 5 && st == PSFS_OK; ++gi) {
         for (int tz : {4, 8, 16}) {
             if (st != PSFS_OK) break;
             const FuseShape gshape = {group_lx, 4, tz, 0};
-            if (!group_shape_supported(gshape, groups[gi])) continue;
+            if (!group_shape_supported(gshape, groups[gi], (int)h->map_elem)) continue;
             st = replan(h, gshape);
             for (int lk = 1; lk <= 3 && st == PSFS_OK; ++lk) {
                 float ms = 0.0f;

@@ -5,11 +5,16 @@
 //
 //   * likelihood: one pass over the packed background (24 B per pixel, the
 //     largest input) computes the log ratio g of Eq. 5-9 for all F frames of
-//     the group.  The F maps are written interleaved per pixel,
-//     [n_cams][H][W][F], one F-wide vector store per pixel.
-//   * fusion: each voxel centre is projected into each camera once (Eq. 3)
-//     and one F-wide vector load gathers g of that pixel for all F frames;
-//     every frame keeps its own log-odds accumulator, output grid and list.
+//     the group.  The maps are written as 32-byte pixel records of P frames
+//     (P = 8 for FP32, 16 for 16-bit maps, F when F is smaller):
+//     [F / P planes][n_cams][H][W][P], one vector store per pixel and plane.
+//   * fusion, one launch per plane: each voxel centre is projected into each
+//     camera once (Eq. 3) and one vector load gathers g of that pixel for the
+//     P frames of the plane; every frame keeps its own log-odds accumulator,
+//     output grid and list.  Records of one 32-byte sector keep the gather at
+//     one sector per (voxel, camera) and a plane of a 128^3 x 8 x 640 x 480
+//     rig (79 MB) inside L2; groups of 16 or 32 frames only add planes, so
+//     the background pass is shared by more frames at the same fusion cost.
 //
 // Per frame and per pixel / voxel the arithmetic is exactly that of the
 // single-frame kernels (the same helper functions, the same camera order of
@@ -156,14 +161,14 @@ __device__ __forceinline__ void load_words(const uint32_t *src, uint32_t *w)
 // ---------------------------------------------------------------------------
 // Likelihood of a frame group
 // ---------------------------------------------------------------------------
-constexpr int kGChunk = 512;                 // pixels per chunk (multiple of 16)
-constexpr int kGImgBytes = 3 * kGChunk;      // 1536 per frame
-constexpr int kGBgBytes = 12 * kGChunk;      // 6144 (3 floats per pixel)
 constexpr int kGThreads = 256;
 template <int F>
 struct GLayout {
-    static constexpr int kStages = F >= 16 ? 2 : 4;                 // ring depth (16 frames: 74 KB)
-    static constexpr int kStage = F * kGImgBytes + 2 * kGBgBytes;   // bytes per ring stage
+    static constexpr int kChunk = F >= 32 ? 256 : 512;              // pixels per chunk (multiple of 16)
+    static constexpr int kImgBytes = 3 * kChunk;                    // one frame's colours
+    static constexpr int kBgBytes = 12 * kChunk;                    // 3 floats per pixel
+    static constexpr int kStages = F >= 32 ? 3 : (F >= 16 ? 2 : 4); // ring depth (16 frames: 74 KB, 32: 92 KB)
+    static constexpr int kStage = F * kImgBytes + 2 * kBgBytes;     // bytes per ring stage
     static constexpr int kSmem = kStages * kStage + kStages * 8;    // + mbarriers
 };
 
@@ -180,10 +185,19 @@ __device__ __forceinline__ void group_pixel(const LikelihoodArgs &a, OutT *out, 
         const float r = base + pixel_quad((float)q[0], (float)q[1], (float)q[2], m0, m1, m2, h0, h1, h2);
         pk.set(f, to_map<OutT>(log_ratio_of_r(r, a.sc)));
     }
-    store_words<GroupWords<OutT, F>::kWords>(reinterpret_cast<uint32_t *>(out + p * F), pk.w);
+    constexpr int kWords = GroupWords<OutT, F>::kWords;
+    if constexpr (kWords <= 8) {
+        store_words<kWords>(reinterpret_cast<uint32_t *>(out + p * F), pk.w);   // one plane: [n_pix][F]
+    } else {
+        // planes of 32-byte records: words 8q to 8q + 7 go to plane q
+        constexpr int kP = 32 / (int)sizeof(OutT);
+#pragma unroll
+        for (int q = 0; q < kWords / 8; ++q)
+            store_words<8>(reinterpret_cast<uint32_t *>(out + ((int64_t)q * a.n_pix + p) * kP), pk.w + 8 * q);
+    }
 }
 
-// Persistent grid over 512-pixel chunks; one thread per CTA streams each
+// Persistent grid over 512-pixel chunks (256 for 32 frames); one thread per CTA streams each
 // chunk's F image slices, means and inverse variances into shared memory
 // with bulk copies through a 4-stage mbarrier ring.  n_tma_pix = n_pix
 // rounded down to 16 pixels; CTA 0 computes the last < 16 pixels with plain
@@ -202,24 +216,24 @@ __global__ void __launch_bounds__(kGThreads) likelihood_group_kernel(const Likel
     }
     __syncthreads();
 
-    const int64_t n_chunks = (n_tma_pix + kGChunk - 1) / kGChunk;
+    const int64_t n_chunks = (n_tma_pix + GLayout<F>::kChunk - 1) / GLayout<F>::kChunk;
     const int64_t my_chunks =
         (int64_t)blockIdx.x < n_chunks ? (n_chunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     auto stage_img = [&](int s) { return smem + s * GLayout<F>::kStage; };
     auto stage_mean = [&](int s) {
-        return reinterpret_cast<float *>(smem + s * GLayout<F>::kStage + F * kGImgBytes);
+        return reinterpret_cast<float *>(smem + s * GLayout<F>::kStage + F * GLayout<F>::kImgBytes);
     };
     auto stage_hinv = [&](int s) {
-        return reinterpret_cast<float *>(smem + s * GLayout<F>::kStage + F * kGImgBytes + kGBgBytes);
+        return reinterpret_cast<float *>(smem + s * GLayout<F>::kStage + F * GLayout<F>::kImgBytes + GLayout<F>::kBgBytes);
     };
     auto issue = [&](int64_t k) {
         const int s = (int)(k % GLayout<F>::kStages);
-        const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kGChunk;
-        const uint32_t np = (uint32_t)min((int64_t)kGChunk, n_tma_pix - p0);
+        const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * GLayout<F>::kChunk;
+        const uint32_t np = (uint32_t)min((int64_t)GLayout<F>::kChunk, n_tma_pix - p0);
         mbar_arrive_expect_tx(&bars[s], (3u * F + 24u) * np);
 #pragma unroll
         for (int f = 0; f < F; ++f)
-            bulk_g2s(stage_img(s) + f * kGImgBytes, a.img + f * a.img_fstride + 3 * p0, 3u * np, &bars[s]);
+            bulk_g2s(stage_img(s) + f * GLayout<F>::kImgBytes, a.img + f * a.img_fstride + 3 * p0, 3u * np, &bars[s]);
         bulk_g2s(stage_mean(s), a.mean + 3 * p0, 12u * np, &bars[s]);
         bulk_g2s(stage_hinv(s), a.hinv + 3 * p0, 12u * np, &bars[s]);
     };
@@ -229,13 +243,13 @@ __global__ void __launch_bounds__(kGThreads) likelihood_group_kernel(const Likel
     for (int64_t k = 0; k < my_chunks; ++k) {
         const int s = (int)(k % GLayout<F>::kStages);
         mbar_wait_bounded(&bars[s], (uint32_t)((k / GLayout<F>::kStages) & 1), a.status);
-        const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * kGChunk;
-        const int np = (int)min((int64_t)kGChunk, n_tma_pix - p0);
+        const int64_t p0 = ((int64_t)blockIdx.x + k * gridDim.x) * GLayout<F>::kChunk;
+        const int np = (int)min((int64_t)GLayout<F>::kChunk, n_tma_pix - p0);
         const unsigned char *im = stage_img(s);
         const float *mu = stage_mean(s);
         const float *hv = stage_hinv(s);
         for (int q = tid; q < np; q += kGThreads)
-            group_pixel<OutT, F>(a, out, p0 + q, im + 3 * q, kGImgBytes, mu + 3 * q, hv + 3 * q);
+            group_pixel<OutT, F>(a, out, p0 + q, im + 3 * q, GLayout<F>::kImgBytes, mu + 3 * q, hv + 3 * q);
         __syncthreads();   // every thread is done with stage s before it is refilled
         if (tid == 0 && k + GLayout<F>::kStages < my_chunks) issue(k + GLayout<F>::kStages);
     }
@@ -267,7 +281,7 @@ cudaError_t launch_lk_group(const LikelihoodArgs &a, cudaStream_t s, int ctas_pe
     }
     const int per_sm = std::max(1, std::min(ctas_per_sm, max_ctas[dev]));
     const int64_t n_tma_pix = a.n_pix / 16 * 16;
-    const int64_t n_chunks = (n_tma_pix + kGChunk - 1) / kGChunk;
+    const int64_t n_chunks = (n_tma_pix + GLayout<F>::kChunk - 1) / GLayout<F>::kChunk;
     int64_t blocks = std::min<int64_t>(n_chunks, (int64_t)per_sm * group_sm_count());
     if (blocks < 1) blocks = 1;
     kern<<<(int)blocks, kGThreads, smem, s>>>(a, n_tma_pix);
@@ -285,6 +299,7 @@ cudaError_t launch_lk_group_typed(const LikelihoodArgs &a, int frames, cudaStrea
     if (frames == 4) return launch_lk_group<OutT, 4>(a, s, ctas_per_sm);
     if (frames == 8) return launch_lk_group<OutT, 8>(a, s, ctas_per_sm);
     if (frames == 16) return launch_lk_group<OutT, 16>(a, s, ctas_per_sm);
+    if (frames == 32) return launch_lk_group<OutT, 32>(a, s, ctas_per_sm);
     return cudaErrorInvalidValue;
 }
 
@@ -446,6 +461,7 @@ cudaError_t launch_fg_shape(const FuseArgs &a, const FuseShape &sh, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
+// One plane of P frames (records of at most 32 bytes).
 template <typename MapT>
 cudaError_t launch_fg_typed(const FuseArgs &a, const FuseShape &sh, int frames, cudaStream_t s)
 {
@@ -453,18 +469,25 @@ cudaError_t launch_fg_typed(const FuseArgs &a, const FuseShape &sh, int frames, 
     if (frames == 2) return launch_fg_shape<MapT, 2>(a, sh, s);
     if (frames == 4) return launch_fg_shape<MapT, 4>(a, sh, s);
     if (frames == 8) return launch_fg_shape<MapT, 8>(a, sh, s);
-    if (frames == 16) return launch_fg_shape<MapT, 16>(a, sh, s);
+    if constexpr (sizeof(MapT) == 2) {
+        if (frames == 16) return launch_fg_shape<MapT, 16>(a, sh, s);
+    }
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-bool group_size_supported(int frames) { return frames == 2 || frames == 4 || frames == 8 || frames == 16; }
-
-bool group_shape_supported(const FuseShape &s, int frames)
+bool group_size_supported(int frames)
 {
+    return frames == 2 || frames == 4 || frames == 8 || frames == 16 || frames == kMaxGroup;
+}
+
+bool group_shape_supported(const FuseShape &s, int frames, int map_elem)
+{
+    // the fusion kernel holds P x TZ accumulators per thread: at most 64
+    const int P = group_plane_frames(frames, map_elem);
     return group_size_supported(frames) && s.wy == 4 && s.staged == 0 && (s.lx == 8 || s.lx == 16) &&
-           (s.tz == 4 || (s.tz == 8 && frames <= 8) || (s.tz == 16 && frames <= 4));
+           (s.tz == 4 || (s.tz == 8 && P <= 8) || (s.tz == 16 && P <= 4));
 }
 
 cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map_dtype, cudaStream_t s,
@@ -479,9 +502,26 @@ cudaError_t launch_fuse_group(const FuseArgs &a, const FuseShape &shape, int fra
                               cudaStream_t s)
 {
     if (a.n_tiles <= 0) return cudaSuccess;
-    if (map_dtype == PSFS_MAP_F16) return launch_fg_typed<__half>(a, shape, frames, s);
-    if (map_dtype == PSFS_MAP_BF16) return launch_fg_typed<__nv_bfloat16>(a, shape, frames, s);
-    return launch_fg_typed<float>(a, shape, frames, s);
+    const bool half = map_dtype == PSFS_MAP_F16 || map_dtype == PSFS_MAP_BF16;
+    const int P = group_plane_frames(frames, half ? 2 : 4);
+    const int64_t plane_bytes = (int64_t)a.n_cams * a.map_stride * 32;
+    for (int q = 0; q * P < frames; ++q) {
+        // plane q: frames qP to qP + P - 1
+        FuseArgs fq = a;
+        fq.maps = static_cast<const char *>(a.maps) + q * plane_bytes;
+        fq.occ = a.occ + (int64_t)q * P * a.occ_fstride;
+        fq.list = a.list + (int64_t)q * P * a.list_fstride;
+        fq.count = a.count + (int64_t)q * P * a.count_fstride;
+        cudaError_t e;
+        if (map_dtype == PSFS_MAP_F16)
+            e = launch_fg_typed<__half>(fq, shape, P, s);
+        else if (map_dtype == PSFS_MAP_BF16)
+            e = launch_fg_typed<__nv_bfloat16>(fq, shape, P, s);
+        else
+            e = launch_fg_typed<float>(fq, shape, P, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace psfs

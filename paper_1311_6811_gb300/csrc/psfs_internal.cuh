@@ -580,12 +580,18 @@ struct SmoothArgs {
 };
 cudaError_t launch_smooth(const SmoothArgs &a, int n_frames, cudaStream_t s);
 
-// Frame groups of the sequence path (psfs_group.cu): F frames share one pass
-// over the background (likelihood) and one projection per voxel and camera
-// (fusion), with the maps of the group interleaved per pixel.  Each frame's
-// arithmetic is that of the single-frame kernels.
+// Frame groups of the sequence path (psfs_group.cu), F = 2, 4, 8, 16 or 32
+// frames: the F frames share one pass over the background (likelihood), and
+// the fusion projects each voxel once per camera for all frames of a 32-byte
+// pixel record.  The group's maps are planes of such records: a record holds
+// P = min(F, 32 / map_elem) frames (8 for FP32, 16 for 16-bit maps), plane q
+// (frames qP to qP + P - 1) is [n_cams][H][W][P], and the F / P planes follow
+// one another; one fusion launch per plane.  Each frame's arithmetic is that
+// of the single-frame kernels.
+constexpr int kMaxGroup = 32;
+inline int group_plane_frames(int frames, int map_elem) { return frames < 32 / map_elem ? frames : 32 / map_elem; }
 bool group_size_supported(int frames);
-bool group_shape_supported(const FuseShape &s, int frames);
+bool group_shape_supported(const FuseShape &s, int frames, int map_elem);
 cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map_dtype, cudaStream_t s,
                                     int ctas_per_sm);
 cudaError_t launch_fuse_group(const FuseArgs &a, const FuseShape &shape, int frames, int map_dtype,

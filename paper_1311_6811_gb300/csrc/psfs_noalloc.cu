@@ -171,7 +171,7 @@ extern "C" psfs_status psfs_reconstruct_noalloc(const psfs_grid *grid, const psf
     sc.a_zero_const_pos = (pd == 0.0);
     sc.a_zero_const_neg = (pd == 1.0);
     const float c0 = (float)(params->log_fg_density + 1.5 * std::log(M_PI));
-    FuseArgs f;
+    FuseArgs f{};
     std::memset(&f, 0, sizeof(f));
     f.maps = maps;
     f.W = W;

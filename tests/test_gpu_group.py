@@ -1,6 +1,7 @@
 """Frame groups of the sequence path: F frames per likelihood launch (one
 pass over the background) and per fusion launch (one projection per voxel
-and camera, one vector gather for all F frames).  Each frame's occupancy,
+and camera, one vector gather per 32-byte pixel record: 8 FP32 or 16
+16-bit frames, one fusion launch per plane of records).  Each frame's occupancy,
 count and voxel set must be bit-identical to one psfs_reconstruct per frame
 with the same tile shape, for every group size, map type and a frame count
 that leaves trailing frames outside the last group; one group's frame is also
@@ -51,10 +52,24 @@ def _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap):
                                       psfs.voxel_list(l1, c1, rec.capacity).numpy())
 
 
+def _plane_frames(group, dtype):
+    """Frames per 32-byte pixel record of the group maps."""
+    return min(group, 8 if dtype == "f32" else 16)
+
+
+def _shape_ok(group, tz, dtype):
+    p = _plane_frames(group, dtype)
+    return tz == 4 or (tz == 8 and p <= 8) or (tz == 16 and p <= 4)
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("group,tz", [(2, 16), (4, 4), (4, 8), (4, 16), (8, 4), (8, 8), (16, 4)])
+@pytest.mark.parametrize("group,tz", [(2, 16), (4, 4), (4, 8), (4, 16), (8, 4), (8, 8), (16, 4), (16, 8)])
 def test_groups_equal_frame_by_frame(group, tz, dtype):
-    """19 frames: whole groups, then 19 mod F trailing frames one per launch."""
+    """19 frames: whole groups, then the trailing frames in smaller groups
+    (8, 2 and one frame for groups of 16) and single frames.  16 FP32 frames
+    are two planes of 8-frame records."""
+    if not _shape_ok(group, tz, dtype):
+        pytest.skip("tile height not supported for this record size")
     sc = _scene(19)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=dtype)
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
@@ -65,6 +80,78 @@ def test_groups_equal_frame_by_frame(group, tz, dtype):
         assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, group)
         occ, lists, counts = _run_sequence(rec, imgs, cap)
         _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap)
+    rec.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("tz", [4, 8])
+def test_groups_of_32_equal_frame_by_frame(tz, dtype):
+    """45 frames: one group of 32 frames (four planes of 8-frame records for
+    FP32 maps, two of 16 for 16-bit maps), then groups of 8 and 4 and one
+    single frame."""
+    if not _shape_ok(32, tz, dtype):
+        pytest.skip("tile height not supported for this record size")
+    sc = _scene(45)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=dtype)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    cap = rec.n_voxels
+    for lx in (8, 16):
+        psfs.psfs_set_fuse_config(rec.handle, lx, 4, tz, 0, 2, 32)
+        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, 32)
+        occ, lists, counts = _run_sequence(rec, imgs, cap)
+        _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap)
+    rec.close()
+
+
+def test_group_of_32_ragged_grid_and_views():
+    """Grid 37 x 29 x 24 (ragged tiles along x, y and z), 3 cameras of 104 x 80
+    whose views miss part of the grid, 33 frames: one group of 32 and a
+    single frame (the pixel count, 24960, is not a multiple of the
+    likelihood's 256-pixel chunks); also the likelihood grid sizes of the
+    32-frame group."""
+    grid = S.Grid(37, 29, 24, (-0.9, -0.7, 0.1), 0.05)
+    sc = S.make_scene(seed=23, grid_n=48, cube_side=2.0, n_cams=3, width=104, height=80, focal=95.0,
+                      n_frames=33, walking=True)
+    rec = psfs.Reconstructor(grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    for tz, lk in ((4, 1), (8, 2), (8, 3)):
+        psfs.psfs_set_fuse_config(rec.handle, 8, 4, tz, 0, lk, 32)
+        occ, lists, counts = _run_sequence(rec, imgs, rec.n_voxels)
+        _assert_frame_by_frame(rec, imgs, occ, lists, counts, rec.n_voxels)
+    rec.close()
+
+
+def test_group_of_32_matches_oracle_and_capacity():
+    """Frames 0, 17 and 31 of a group of 32 against the FP64 oracle; then a
+    capacity below every frame's count: full counts, `capacity` valid
+    entries per frame, PSFS_ERR_CAPACITY."""
+    sc = _scene(32)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 4, 0, 2, 32)
+    occ, lists, counts = _run_sequence(rec, imgs, rec.n_voxels)
+    for f in (0, 17, 31):
+        got = {"occ": occ[f].cpu().numpy().astype(np.float64), "count": int(counts[f]) & 0xFFFFFFFF,
+               "list": psfs.voxel_list(lists[f], counts[f:f + 1], rec.n_voxels).numpy(), "status": psfs.PSFS_OK}
+        ref = oracle.reconstruct(sc.grid, sc.cams, sc.images[f], sc.mean, sc.var, sc.params)
+        assert ref["list"].size > 500
+        print(compare(got, ref))
+    full = [int(c) for c in counts]
+    cap = min(full) // 2
+    V = rec.n_voxels
+    occ2 = torch.empty((32, V), dtype=torch.float32, device="cuda")
+    counts2 = torch.zeros((32,), dtype=torch.int32, device="cuda")
+    lists_flat = torch.full((32 * cap,), -1, dtype=torch.int32, device="cuda")
+    psfs.psfs_reconstruct_sequence(rec.handle, 32, imgs, occ2, lists_flat, cap, counts2)
+    assert rec.sync() == psfs.PSFS_ERR_CAPACITY
+    assert [int(c) for c in counts2] == full
+    lf = lists_flat.view(32, cap).cpu().numpy()
+    assert (lf >= 0).all() and (lf < V).all()
+    for f in range(32):
+        assert np.isin(lf[f], psfs.voxel_list(lists[f], counts[f:f + 1], V).numpy()).all()
     rec.close()
 
 
@@ -173,9 +260,21 @@ def test_group_config_validation():
     sc = _scene(2)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
     for bad in [(8, 4, 8, 0, 0, 3), (8, 4, 16, 0, 0, 8), (8, 4, 8, 1, 0, 4), (32, 4, 8, 0, 0, 2),
-                (8, 4, 8, 0, 0, -1), (32, 4, 4, 0, 0, 4), (8, 4, 8, 0, 0, 16), (8, 4, 4, 0, 0, 32)]:
+                (8, 4, 8, 0, 0, -1), (32, 4, 4, 0, 0, 4), (8, 4, 16, 0, 0, 16), (8, 4, 16, 0, 0, 32),
+                (32, 4, 4, 0, 0, 32), (8, 4, 8, 1, 0, 32), (8, 4, 4, 0, 0, 64)]:
         with pytest.raises(psfs.PsfsError):
             psfs.psfs_set_fuse_config(rec.handle, *bad)
+    # FP32 records hold 8 frames: 16 and 32 frames with voxels_z 8 are fine
+    for good in [(8, 4, 8, 0, 0, 16), (16, 4, 8, 0, 0, 32)]:
+        psfs.psfs_set_fuse_config(rec.handle, *good)
+    # 16-bit records hold 16 frames: voxels_z 4 only from 16 frames on
+    rec16 = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype="f16")
+    for bad in [(8, 4, 8, 0, 0, 16), (8, 4, 8, 0, 0, 32)]:
+        with pytest.raises(psfs.PsfsError):
+            psfs.psfs_set_fuse_config(rec16.handle, *bad)
+    psfs.psfs_set_fuse_config(rec16.handle, 8, 4, 8, 0, 0, 8)
+    psfs.psfs_set_fuse_config(rec16.handle, 8, 4, 4, 0, 0, 32)
+    rec16.close()
     psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 0, 4)
     assert psfs.psfs_get_fuse_config(rec.handle, full=True)[5] == 4
     # 0 keeps the current group size
@@ -190,7 +289,7 @@ def test_autotune_picks_a_sequence_configuration():
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
     psfs.psfs_autotune(rec.handle, to_dev(sc.images[0]), reps=1)
     cfg = psfs.psfs_get_fuse_config(rec.handle, full=True)
-    assert cfg[5] in (1, 2, 4, 8, 16) and 1 <= cfg[4] <= 4
+    assert cfg[5] in (1, 2, 4, 8, 16, 32) and 1 <= cfg[4] <= 4
     assert rec.sync() == psfs.PSFS_OK
     rec.close()
 
