@@ -176,7 +176,8 @@ psfs_status psfs_reconstruct(psfs_handle *h, const uint8_t *images, float *occup
  * images + f * (n_cams * height * width * 3) and writes
  * occupancy + f * (nx * ny * nz), voxel_lists + f * capacity and counts[f].
  * Frames run in units of frames_per_group frames (psfs_fuse_config; one
- * likelihood and one fusion launch per unit).  The likelihood stage of unit
+ * likelihood launch and one fusion launch per plane of pixel records per
+ * unit).  The likelihood stage of unit
  * u + 1 runs on a second stream concurrently with the fusion stage of unit u
  * (two map buffers), so that the HBM-bound and the gather-bound kernels
  * overlap; the whole sequence is ordered after earlier work on the handle's

@@ -564,7 +564,9 @@ static psfs_status ensure_group_maps(psfs_handle *h, int frames)
 
 // Frames in the next unit of a sequence: the largest group size that fits the
 // remaining frames (group, group / 2, ... down to 2 frames, each with the
-// tile shape), else one frame.
+// tile shape), else one frame.  (Starting with smaller units to shorten the
+// first likelihood pass, which nothing overlaps, measured slower: smaller
+// groups cost more per frame in the likelihood.)
 static int unit_frames(const psfs_handle *h, int group, int remaining)
 {
     for (int g = group; g >= 2; g >>= 1)
@@ -573,10 +575,11 @@ static int unit_frames(const psfs_handle *h, int group, int remaining)
 }
 
 // Enqueues n_frames frames with the given element strides between frames
-// (a stride of 0 repeats the same buffer, which only the autotuner does).
-// Frames go in units: groups of `group` frames (likelihood and fusion of the
-// whole group in one launch each) while whole groups remain, then the largest
-// smaller groups that fit, then single frames.  Unit u's likelihood (stream 0)
+// (a stride of 0 repeats the same buffer, which only the autotuner does when
+// it has no room for copies of its frame).
+// Frames go in units (unit_frames): groups of `group` frames (one likelihood
+// launch and one fusion launch per plane of pixel records) while whole groups
+// remain, then the largest smaller groups that fit, then single frames.  Unit u's likelihood (stream 0)
 // writes map buffer u & 1 while the fusion of unit u - 1 (stream 1) reads the
 // other one.
 static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images, size_t img_stride,
@@ -587,7 +590,7 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
     psfs_status st = seq_setup(h);
     if (st != PSFS_OK) return st;
     if (group > 1 && !group_shape_supported(h->shape, group, (int)h->map_elem)) group = 1;
-    const int first_unit = unit_frames(h, group, n_frames);
+    const int first_unit = unit_frames(h, group, n_frames);   // the largest
     if (first_unit > 1) {
         st = ensure_group_maps(h, first_unit);
         if (st != PSFS_OK) return st;
@@ -1263,18 +1266,36 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
             }
     }
     // second stage: the sequence path, timed on kTuneFrames frames (distinct
-    // outputs, the same images) per repetition: CTAs per SM of the likelihood
-    // grid (1 to 4) with one frame per launch, then frame groups of 2, 4, 8,
-    // 16 and 32 frames with the direct tile shapes that support them
+    // outputs; copies of the one frame at distinct addresses, so that the
+    // images come from HBM as in a real sequence, or the same buffer when
+    // there is no room for the copies) per repetition: CTAs per SM of the
+    // likelihood grid (1 to 4) with one frame per launch, then frame groups of
+    // 2, 4, 8, 16 and 32 frames with the direct tile shapes that support them
+    const size_t frame_bytes = (size_t)h->n_pix * 3;
+    uint8_t *tune_imgs = nullptr;
+    size_t tune_stride = 0;
+    if (st == PSFS_OK && frame_bytes % 16 == 0) {   // frame strides of bulk copies: 16-byte multiples
+        if (cudaMalloc(&tune_imgs, (size_t)kTuneFrames * frame_bytes) == cudaSuccess) {
+            for (int f = 0; f < kTuneFrames && st == PSFS_OK; ++f)
+                if (cudaMemcpyAsync(tune_imgs + (size_t)f * frame_bytes, images, frame_bytes,
+                                    cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+                    st = fail(PSFS_ERR_CUDA, "autotune frame copies");
+            tune_stride = frame_bytes;
+        } else {
+            cudaGetLastError();
+            tune_imgs = nullptr;
+        }
+    }
+    const uint8_t *seq_imgs = tune_imgs ? tune_imgs : images;
     auto time_sequence = [&](int lk, int group, float *ms_out) -> psfs_status {
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(PSFS_ERR_CUDA, "autotune sync");
-        psfs_status s2 = enqueue_sequence(h, kTuneFrames, images, 0, occ, n_vox, list, seq_cap, seq_cap, tcounts,
-                                          1, lk, group);   // warm-up (allocates group buffers)
+        psfs_status s2 = enqueue_sequence(h, kTuneFrames, seq_imgs, tune_stride, occ, n_vox, list, seq_cap,
+                                          seq_cap, tcounts, 1, lk, group);   // warm-up (allocates group buffers)
         if (s2 != PSFS_OK) return s2;
         cudaError_t err = cudaEventRecord(e0, h->stream);
         for (int r = 0; r < reps && s2 == PSFS_OK && err == cudaSuccess; ++r)
-            s2 = enqueue_sequence(h, kTuneFrames, images, 0, occ, n_vox, list, seq_cap, seq_cap, tcounts, 1, lk,
-                                  group);
+            s2 = enqueue_sequence(h, kTuneFrames, seq_imgs, tune_stride, occ, n_vox, list, seq_cap, seq_cap,
+                                  tcounts, 1, lk, group);
         if (s2 != PSFS_OK) return s2;
         if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
         if (err == cudaSuccess) err = cudaEventSynchronize(e1);
@@ -1322,6 +1343,7 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     cudaFree(occ);
     cudaFree(list);
     cudaFree(tcounts);
+    cudaFree(tune_imgs);
     cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t), h->stream);   // the scratch list never overflows
     if (st != PSFS_OK) return st;
     st = replan(h, best_shape);

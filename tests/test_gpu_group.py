@@ -65,12 +65,11 @@ def _shape_ok(group, tz, dtype):
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("group,tz", [(2, 16), (4, 4), (4, 8), (4, 16), (8, 4), (8, 8), (16, 4), (16, 8)])
 def test_groups_equal_frame_by_frame(group, tz, dtype):
-    """19 frames: whole groups, then the trailing frames in smaller groups
-    (8, 2 and one frame for groups of 16) and single frames.  16 FP32 frames
-    are two planes of 8-frame records."""
+    """33 frames: whole groups, then the trailing frames in smaller groups
+    and single frames.  16 FP32 frames are two planes of 8-frame records."""
     if not _shape_ok(group, tz, dtype):
         pytest.skip("tile height not supported for this record size")
-    sc = _scene(19)
+    sc = _scene(33)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=dtype)
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
     imgs = to_dev(sc.images)
@@ -86,12 +85,12 @@ def test_groups_equal_frame_by_frame(group, tz, dtype):
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("tz", [4, 8])
 def test_groups_of_32_equal_frame_by_frame(tz, dtype):
-    """45 frames: one group of 32 frames (four planes of 8-frame records for
-    FP32 maps, two of 16 for 16-bit maps), then groups of 8 and 4 and one
+    """61 frames: one group of 32 frames (four planes of 8-frame records for
+    FP32 maps, two of 16 for 16-bit maps), then groups of 16, 8 and 4 and one
     single frame."""
     if not _shape_ok(32, tz, dtype):
         pytest.skip("tile height not supported for this record size")
-    sc = _scene(45)
+    sc = _scene(61)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=dtype)
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
     imgs = to_dev(sc.images)
@@ -106,13 +105,13 @@ def test_groups_of_32_equal_frame_by_frame(tz, dtype):
 
 def test_group_of_32_ragged_grid_and_views():
     """Grid 37 x 29 x 24 (ragged tiles along x, y and z), 3 cameras of 104 x 80
-    whose views miss part of the grid, 33 frames: one group of 32 and a
-    single frame (the pixel count, 24960, is not a multiple of the
+    whose views miss part of the grid, 57 frames: groups of 32, 16 and 8
+    and a single frame (the pixel count, 24960, is not a multiple of the
     likelihood's 256-pixel chunks); also the likelihood grid sizes of the
     32-frame group."""
     grid = S.Grid(37, 29, 24, (-0.9, -0.7, 0.1), 0.05)
     sc = S.make_scene(seed=23, grid_n=48, cube_side=2.0, n_cams=3, width=104, height=80, focal=95.0,
-                      n_frames=33, walking=True)
+                      n_frames=57, walking=True)
     rec = psfs.Reconstructor(grid, sc.cams, sc.params)
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
     imgs = to_dev(sc.images)
@@ -124,16 +123,18 @@ def test_group_of_32_ragged_grid_and_views():
 
 
 def test_group_of_32_matches_oracle_and_capacity():
-    """Frames 0, 17 and 31 of a group of 32 against the FP64 oracle; then a
-    capacity below every frame's count: full counts, `capacity` valid
-    entries per frame, PSFS_ERR_CAPACITY."""
-    sc = _scene(32)
+    """56 frames (units of 32, 16 and 8): frames 0, 17 and 31 of the group of
+    32 and frame 55 against the FP64 oracle; then a capacity below every
+    frame's count: full counts, `capacity` valid entries per frame,
+    PSFS_ERR_CAPACITY."""
+    n = 56
+    sc = _scene(n)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
     imgs = to_dev(sc.images)
     psfs.psfs_set_fuse_config(rec.handle, 8, 4, 4, 0, 2, 32)
     occ, lists, counts = _run_sequence(rec, imgs, rec.n_voxels)
-    for f in (0, 17, 31):
+    for f in (0, 17, 31, 55):
         got = {"occ": occ[f].cpu().numpy().astype(np.float64), "count": int(counts[f]) & 0xFFFFFFFF,
                "list": psfs.voxel_list(lists[f], counts[f:f + 1], rec.n_voxels).numpy(), "status": psfs.PSFS_OK}
         ref = oracle.reconstruct(sc.grid, sc.cams, sc.images[f], sc.mean, sc.var, sc.params)
@@ -142,15 +143,15 @@ def test_group_of_32_matches_oracle_and_capacity():
     full = [int(c) for c in counts]
     cap = min(full) // 2
     V = rec.n_voxels
-    occ2 = torch.empty((32, V), dtype=torch.float32, device="cuda")
-    counts2 = torch.zeros((32,), dtype=torch.int32, device="cuda")
-    lists_flat = torch.full((32 * cap,), -1, dtype=torch.int32, device="cuda")
-    psfs.psfs_reconstruct_sequence(rec.handle, 32, imgs, occ2, lists_flat, cap, counts2)
+    occ2 = torch.empty((n, V), dtype=torch.float32, device="cuda")
+    counts2 = torch.zeros((n,), dtype=torch.int32, device="cuda")
+    lists_flat = torch.full((n * cap,), -1, dtype=torch.int32, device="cuda")
+    psfs.psfs_reconstruct_sequence(rec.handle, n, imgs, occ2, lists_flat, cap, counts2)
     assert rec.sync() == psfs.PSFS_ERR_CAPACITY
     assert [int(c) for c in counts2] == full
-    lf = lists_flat.view(32, cap).cpu().numpy()
+    lf = lists_flat.view(n, cap).cpu().numpy()
     assert (lf >= 0).all() and (lf < V).all()
-    for f in range(32):
+    for f in range(n):
         assert np.isin(lf[f], psfs.voxel_list(lists[f], counts[f:f + 1], V).numpy()).all()
     rec.close()
 
