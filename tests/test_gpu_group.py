@@ -298,13 +298,13 @@ def test_autotune_picks_a_sequence_configuration():
 @pytest.mark.parametrize("pinned", [True, False])
 def test_sequence_host_equals_device(pinned):
     """psfs_reconstruct_sequence_host (copies in and out overlapping the
-    kernels, two staging slots reused across 5 chunks) gives the device
+    kernels, two staging slots of 16 frames reused across 3 chunks) gives the device
     sequence's occupancy, counts and voxel sets."""
     n = 37
     sc = _scene(n)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
-    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 2, 2)   # groups of 2: chunks of 8 frames
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 2, 2)   # groups of 2
     V, cap = rec.n_voxels, rec.n_voxels // 4
     occ_d, lists_d, counts_d = _run_sequence(rec, to_dev(sc.images), cap)
 
