@@ -36,7 +36,7 @@ constexpr int kSumsPerThread = (kSums + kThreads - 1) / kThreads;   // 3
 __global__ void __launch_bounds__(kThreads) smooth_kernel(const SmoothArgs a, int tiles_z)
 {
     __shared__ float v[2][kPlane];
-    __shared__ float sx[2][kHY][kSX];
+    __shared__ float sx[2][kSums];                // [kHY][kSX] x-sums per buffer
     __shared__ uint32_t s_bal[kSZ][2][8];   // ballot per output plane, row half and warp
     __shared__ uint32_t s_off[2][8];
     __shared__ uint32_t s_base;
@@ -46,13 +46,14 @@ __global__ void __launch_bounds__(kThreads) smooth_kernel(const SmoothArgs a, in
     const int f = blockIdx.z / tiles_z;
     const int x0 = blockIdx.x * kSX, y0 = blockIdx.y * kSY, z0 = (blockIdx.z - f * tiles_z) * kSZ;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const size_t n_vox = (size_t)nx * ny * nz, nxy = (size_t)nx * ny;
+    // per-frame indices fit 32 bits (the handle's voxel count does)
+    const uint32_t nxy = (uint32_t)nx * (uint32_t)ny, n_vox = nxy * (uint32_t)nz;
     const float *prob = a.prob + (size_t)f * n_vox;
     float *out = a.smoothed ? a.smoothed + (size_t)f * n_vox : nullptr;
 
     // this thread's halo elements e = tid + k * 256 of every plane (row e / 34,
     // column e % 34): in-plane offset and in-grid test, the same for all planes
-    size_t off[kPerThread];
+    uint32_t off[kPerThread];
     bool ok[kPerThread];
 #pragma unroll
     for (int k = 0; k < kPerThread; ++k) {
@@ -60,25 +61,34 @@ __global__ void __launch_bounds__(kThreads) smooth_kernel(const SmoothArgs a, in
         const int y = e / kHX, x = e - y * kHX;
         const int ex = x0 - 1 + x, ey = y0 - 1 + y;
         ok[k] = e < kPlane && ex >= 0 && ey >= 0 && ex < nx && ey < ny;
-        off[k] = ok[k] ? (size_t)ex + (size_t)nx * ey : 0;
+        off[k] = ok[k] ? (uint32_t)ex + (uint32_t)nx * (uint32_t)ey : 0u;
+    }
+    // this thread's x-sums e = tid + k * 256 (row e / 32, column e % 32): the
+    // sum's index in sx is e, its first term's index in v is e + 2 (e / 32)
+    int vsrc[kSumsPerThread];
+#pragma unroll
+    for (int k = 0; k < kSumsPerThread; ++k) {
+        const int e = tid + k * kThreads;
+        vsrc[k] = e + 2 * (e >> 5);
     }
     auto load_plane = [&](int gz, float (&r)[kPerThread]) {
         const bool okz = gz >= 0 && gz < nz;
-        const float *pl = prob + (okz ? (size_t)gz * nxy : 0);
+        const uint32_t zoff = okz ? (uint32_t)gz * nxy : 0u;
 #pragma unroll
-        for (int k = 0; k < kPerThread; ++k) r[k] = (okz && ok[k]) ? __ldg(pl + off[k]) : 0.0f;
+        for (int k = 0; k < kPerThread; ++k) r[k] = (okz && ok[k]) ? __ldg(prob + (zoff + off[k])) : 0.0f;
     };
     auto store_plane = [&](int buf, const float (&r)[kPerThread]) {
 #pragma unroll
         for (int k = 0; k < kPerThread; ++k)
-            if (tid + k * kThreads < kPlane) v[buf][tid + k * kThreads] = r[k];
+            if (k * kThreads + kThreads <= kPlane || tid + k * kThreads < kPlane) v[buf][tid + k * kThreads] = r[k];
     };
 
     // the two columns: clipped neighbourhood counts and output offsets
-    int gx = x0 + lx, gy[2] = {y0 + ly, y0 + ly + 8};
+    const int gx = x0 + lx;
+    int gy[2] = {y0 + ly, y0 + ly + 8};
     bool in_xy[2];
     float inv1[2], inv2[2], inv3[2];
-    size_t col[2];
+    uint32_t col[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         in_xy[h] = gx < nx && gy[h] < ny;
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(kThreads) smooth_kernel(const SmoothArgs a, in
         inv1[h] = 1.0f / (float)cxy;
         inv2[h] = 1.0f / (float)(2 * cxy);
         inv3[h] = 1.0f / (float)(3 * cxy);
-        col[h] = (size_t)gx + (size_t)nx * gy[h];
+        col[h] = (uint32_t)gx + (uint32_t)nx * (uint32_t)gy[h];
     }
 
     // prologue: plane z0 - 1 in buffer 0, plane z0 in registers
@@ -98,16 +108,17 @@ __global__ void __launch_bounds__(kThreads) smooth_kernel(const SmoothArgs a, in
 
     float ya[2] = {0.0f, 0.0f}, yb[2] = {0.0f, 0.0f};   // y-sums of planes p - 2, p - 1
     uint32_t warp_count[2] = {0u, 0u};
-#pragma unroll 1
+    // kSZ + 2 = 34 planes: unrolled by two, so that the buffer of each copy
+    // (q & 1) is a compile-time constant
+#pragma unroll 2
     for (int q = 0; q < kSZ + 2; ++q) {
         const int buf = q & 1;
         // x-sums of plane p = z0 - 1 + q (in v[buf]) into sx[buf]
 #pragma unroll
         for (int k = 0; k < kSumsPerThread; ++k) {
-            const int e = tid + k * kThreads;
-            if (e < kSums) {
-                const int y = e >> 5, x = e & 31;
-                sx[buf][y][x] = (v[buf][y * kHX + x] + v[buf][y * kHX + x + 1]) + v[buf][y * kHX + x + 2];
+            if (k * kThreads + kThreads <= kSums || tid + k * kThreads < kSums) {
+                const float *vp = &v[buf][vsrc[k]];
+                sx[buf][tid + k * kThreads] = (vp[0] + vp[1]) + vp[2];
             }
         }
         // plane p + 1 into the other buffer, plane p + 2 in flight
@@ -115,17 +126,17 @@ __global__ void __launch_bounds__(kThreads) smooth_kernel(const SmoothArgs a, in
         if (q + 2 < kSZ + 2) load_plane(z0 + 1 + q, nxt);
         __syncthreads();
         // y-sums of this thread's two columns; z-sums of plane p - 1
+        const int t = q - 2, gz = z0 + t;
+        const int cz = 1 + (gz > 0) + (gz + 1 < nz);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int yy = ly + 8 * h;
-            const float yc = (sx[buf][yy][lx] + sx[buf][yy + 1][lx]) + sx[buf][yy + 2][lx];
+            const float *sp = &sx[buf][tid + 256 * h];
+            const float yc = (sp[0] + sp[kSX]) + sp[2 * kSX];
             if (q >= 2) {
-                const int t = q - 2, gz = z0 + t;
                 const bool valid = in_xy[h] && gz < nz;
                 const float sum = (ya[h] + yb[h]) + yc;
-                const int cz = 1 + (gz > 0) + (gz + 1 < nz);
                 const float sm = sum * (cz == 3 ? inv3[h] : cz == 2 ? inv2[h] : inv1[h]);
-                if (valid && out) __stcs(out + col[h] + (size_t)gz * nxy, sm);
+                if (valid && out) __stcs(out + (col[h] + (uint32_t)gz * nxy), sm);
                 const uint32_t b = __ballot_sync(0xFFFFFFFFu, valid && sm > a.threshold);
                 if (lx == 0) s_bal[t][h][ly] = b;
                 warp_count[h] += __popc(b);
