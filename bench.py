@@ -678,6 +678,17 @@ def run_ours(args):
             dst.copy_(src, non_blocking=True)
             torch.cuda.synchronize(dev)
             link[name] = src.numel() * src.element_size() / (time.perf_counter() - t0) / 1e9
+        # both directions at once on two streams, as the host-buffer path
+        # runs them: their combined rate bounds the end-to-end step
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s_in):
+            d_img_tmp.copy_(h_images, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            h_occ.copy_(occ, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        link["both_gbs"] = (h_images.numel() + occ.numel() * 4) / (time.perf_counter() - t0) / 1e9
         del d_img_tmp
         e2e = {"value": sum_over_ranks(float(F * V * K * e2e_steps), dev) / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": F * n_pix * 3, "d2h_bytes_per_step": int(d2h / e2e_steps),

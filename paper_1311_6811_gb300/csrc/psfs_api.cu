@@ -71,12 +71,12 @@ struct psfs_handle {
     // host-buffer sequence path (first use): two chunk slots of device
     // staging, copies in and out on two streams of their own
     cudaStream_t io_stream[2] = {nullptr, nullptr};   // [0] host to device, [1] device to host
-    cudaEvent_t io_ev_in[2] = {nullptr, nullptr}, io_ev_comp[2] = {nullptr, nullptr};
-    cudaEvent_t io_ev_cnt[2] = {nullptr, nullptr}, io_ev_out[2] = {nullptr, nullptr};
-    uint8_t *io_img[2] = {nullptr, nullptr};
-    float *io_occ[2] = {nullptr, nullptr};
-    uint32_t *io_list[2] = {nullptr, nullptr};
-    uint32_t *io_cnt[2] = {nullptr, nullptr};
+    cudaEvent_t io_ev_in[kIoSlots] = {}, io_ev_comp[kIoSlots] = {};
+    cudaEvent_t io_ev_cnt[kIoSlots] = {}, io_ev_out[kIoSlots] = {};
+    uint8_t *io_img[kIoSlots] = {};
+    float *io_occ[kIoSlots] = {};
+    uint32_t *io_list[kIoSlots] = {};
+    uint32_t *io_cnt[kIoSlots] = {};
     int io_frames = 0;          // frames per slot
     uint32_t io_cap = 0;        // list entries per frame
 
@@ -175,6 +175,8 @@ void free_handle(psfs_handle *h)
     for (int n = 0; n < 2; ++n) {
         if (h->io_stream[n]) cudaStreamSynchronize(h->io_stream[n]);
         if (h->io_stream[n]) cudaStreamDestroy(h->io_stream[n]);
+    }
+    for (int n = 0; n < kIoSlots; ++n) {
         for (cudaEvent_t e : {h->io_ev_in[n], h->io_ev_comp[n], h->io_ev_cnt[n], h->io_ev_out[n]})
             if (e) cudaEventDestroy(e);
         cudaFree(h->io_img[n]);
@@ -687,12 +689,12 @@ psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const ui
                             capacity, counts, 1, h->seq_lk_ctas, h->seq_group);
 }
 
-// Staging of the host-buffer sequence path: two slots of `frames` frames.
+// Staging of the host-buffer sequence path: kIoSlots slots of `frames` frames.
 static psfs_status io_setup(psfs_handle *h, int frames, uint32_t capacity)
 {
     if (!h->io_stream[0]) {
-        for (int n = 0; n < 2; ++n) {
-            PSFS_CK(cudaStreamCreateWithFlags(&h->io_stream[n], cudaStreamNonBlocking));
+        for (int n = 0; n < 2; ++n) PSFS_CK(cudaStreamCreateWithFlags(&h->io_stream[n], cudaStreamNonBlocking));
+        for (int n = 0; n < kIoSlots; ++n) {
             PSFS_CK(cudaEventCreateWithFlags(&h->io_ev_in[n], cudaEventDisableTiming));
             PSFS_CK(cudaEventCreateWithFlags(&h->io_ev_comp[n], cudaEventDisableTiming));
             PSFS_CK(cudaEventCreateWithFlags(&h->io_ev_cnt[n], cudaEventDisableTiming));
@@ -708,7 +710,7 @@ static psfs_status io_setup(psfs_handle *h, int frames, uint32_t capacity)
     capacity = std::max(capacity, h->io_cap);
     h->io_frames = 0;
     h->io_cap = 0;
-    for (int n = 0; n < 2; ++n) {
+    for (int n = 0; n < kIoSlots; ++n) {
         cudaFree(h->io_img[n]);
         cudaFree(h->io_occ[n]);
         cudaFree(h->io_list[n]);
@@ -718,7 +720,7 @@ static psfs_status io_setup(psfs_handle *h, int frames, uint32_t capacity)
         h->io_list[n] = nullptr;
         h->io_cnt[n] = nullptr;
     }
-    for (int n = 0; n < 2; ++n) {
+    for (int n = 0; n < kIoSlots; ++n) {
         if (cudaMalloc(&h->io_img[n], (size_t)frames * h->n_pix * 3) != cudaSuccess ||
             cudaMalloc(&h->io_occ[n], (size_t)frames * n_vox * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&h->io_list[n], (size_t)frames * std::max<uint32_t>(capacity, 1) * sizeof(uint32_t)) !=
@@ -765,7 +767,7 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
     bool overflow = false;
     // list entries of chunk p go out once its counts are on the host
     auto drain_lists = [&](int p) -> psfs_status {
-        const int q = p & 1, f0 = p * chunk, nf = std::min(chunk, n_frames - f0);
+        const int q = p % kIoSlots, f0 = p * chunk, nf = std::min(chunk, n_frames - f0);
         PSFS_CK(cudaEventSynchronize(h->io_ev_cnt[q]));
         for (int f = 0; f < nf; ++f) {
             const uint32_t n = h_counts[f0 + f];
@@ -778,26 +780,28 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
         PSFS_CK(cudaEventRecord(h->io_ev_out[q], cout));
         return PSFS_OK;
     };
-    // slot q = k & 1: the copy in of chunk k waits until chunk k - 2's
+    // slot q = k mod 3: the copy in of chunk k waits until chunk k - 3's
     // kernels have read the images of slot q; chunk k's kernels wait until
-    // chunk k - 2's results have been copied out of slot q.  The list copies
-    // of chunk k - 1 are enqueued (once its counts are on the host) before
+    // chunk k - 3's results have been copied out of slot q.  The list copies
+    // of chunk k - 2 are enqueued (once its counts are on the host, which
+    // they are by then unless the copies out lag two chunks behind) before
     // the copies out of chunk k, so copies in, kernels and copies out of
-    // consecutive chunks overlap.
+    // consecutive chunks overlap and the host rarely waits.
+    constexpr int kLag = kIoSlots - 1;
     for (int k = 0; k < n_chunks && st == PSFS_OK; ++k) {
-        const int q = k & 1, f0 = k * chunk, nf = std::min(chunk, n_frames - f0);
-        if (k >= 2) PSFS_CK(cudaStreamWaitEvent(cin, h->io_ev_comp[q], 0));
+        const int q = k % kIoSlots, f0 = k * chunk, nf = std::min(chunk, n_frames - f0);
+        if (k >= kIoSlots) PSFS_CK(cudaStreamWaitEvent(cin, h->io_ev_comp[q], 0));
         PSFS_CK(cudaMemcpyAsync(h->io_img[q], h_images + (size_t)f0 * frame_bytes, (size_t)nf * frame_bytes,
                                 cudaMemcpyHostToDevice, cin));
         PSFS_CK(cudaEventRecord(h->io_ev_in[q], cin));
         PSFS_CK(cudaStreamWaitEvent(h->stream, h->io_ev_in[q], 0));
-        if (k >= 2) PSFS_CK(cudaStreamWaitEvent(h->stream, h->io_ev_out[q], 0));
+        if (k >= kIoSlots) PSFS_CK(cudaStreamWaitEvent(h->stream, h->io_ev_out[q], 0));
         st = enqueue_sequence(h, nf, h->io_img[q], frame_bytes, h->io_occ[q], n_vox, h->io_list[q], lcap, capacity,
                               h->io_cnt[q], 1, h->seq_lk_ctas, h->seq_group);
         if (st != PSFS_OK) break;
         PSFS_CK(cudaEventRecord(h->io_ev_comp[q], h->stream));
-        if (k >= 1) {
-            st = drain_lists(k - 1);
+        if (k >= kLag) {
+            st = drain_lists(k - kLag);
             if (st != PSFS_OK) break;
         }
         PSFS_CK(cudaStreamWaitEvent(cout, h->io_ev_comp[q], 0));
@@ -808,7 +812,7 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
             PSFS_CK(cudaMemcpyAsync(h_occupancy + (size_t)f0 * n_vox, h->io_occ[q], (size_t)nf * n_vox * sizeof(float),
                                     cudaMemcpyDeviceToHost, cout));
     }
-    if (st == PSFS_OK) st = drain_lists(n_chunks - 1);
+    for (int p = std::max(0, n_chunks - kLag); p < n_chunks && st == PSFS_OK; ++p) st = drain_lists(p);
     PSFS_CK(cudaStreamSynchronize(cout));
     PSFS_CK(cudaStreamSynchronize(h->stream));
     if (st != PSFS_OK) return st;

@@ -298,9 +298,9 @@ def test_autotune_picks_a_sequence_configuration():
 @pytest.mark.parametrize("pinned", [True, False])
 def test_sequence_host_equals_device(pinned):
     """psfs_reconstruct_sequence_host (copies in and out overlapping the
-    kernels, two staging slots of 16 frames reused across 3 chunks) gives the device
-    sequence's occupancy, counts and voxel sets."""
-    n = 37
+    kernels, three staging slots of 16 frames reused across 5 chunks) gives
+    the device sequence's occupancy, counts and voxel sets."""
+    n = 70
     sc = _scene(n)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
