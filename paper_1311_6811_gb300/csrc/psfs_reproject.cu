@@ -8,7 +8,7 @@
 // One thread per (listed voxel, camera): the eight cube corners are projected
 // with the forward kernels' matrices, the pixels whose centres can fall
 // inside that projection (its bounding box, widened against float32
-// rounding) are tested exactly with a slab test of their centre rays in
+// rounding) are tested with a float32 slab test of their centre rays in
 // voxel-index coordinates, and a hit stores 1 (every writer stores the same
 // value, so no atomics are needed).  Run on the surface list, the work is
 // proportional to the body's surface; the silhouette of a solid equals that
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kRpThreads) reproject_kernel(const __grid_cons
         }
         // candidate pixels: centres x + 1/2 within the box, widened by 0.01 px
         // plus a relative float32 margin; the whole image when a corner is not
-        // in front of the camera (the exact test decides)
+        // in front of the camera (the per-pixel test decides)
         int xa = 0, xb = W - 1, ya = 0, yb = H - 1;
         if (!behind) {
             const float du = 0.01f + 1e-5f * fmaxf(fabsf(umin), fabsf(umax));
@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kRpThreads) reproject_kernel(const __grid_cons
         o1[0] = (float)ix - 0.5f - a.inv[c].qc[0];
         o1[1] = (float)jy - 0.5f - a.inv[c].qc[1];
         o1[2] = (float)kz - 0.5f - a.inv[c].qc[2];
+        const float o2[3] = {o1[0] + 1.0f, o1[1] + 1.0f, o1[2] + 1.0f};
         uint8_t *mask = masks + (size_t)c * W * H;
         for (int y = ya; y <= yb; ++y) {
             const float py = (float)y + 0.5f;
@@ -89,8 +90,11 @@ __global__ void __launch_bounds__(kRpThreads) reproject_kernel(const __grid_cons
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
                     const float d = fmaf(mi[3 * ax], px, fmaf(mi[3 * ax + 1], py, mi[3 * ax + 2]));
-                    const float id = 1.0f / d;
-                    const float t1 = o1[ax] * id, t2 = (o1[ax] + 1.0f) * id;
+                    // hardware reciprocal (about 1 ulp; 1/0 = inf as with the
+                    // division): the slab distances move by far less than
+                    // the 2e-3 voxel the silhouettes are checked against
+                    const float id = rcp_approx(d);
+                    const float t1 = o1[ax] * id, t2 = o2[ax] * id;
                     t_in = fmaxf(t_in, fminf(t1, t2));
                     t_out = fminf(t_out, fmaxf(t1, t2));
                 }
