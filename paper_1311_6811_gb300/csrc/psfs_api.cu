@@ -19,6 +19,9 @@
 
 using namespace psfs;
 
+// Device staging slots of the host-buffer sequence path.
+constexpr int kIoSlots = 3;
+
 struct psfs_handle {
     int device = 0;
     cudaStream_t stream = nullptr;

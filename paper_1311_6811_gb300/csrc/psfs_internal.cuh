@@ -589,8 +589,6 @@ cudaError_t launch_smooth(const SmoothArgs &a, int n_frames, cudaStream_t s);
 // one another; one fusion launch per plane.  Each frame's arithmetic is that
 // of the single-frame kernels.
 constexpr int kMaxGroup = 32;
-// Device staging slots of the host-buffer sequence path.
-constexpr int kIoSlots = 3;
 inline int group_plane_frames(int frames, int map_elem) { return frames < 32 / map_elem ? frames : 32 / map_elem; }
 bool group_size_supported(int frames);
 bool group_shape_supported(const FuseShape &s, int frames, int map_elem);
