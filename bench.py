@@ -525,7 +525,7 @@ def run_ours(args):
                 "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": traffic,
                 "alg_bytes_per_launch": stages[dom]["alg_bytes_per_launch"],
                 "units_per_step": units,
-                "note": ("the fusion kernels are bound by L1 gather throughput (ncu: 79 % of L1 peak for "
+                "note": ("the fusion kernels are bound by L1 gather throughput (ncu: 72 % of L1 peak, 66 % of its data pipe, for "
                          "fuse_group_kernel), not by HBM")
                         if dom == "fuse" else None}
     # the whole step against the per-frame algorithmic bytes of the single-frame
