@@ -221,19 +221,20 @@ def ncu_traffic(kernel: str, config: dict):
     try:
         with open(path) as f:
             d = json.load(f)
-        rec = d.get("kernels", {}).get(kernel)
-        if not rec:
+        recs = d.get("kernels", {}).get(kernel)
+        if not recs:
             return None
-        h = hashlib.sha256()
-        for name in rec["sources"]:
-            with open(os.path.join(ROOT, "paper_1311_6811_gb300", "csrc", name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
-        if h.hexdigest()[:16] != rec["sources_sha"]:
-            return None
-        if any(config.get(k_) != v for k_, v in rec.get("config", {}).items()):
-            return None
-        return float(rec["dram_bytes_per_launch"])
+        for rec in (recs if isinstance(recs, list) else [recs]):   # one record per launch configuration
+            if any(config.get(k_) != v for k_, v in rec.get("config", {}).items()):
+                continue
+            h = hashlib.sha256()
+            for name in rec["sources"]:
+                with open(os.path.join(ROOT, "paper_1311_6811_gb300", "csrc", name), "rb") as f:
+                    h.update(name.encode())
+                    h.update(f.read())
+            if h.hexdigest()[:16] == rec["sources_sha"]:
+                return float(rec["dram_bytes_per_launch"])
+        return None
     except (ValueError, KeyError, OSError):
         return None
 
