@@ -179,9 +179,11 @@ __global__ void __launch_bounds__(256) backward_pixel_kernel(const __grid_consta
             for (int q = 0; q < n_s; ++q) {
                 float b0, c0, eb, ec;
                 window(s0 + q, b0, c0, eb, ec);
-                // an integer in [lo, hi] clipped to the grid <=> floor(min(hi, n - 1)) >= max(lo, 0)
-                const bool hit = fminf(floorf(b0 + eb), nb1) >= fmaxf(b0 - eb, 0.0f) &&
-                                 fminf(floorf(c0 + ec), nc1) >= fmaxf(c0 - ec, 0.0f);
+                // an integer in [lo, hi] <=> floor(hi) >= lo.  The grid bounds
+                // are left to the visit below (it clips the lattice range), so
+                // this marks a superset of the slices with in-grid candidates
+                // for fewer instructions per slice
+                const bool hit = floorf(b0 + eb) >= b0 - eb && floorf(c0 + ec) >= c0 - ec;
                 mask |= (uint64_t)hit << q;
             }
             while (mask) {
