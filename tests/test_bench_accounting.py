@@ -1,0 +1,60 @@
+"""Host-side accounting of bench.py (CPU): the unit plan it mirrors from the
+sequence path, and the lookup of committed ncu DRAM traffic, which must
+refuse a record taken on other kernel sources or another launch shape."""
+
+import json
+
+import bench
+
+
+def test_sequence_units_groups_then_smaller_groups():
+    # 100 frames in groups of 32: three whole groups, then 4 frames
+    assert bench.sequence_units(100, 32, 4, 4) == [32, 32, 32, 4]
+    # trailing frames go to the largest smaller groups that fit
+    assert bench.sequence_units(61, 32, 4, 4) == [32, 16, 8, 4, 1]
+    assert bench.sequence_units(19, 8, 4, 4) == [8, 8, 2, 1]
+    # one frame per launch without groups
+    assert bench.sequence_units(3, 1) == [1, 1, 1]
+
+
+def test_sequence_units_respect_the_tile_height():
+    # FP32 records hold 8 frames: 16 and 32 frames run at voxels_z 8
+    assert bench.sequence_units(40, 32, 8, 4) == [32, 8]
+    # 16-bit records hold 16 frames: voxels_z 8 only up to 8 frames
+    assert bench.sequence_units(40, 32, 8, 2) == [8, 8, 8, 8, 8]
+    # voxels_z 16 only for records of at most 4 frames
+    assert bench.sequence_units(10, 8, 16, 4) == [4, 4, 2]
+
+
+def test_units_cover_every_frame():
+    for n in (1, 7, 31, 32, 33, 100, 257):
+        for g in (1, 2, 4, 8, 16, 32):
+            for tz in (4, 8, 16):
+                for elem in (2, 4):
+                    u = bench.sequence_units(n, g, tz, elem)
+                    assert sum(u) == n and all(x >= 1 for x in u)
+
+
+def test_ncu_traffic_matches_sources_and_shape(tmp_path, monkeypatch):
+    rec = json.load(open(bench.os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")))
+    fuse = rec["kernels"]["fuse_group_kernel"]
+    fuse = fuse if isinstance(fuse, list) else [fuse]
+    shapes = {(r["config"]["lanes_x"], r["config"]["voxels_z"]): r["dram_bytes_per_launch"] for r in fuse}
+    for (lx, tz), b in shapes.items():
+        got = bench.ncu_traffic("fuse_group_kernel", {"lanes_x": lx, "voxels_z": tz, "frames_per_group": 8})
+        assert got == float(b)
+    # a launch shape without a record
+    assert bench.ncu_traffic("fuse_group_kernel", {"lanes_x": 32, "voxels_z": 4, "frames_per_group": 8}) is None
+    assert bench.ncu_traffic("no_such_kernel", {}) is None
+
+    # the same record against edited kernel sources: refused
+    csrc = tmp_path / "paper_1311_6811_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in fuse[0]["sources"]:
+        src = bench.os.path.join(bench.ROOT, "paper_1311_6811_gb300", "csrc", name)
+        (csrc / name).write_bytes(open(src, "rb").read() + b"\n// edited\n")
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    lx, tz = next(iter(shapes))
+    assert bench.ncu_traffic("fuse_group_kernel", {"lanes_x": lx, "voxels_z": tz, "frames_per_group": 8}) is None
