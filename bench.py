@@ -727,7 +727,8 @@ def run_ours(args):
                            "autotune_fuse_us": {"x".join(map(str, k)): round(1e3 * v, 2) for k, v in tune_ms.items()},
                            "launch": ("psfs_batch_run (one persistent kernel, CUDA graph)" if batch is not None
                                       else f"psfs_reconstruct_sequence (frame groups of {G}: one background pass "
-                                      "and one projection per group; 2 streams, double-buffered maps)"),
+                                      f"per group, one fusion launch per plane of {min(max(G, 1), 32 // map_elem)} "
+                                      "frames; 2 streams, double-buffered maps)"),
                            "background_l2_resident": not args.no_l2_background},
                 "stages": stages, "roofline": roofline, "roofline_sequence": roofline_sequence,
                 "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
