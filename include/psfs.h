@@ -194,7 +194,7 @@ psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const ui
  * h_occupancy + f * (nx * ny * nz) (h_occupancy may be NULL: no occupancy
  * copy), h_counts[f] and the first min(h_counts[f], capacity) entries of
  * h_lists + f * capacity.  Frames go through three device staging slots of
- * 16 frames each (allocated on first use, grown on demand): the copy in of
+ * 8 frames each (allocated on first use, grown on demand): the copy in of
  * one slot and the copy out of another overlap the kernels of the third.  Pinned
  * host buffers (cudaHostAlloc / cudaHostRegister) let the copies run
  * asynchronously; pageable ones work but serialise them.  Returns after the

@@ -753,12 +753,12 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
     if (n_vox % 4 != 0) return fail(PSFS_ERR_INVALID_ARG, "voxel count not a multiple of 4");
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     DeviceGuard guard(h->device);
-    // chunks of 16 frames per slot: the copies of one chunk overlap the
+    // chunks of 8 frames per slot: the copies of one chunk overlap the
     // kernels of the next.  The host link (about 200 GB/s each way) is slower
     // than the kernels by several times, so short chunks, which shorten the
     // first copy in and the last copy out that nothing overlaps, beat the
     // larger frame groups that longer chunks would allow.
-    const int chunk = std::min<int>(n_frames, 16);
+    const int chunk = std::min<int>(n_frames, 8);
     psfs_status st = io_setup(h, chunk, capacity);
     if (st != PSFS_OK) return st;
     const size_t frame_bytes = (size_t)h->n_pix * 3;

@@ -298,7 +298,7 @@ def test_autotune_picks_a_sequence_configuration():
 @pytest.mark.parametrize("pinned", [True, False])
 def test_sequence_host_equals_device(pinned):
     """psfs_reconstruct_sequence_host (copies in and out overlapping the
-    kernels, three staging slots of 16 frames reused across 5 chunks) gives
+    kernels, three staging slots of 8 frames reused across 9 chunks) gives
     the device sequence's occupancy, counts and voxel sets."""
     n = 70
     sc = _scene(n)
