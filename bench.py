@@ -809,10 +809,29 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg):
         out[f"{dtype}_batched_frames_per_group"] = G
         if dtype != "f32":
             out[f"{dtype}_batched_max_abs_occ_diff_vs_f32"] = float((occ_s - occ_f32[:nseq]).abs().max())
+        # batched forward + adjoint: the sequence forward, the loss gradient
+        # against the FP32 occupancy, psfs_backward_sequence (owner passes of
+        # 8 frames; d_slm per frame, d_mean and d_var summed over the frames)
+        d_occ_s = torch.empty((nseq, V), dtype=torch.float32, device=dev)
+        d_slm_s = torch.empty((nseq, n_pix), dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            for rep in range(2):   # the first pass warms up (allocates the adjoint scratch)
+                if rep == 1:
+                    e[0].record(stream)
+                psfs.psfs_reconstruct_sequence(rec.handle, nseq, d_images[:nseq], occ_s, lst_s, cap_s, cnt_s)
+                torch.sub(occ_s, occ_f32[:nseq], out=d_occ_s)
+                d_occ_s.mul_(2.0)
+                psfs.psfs_backward_sequence(rec.handle, nseq, d_images[:nseq], d_occ_s, d_slm_s, d_mean, d_var)
+            e[3].record(stream)
+        stream.synchronize()
+        assert rec.sync() == psfs.PSFS_OK
+        out[f"{dtype}_batched_forward_backward_us"] = 1e3 * e[0].elapsed_time(e[3]) / nseq
         rec.close()
     out["note"] = ("*_forward_us / *_forward_backward_us: one frame per call (no stream overlap); backward = "
                    "recomputed maps + voxel pass + per-pixel owner pass + chain rule to SLM, mean, var.  "
-                   "*_batched_forward_us: psfs_reconstruct_sequence over 32 frames in frame groups")
+                   "*_batched_forward_us: psfs_reconstruct_sequence over 32 frames in frame groups; "
+                   "*_batched_forward_backward_us: that forward + loss gradient + psfs_backward_sequence "
+                   "(owner passes of 8 frames)")
     return out
 
 

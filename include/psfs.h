@@ -345,6 +345,22 @@ psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *sl
 psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_occ,
                           float *d_slm, float *d_mean, float *d_var);
 
+/* psfs_backward over n_frames frames of this rig, one call: frame f reads
+ * images + f * (n_cams * height * width * 3) and d_occ + f * (nx * ny * nz)
+ * (device, 16-byte aligned), and writes d_slm + f * (n_cams * height * width)
+ * (may be NULL).  d_mean and d_var (may be NULL) receive the sum over the
+ * frames of each frame's gradient, added in frame order (the background model
+ * is shared by the frames).  Frames go through the recomputed forward and the
+ * voxel pass one by one, and through the per-pixel owner pass in groups of up
+ * to 8 frames: one walk of each pixel's ray serves the group.  Each frame's
+ * d_slm is bit-identical to psfs_backward's; d_mean and d_var equal the FP32
+ * sum, in frame order, of psfs_backward's.  Scratch: 8 * nx * ny * nz floats
+ * (first call).  Requirements as psfs_reconstruct_sequence (frame size and
+ * voxel count multiples of 16 and 4).  Errors: INVALID_ARG, NOT_READY, NOMEM,
+ * CUDA. */
+psfs_status psfs_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
+                                   const float *d_occ, float *d_slm, float *d_mean, float *d_var);
+
 /* Adjoint of psfs_fuse_slm: given the SLM maps `slm` of the forward (device
  * float32 [n_cams][height][width]) and d_occ, writes dLoss/dSLM to d_slm
  * (device float32 [n_cams][height][width]).  Recomputes the forward.

@@ -22,6 +22,13 @@ using namespace psfs;
 // Device staging slots of the host-buffer sequence path.
 constexpr int kIoSlots = 3;
 
+namespace psfs {
+// The adjoint's pixel pass over up to kBwFrames frames (psfs_backward.cu).
+constexpr int kBwFrames = 8;
+cudaError_t launch_backward_pixel_group(const BackwardArgs &b, int n_frames, int64_t img_fstride,
+                                        int64_t dl_fstride, bool accumulate, cudaStream_t s);
+}  // namespace psfs
+
 struct psfs_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -95,6 +102,7 @@ struct psfs_handle {
 
     // adjoint scratch (allocated on first use)
     float *dl = nullptr;        // [n_vox] dLoss / dlogodds
+    float *dl_seq = nullptr;    // [kBwFrames][n_vox] the same for psfs_backward_sequence
     float *dg = nullptr;        // [n_pix] dLoss / dg
 };
 
@@ -170,6 +178,7 @@ void free_handle(psfs_handle *h)
     cudaFree(h->st_occ);
     cudaFree(h->st_list);
     cudaFree(h->dl);
+    cudaFree(h->dl_seq);
     cudaFree(h->dg);
     cudaFree(h->maps2);
     cudaFree(h->gmaps[0]);
@@ -1082,6 +1091,8 @@ psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *sl
     return PSFS_OK;
 }
 
+static void fill_backward_args(psfs_handle *h, BackwardArgs &b);
+
 static psfs_status enqueue_backward(psfs_handle *h, const uint8_t *images, const float *slm, const float *d_occ,
                                     float *d_slm, float *d_mean, float *d_var)
 {
@@ -1093,26 +1104,14 @@ static psfs_status enqueue_backward(psfs_handle *h, const uint8_t *images, const
         }
     }
     BackwardArgs b;
-    std::memset(&b, 0, sizeof(b));
-    b.f = h->fuse;
+    fill_backward_args(h, b);
     b.d_occ = d_occ;
     b.dl = h->dl;
     b.img = images;
     b.slm = slm;
-    b.mean = h->bg_mean;
-    b.hinv = h->bg_hinv;
-    b.c0 = h->c0;
-    b.sc = h->sc;
-    const double pd = h->params.p_detect, q = 0.5 * (h->params.p_detect + h->params.p_false_alarm);
-    b.da = (float)(2.0 * pd - 1.0);
-    b.one_minus_pd = (float)(1.0 - pd);
-    b.db = (float)(2.0 * q - 1.0);
-    b.one_minus_q = (float)(1.0 - q);
     b.d_slm = d_slm;
     b.d_mean = d_mean;
     b.d_var = d_var;
-    b.n_pix = h->n_pix;
-    plan_backward_inv(h->grid, h->cams.data(), h->n_cams, h->fuse, b.inv);
     // recompute the forward maps
     if (images) {
         LikelihoodArgs la{};
@@ -1153,6 +1152,77 @@ static psfs_status enqueue_backward(psfs_handle *h, const uint8_t *images, const
     return PSFS_OK;
 }
 
+// The arguments of the adjoint that depend on the handle only.
+static void fill_backward_args(psfs_handle *h, BackwardArgs &b)
+{
+    std::memset(&b, 0, sizeof(b));
+    b.f = h->fuse;
+    b.mean = h->bg_mean;
+    b.hinv = h->bg_hinv;
+    b.c0 = h->c0;
+    b.sc = h->sc;
+    const double pd = h->params.p_detect, q = 0.5 * (h->params.p_detect + h->params.p_false_alarm);
+    b.da = (float)(2.0 * pd - 1.0);
+    b.one_minus_pd = (float)(1.0 - pd);
+    b.db = (float)(2.0 * q - 1.0);
+    b.one_minus_q = (float)(1.0 - q);
+    b.n_pix = h->n_pix;
+    plan_backward_inv(h->grid, h->cams.data(), h->n_cams, h->fuse, b.inv);
+}
+
+// Frames in groups of kBwFrames: per frame the forward maps and the voxel
+// pass (dLoss/dL of frame f into slot f of dl_seq), then one pixel pass for
+// the group.
+static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
+                                             const float *d_occ, float *d_slm, float *d_mean, float *d_var)
+{
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    if (!h->dl_seq) {
+        if (cudaMalloc(&h->dl_seq, (size_t)kBwFrames * n_vox * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "adjoint sequence scratch");
+        }
+    }
+    BackwardArgs b;
+    fill_backward_args(h, b);
+    b.d_mean = d_mean;
+    b.d_var = d_var;
+    const size_t frame_bytes = (size_t)h->n_pix * 3;
+    for (int g0 = 0; g0 < n_frames; g0 += kBwFrames) {
+        const int nf = std::min(kBwFrames, n_frames - g0);
+        for (int f = 0; f < nf; ++f) {
+            LikelihoodArgs la{};
+            la.img = images + (size_t)(g0 + f) * frame_bytes;
+            la.mean = h->bg_mean;
+            la.hinv = h->bg_hinv;
+            la.n_pix = h->n_pix;
+            la.c0 = h->c0;
+            la.sc = h->sc;
+            la.out = h->maps;
+            la.zero_word = nullptr;
+            la.status = h->d_words;
+            {
+                ProfScope ps(h, PSFS_STAGE_LIKELIHOOD);
+                PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, h->stream));
+            }
+            BackwardArgs bv = b;
+            bv.d_occ = d_occ + (size_t)(g0 + f) * n_vox;
+            bv.dl = h->dl_seq + (size_t)f * n_vox;
+            ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL);
+            FuseShape direct = h->shape;
+            direct.staged = 0;
+            PSFS_CK(launch_backward_voxel(bv, direct, h->params.map_dtype, h->stream));
+        }
+        BackwardArgs bp = b;
+        bp.dl = h->dl_seq;
+        bp.img = images + (size_t)g0 * frame_bytes;
+        bp.d_slm = d_slm ? d_slm + (size_t)g0 * h->n_pix : nullptr;
+        ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL);
+        PSFS_CK(launch_backward_pixel_group(bp, nf, (int64_t)frame_bytes, (int64_t)n_vox, g0 > 0, h->stream));
+    }
+    return PSFS_OK;
+}
+
 psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_occ, float *d_slm,
                           float *d_mean, float *d_var)
 {
@@ -1164,6 +1234,24 @@ psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     DeviceGuard guard(h->device);
     return enqueue_backward(h, images, nullptr, d_occ, d_slm, d_mean, d_var);
+}
+
+psfs_status psfs_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images, const float *d_occ,
+                                   float *d_slm, float *d_mean, float *d_var)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (n_frames < 0) return fail(PSFS_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames == 0) return PSFS_OK;
+    if (!images || !aligned(images, 16)) return fail(PSFS_ERR_INVALID_ARG, "images NULL or not 16-byte aligned");
+    if ((h->n_pix * 3) % 16 != 0) return fail(PSFS_ERR_INVALID_ARG, "frame size not a multiple of 16 bytes");
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    if (n_vox % 4 != 0) return fail(PSFS_ERR_INVALID_ARG, "voxel count not a multiple of 4");
+    if (!d_occ || !aligned(d_occ, 16)) return fail(PSFS_ERR_INVALID_ARG, "d_occ NULL or not 16-byte aligned");
+    if ((d_slm && !aligned(d_slm, 16)) || (d_mean && !aligned(d_mean, 16)) || (d_var && !aligned(d_var, 16)))
+        return fail(PSFS_ERR_INVALID_ARG, "gradient buffer not 16-byte aligned");
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    DeviceGuard guard(h->device);
+    return enqueue_backward_sequence(h, n_frames, images, d_occ, d_slm, d_mean, d_var);
 }
 
 psfs_status psfs_backward_slm(psfs_handle *h, const float *slm, const float *d_occ, float *d_slm)

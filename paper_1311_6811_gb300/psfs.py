@@ -116,6 +116,7 @@ def load(build_if_missing: bool = True):
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
             "psfs_backward": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
+            "psfs_backward_sequence": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
             "psfs_backward_slm": (st, [_vp, _vp, _vp, _vp]),
             "psfs_reconstruct_noalloc": (st, [ctypes.POINTER(psfs_grid), ctypes.POINTER(psfs_camera),
                                               ctypes.c_int32, ctypes.POINTER(psfs_params), _vp, _vp, _vp,
@@ -383,6 +384,17 @@ def psfs_backward(h: int, images, d_occ, d_slm=None, d_mean=None, d_var=None):
                                 _dev_ptr(d_slm, "d_slm", torch.float32),
                                 _dev_ptr(d_mean, "d_mean", torch.float32),
                                 _dev_ptr(d_var, "d_var", torch.float32)), "psfs_backward")
+
+
+def psfs_backward_sequence(h: int, n_frames: int, images, d_occ, d_slm=None, d_mean=None, d_var=None):
+    """Adjoint of n_frames frames (see include/psfs.h): d_slm per frame,
+    d_mean and d_var summed over the frames in frame order."""
+    import torch
+    _check(load().psfs_backward_sequence(h, int(n_frames), _dev_ptr(images, "images", torch.uint8),
+                                         _dev_ptr(d_occ, "d_occ", torch.float32),
+                                         _dev_ptr(d_slm, "d_slm", torch.float32),
+                                         _dev_ptr(d_mean, "d_mean", torch.float32),
+                                         _dev_ptr(d_var, "d_var", torch.float32)), "psfs_backward_sequence")
 
 
 PSFS_NOALLOC_MAX_PIXELS = 4 * 1024 * 1024

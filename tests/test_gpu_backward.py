@@ -217,3 +217,47 @@ def test_backward_full_size_128cube():
         fd = float(np.sum((op - om) * (op + om - 2 * t))) / (2 * H_FD)
         assert abs(g[idx] - fd) <= 5e-3 * abs(fd) + 1e-5 * np.abs(g).max(), (idx, g[idx], fd)
     rec.close()
+
+
+def test_backward_sequence_equals_per_frame():
+    """11 frames (pixel passes of 8 and 3 frames): psfs_backward_sequence's
+    d_slm of every frame is bit-identical to psfs_backward's, and its d_mean
+    and d_var are the frame-ordered FP32 sums of psfs_backward's; NULL outputs
+    are skipped."""
+    n = 11
+    sc = S.make_scene(seed=31, grid_n=48, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0,
+                      n_frames=n, walking=True)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    V = rec.n_voxels
+    n_pix = imgs[0].numel() // 3
+    g = torch.Generator().manual_seed(9)
+    d_occ = torch.randn(n, V, generator=g).cuda()
+    d_slm = torch.full((n, n_pix), 7.0, device="cuda")
+    d_mean = torch.full((n_pix * 3,), 7.0, device="cuda")
+    d_var = torch.full((n_pix * 3,), 7.0, device="cuda")
+    psfs.psfs_backward_sequence(rec.handle, n, imgs, d_occ, d_slm, d_mean, d_var)
+    assert rec.sync() == psfs.PSFS_OK
+    sum_m = torch.zeros(n_pix * 3, device="cuda")
+    sum_v = torch.zeros(n_pix * 3, device="cuda")
+    owned = 0
+    for f in range(n):
+        s1 = torch.empty(n_pix, device="cuda")
+        m1 = torch.empty(n_pix * 3, device="cuda")
+        v1 = torch.empty(n_pix * 3, device="cuda")
+        psfs.psfs_backward(rec.handle, imgs[f], d_occ[f], s1, m1, v1)
+        assert rec.sync() == psfs.PSFS_OK
+        np.testing.assert_array_equal(d_slm[f].cpu().numpy(), s1.cpu().numpy(), err_msg=f"frame {f}")
+        owned += int((s1 != 0).sum())
+        sum_m += m1
+        sum_v += v1
+    assert owned > 1000
+    np.testing.assert_array_equal(d_mean.cpu().numpy(), sum_m.cpu().numpy())
+    np.testing.assert_array_equal(d_var.cpu().numpy(), sum_v.cpu().numpy())
+    # only the mean gradient
+    d_mean2 = torch.full((n_pix * 3,), 7.0, device="cuda")
+    psfs.psfs_backward_sequence(rec.handle, n, imgs, d_occ, None, d_mean2, None)
+    assert rec.sync() == psfs.PSFS_OK
+    np.testing.assert_array_equal(d_mean2.cpu().numpy(), sum_m.cpu().numpy())
+    rec.close()
