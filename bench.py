@@ -570,7 +570,7 @@ def run_ours(args):
                            "alg_bytes_per_frame": surf_bytes,
                            "achieved_gbs": surf_bytes / (us_call / F * 1e-6) / 1e9,
                            "hbm_frac": surf_bytes / (us_call / F * 1e-6) / 1e9 / peak_s,
-                           "note": "psfs_surface over the step's 100 lists in one call (memset + 2 kernels); "
+                           "note": "psfs_surface over the step's lists in one call (memset + 2 kernels); "
                                    "latency-bound: ~30 K listed voxels per frame"}}
         # silhouettes of the surface voxels in every camera
         masks = torch.empty((F, K, HEIGHT, WIDTH), dtype=torch.uint8, device=dev)
@@ -592,9 +592,9 @@ def run_ours(args):
                             "alg_bytes_per_frame": rp_bytes,
                             "achieved_gbs": rp_bytes / (us_rp * 1e-6) / 1e9,
                             "hbm_frac": rp_bytes / (us_rp * 1e-6) / 1e9 / peak_s,
-                            "note": "psfs_reproject of the step's 100 surface lists in one call (mask memset + "
-                                    "1 kernel): one thread per (surface voxel, camera), exact centre-ray tests "
-                                    "over the cube's projected box"}
+                            "note": "psfs_reproject of the step's surface lists in one call (mask memset + "
+                                    "1 kernel): one thread per (surface voxel, camera), float32 centre-ray slab "
+                                    "tests over the cube's projected box"}
         # tracker weights of 200 particles (10 cylinders each, around frame 0's
         # body) against frame 0's silhouettes
         caps0 = sc.capsules[0]
@@ -642,7 +642,7 @@ def run_ours(args):
                          "voxels_above_threshold_per_frame": n_sm, "alg_bytes_per_frame": sm_bytes,
                          "achieved_gbs": sm_bytes / (us_sm * 1e-6) / 1e9,
                          "hbm_frac": sm_bytes / (us_sm * 1e-6) / 1e9 / peak_s,
-                         "note": "psfs_smooth over the step's 100 occupancy grids in one call: read the "
+                         "note": "psfs_smooth over the step's occupancy grids in one call: read the "
                                  "probabilities, write the smoothed grid and the list (memset + 1 kernel)"}
         del sm_grid
 
