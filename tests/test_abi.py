@@ -147,5 +147,6 @@ def test_calls_reject_null_handle(lib):
     assert lib.psfs_fuse_slm(None, None, None, None, 0, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_get_likelihood(None, None, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_backward(None, None, None, None, None, None) == psfs.PSFS_ERR_INVALID_ARG
+    assert lib.psfs_backward_sequence(None, 2, None, None, None, None, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_sync(None) == psfs.PSFS_ERR_INVALID_ARG
     lib.psfs_destroy(None)
