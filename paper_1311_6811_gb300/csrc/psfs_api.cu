@@ -78,7 +78,7 @@ struct psfs_handle {
     void *gmaps[2] = {nullptr, nullptr};
     int group_cap = 0;
 
-    // host-buffer sequence path (first use): two chunk slots of device
+    // host-buffer sequence path (first use): kIoSlots chunk slots of device
     // staging, copies in and out on two streams of their own
     cudaStream_t io_stream[2] = {nullptr, nullptr};   // [0] host to device, [1] device to host
     cudaEvent_t io_ev_in[kIoSlots] = {}, io_ev_comp[kIoSlots] = {};
