@@ -484,7 +484,10 @@ void psfs_batch_destroy(psfs_batch *b);
  *                               checked here)
  *   images, occupancy, voxel_list, capacity, count
  *                               as psfs_reconstruct (4-byte aligned device
- *                               pointers; count > capacity signals overflow)
+ *                               pointers).  The call never returns
+ *                               PSFS_ERR_CAPACITY: an overflow shows only as
+ *                               count > capacity once the kernels have run,
+ *                               with the first capacity entries in the list
  *   stream                      cudaStream_t to enqueue on (NULL = legacy)
  * Allocates nothing: its only scratch (the frame's log-ratio maps and a status
  * word) is a fixed __device__ array of PSFS_NOALLOC_MAX_PIXELS floats plus 256
@@ -493,8 +496,9 @@ void psfs_batch_destroy(psfs_batch *b);
  * per device), so make it before any stream capture.  Calls share the array:
  * calls that overlap on the GPU race and give wrong results; order them on
  * one stream.  Same results as psfs_reconstruct.  Enqueues two kernels and
- * returns.  Errors: INVALID_ARG (also n_cams * height * width >
- * PSFS_NOALLOC_MAX_PIXELS), CUDA. */
+ * returns.  Errors (described by psfs_last_error_message): INVALID_ARG (as
+ * psfs_create, including a grid axis longer than 2^24, and also n_cams *
+ * height * width > PSFS_NOALLOC_MAX_PIXELS), CUDA. */
 psfs_status psfs_reconstruct_noalloc(const psfs_grid *grid, const psfs_camera *cams, int32_t n_cams,
                                      const psfs_params *params, const float *mean, const float *var,
                                      const uint8_t *images, float *occupancy, uint32_t *voxel_list,

@@ -106,21 +106,49 @@ struct psfs_handle {
     float *dg = nullptr;        // [n_pix] dLoss / dg
 };
 
+namespace psfs {
+
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
-psfs_status fail(psfs_status s, const char *what)
+psfs_status record_failure(psfs_status s, const char *what)
 {
     g_last_error = what;
     return s;
 }
 
-psfs_status fail_cuda(cudaError_t e, const char *where)
+psfs_status record_cuda_failure(cudaError_t e, const char *where)
 {
     g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
     return PSFS_ERR_CUDA;
 }
+
+const char *last_failure() { return g_last_error.c_str(); }
+
+int device_sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 1;   // grid-stride launches stay correct with any grid size
+    }
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) cudaGetLastError();
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
+}  // namespace psfs
+
+namespace {
+
+psfs_status fail(psfs_status s, const char *what) { return psfs::record_failure(s, what); }
+
+psfs_status fail_cuda(cudaError_t e, const char *where) { return psfs::record_cuda_failure(e, where); }
 
 #define PSFS_CK(call)                                                  \
     do {                                                               \
@@ -348,7 +376,7 @@ const char *psfs_status_string(psfs_status s)
     return "unknown status";
 }
 
-const char *psfs_last_error_message(void) { return g_last_error.c_str(); }
+const char *psfs_last_error_message(void) { return psfs::last_failure(); }
 
 void psfs_params_default(psfs_params *p)
 {

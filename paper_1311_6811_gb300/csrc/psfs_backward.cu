@@ -366,11 +366,8 @@ cudaError_t launch_backward_voxel(const BackwardArgs &b, const FuseShape &shape,
 
 cudaError_t launch_backward_pixel(const BackwardArgs &b, cudaStream_t s)
 {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int64_t blocks = (b.n_pix + 255) / 256;
-    const int64_t cap = 8 * (int64_t)(sms > 0 ? sms : 152);
+    const int64_t cap = 8 * (int64_t)device_sm_count();
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     backward_pixel_kernel<<<(int)blocks, 256, 0, s>>>(b);
@@ -381,11 +378,8 @@ cudaError_t launch_backward_pixel_group(const BackwardArgs &b, int n_frames, int
                                         int64_t dl_fstride, bool accumulate, cudaStream_t s)
 {
     if (n_frames < 1 || n_frames > kBwGroup || !b.img) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int64_t blocks = (b.n_pix + 255) / 256;
-    const int64_t cap = 8 * (int64_t)(sms > 0 ? sms : 152);
+    const int64_t cap = 8 * (int64_t)device_sm_count();
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     backward_pixel_group_kernel<<<(int)blocks, 256, 0, s>>>(b, n_frames, img_fstride, dl_fstride,

@@ -29,20 +29,6 @@ namespace psfs {
 
 namespace {
 
-int group_sm_count()
-{
-    static int cached[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return 152;
-    if (!cached[dev]) {
-        int n = 0;
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = n > 0 ? n : 152;
-    }
-    return cached[dev];
-}
-
 // ---------------------------------------------------------------------------
 // F-wide map vectors
 // ---------------------------------------------------------------------------
@@ -283,7 +269,7 @@ cudaError_t launch_lk_group(const LikelihoodArgs &a, cudaStream_t s, int ctas_pe
     const int per_sm = std::max(1, std::min(ctas_per_sm, max_ctas[dev]));
     const int64_t n_tma_pix = a.n_pix / 16 * 16;
     const int64_t n_chunks = (n_tma_pix + GLayout<F>::kChunk - 1) / GLayout<F>::kChunk;
-    int64_t blocks = std::min<int64_t>(n_chunks, (int64_t)per_sm * group_sm_count());
+    int64_t blocks = std::min<int64_t>(n_chunks, (int64_t)per_sm * device_sm_count());
     if (blocks < 1) blocks = 1;
     kern<<<(int)blocks, kGThreads, smem, s>>>(a, n_tma_pix);
     return cudaGetLastError();

@@ -431,6 +431,16 @@ __device__ __forceinline__ float dlog_ratio_dr(float r, const SensorConsts &c)
     return t1 - div_fast(c.q * u, B);
 }
 
+// The text that psfs_last_error_message returns: every failing entry point
+// records it (per calling thread) and returns the status it is given
+// (psfs_api.cu).
+psfs_status record_failure(psfs_status s, const char *what);
+psfs_status record_cuda_failure(cudaError_t e, const char *where);
+const char *last_failure();
+
+// Streaming multiprocessors of the current device (cached per device).
+int device_sm_count();
+
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------

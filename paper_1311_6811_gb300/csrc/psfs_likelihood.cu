@@ -16,21 +16,6 @@ namespace psfs {
 
 namespace {
 
-int sm_count()
-{
-    static int cached[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return 152;
-    if (!cached[dev]) {
-        int n = 0;
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = n > 0 ? n : 152;
-    }
-    return cached[dev];
-}
-
-
 template <typename OutT>
 __device__ __forceinline__ void store1(OutT *out, int64_t p, float a);
 template <>
@@ -158,7 +143,7 @@ __global__ void __launch_bounds__(256) pack_background_kernel(const float *mean,
 int grid_for(int64_t work, int threads)
 {
     int64_t blocks = (work + threads - 1) / threads;
-    int64_t cap = (int64_t)sm_count() * 8;
+    int64_t cap = (int64_t)device_sm_count() * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     return (int)blocks;
@@ -179,7 +164,7 @@ cudaError_t launch_likelihood_shape(const LikelihoodArgs &a, cudaStream_t s, int
     }
     const int64_t n_tma_pix = a.n_pix / 16 * 16;
     const int64_t n_chunks = (n_tma_pix + kLkChunk - 1) / kLkChunk;
-    int64_t blocks = std::min<int64_t>(n_chunks, ctas_per_sm * (int64_t)sm_count());
+    int64_t blocks = std::min<int64_t>(n_chunks, ctas_per_sm * (int64_t)device_sm_count());
     if (blocks < 1) blocks = 1;
     kern<<<(int)blocks, kThreads, smem, s>>>(a, n_tma_pix);
     return cudaGetLastError();

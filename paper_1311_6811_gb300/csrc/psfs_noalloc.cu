@@ -12,7 +12,10 @@
 //
 // All calls share the array and it keeps the last call's contents: the
 // status word and the caller's count are cleared by the first kernel of each
-// call, and the maps are fully rewritten before they are read.  Calls that
+// call, and the maps are fully rewritten before they are read.  The status
+// word only gives the fusion epilogue somewhere to record an overflow; no
+// call reads it back, so a caller learns of an overflow from count >
+// capacity alone.  Calls that
 // overlap on the GPU (different streams, no ordering between them) race on
 // the maps and give wrong results; order them on one stream.
 //
@@ -128,37 +131,48 @@ extern "C" psfs_status psfs_reconstruct_noalloc(const psfs_grid *grid, const psf
                                                 const uint8_t *images, float *occupancy, uint32_t *voxel_list,
                                                 uint32_t capacity, uint32_t *count, void *stream)
 {
-    // argument checks (as psfs_create and psfs_reconstruct make them)
-    if (!grid || !cams || !params || !mean || !var || !images || !occupancy || !count) return PSFS_ERR_INVALID_ARG;
-    if (capacity > 0 && !voxel_list) return PSFS_ERR_INVALID_ARG;
+    // argument checks: those psfs_create and psfs_reconstruct make, each
+    // recorded for psfs_last_error_message
+    auto bad = [](const char *what) { return record_failure(PSFS_ERR_INVALID_ARG, what); };
+    if (!grid || !cams || !params) return bad("grid, cams or params is NULL");
+    if (!mean || !var || !images || !occupancy || !count) return bad("a device buffer is NULL");
+    if (capacity > 0 && !voxel_list) return bad("voxel_list is NULL with capacity > 0");
     if (!aligned4(mean) || !aligned4(var) || !aligned4(occupancy) || !aligned4(count) ||
         (voxel_list && !aligned4(voxel_list)))
-        return PSFS_ERR_INVALID_ARG;
-    if (n_cams < 1 || n_cams > PSFS_MAX_CAMS) return PSFS_ERR_INVALID_ARG;
-    if (params->map_dtype != PSFS_MAP_F32) return PSFS_ERR_INVALID_ARG;
+        return bad("a float or uint32 device buffer is not 4-byte aligned");
+    if (n_cams < 1 || n_cams > PSFS_MAX_CAMS) return bad("n_cams outside [1, PSFS_MAX_CAMS]");
+    if (params->map_dtype != PSFS_MAP_F32) return bad("params->map_dtype must be PSFS_MAP_F32");
     const double pv[5] = {params->p_detect, params->p_false_alarm, params->prior, params->threshold,
                           params->log_fg_density};
     if (!finite_n(pv, 5) || params->p_detect < 0 || params->p_detect > 1 || params->p_false_alarm < 0 ||
         params->p_false_alarm > 1 || !(params->prior > 0 && params->prior < 1) ||
         !(params->threshold > 0 && params->threshold < 1))
-        return PSFS_ERR_INVALID_ARG;
+        return bad("params out of range (rates in [0, 1], prior and threshold in (0, 1), all finite)");
     const double pd = params->p_detect, q = 0.5 * (params->p_detect + params->p_false_alarm);
-    if (!(q > 0 && q < 1)) return PSFS_ERR_INVALID_ARG;
+    if (!(q > 0 && q < 1)) return bad("(p_detect + p_false_alarm) / 2 must lie in (0, 1)");
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !finite_n(grid->origin, 3) ||
         !std::isfinite(grid->voxel_size) || !(grid->voxel_size > 0))
-        return PSFS_ERR_INVALID_ARG;
-    if ((uint64_t)grid->nx * grid->ny * grid->nz >= (1ull << 32)) return PSFS_ERR_INVALID_ARG;
+        return bad("grid sizes < 1, or origin / voxel_size not finite and positive");
+    // tile coordinates are packed in 21 bits per axis and voxel indices must
+    // stay exact in float32 (the same limit as psfs_create)
+    if (grid->nx > (1 << 24) || grid->ny > (1 << 24) || grid->nz > (1 << 24))
+        return bad("grid axis longer than 2^24");
+    if ((uint64_t)grid->nx * grid->ny * grid->nz >= (1ull << 32)) return bad("grid has 2^32 or more voxels");
     const int W = cams[0].width, H = cams[0].height;
-    if (W < 1 || H < 1 || W > 16384 || H > 16384) return PSFS_ERR_INVALID_ARG;
+    if (W < 1 || H < 1 || W > 16384 || H > 16384) return bad("image size outside [1, 16384]");
     for (int c = 0; c < n_cams; ++c)
         if (cams[c].width != W || cams[c].height != H || !finite_n(cams[c].K, 9) || !finite_n(cams[c].R, 9) ||
             !finite_n(cams[c].t, 3))
-            return PSFS_ERR_INVALID_ARG;
+            return bad("cameras differ in image size or have non-finite K, R or t");
     const int64_t n_pix = (int64_t)n_cams * W * H;
-    if (n_pix > (int64_t)PSFS_NOALLOC_MAX_PIXELS) return PSFS_ERR_INVALID_ARG;   // beyond the fixed scratch
+    if (n_pix > (int64_t)PSFS_NOALLOC_MAX_PIXELS)
+        return bad("n_cams * height * width exceeds PSFS_NOALLOC_MAX_PIXELS (the fixed scratch)");
 
     uint32_t *scratch = nullptr;
-    if (scratch_on_current_device(&scratch) != cudaSuccess) return PSFS_ERR_CUDA;
+    {
+        const cudaError_t e = scratch_on_current_device(&scratch);
+        if (e != cudaSuccess) return record_cuda_failure(e, "device address of the no-alloc scratch");
+    }
     uint32_t *status = scratch;
     float *maps = reinterpret_cast<float *>(scratch + kNoallocHeaderWords);
 
@@ -211,15 +225,18 @@ extern "C" psfs_status psfs_reconstruct_noalloc(const psfs_grid *grid, const psf
     const int nty = (grid->ny + (32 / kNoallocLX) * kNoallocWY - 1) / ((32 / kNoallocLX) * kNoallocWY);
     const int ntz = (grid->nz + kNoallocTZ - 1) / kNoallocTZ;
     const int64_t n_tiles = (int64_t)ntx * nty * ntz;
-    if (n_tiles > 0x7FFFFFFF) return PSFS_ERR_INVALID_ARG;
+    if (n_tiles > 0x7FFFFFFF) return bad("grid has too many tiles for one launch");
     f.n_tiles = (int)n_tiles;
 
     cudaStream_t s = (cudaStream_t)stream;
     int64_t blocks = (n_pix + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    const int64_t cap = 8 * (int64_t)device_sm_count();   // grid-stride loop: any size is correct
+    if (blocks > cap) blocks = cap;
     noalloc_likelihood_kernel<<<(int)blocks, 256, 0, s>>>(images, mean, var, n_pix, c0, sc, maps, count, status);
-    if (cudaGetLastError() != cudaSuccess) return PSFS_ERR_CUDA;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return record_cuda_failure(e, "no-alloc likelihood launch");
     noalloc_fuse_kernel<<<(int)n_tiles, dim3(32, kNoallocWY), 0, s>>>(f, ntx, nty);
-    if (cudaGetLastError() != cudaSuccess) return PSFS_ERR_CUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return record_cuda_failure(e, "no-alloc fusion launch");
     return PSFS_OK;
 }

@@ -403,19 +403,40 @@ PSFS_NOALLOC_MAX_PIXELS = 4 * 1024 * 1024
 def psfs_reconstruct_noalloc(grid, cams, params, mean, var, images, occupancy, voxel_list, capacity: int, count,
                              stream=None):
     """One frame without any device allocation (see include/psfs.h); no handle.
-    `stream` is a torch CUDA stream, an integer cudaStream_t or None (current)."""
+    `stream` is a torch CUDA stream, an integer cudaStream_t or None (current).
+
+    The C entry point has no handle that knows the buffer sizes, so this
+    wrapper checks every tensor against the sizes the grid and the cameras
+    imply, and that each lives on the current CUDA device, before the call:
+    an undersized or misplaced buffer would otherwise be an out-of-bounds
+    device access."""
     import torch
     g = make_grid(grid) if not isinstance(grid, psfs_grid) else grid
     c = make_cameras(cams) if not isinstance(cams, ctypes.Array) else cams
     p = params if isinstance(params, psfs_params) else make_params(params)
+    n_pix = len(c) * int(c[0].width) * int(c[0].height) if len(c) else 0
+    n_vox = int(g.nx) * int(g.ny) * int(g.nz)
+    dev = torch.cuda.current_device()
+    tensors = {"mean": mean, "var": var, "images": images, "occupancy": occupancy, "voxel_list": voxel_list,
+               "count": count}
+    for name, t in tensors.items():
+        if isinstance(t, torch.Tensor) and (not t.is_cuda or t.device.index != dev):
+            raise ValueError(f"{name}: tensor must be on the current CUDA device (cuda:{dev})")
+    if isinstance(voxel_list, torch.Tensor) and voxel_list.numel() < int(capacity):
+        raise ValueError(f"voxel_list: {voxel_list.numel()} entries < capacity {int(capacity)}")
+    if isinstance(voxel_list, torch.Tensor) and voxel_list.element_size() != 4:
+        raise ValueError("voxel_list: expected 4-byte entries")
+    if isinstance(count, torch.Tensor) and (count.numel() < 1 or count.element_size() != 4):
+        raise ValueError("count: expected at least one 4-byte element")
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     elif not isinstance(stream, int):
         stream = stream.cuda_stream
     _check(load().psfs_reconstruct_noalloc(ctypes.byref(g), c, len(c), ctypes.byref(p),
-                                           _dev_ptr(mean, "mean", torch.float32), _dev_ptr(var, "var", torch.float32),
-                                           _dev_ptr(images, "images", torch.uint8),
-                                           _dev_ptr(occupancy, "occupancy", torch.float32),
+                                           _dev_ptr(mean, "mean", torch.float32, n_pix * 3),
+                                           _dev_ptr(var, "var", torch.float32, n_pix * 3),
+                                           _dev_ptr(images, "images", torch.uint8, n_pix * 3),
+                                           _dev_ptr(occupancy, "occupancy", torch.float32, n_vox),
                                            _dev_ptr(voxel_list, "voxel_list"), int(capacity),
                                            _dev_ptr(count, "count"), _vp(stream)), "psfs_reconstruct_noalloc")
 

@@ -150,3 +150,47 @@ def test_calls_reject_null_handle(lib):
     assert lib.psfs_backward_sequence(None, 2, None, None, None, None, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_sync(None) == psfs.PSFS_ERR_INVALID_ARG
     lib.psfs_destroy(None)
+
+
+@pytest.mark.parametrize("case", ["null_grid", "null_images", "null_list", "misaligned_occ", "n_cams0",
+                                  "n_cams_big", "axis_2_24", "f16_maps", "too_many_pixels", "bad_prior"])
+def test_noalloc_rejects_bad_arguments_before_any_cuda_call(lib, case):
+    """psfs_reconstruct_noalloc checks everything on the host first, records a
+    message and returns PSFS_ERR_INVALID_ARG; the fake device addresses below
+    are never dereferenced."""
+    grid, cams, p = _good()
+    n = 2
+    buf = 1 << 20   # a 256-byte aligned stand-in address
+    mean = var = images = occ = lst = cnt = buf
+    cap = 16
+    if case == "null_grid":
+        grid = None
+    elif case == "null_images":
+        images = None
+    elif case == "null_list":
+        lst = None
+    elif case == "misaligned_occ":
+        occ = buf + 2
+    elif case == "n_cams0":
+        n = 0
+    elif case == "n_cams_big":
+        n = psfs.PSFS_MAX_CAMS + 1
+    elif case == "axis_2_24":
+        grid.nx, grid.ny, grid.nz = (1 << 24) + 1, 1, 1
+    elif case == "f16_maps":
+        p.map_dtype = psfs.PSFS_MAP_F16
+    elif case == "too_many_pixels":
+        cams[0].width = cams[1].width = 4096
+        cams[0].height = cams[1].height = 1024   # 2 x 4 Mi pixels > PSFS_NOALLOC_MAX_PIXELS
+    elif case == "bad_prior":
+        p.prior = 0.0
+    psfs.load().psfs_last_error_message()   # any earlier message is replaced below
+    st = lib.psfs_reconstruct_noalloc(ctypes.byref(grid) if grid is not None else None, cams, n,
+                                      ctypes.byref(p), mean, var, images, occ, lst, cap, cnt, None)
+    assert st == psfs.PSFS_ERR_INVALID_ARG
+    msg = psfs.psfs_last_error_message()
+    assert msg, case
+    if case == "axis_2_24":
+        assert "2^24" in msg
+    if case == "too_many_pixels":
+        assert "PSFS_NOALLOC_MAX_PIXELS" in msg

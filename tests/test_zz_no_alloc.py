@@ -62,9 +62,56 @@ def test_noalloc_rejects_frames_beyond_its_scratch():
     cams = S.ring_cameras(rng, 8, 1280, 720, 1200.0, (0.0, 0.0, 1.0))   # 7.4 M pixels > 4 M
     grid = S.Grid(8, 8, 8, (-0.2, -0.2, 0.8), 0.05)
     small = torch.zeros(16, dtype=torch.float32, device="cuda")
+    # raw addresses skip the binding's size checks, so that the library's own
+    # limit check is what rejects the call (before any device access)
     with pytest.raises(psfs.PsfsError) as e:
+        psfs.psfs_reconstruct_noalloc(grid, cams, S.Params(), small.data_ptr(), small.data_ptr(),
+                                      torch.zeros(16, dtype=torch.uint8, device="cuda").data_ptr(),
+                                      small.data_ptr(), torch.zeros(16, dtype=torch.int32, device="cuda").data_ptr(),
+                                      16, torch.zeros(1, dtype=torch.int32, device="cuda").data_ptr())
+    assert e.value.status == psfs.PSFS_ERR_INVALID_ARG
+    assert "PSFS_NOALLOC_MAX_PIXELS" in psfs.psfs_last_error_message()
+    # through tensors, the binding refuses the undersized buffers itself
+    with pytest.raises(ValueError):
         psfs.psfs_reconstruct_noalloc(grid, cams, S.Params(), small, small,
                                       torch.zeros(16, dtype=torch.uint8, device="cuda"), small,
                                       torch.zeros(16, dtype=torch.int32, device="cuda"), 16,
                                       torch.zeros(1, dtype=torch.int32, device="cuda"))
-    assert e.value.status == psfs.PSFS_ERR_INVALID_ARG
+
+
+def test_noalloc_overflow_side_stream_and_oracle():
+    """A list smaller than the occupied set: count holds the true count and
+    the list the first `capacity` entries, all of them occupied voxels.  The
+    call is made on a side stream, and the full-capacity result is compared
+    with the FP64 oracle at the parity tolerance."""
+    import oracle
+    from tests.gpu_helpers import compare
+
+    sc = S.make_scene(seed=32, grid_n=40, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0)
+    mean, var, img = to_dev(sc.mean), to_dev(sc.var), to_dev(sc.images)
+    V = sc.grid.n_voxels
+    occ = torch.empty(V, dtype=torch.float32, device="cuda")
+    lst = torch.empty(V, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        psfs.psfs_reconstruct_noalloc(sc.grid, sc.cams, sc.params, mean, var, img, occ, lst, V, cnt, stream=side)
+    side.synchronize()
+    full = int(cnt.item())
+    got = {"occ": occ.cpu().numpy().astype(np.float64), "count": full,
+           "list": psfs.voxel_list(lst, cnt, V).numpy(), "status": psfs.PSFS_OK}
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    rep = compare(got, ref)
+    assert full > 8, rep
+    full_set = set(got["list"].tolist())
+
+    cap = full // 3
+    small = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(side):
+        psfs.psfs_reconstruct_noalloc(sc.grid, sc.cams, sc.params, mean, var, img, occ, small, cap, cnt,
+                                      stream=side)
+    side.synchronize()
+    assert int(cnt.item()) == full   # the true count, beyond the capacity
+    head = small.cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+    assert len(set(head.tolist())) == cap and set(head.tolist()) <= full_set
