@@ -36,9 +36,27 @@ def test_units_cover_every_frame():
 
 
 def test_ncu_traffic_matches_sources_and_shape(tmp_path, monkeypatch):
+    """A traffic record is used only for the launch shape it was taken on and
+    only while the kernel sources hash to the recorded digest."""
+    import hashlib
     rec = json.load(open(bench.os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")))
     fuse = rec["kernels"]["fuse_group_kernel"]
     fuse = fuse if isinstance(fuse, list) else [fuse]
+    names = fuse[0]["sources"]
+    csrc = tmp_path / "paper_1311_6811_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    h = hashlib.sha256()
+    for name in names:
+        data = b"// kernel source " + name.encode() + b"\n"
+        (csrc / name).write_bytes(data)
+        h.update(name.encode())
+        h.update(data)
+    digest = h.hexdigest()[:16]
+    for r in fuse:
+        r["sources"], r["sources_sha"] = names, digest
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     shapes = {(r["config"]["lanes_x"], r["config"]["voxels_z"]): r["dram_bytes_per_launch"] for r in fuse}
     for (lx, tz), b in shapes.items():
         got = bench.ncu_traffic("fuse_group_kernel", {"lanes_x": lx, "voxels_z": tz, "frames_per_group": 8})
@@ -46,15 +64,7 @@ def test_ncu_traffic_matches_sources_and_shape(tmp_path, monkeypatch):
     # a launch shape without a record
     assert bench.ncu_traffic("fuse_group_kernel", {"lanes_x": 32, "voxels_z": 4, "frames_per_group": 8}) is None
     assert bench.ncu_traffic("no_such_kernel", {}) is None
-
     # the same record against edited kernel sources: refused
-    csrc = tmp_path / "paper_1311_6811_gb300" / "csrc"
-    csrc.mkdir(parents=True)
-    for name in fuse[0]["sources"]:
-        src = bench.os.path.join(bench.ROOT, "paper_1311_6811_gb300", "csrc", name)
-        (csrc / name).write_bytes(open(src, "rb").read() + b"\n// edited\n")
-    (tmp_path / "profiles").mkdir()
-    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(rec))
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (csrc / names[0]).write_bytes((csrc / names[0]).read_bytes() + b"// edited\n")
     lx, tz = next(iter(shapes))
     assert bench.ncu_traffic("fuse_group_kernel", {"lanes_x": lx, "voxels_z": tz, "frames_per_group": 8}) is None
