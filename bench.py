@@ -240,7 +240,15 @@ def ncu_traffic(kernel: str, config: dict):
 
 
 def make_scene(args):
+    """This rank's frames: with N ranks the sequence has N x `--frames` frames
+    and rank r renders frames r, r + N, ... of it (round-robin partition;
+    per-rank work stays fixed as N grows)."""
     from synth import scene as S
+    from paper_1311_6811_gb300 import replicas
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        return S.scene_128cube_8cam(seed=args.seed, n_frames=args.frames * ws, workers=args.workers,
+                                    frame_ids=replicas.rank_frames(args.frames * ws, rank, ws))
     return S.scene_128cube_8cam(seed=args.seed, n_frames=args.frames, workers=args.workers)
 
 
@@ -275,6 +283,51 @@ def _oracle_worker_frame(f):
     return int(out["list"].size)
 
 
+TIE_EPS = 1e-4   # |L_FP64 - logit(threshold)| below this: a near-threshold tie (FP32 summation bound)
+
+
+def _oracle_worker_compare(job):
+    """Reconstructs one frame with the FP64 oracle and compares each GPU
+    variant's occupancy and voxel list of that frame with it: occupancy error
+    outside the boundary bucket (a voxel whose FP64 projection lies within
+    1e-3 px of a pixel edge in some camera), and the occupied-set difference,
+    split into boundary, tie and unexplained voxels."""
+    pos, variants = job
+    p = _W["params"]
+    ref = _W["oracle"].reconstruct(_W["grid"], _W["cams"], _W["images"][pos], _W["mean"], _W["var"], p)
+    tau = float(getattr(p, "threshold", 0.5))
+    keep = ~ref["boundary"]
+    tie = np.abs(ref["logodds"] - math.log(tau / (1.0 - tau))) < TIE_EPS
+    out = {}
+    for name, (occ, lst, count) in variants.items():
+        d = np.abs(occ.astype(np.float64) - ref["occ"])
+        got = np.zeros(ref["occ"].size, bool)
+        got[lst.astype(np.int64) & 0xFFFFFFFF] = True
+        diff = np.flatnonzero(got != ref["occupied"])
+        out[name] = {"max_abs": float(d[keep].max()) if keep.any() else 0.0,
+                     "mean_abs": float(d[keep].mean()) if keep.any() else 0.0,
+                     "boundary_voxels": int(ref["boundary"].sum()), "tie_voxels": int(tie.sum()),
+                     "set_diff": int(diff.size),
+                     "set_diff_boundary": int(ref["boundary"][diff].sum()),
+                     "set_diff_unexplained": int((~(ref["boundary"] | tie))[diff].sum()),
+                     "count": int(count), "count_fp64": int(ref["list"].size)}
+    return out
+
+
+def summarize_errors(per_frame):
+    """Max / mean / sums over the compared frames of one variant."""
+    if not per_frame:
+        return None
+    return {"frames": sorted(per_frame),
+            "max_abs": max(r["max_abs"] for r in per_frame.values()),
+            "mean_abs": float(np.mean([r["mean_abs"] for r in per_frame.values()])),
+            "boundary_voxels": sum(r["boundary_voxels"] for r in per_frame.values()),
+            "tie_voxels": sum(r["tie_voxels"] for r in per_frame.values()),
+            "set_diff": sum(r["set_diff"] for r in per_frame.values()),
+            "set_diff_unexplained": sum(r["set_diff_unexplained"] for r in per_frame.values()),
+            "count_diff_max": max(abs(r["count"] - r["count_fp64"]) for r in per_frame.values())}
+
+
 class OraclePool:
     def __init__(self, sc, images, n_workers):
         import multiprocessing as mp
@@ -296,6 +349,10 @@ class OraclePool:
     def run(self, frames):
         return self.pool.map(_oracle_worker_frame, list(frames), chunksize=1)
 
+    def compare(self, jobs):
+        """jobs: [(frame position in the pool's images, {variant: (occ, list, count)})]."""
+        return self.pool.map(_oracle_worker_compare, list(jobs), chunksize=1)
+
     def close(self):
         self.pool.close()
         self.pool.join()
@@ -304,14 +361,18 @@ class OraclePool:
             shm.unlink()
 
 
-def cpu_baseline(sc, n_frames: int):
+def cpu_baseline(sc, n_frames: int, gpu_outputs=None):
     """The FP64 oracle as it stands: whole frames in parallel on every host
-    core (frames are independent), and single-threaded for reference."""
+    core (frames are independent), and single-threaded for reference.
+
+    gpu_outputs: {frame: {variant: (occ, list, count)}} of the timed GPU
+    outputs; the same pool then reconstructs those frames again (outside the
+    timing) and compares, giving the error against FP64 per variant."""
     import oracle
     oracle.build()
     v = sc.grid.n_voxels * sc.n_cams
-    images = sc.images if sc.images.ndim == 5 else sc.images[None]
-    images = images[:max(1, n_frames)]
+    all_images = sc.images if sc.images.ndim == 5 else sc.images[None]
+    images = all_images[:max(1, n_frames)]
     n1 = min(2, len(images))
     t0 = time.perf_counter()
     for f in range(n1):
@@ -320,32 +381,52 @@ def cpu_baseline(sc, n_frames: int):
     single = {"value": n1 * v / dt1 / 1e9, "unit": UNIT, "cores": 1, "sample": f"{n1} frames, 1 thread, {dt1:.1f} s"}
     cores = host_cores()
     nf = len(images)
-    pool = OraclePool(sc, images[:nf], cores)
+    # frames to compare that lie beyond the timed sample go after it
+    extra = sorted(f for f in (gpu_outputs or {}) if f >= nf)
+    pos = {f: f for f in range(nf)}
+    pos.update({f: nf + i for i, f in enumerate(extra)})
+    pool_images = np.concatenate([images, all_images[extra]]) if extra else images
+    pool = OraclePool(sc, pool_images, cores)
+    errors = None
     try:
         pool.run(range(min(cores, nf)))   # warm-up: workers started and the oracle loaded
         t0 = time.perf_counter()
         pool.run(range(nf))
         dt = time.perf_counter() - t0
+        if gpu_outputs:
+            frames = sorted(gpu_outputs)
+            res = pool.compare([(pos[f], gpu_outputs[f]) for f in frames])
+            per_variant = {}
+            for f, r in zip(frames, res):
+                for name, rep in r.items():
+                    per_variant.setdefault(name, {})[f] = rep
+            errors = {name: summarize_errors(pf) for name, pf in per_variant.items()}
     finally:
         pool.close()
     return {"value": nf * v / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{nf} frames of the sequence, FP64 C oracle, one frame per process on {cores} host cores, "
                       f"{dt:.1f} s",
-            "single_thread": single}
+            "single_thread": single}, errors
 
 
 # --------------------------------------------------------------------------- #
 # reference arm: the oracle on the host cores
 # --------------------------------------------------------------------------- #
-def run_reference(args):
+def run_reference(args, scene_maker=None, cores=None):
+    """The reference arm: the FP64 oracle on the host cores, rank 0 only
+    (other ranks return 0 without work).  `scene_maker(n_frames)` and `cores`
+    replace the 128^3 x 8 workload and the core count (tests)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     from synth import scene as S
-    cores = host_cores()
+    cores = cores or host_cores()
     # each step: one frame per host core, all in parallel (independent frames)
     n_frames = max(1, min(cores, args.frames))
-    sc = S.scene_128cube_8cam(seed=args.seed, n_frames=n_frames, workers=args.workers)
+    if scene_maker is None:
+        sc = S.scene_128cube_8cam(seed=args.seed, n_frames=n_frames, workers=args.workers)
+    else:
+        sc = scene_maker(n_frames)
     imgs = sc.images if sc.images.ndim == 5 else sc.images[None]
     v = sc.grid.n_voxels * sc.n_cams
     pool = OraclePool(sc, imgs, cores)
@@ -468,6 +549,23 @@ def run_ours(args):
     st = psfs.psfs_sync(h)
     if st != psfs.PSFS_OK:
         raise RuntimeError(f"timed frame failed: {psfs.psfs_status_string(st)}")
+    # the timed outputs of a few frames (first group, a middle group, the
+    # trailing unit), kept on the host for the comparison with the FP64 oracle
+    err_frames = sorted({f for f in (0, 17, 33, 66, F - 1) if 0 <= f < F})
+    gpu_outputs = {f: {"f32" if args.map_dtype == "f32" else args.map_dtype: host_frame(occ, lists, counts, f, cap)}
+                   for f in err_frames}
+    # with N ranks: the per-frame counts and lists of the whole sequence,
+    # gathered back into frame order (after the timed region; frames need no
+    # exchange while they are reconstructed)
+    gathered = None
+    if ws > 1:
+        from paper_1311_6811_gb300 import replicas
+        n_glob = F * ws
+        width = int(min(cap, int(counts.max().item()) & 0xFFFFFFFF)) if F else 0
+        g_counts, g_lists = replicas.gather_frames(counts, lists[:, :max(width, 1)].contiguous(), n_glob, rank, ws)
+        gathered = {"frames": n_glob, "partition": "round-robin (rank r: frames r, r + N, ...)",
+                    "occupied_per_frame": float(np.mean(g_counts)),
+                    "lists_complete": all(l.numel() == min(c, cap) for c, l in zip(g_counts, g_lists))}
     ms = max_over_ranks(ms_local, dev)
     total_evals = sum_over_ranks(float(F * V * K * args.steps), dev)
     value = total_evals / (ms * 1e-3) / 1e9
@@ -700,11 +798,22 @@ def run_ours(args):
 
     forms = None
     if not args.no_forms:
-        forms = time_forms(args, sc, d_images, occ, dev, psfs, fuse_cfg)
+        forms = time_forms(args, sc, d_images, occ, dev, psfs, fuse_cfg, gpu_outputs)
 
     cpu = None
+    err_vs_fp64 = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline(sc, min(max(args.cpu_sample_frames, 2 * host_cores()), F))
+        cpu, err = cpu_baseline(sc, min(max(args.cpu_sample_frames, 2 * host_cores()), F), gpu_outputs)
+        if err:
+            headline = "f32" if args.map_dtype == "f32" else args.map_dtype
+            err_vs_fp64 = dict(err.get(headline) or {})
+            err_vs_fp64["what"] = ("timed outputs of the sampled frames against the FP64 oracle: max / mean "
+                                   "|occupancy - FP64| outside the boundary bucket (FP64 projection within 1e-3 px "
+                                   "of a pixel edge), occupied-set differences (unexplained = outside the boundary "
+                                   f"and |L - logit tau| < {TIE_EPS} tie buckets)")
+            for name, rep in err.items():
+                if name != headline and forms is not None:
+                    forms[f"{name}_batched_err_vs_fp64"] = rep
 
     if batch is not None:
         psfs.psfs_batch_destroy(batch)
@@ -720,6 +829,7 @@ def run_ours(args):
                            "occupied_voxels_per_frame": mean_count,
                            "l2": f"inputs larger than L2: {F * n_pix * 3 / 1e6:.0f} MB of images per step",
                            "parallelism": f"replicas x{ws} (frames independent)",
+                           "sequence_across_ranks": gathered,
                            "fuse_tile": {"lanes_x": fuse_cfg[0], "warps": fuse_cfg[1], "voxels_z": fuse_cfg[2],
                                          "staged": fuse_cfg[3]},
                            "likelihood_ctas_per_sm": fuse_cfg[4],
@@ -730,6 +840,7 @@ def run_ours(args):
                                       f"per group, one fusion launch per plane of {min(max(G, 1), 32 // map_elem)} "
                                       "frames; 2 streams, double-buffered maps)"),
                            "background_l2_resident": not args.no_l2_background},
+                "err_vs_fp64": err_vs_fp64,
                 "stages": stages, "roofline": roofline, "roofline_sequence": roofline_sequence,
                 "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
                 "next": nxt,
@@ -738,7 +849,13 @@ def run_ours(args):
     return 0
 
 
-def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg):
+def host_frame(occ, lists, counts, f, cap):
+    """(occupancy, voxel list, count) of frame f, copied to the host."""
+    n = int(counts[f].item()) & 0xFFFFFFFF
+    return (occ[f].cpu().numpy(), lists[f, :min(n, cap)].cpu().numpy(), n)
+
+
+def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=None):
     """Per-frame device time of the plain FP32 forward, and of forward +
     adjoint with FP32 and with FP16 maps (the loss is sum (occ - target)^2 with
     the previous frame's FP32 occupancy as target), CUDA events on the
@@ -809,6 +926,11 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg):
         out[f"{dtype}_batched_frames_per_group"] = G
         if dtype != "f32":
             out[f"{dtype}_batched_max_abs_occ_diff_vs_f32"] = float((occ_s - occ_f32[:nseq]).abs().max())
+            if gpu_outputs is not None:
+                # frames of the batched 16-bit forward, compared with FP64 by the CPU leg
+                for f in sorted(gpu_outputs):
+                    if f < nseq and dtype not in gpu_outputs[f]:
+                        gpu_outputs[f][dtype] = host_frame(occ_s, lst_s, cnt_s, f, cap_s)
         # batched forward + adjoint: the sequence forward, the loss gradient
         # against the FP32 occupancy, psfs_backward_sequence (owner passes of
         # 8 frames; d_slm per frame, d_mean and d_var summed over the frames)

@@ -331,6 +331,14 @@ psfs_status psfs_fuse_slm(psfs_handle *h, const float *slm, float *occupancy,
  * Errors: INVALID_ARG, NOT_READY, CUDA. */
 psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *slm_out);
 
+/* The per-pixel log ratios g = log(a(s) / b(s)) of Eq. 5-9 exactly as the
+ * reconstruction stores them for the frame `images`: [n_cams][height][width]
+ * elements of the handle's map_dtype (float32, IEEE half or bfloat16) written
+ * to device `map_out` (16-byte aligned).  For inspection and tests (the
+ * fusion of Eq. 3-4 sums these stored values).
+ * Errors: INVALID_ARG, NOT_READY, CUDA. */
+psfs_status psfs_get_log_ratio(psfs_handle *h, const uint8_t *images, void *map_out);
+
 /* Adjoint of psfs_reconstruct (the paper runs the forward only; this is the
  * gradient of a loss on the posterior of Eq. 3-4).  Given d_occ = dLoss/d
  * occupancy (device float32 [nz][ny][nx]) for the frame `images`, recomputes
@@ -466,6 +474,18 @@ psfs_status psfs_batch_set_config(psfs_batch *b, const psfs_fuse_config *cfg);
  * tile shapes (candidate order lanes_x 8, 16, 32 x voxels_z 8, 16; times in
  * candidate_ms[6] if not NULL), keeps the fastest. */
 psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *best, float *candidate_ms);
+
+/* Failure detection of the batched launch.  A fusion item waits for every
+ * likelihood chunk of its frame (items of other CTAs, counted on the device);
+ * the wait is bounded: after `limit_ns` (default 1 s) the item records a
+ * timeout, which psfs_batch_sync returns as PSFS_ERR_TIMEOUT, and once one
+ * wait has run out every later wait of the launch gives up at once.  This
+ * sets that limit (1 us to 10 s) and, for tests of the timeout path only,
+ * `hold_frame`: a frame whose items then wait for one chunk more than the
+ * frame has, so that their wait must run out (-1: none; the results of a
+ * launch with a held frame are invalid).  Re-plans and re-captures the graph.
+ * Errors: INVALID_ARG, CUDA, NOMEM. */
+psfs_status psfs_batch_set_wait_limit(psfs_batch *b, uint64_t limit_ns, int32_t hold_frame);
 
 void psfs_batch_destroy(psfs_batch *b);
 

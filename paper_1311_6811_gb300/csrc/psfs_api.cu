@@ -1119,6 +1119,27 @@ psfs_status psfs_get_likelihood(psfs_handle *h, const uint8_t *images, float *sl
     return PSFS_OK;
 }
 
+psfs_status psfs_get_log_ratio(psfs_handle *h, const uint8_t *images, void *map_out)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (!images || !aligned(images, 16)) return fail(PSFS_ERR_INVALID_ARG, "images NULL or not 16-byte aligned");
+    if (!map_out || !aligned(map_out, 16)) return fail(PSFS_ERR_INVALID_ARG, "map_out NULL or not 16-byte aligned");
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    DeviceGuard guard(h->device);
+    LikelihoodArgs la{};
+    la.img = images;
+    la.mean = h->bg_mean;
+    la.hinv = h->bg_hinv;
+    la.n_pix = h->n_pix;
+    la.c0 = h->c0;
+    la.sc = h->sc;
+    la.out = map_out;   // the kernel psfs_reconstruct runs, into the caller's buffer
+    la.zero_word = nullptr;
+    la.status = h->d_words;
+    PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, h->stream));
+    return PSFS_OK;
+}
+
 static void fill_backward_args(psfs_handle *h, BackwardArgs &b);
 
 static psfs_status enqueue_backward(psfs_handle *h, const uint8_t *images, const float *slm, const float *d_occ,
@@ -1560,6 +1581,8 @@ struct psfs_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int blocks = 0;
+    uint64_t wait_ns = kWaitNs;   // limit of the fusion tiles' waits
+    int hold_frame = -1;          // test hook: this frame's tiles wait for one chunk too many
 };
 
 namespace {
@@ -1641,6 +1664,7 @@ psfs_status batch_build(psfs_batch *b, const FuseShape &shape)
         bf.hinv = h->bg_hinv;
         bf.n_pix = h->n_pix;
         bf.n_chunks = (uint32_t)((h->n_pix + kBatchChunk - 1) / kBatchChunk);
+        bf.wait_chunks = bf.n_chunks + (f == b->hold_frame ? 1u : 0u);
         bf.c0 = h->c0;
         bf.sc = h->sc;
         n_chunks[f] = bf.n_chunks;
@@ -1674,6 +1698,7 @@ psfs_status batch_build(psfs_batch *b, const FuseShape &shape)
     bl.done = b->d_words + 16;
     bl.status = b->d_words;
     bl.blocks = b->blocks;
+    bl.wait_ns = b->wait_ns;
     PSFS_CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(b->d_words + 16, 0, sizeof(uint32_t) * (size_t)F, b->cap_stream);
     if (e == cudaSuccess) e = launch_batch(bl, shape, b->map_dtype, b->cap_stream);
@@ -1826,6 +1851,20 @@ psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *b
         best->seq_likelihood_ctas = 0;
     }
     return PSFS_OK;
+}
+
+psfs_status psfs_batch_set_wait_limit(psfs_batch *b, uint64_t limit_ns, int32_t hold_frame)
+{
+    if (!b) return fail(PSFS_ERR_INVALID_ARG, "batch is NULL");
+    if (limit_ns < 1000 || limit_ns > 10ull * kWaitNs)
+        return fail(PSFS_ERR_INVALID_ARG, "wait limit outside [1 us, 10 s]");
+    if (hold_frame < -1 || hold_frame >= (int32_t)b->frames.size())
+        return fail(PSFS_ERR_INVALID_ARG, "hold_frame is not -1 or a frame of the batch");
+    DeviceGuard guard(b->device);
+    PSFS_CK(cudaStreamSynchronize(b->user_stream));
+    b->wait_ns = limit_ns;
+    b->hold_frame = hold_frame;
+    return batch_build(b, b->shape);
 }
 
 void psfs_batch_destroy(psfs_batch *b) { batch_free(b); }

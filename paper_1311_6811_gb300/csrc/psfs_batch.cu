@@ -75,12 +75,15 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchLaunch b)
         } else {
             const FuseArgs &a = fr.fa;
             if (tid == 0) {
-                // wait, at most 1 s, for every likelihood chunk of this frame
-                if (ld_acquire(&b.done[f]) < fr.n_chunks) {
+                // wait, at most b.wait_ns, for every likelihood chunk of this
+                // frame; once any wait of the launch has run out the others
+                // give up at once (the launch's results are already invalid),
+                // so a stuck frame costs one wait limit, not one per tile
+                if (ld_acquire(&b.done[f]) < fr.wait_chunks) {
                     const uint64_t t0 = globaltimer_ns();
-                    while (ld_acquire(&b.done[f]) < fr.n_chunks) {
+                    while (ld_acquire(&b.done[f]) < fr.wait_chunks) {
                         __nanosleep(256);
-                        if (globaltimer_ns() - t0 > kWaitNs) {
+                        if ((ld_acquire(b.status) & kStatusTimeout) || globaltimer_ns() - t0 > b.wait_ns) {
                             atomicOr(b.status, kStatusTimeout);
                             break;
                         }

@@ -527,6 +527,7 @@ struct BatchFrame {
     const float *hinv;
     int64_t n_pix;
     uint32_t n_chunks;
+    uint32_t wait_chunks;   // chunk count the fusion tiles wait for (n_chunks; more only in the hold test)
     float c0;
     SensorConsts sc;
 };
@@ -545,6 +546,7 @@ struct BatchLaunch {
     uint32_t *done;             // device, [n_frames] completed chunks (zeroed before the launch)
     uint32_t *status;
     int blocks;
+    uint64_t wait_ns;           // limit of a fusion tile's wait for its frame's chunks
 };
 
 cudaError_t launch_batch(const BatchLaunch &b, const FuseShape &shape, int map_dtype, cudaStream_t s);

@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
             "psfs_set_background_l2": (st, [_vp, ctypes.c_int32]),
             "psfs_fuse_slm": (st, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
             "psfs_get_likelihood": (st, [_vp, _vp, _vp]),
+            "psfs_get_log_ratio": (st, [_vp, _vp, _vp]),
             "psfs_backward": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
             "psfs_backward_sequence": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
             "psfs_backward_slm": (st, [_vp, _vp, _vp, _vp]),
@@ -133,6 +134,7 @@ def load(build_if_missing: bool = True):
             "psfs_batch_set_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
             "psfs_batch_autotune": (st, [_vp, ctypes.c_int32, ctypes.POINTER(psfs_fuse_config),
                                          ctypes.POINTER(ctypes.c_float)]),
+            "psfs_batch_set_wait_limit": (st, [_vp, ctypes.c_uint64, ctypes.c_int32]),
             "psfs_batch_destroy": (None, [_vp]),
             "psfs_profile_enable": (st, [_vp, ctypes.c_int32]),
             "psfs_profile_read": (st, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
@@ -377,6 +379,15 @@ def psfs_get_likelihood(h: int, images, slm_out):
                                       _dev_ptr(slm_out, "slm_out", torch.float32)), "psfs_get_likelihood")
 
 
+def psfs_get_log_ratio(h: int, images, map_out):
+    """The stored log-ratio maps of `images` in the handle's map dtype
+    (map_out: contiguous CUDA tensor of n_cams * H * W float32 / float16 /
+    bfloat16 elements)."""
+    import torch
+    _check(load().psfs_get_log_ratio(h, _dev_ptr(images, "images", torch.uint8),
+                                     _dev_ptr(map_out, "map_out")), "psfs_get_log_ratio")
+
+
 def psfs_backward(h: int, images, d_occ, d_slm=None, d_mean=None, d_var=None):
     import torch
     _check(load().psfs_backward(h, _dev_ptr(images, "images", torch.uint8),
@@ -541,6 +552,12 @@ def psfs_batch_autotune(b: int, reps: int = 3, timings: Optional[dict] = None) -
     return cfg.as_tuple()
 
 
+def psfs_batch_set_wait_limit(b: int, limit_ns: int, hold_frame: int = -1):
+    """Limit of the batched fusion items' bounded waits; `hold_frame` (tests
+    only) makes one frame's items wait for a chunk that never comes."""
+    _check(load().psfs_batch_set_wait_limit(b, int(limit_ns), int(hold_frame)), "psfs_batch_set_wait_limit")
+
+
 def psfs_batch_destroy(b: int):
     if b:
         load().psfs_batch_destroy(b)
@@ -593,6 +610,7 @@ class Reconstructor:
         self.image_shape = (self.n_cams, int(_get(c0, "height")), int(_get(c0, "width")), 3)
         self.capacity = int(capacity) if capacity is not None else self.n_voxels
         self.grid, self.cams, self.params = grid, list(cams), params
+        self.map_dtype = int(make_params(params, map_dtype).map_dtype)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -630,6 +648,14 @@ class Reconstructor:
         import torch
         out = torch.empty(self.image_shape[:3], dtype=torch.float32, device=self.device)
         psfs_get_likelihood(self.handle, images, out)
+        return out
+
+    def log_ratio(self, images):
+        """The stored log-ratio maps of `images`, in the handle's map dtype."""
+        import torch
+        dt = {PSFS_MAP_F32: torch.float32, PSFS_MAP_F16: torch.float16, PSFS_MAP_BF16: torch.bfloat16}
+        out = torch.empty(self.image_shape[:3], dtype=dt[self.map_dtype], device=self.device)
+        psfs_get_log_ratio(self.handle, images, out)
         return out
 
     def sync(self) -> int:

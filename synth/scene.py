@@ -456,13 +456,15 @@ def _render_frame(args):
 def make_scene(*, seed: int, grid_n: int, cube_side: float, n_cams: int, width: int,
                height: int, focal: float, n_frames: int = 1, heights=(1.5, 1.5),
                n_bodies: int = 1, walking: bool = False, ring_radius: float = 3.0,
-               params: Optional[Params] = None, workers: int = 1) -> Scene:
+               params: Optional[Params] = None, workers: int = 1,
+               frame_ids: Optional[Sequence[int]] = None) -> Scene:
     """Body (or bodies) on a ring of cameras, per-pixel Gaussian background.
 
     Cameras, background, colours and poses come from one generator seeded with
     `seed`; the noise of frame f from a generator seeded with (seed, 1 + f), so
     frames can be rendered by `workers` processes (spawned) with identical
-    results.
+    results.  `frame_ids` renders only those frames of the `n_frames`-frame
+    sequence, in that order (each exactly as in the whole sequence).
     """
     rng = np.random.default_rng(seed)
     grid = cube_grid(grid_n, cube_side)
@@ -486,16 +488,19 @@ def make_scene(*, seed: int, grid_n: int, cube_side: float, n_cams: int, width: 
         for b in range(n_bodies):
             caps.extend(body_capsules(tracks[b][f], body_cols[b]))
         caps_per_frame.append(caps)
-    jobs = [(seed, f, cams, caps_per_frame[f], mean, sigma) for f in range(n_frames)]
-    if workers > 1 and n_frames > 1:
+    ids = list(range(n_frames)) if frame_ids is None else [int(f) for f in frame_ids]
+    if any(not 0 <= f < n_frames for f in ids):
+        raise ValueError("frame_ids outside the sequence")
+    jobs = [(seed, f, cams, caps_per_frame[f], mean, sigma) for f in ids]
+    if workers > 1 and len(jobs) > 1:
         import multiprocessing as mp
-        with mp.get_context("spawn").Pool(min(workers, n_frames)) as pool:
+        with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
             frames = pool.map(_render_frame, jobs, chunksize=1)
     else:
         frames = [_render_frame(j) for j in jobs]
-    images = np.stack(frames) if n_frames > 1 else frames[0]
+    images = np.stack(frames) if (n_frames > 1 or frame_ids is not None) else frames[0]
     return Scene(grid, cams, images, mean.astype(np.float32), var.astype(np.float32),
-                 params or Params(), caps_per_frame)
+                 params or Params(), [caps_per_frame[f] for f in ids])
 
 
 # The workloads, by what they are.
@@ -505,12 +510,12 @@ def scene_64cube_4cam(seed: int = 0) -> Scene:
                       focal=300.0)
 
 
-def scene_128cube_8cam(seed: int = 1, n_frames: int = 100, workers: int = 1) -> Scene:
+def scene_128cube_8cam(seed: int = 1, n_frames: int = 100, workers: int = 1, frame_ids=None) -> Scene:
     """128^3 grid over a 2.2 m cube, 8 cameras 640x480 (f = 600 px), heights 1.2-2.2 m,
-    a walking sequence of `n_frames` frames."""
+    a walking sequence of `n_frames` frames (only `frame_ids` of them, if given)."""
     return make_scene(seed=seed, grid_n=128, cube_side=2.2, n_cams=8, width=640, height=480,
                       focal=600.0, n_frames=n_frames, heights=(1.2, 2.2), walking=True,
-                      workers=workers)
+                      workers=workers, frame_ids=frame_ids)
 
 
 def scene_256cube_16cam(seed: int = 2) -> Scene:

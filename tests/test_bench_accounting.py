@@ -68,3 +68,33 @@ def test_ncu_traffic_matches_sources_and_shape(tmp_path, monkeypatch):
     (csrc / names[0]).write_bytes((csrc / names[0]).read_bytes() + b"// edited\n")
     lx, tz = next(iter(shapes))
     assert bench.ncu_traffic("fuse_group_kernel", {"lanes_x": lx, "voxels_z": tz, "frames_per_group": 8}) is None
+
+
+def test_error_report_against_fp64(monkeypatch):
+    """The bench's comparison of GPU outputs with the FP64 oracle: the oracle's
+    own result reports no error; a flipped voxel outside the boundary and tie
+    buckets is counted as unexplained, a shifted occupancy as its error."""
+    import numpy as np
+    import oracle
+    from synth import scene as S
+    sc = S.make_scene(seed=3, grid_n=16, cube_side=2.0, n_cams=2, width=64, height=48, focal=60.0)
+    for k, v in {"images": sc.images[None], "mean": sc.mean, "var": sc.var, "grid": sc.grid, "cams": sc.cams,
+                 "params": sc.params, "oracle": oracle}.items():
+        monkeypatch.setitem(bench._W, k, v)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    occ = ref["occ"].astype(np.float32)
+    lst = ref["list"].astype(np.uint32)
+    rep = bench._oracle_worker_compare((0, {"same": (occ, lst, lst.size)}))["same"]
+    assert rep["set_diff"] == 0 and rep["set_diff_unexplained"] == 0 and rep["max_abs"] < 1e-7
+    # flip the clearest voxel outside both buckets and shift one occupancy
+    ok = ~ref["boundary"] & (np.abs(ref["logodds"]) > 1.0)
+    v = int(np.flatnonzero(ok)[0])
+    got = set(lst.tolist()) ^ {v}
+    lst2 = np.array(sorted(got), np.uint32)
+    occ2 = occ.copy()
+    occ2[v] += 0.25
+    rep = bench._oracle_worker_compare((0, {"bad": (occ2, lst2, lst2.size)}))["bad"]
+    assert rep["set_diff"] == 1 and rep["set_diff_unexplained"] == 1
+    assert abs(rep["max_abs"] - 0.25) < 1e-6
+    s = bench.summarize_errors({0: rep, 5: rep})
+    assert s["frames"] == [0, 5] and s["set_diff_unexplained"] == 2

@@ -133,3 +133,34 @@ def test_batch_64_heterogeneous_frames():
     psfs.psfs_batch_destroy(b)
     for rec, _ in recs:
         rec.close()
+
+
+def test_batch_wait_timeout_is_reported_and_recovers():
+    """Failure detection without a fault: with a 1 ms limit and one frame
+    held (its fusion items wait for a chunk that never comes), the bounded
+    device-side wait runs out, psfs_batch_sync returns PSFS_ERR_TIMEOUT, and
+    the context stays usable: the next launch without the hold returns
+    PSFS_OK with every frame as psfs_reconstruct gives it."""
+    scenes = _frames([(32, 2.0, 4, 160, 120, 150.0), (40, 2.0, 3, 128, 96, 120.0),
+                      (24, 1.5, 5, 96, 80, 90.0)], seed=70)
+    b, recs, outs = _run_batch(scenes)
+    psfs.psfs_batch_set_wait_limit(b, 1_000_000, hold_frame=1)
+    psfs.psfs_batch_run(b)
+    assert psfs.psfs_batch_sync(b) == psfs.PSFS_ERR_TIMEOUT
+    assert "timed out" in psfs.psfs_last_error_message()
+    psfs.psfs_batch_set_wait_limit(b, 1_000_000_000, hold_frame=-1)
+    psfs.psfs_batch_run(b)
+    assert psfs.psfs_batch_sync(b) == psfs.PSFS_OK
+    for (rec, img), out in zip(recs, outs):
+        got = _host(out)
+        occ, lst, cnt = rec.reconstruct(img)
+        assert rec.sync() == psfs.PSFS_OK
+        np.testing.assert_array_equal(got[0], occ.cpu().numpy().ravel())
+        np.testing.assert_array_equal(got[1], psfs.voxel_list(lst, cnt, rec.capacity).numpy())
+    with pytest.raises(psfs.PsfsError):
+        psfs.psfs_batch_set_wait_limit(b, 10, hold_frame=-1)        # below 1 us
+    with pytest.raises(psfs.PsfsError):
+        psfs.psfs_batch_set_wait_limit(b, 1_000_000, hold_frame=3)  # no such frame
+    psfs.psfs_batch_destroy(b)
+    for rec, _ in recs:
+        rec.close()
