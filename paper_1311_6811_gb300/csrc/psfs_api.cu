@@ -22,12 +22,6 @@ using namespace psfs;
 // Device staging slots of the host-buffer sequence path.
 constexpr int kIoSlots = 3;
 
-namespace psfs {
-// The adjoint's pixel pass over up to kBwFrames frames (psfs_backward.cu).
-constexpr int kBwFrames = 8;
-cudaError_t launch_backward_pixel_group(const BackwardArgs &b, int n_frames, int64_t img_fstride,
-                                        int64_t dl_fstride, bool accumulate, cudaStream_t s);
-}  // namespace psfs
 
 struct psfs_handle {
     int device = 0;
@@ -102,8 +96,14 @@ struct psfs_handle {
 
     // adjoint scratch (allocated on first use)
     float *dl = nullptr;        // [n_vox] dLoss / dlogodds
-    float *dl_seq = nullptr;    // [kBwFrames][n_vox] the same for psfs_backward_sequence
-    float *dg = nullptr;        // [n_pix] dLoss / dg
+    float *dl_rec = nullptr;    // [n_vox][kBwRecord] the same for psfs_backward_sequence
+    // owner lists of the pixel pass (built by the first adjoint call): pixel
+    // p owns own_vox[own_off[p] .. own_off[p + 1])
+    uint32_t *own_off = nullptr;   // [n_pix + 1]
+    uint32_t *own_vox = nullptr;   // [n_vox * n_cams] (upper bound of the pairs)
+    uint32_t *own_cnt = nullptr;   // [n_pix] counts, then fill cursors
+    uint32_t *own_sums = nullptr;  // block totals of the offset scan
+    bool own_ready = false;
 };
 
 namespace psfs {
@@ -206,8 +206,11 @@ void free_handle(psfs_handle *h)
     cudaFree(h->st_occ);
     cudaFree(h->st_list);
     cudaFree(h->dl);
-    cudaFree(h->dl_seq);
-    cudaFree(h->dg);
+    cudaFree(h->dl_rec);
+    cudaFree(h->own_off);
+    cudaFree(h->own_vox);
+    cudaFree(h->own_cnt);
+    cudaFree(h->own_sums);
     cudaFree(h->maps2);
     cudaFree(h->gmaps[0]);
     cudaFree(h->gmaps[1]);
@@ -1142,6 +1145,31 @@ psfs_status psfs_get_log_ratio(psfs_handle *h, const uint8_t *images, void *map_
 
 static void fill_backward_args(psfs_handle *h, BackwardArgs &b);
 
+// The owner lists of the pixel pass, built on the handle's stream by the
+// first adjoint call (they depend on the grid and the rig only).
+static psfs_status ensure_owner_lists(psfs_handle *h)
+{
+    if (h->own_ready) return PSFS_OK;
+    if (!owner_lists_supported(h->fuse, h->n_pix))
+        return fail(PSFS_ERR_INVALID_ARG, "adjoint: n_voxels * n_cams must be below 2^32");
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    const size_t n_chunks = (size_t)(h->n_pix + 1 + 4095) / 4096;
+    if (!h->own_off) {
+        if (cudaMalloc(&h->own_off, ((size_t)h->n_pix + 1) * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&h->own_cnt, (size_t)h->n_pix * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&h->own_sums, n_chunks * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&h->own_vox, std::max<size_t>(1, n_vox * (size_t)h->n_cams) * sizeof(uint32_t)) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "adjoint owner lists");
+        }
+    }
+    FuseArgs fa = h->fuse;
+    PSFS_CK(launch_build_owners(fa, h->n_pix, h->own_cnt, h->own_sums, h->own_off, h->own_vox, h->stream));
+    h->own_ready = true;
+    return PSFS_OK;
+}
+
 static psfs_status enqueue_backward(psfs_handle *h, const uint8_t *images, const float *slm, const float *d_occ,
                                     float *d_slm, float *d_mean, float *d_var)
 {
@@ -1152,6 +1180,8 @@ static psfs_status enqueue_backward(psfs_handle *h, const uint8_t *images, const
             return fail(PSFS_ERR_NOMEM, "adjoint scratch");
         }
     }
+    psfs_status st = ensure_owner_lists(h);
+    if (st != PSFS_OK) return st;
     BackwardArgs b;
     fill_backward_args(h, b);
     b.d_occ = d_occ;
@@ -1196,7 +1226,7 @@ static psfs_status enqueue_backward(psfs_handle *h, const uint8_t *images, const
     }
     {
         ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL);
-        PSFS_CK(launch_backward_pixel(b, h->stream));
+        PSFS_CK(launch_owner_pixel(b, h->own_off, h->own_vox, h->stream));
     }
     return PSFS_OK;
 }
@@ -1216,29 +1246,31 @@ static void fill_backward_args(psfs_handle *h, BackwardArgs &b)
     b.db = (float)(2.0 * q - 1.0);
     b.one_minus_q = (float)(1.0 - q);
     b.n_pix = h->n_pix;
-    plan_backward_inv(h->grid, h->cams.data(), h->n_cams, h->fuse, b.inv);
+    b.dl_stride = 1;
 }
 
-// Frames in groups of kBwFrames: per frame the forward maps and the voxel
-// pass (dLoss/dL of frame f into slot f of dl_seq), then one pixel pass for
-// the group.
+// Frames in groups of kBwRecord: per frame the forward maps and the voxel
+// pass (dLoss/dL of frame f into slot f of the voxels' records), then one
+// pixel pass for the group.
 static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
                                              const float *d_occ, float *d_slm, float *d_mean, float *d_var)
 {
     const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
-    if (!h->dl_seq) {
-        if (cudaMalloc(&h->dl_seq, (size_t)kBwFrames * n_vox * sizeof(float)) != cudaSuccess) {
+    if (!h->dl_rec) {
+        if (cudaMalloc(&h->dl_rec, (size_t)kBwRecord * n_vox * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return fail(PSFS_ERR_NOMEM, "adjoint sequence scratch");
         }
     }
+    psfs_status st = ensure_owner_lists(h);
+    if (st != PSFS_OK) return st;
     BackwardArgs b;
     fill_backward_args(h, b);
     b.d_mean = d_mean;
     b.d_var = d_var;
     const size_t frame_bytes = (size_t)h->n_pix * 3;
-    for (int g0 = 0; g0 < n_frames; g0 += kBwFrames) {
-        const int nf = std::min(kBwFrames, n_frames - g0);
+    for (int g0 = 0; g0 < n_frames; g0 += kBwRecord) {
+        const int nf = std::min(kBwRecord, n_frames - g0);
         for (int f = 0; f < nf; ++f) {
             LikelihoodArgs la{};
             la.img = images + (size_t)(g0 + f) * frame_bytes;
@@ -1256,18 +1288,20 @@ static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, c
             }
             BackwardArgs bv = b;
             bv.d_occ = d_occ + (size_t)(g0 + f) * n_vox;
-            bv.dl = h->dl_seq + (size_t)f * n_vox;
+            bv.dl = h->dl_rec + f;
+            bv.dl_stride = kBwRecord;
             ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL);
             FuseShape direct = h->shape;
             direct.staged = 0;
             PSFS_CK(launch_backward_voxel(bv, direct, h->params.map_dtype, h->stream));
         }
         BackwardArgs bp = b;
-        bp.dl = h->dl_seq;
+        bp.dl = h->dl_rec;
+        bp.dl_stride = kBwRecord;
         bp.img = images + (size_t)g0 * frame_bytes;
         bp.d_slm = d_slm ? d_slm + (size_t)g0 * h->n_pix : nullptr;
         ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL);
-        PSFS_CK(launch_backward_pixel_group(bp, nf, (int64_t)frame_bytes, (int64_t)n_vox, g0 > 0, h->stream));
+        PSFS_CK(launch_owner_pixel_group(bp, h->own_off, h->own_vox, nf, (int64_t)frame_bytes, g0 > 0, h->stream));
     }
     return PSFS_OK;
 }

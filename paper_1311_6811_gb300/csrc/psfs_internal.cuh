@@ -496,10 +496,15 @@ struct WeightArgs {
 };
 cudaError_t launch_weights(const WeightArgs &a, int n_particles, cudaStream_t s);
 
+// Frames per record of dLoss/dL in the batched adjoint (and per pass of its
+// pixel pass): frame f of voxel v at dl[v * kBwRecord + f], 32 bytes per voxel.
+constexpr int kBwRecord = 8;
+
 struct BackwardArgs {
     FuseArgs f;                   // grid, cameras, maps (for the voxel pass), tiles
     const float *d_occ;           // [n_vox]
-    float *dl;                    // [n_vox] dLoss/dL scratch
+    float *dl;                    // dLoss/dL scratch: voxel v at dl[v * dl_stride]
+    int dl_stride;                // 1 (one frame) or kBwRecord (records of the batched adjoint)
     // pixel pass
     const uint8_t *img;           // [n_pix][3] (NULL: `slm` given instead)
     const float *slm;             // [n_pix] caller-supplied SLM (psfs_backward_slm)
@@ -509,7 +514,6 @@ struct BackwardArgs {
     float da, one_minus_pd, db, one_minus_q;   // a(s), b(s) of Eq. 5-9
     float *d_slm, *d_mean, *d_var;             // outputs, any may be NULL
     int64_t n_pix;
-    PixelInv inv[PSFS_MAX_CAMS];
 };
 
 cudaError_t launch_backward_voxel(const BackwardArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
@@ -552,7 +556,19 @@ struct BatchLaunch {
 cudaError_t launch_batch(const BatchLaunch &b, const FuseShape &shape, int map_dtype, cudaStream_t s);
 void plan_backward_inv(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const FuseArgs &f,
                        PixelInv *inv);
-cudaError_t launch_backward_pixel(const BackwardArgs &a, cudaStream_t s);
+// Owner lists of the adjoint's pixel pass (psfs_owners.cu): for every pixel
+// of every camera, the voxels whose centre the forward projects into it, in
+// ascending order: segment p is vox[off[p] .. off[p + 1]).  Buffers: cnt
+// [n_pix], sums [ceil((n_pix + 1) / 4096)], off [n_pix + 1], vox [n_vox *
+// n_cams].  Supported while n_vox * n_cams < 2^32.
+bool owner_lists_supported(const FuseArgs &a, int64_t n_pix);
+cudaError_t launch_build_owners(const FuseArgs &a, int64_t n_pix, uint32_t *cnt, uint32_t *sums, uint32_t *off,
+                                uint32_t *vox, cudaStream_t s);
+// Pixel pass of one frame (b.dl dense, dl_stride 1), and of n_frames <=
+// kBwRecord frames of records (frame f's colour at b.img + f img_fstride).
+cudaError_t launch_owner_pixel(const BackwardArgs &b, const uint32_t *off, const uint32_t *vox, cudaStream_t s);
+cudaError_t launch_owner_pixel_group(const BackwardArgs &b, const uint32_t *off, const uint32_t *vox, int n_frames,
+                                     int64_t img_fstride, bool accumulate, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 cudaError_t launch_fuse_staged(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);
 

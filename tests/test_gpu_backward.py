@@ -261,3 +261,69 @@ def test_backward_sequence_equals_per_frame():
     assert rec.sync() == psfs.PSFS_OK
     np.testing.assert_array_equal(d_mean2.cpu().numpy(), sum_m.cpu().numpy())
     rec.close()
+
+
+def test_backward_cameras_inside_the_grid_and_deterministic():
+    """An 8 m grid that contains the camera ring (voxels behind, beside and in
+    front of every camera; long owner segments near the cameras): the adjoint
+    against the oracle's, and two calls give the same bits."""
+    sc = S.make_scene(seed=14, grid_n=48, cube_side=8.0, n_cams=4, width=160, height=120, focal=150.0)
+    rng = np.random.default_rng(14)
+    target = rng.uniform(0, 1, size=sc.grid.n_voxels)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    img = to_dev(sc.images)
+    occ, _, _ = rec.reconstruct(img)
+    d_occ = (2 * (occ.reshape(-1) - to_dev(target.astype(np.float32)))).contiguous()
+    n_pix = sc.images.size // 3
+    outs = []
+    for _ in range(2):
+        d_slm = torch.empty(n_pix, dtype=torch.float32, device="cuda")
+        d_mean = torch.empty(sc.images.shape, dtype=torch.float32, device="cuda")
+        d_var = torch.empty(sc.images.shape, dtype=torch.float32, device="cuda")
+        psfs.psfs_backward(rec.handle, img, d_occ, d_slm, d_mean, d_var)
+        assert rec.sync() == psfs.PSFS_OK
+        outs.append((d_slm.cpu().numpy(), d_mean.cpu().numpy(), d_var.cpu().numpy()))
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    ds, dm, dv = oracle.backward(sc.grid, sc.cams, sc.images, sc.mean, sc.var, 2 * (ref["occ"] - target), sc.params)
+    keep = ~_ambiguous_pixels(sc.grid, sc.cams, ref["boundary"])
+    _compare(outs[0][0], ds, keep)
+    keep3 = np.repeat(keep, 3)
+    _compare(outs[0][1], dm, keep3)
+    _compare(outs[0][2], dv, keep3)
+    rec.close()
+
+
+@pytest.mark.parametrize("dtype,bound", [("f16", 2e-2), ("bf16", 2e-1)])
+def test_reduced_precision_adjoint_error_vs_fp64(dtype, bound):
+    """The adjoint with 16-bit maps (the forward it recomputes sums stored
+    16-bit log ratios) against the FP64 oracle's adjoint: the error of d_slm,
+    d_mean and d_var relative to each gradient's largest magnitude is
+    reported, under a loose sanity bound."""
+    sc, target = _frame(sc_seed=45, grid_n=48)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=dtype)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    img = to_dev(sc.images)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    # the same d_occ on both sides: the FP64 loss gradient at the FP64 occupancy
+    d_occ64 = 2 * (ref["occ"] - target)
+    d_occ = to_dev(d_occ64.astype(np.float32))
+    n_pix = sc.images.size // 3
+    d_slm = torch.empty(n_pix, dtype=torch.float32, device="cuda")
+    d_mean = torch.empty(sc.images.shape, dtype=torch.float32, device="cuda")
+    d_var = torch.empty(sc.images.shape, dtype=torch.float32, device="cuda")
+    psfs.psfs_backward(rec.handle, img, d_occ, d_slm, d_mean, d_var)
+    assert rec.sync() == psfs.PSFS_OK
+    ds, dm, dv = oracle.backward(sc.grid, sc.cams, sc.images, sc.mean, sc.var, d_occ64, sc.params)
+    keep = ~_ambiguous_pixels(sc.grid, sc.cams, ref["boundary"])
+    keep3 = np.repeat(keep, 3)
+    errs = {}
+    for name, got, want, k in (("d_slm", d_slm, ds, keep), ("d_mean", d_mean, dm, keep3),
+                               ("d_var", d_var, dv, keep3)):
+        g, w = got.cpu().numpy().ravel()[k].astype(np.float64), want.ravel()[k]
+        errs[name] = float(np.abs(g - w).max() / max(np.abs(w).max(), 1e-30))
+    print(dtype, "adjoint error vs FP64 (max |err| / max |grad|):", errs)
+    assert max(errs.values()) < bound, errs
+    rec.close()

@@ -146,7 +146,9 @@ def test_batch_wait_timeout_is_reported_and_recovers():
     b, recs, outs = _run_batch(scenes)
     psfs.psfs_batch_set_wait_limit(b, 1_000_000, hold_frame=1)
     psfs.psfs_batch_run(b)
-    assert psfs.psfs_batch_sync(b) == psfs.PSFS_ERR_TIMEOUT
+    with pytest.raises(psfs.PsfsError) as e:
+        psfs.psfs_batch_sync(b)
+    assert e.value.status == psfs.PSFS_ERR_TIMEOUT
     assert "timed out" in psfs.psfs_last_error_message()
     psfs.psfs_batch_set_wait_limit(b, 1_000_000_000, hold_frame=-1)
     psfs.psfs_batch_run(b)
