@@ -60,6 +60,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the per-frame FP32/FP16 forward and forward+backward timings")
     ap.add_argument("--forms-frames", type=int, default=20)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 64^3 x 4, 256^3 x 16 (16-bit maps) and 64-frame batch workloads")
     ap.add_argument("--launch", choices=["sequence", "batch"], default="sequence",
                     help="sequence: psfs_reconstruct_sequence (2 streams); batch: one persistent CUDA-graph launch")
     ap.add_argument("--no-l2-background", action="store_true",
@@ -800,6 +802,10 @@ def run_ours(args):
     if not args.no_forms:
         forms = time_forms(args, sc, d_images, occ, dev, psfs, fuse_cfg, gpu_outputs)
 
+    configs = None
+    if not args.no_configs and rank == 0:
+        configs = time_configs(args, dev, psfs)
+
     cpu = None
     err_vs_fp64 = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -841,12 +847,187 @@ def run_ours(args):
                                       "frames; 2 streams, double-buffered maps)"),
                            "background_l2_resident": not args.no_l2_background},
                 "err_vs_fp64": err_vs_fp64,
+                "configs": configs,
                 "stages": stages, "roofline": roofline, "roofline_sequence": roofline_sequence,
                 "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
                 "next": nxt,
                 "gpu_launches": gpu_launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
+
+
+# --------------------------------------------------------------------------- #
+# the other workloads: 64^3 x 4 (one frame), 256^3 x 16 with 16-bit maps,
+# the 64-frame heterogeneous batch in one graph launch
+# --------------------------------------------------------------------------- #
+def _err_report(occ, lst, count, ref, threshold=0.5):
+    """Error of one GPU frame against the FP64 oracle's reconstruction of it."""
+    keep = ~ref["boundary"]
+    d = np.abs(np.asarray(occ, np.float64).ravel() - ref["occ"])
+    got = np.zeros(ref["occ"].size, bool)
+    got[np.asarray(lst, np.int64) & 0xFFFFFFFF] = True
+    diff = np.flatnonzero(got != ref["occupied"])
+    tie = np.abs(ref["logodds"] - math.log(threshold / (1 - threshold))) < TIE_EPS
+    return {"max_abs": float(d[keep].max()) if keep.any() else 0.0,
+            "mean_abs": float(d[keep].mean()) if keep.any() else 0.0,
+            "hamming": int(diff.size), "hamming_unexplained": int((~(ref["boundary"] | tie))[diff].sum()),
+            "boundary_voxels": int(ref["boundary"].sum()), "tie_voxels": int(tie.sum()),
+            "count": int(count), "count_fp64": int(ref["list"].size)}
+
+
+def _stage_roofline(prof, stage_bytes, peak):
+    """Dominant stage of the library's event profile: algorithmic bytes per
+    launch over its average launch time."""
+    rows = {}
+    for name, (t_ms, n) in prof.items():
+        if name in stage_bytes and n:
+            rows[name] = (t_ms, n, stage_bytes[name])
+    if not rows:
+        return None
+    dom = max(rows, key=lambda k: rows[k][0])
+    t_ms, n, b = rows[dom]
+    ach = b / (t_ms / n * 1e-3) / 1e9
+    return {"bound": "hbm", "stage": dom, "avg_us": 1e3 * t_ms / n, "alg_bytes_per_launch": b,
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "shares": {k: v[0] / sum(r[0] for r in rows.values()) for k, v in rows.items()}}
+
+
+def time_single_frame(psfs, dev, sc, map_dtype, reps, flush=None):
+    """One frame per psfs_reconstruct call: device time per frame (CUDA events
+    around each call on the handle's stream; with `flush`, a buffer larger
+    than L2 is written before each call), per-stage profile, outputs."""
+    import torch
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=map_dtype, stream=stream, device=dev)
+        rec.set_background(torch.from_numpy(sc.mean).to(dev), torch.from_numpy(sc.var).to(dev))
+        img = torch.from_numpy(np.ascontiguousarray(sc.images)).to(dev)
+        out = rec.alloc_outputs()
+        rec.reconstruct(img, out)
+    stream.synchronize()
+    psfs.psfs_autotune(rec.handle, img, reps=2)
+    with torch.cuda.stream(stream):
+        rec.reconstruct(img, out)   # warm-up with the chosen shape
+    stream.synchronize()
+    psfs.psfs_profile_enable(rec.handle, 4 * reps + 8)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    with torch.cuda.stream(stream):
+        for e0, e1 in evs:
+            if flush is not None:
+                flush.add_(1.0)
+            e0.record(stream)
+            rec.reconstruct(img, out)
+            e1.record(stream)
+    stream.synchronize()
+    assert rec.sync() == psfs.PSFS_OK
+    prof = psfs.psfs_profile_read(rec.handle)
+    psfs.psfs_profile_enable(rec.handle, 0)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / reps
+    occ, lst, cnt = out
+    n = int(cnt.item()) & 0xFFFFFFFF
+    res = (occ.cpu().numpy().ravel(), lst[:min(n, rec.capacity)].cpu().numpy(), n)
+    cfg = psfs.psfs_get_fuse_config(rec.handle)
+    rec.close()
+    return ms, prof, res, cfg
+
+
+def time_configs(args, dev, psfs):
+    """The other configurations of the workload list, each with its throughput,
+    the roofline of its dominant kernel and its error against FP64."""
+    import torch
+    from synth import scene as S
+    import oracle
+    oracle.build()
+    peak, _ = measured_peaks()
+    out = {}
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    # 64^3 x 4 cameras 320x240, FP32, one frame per call (L2 flushed between calls)
+    sc = S.scene_64cube_4cam(seed=0)
+    ms, prof, res, cfg = time_single_frame(psfs, dev, sc, "f32", reps=50, flush=flush)
+    V, K, n_pix = sc.grid.n_voxels, sc.n_cams, sc.images.size // 3
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    out["c1"] = {"workload": "64^3 grid x 4 cams 320x240, FP32, one frame per psfs_reconstruct call",
+                 "ms_per_frame": ms, "frames_per_s": 1e3 / ms, "gvox_cam_per_s": V * K / (ms * 1e-3) / 1e9,
+                 "timing": "CUDA events around each call; a 256 MB buffer written before each call (L2 flushed)",
+                 "fuse_tile": list(cfg),
+                 "roofline": _stage_roofline(prof, {"likelihood": n_pix * (3 + 24 + 4),
+                                                    "fuse": n_pix * 4 + V * 4 + res[2] * 4}, peak),
+                 "err_vs_fp64": _err_report(*res, ref)}
+
+    # 256^3 x 16 cameras 1280x720, two bodies, FP16 then BF16 maps (inputs > L2)
+    sc = S.scene_256cube_16cam(seed=2)
+    V, K, n_pix = sc.grid.n_voxels, sc.n_cams, sc.images.size // 3
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    for dt in ("f16", "bf16"):
+        ms, prof, res, cfg = time_single_frame(psfs, dev, sc, dt, reps=10)
+        out[f"c3_{dt}"] = {"workload": f"256^3 grid x 16 cams 1280x720, two bodies, {dt} maps (FP32 accumulation), "
+                                       "one frame per psfs_reconstruct call",
+                           "ms_per_frame": ms, "frames_per_s": 1e3 / ms,
+                           "gvox_cam_per_s": V * K / (ms * 1e-3) / 1e9,
+                           "timing": "CUDA events around back-to-back calls; inputs (398 MB) larger than L2",
+                           "fuse_tile": list(cfg),
+                           "roofline": _stage_roofline(prof, {"likelihood": n_pix * (3 + 24 + 2),
+                                                              "fuse": n_pix * 2 + V * 4 + res[2] * 4}, peak),
+                           "err_vs_fp64": _err_report(*res, ref)}
+    del ref
+
+    # 64 heterogeneous frames in one persistent CUDA-graph launch, FP32
+    scenes = S.batch_64_scenes(seed=64, workers=args.workers)
+    stream = torch.cuda.Stream(device=dev)
+    recs, frames, outs = [], [], []
+    with torch.cuda.stream(stream):
+        for sc in scenes:
+            rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, stream=stream, device=dev)
+            rec.set_background(torch.from_numpy(sc.mean).to(dev), torch.from_numpy(sc.var).to(dev))
+            img = torch.from_numpy(np.ascontiguousarray(sc.images)).to(dev)
+            o = rec.alloc_outputs()
+            recs.append((rec, img))
+            frames.append((rec.handle, img, o[0], o[1], rec.capacity, o[2]))
+            outs.append(o)
+    stream.synchronize()
+    b = psfs.psfs_batch_create(frames, stream=stream)
+    tune = {}
+    best = psfs.psfs_batch_autotune(b, reps=2, timings=tune)
+    psfs.psfs_batch_run(b)
+    assert psfs.psfs_batch_sync(b) == psfs.PSFS_OK
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        psfs.psfs_batch_run(b)
+    e1.record(stream)
+    stream.synchronize()
+    assert psfs.psfs_batch_sync(b) == psfs.PSFS_OK
+    ms = e0.elapsed_time(e1) / reps
+    evals = sum(sc.grid.n_voxels * sc.n_cams for sc in scenes)
+    counts = [int(o[2].item()) & 0xFFFFFFFF for o in outs]
+    alg = sum(sc.images.size // 3 * (3 + 24 + 2 * 4) + sc.grid.n_voxels * 4 + c * 4 for sc, c in zip(scenes, counts))
+    errs = {}
+    for k in (0, 37):
+        sc = scenes[k]
+        ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+        occ, lst, cnt = outs[k]
+        errs[k] = _err_report(occ.cpu().numpy().ravel(), lst[:min(counts[k], recs[k][0].capacity)].cpu().numpy(),
+                              counts[k], ref)
+    psfs.psfs_batch_destroy(b)
+    for rec, _ in recs:
+        rec.close()
+    ach = alg / (ms * 1e-3) / 1e9
+    out["c4"] = {"workload": "64 frames, grids from {96,128,160,192}^3, 4-12 cams, 640x480 or 960x540, own pose and "
+                             "background each, FP32, one persistent kernel per psfs_batch_run (CUDA graph)",
+                 "ms_per_launch": ms, "ms_per_frame": ms / len(scenes), "frames_per_s": len(scenes) / (ms * 1e-3),
+                 "gvox_cam_per_s": evals / (ms * 1e-3) / 1e9, "voxel_camera_evals": evals,
+                 "timing": "CUDA events around back-to-back graph launches; inputs (GBs) larger than L2",
+                 "tile": list(best), "autotune_ms": {"x".join(map(str, k)): round(v, 3) for k, v in tune.items()},
+                 "roofline": {"bound": "hbm", "kernel": "batch_kernel", "alg_bytes_per_launch": alg, "achieved": ach,
+                              "peak": peak, "unit": "GB/s", "frac": ach / peak},
+                 "err_vs_fp64": {"frames": sorted(errs), "max_abs": max(e["max_abs"] for e in errs.values()),
+                                 "hamming": sum(e["hamming"] for e in errs.values()),
+                                 "hamming_unexplained": sum(e["hamming_unexplained"] for e in errs.values()),
+                                 "boundary_voxels": sum(e["boundary_voxels"] for e in errs.values())}}
+    del flush
+    return out
 
 
 def host_frame(occ, lists, counts, f, cap):

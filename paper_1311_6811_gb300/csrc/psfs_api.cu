@@ -104,6 +104,13 @@ struct psfs_handle {
     uint32_t *own_cnt = nullptr;   // [n_pix] counts, then fill cursors
     uint32_t *own_sums = nullptr;  // block totals of the offset scan
     bool own_ready = false;
+    // batched adjoint (psfs_backward_sequence, first use): its own tile plan
+    // in the shape of the frame-group kernels, and maps of up to kBwRecord
+    // frames as one plane of records [n_pix][frames]
+    FuseArgs bw_fuse{};
+    uint64_t *bw_tiles = nullptr;
+    int4 *bw_tilecam = nullptr;
+    void *bw_maps = nullptr;
 };
 
 namespace psfs {
@@ -211,6 +218,9 @@ void free_handle(psfs_handle *h)
     cudaFree(h->own_vox);
     cudaFree(h->own_cnt);
     cudaFree(h->own_sums);
+    cudaFree(h->bw_tiles);
+    cudaFree(h->bw_tilecam);
+    cudaFree(h->bw_maps);
     cudaFree(h->maps2);
     cudaFree(h->gmaps[0]);
     cudaFree(h->gmaps[1]);
@@ -1249,11 +1259,11 @@ static void fill_backward_args(psfs_handle *h, BackwardArgs &b)
     b.dl_stride = 1;
 }
 
-// Frames in groups of kBwRecord: per frame the forward maps and the voxel
-// pass (dLoss/dL of frame f into slot f of the voxels' records), then one
-// pixel pass for the group.
-static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
-                                             const float *d_occ, float *d_slm, float *d_mean, float *d_var)
+// Tile shape of the batched adjoint's voxel pass (a frame-group shape: lanes_x
+// 8, voxels_z 4), planned once per handle on first use.
+constexpr FuseShape kBwShape = {8, 4, 4, 0};
+
+static psfs_status ensure_backward_group(psfs_handle *h)
 {
     const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
     if (!h->dl_rec) {
@@ -1262,7 +1272,53 @@ static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, c
             return fail(PSFS_ERR_NOMEM, "adjoint sequence scratch");
         }
     }
+    if (!h->bw_maps) {
+        if (cudaMalloc(&h->bw_maps, (size_t)h->n_pix * kBwRecord * h->map_elem) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "adjoint sequence maps");
+        }
+    }
+    if (!h->bw_tiles) {
+        std::vector<uint64_t> tiles;
+        std::vector<int4> tilecam;
+        FuseArgs fa;
+        plan_fuse(h->grid, h->cams.data(), h->n_cams, h->params, kBwShape, &fa, &tiles, &tilecam);
+        if (cudaMalloc(&h->bw_tiles, std::max<size_t>(1, tiles.size()) * sizeof(uint64_t)) != cudaSuccess ||
+            cudaMalloc(&h->bw_tilecam, std::max<size_t>(1, tilecam.size()) * sizeof(int4)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h->bw_tiles);
+            h->bw_tiles = nullptr;
+            return fail(PSFS_ERR_NOMEM, "adjoint sequence tile plan");
+        }
+        PSFS_CK(cudaMemcpyAsync(h->bw_tiles, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                h->stream));
+        PSFS_CK(cudaMemcpyAsync(h->bw_tilecam, tilecam.data(), tilecam.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice, h->stream));
+        PSFS_CK(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
+        fa.tiles = h->bw_tiles;
+        fa.tilecam = h->bw_tilecam;
+        fa.maps = h->bw_maps;
+        fa.tmap_ok = 0;
+        fa.status = h->d_words;
+        h->bw_fuse = fa;
+    }
+    return PSFS_OK;
+}
+
+// Frames in groups of kBwRecord.  A group of nf frames runs in units of 8, 4,
+// 2 and 1 frames (the binary digits of nf, largest first, so that a unit of
+// P frames starts at a record slot that is a multiple of P): per unit one
+// likelihood pass over the background for its P frames (maps as one plane
+// of P-frame records) and one voxel pass that gathers each record once per
+// (voxel, camera) and writes dLoss/dL of the P frames into their slots; then
+// one pixel pass for the group.  Per frame the arithmetic is that of
+// psfs_backward, so d_slm is bit-identical to it.
+static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
+                                             const float *d_occ, float *d_slm, float *d_mean, float *d_var)
+{
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
     psfs_status st = ensure_owner_lists(h);
+    if (st == PSFS_OK) st = ensure_backward_group(h);
     if (st != PSFS_OK) return st;
     BackwardArgs b;
     fill_backward_args(h, b);
@@ -1271,29 +1327,41 @@ static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, c
     const size_t frame_bytes = (size_t)h->n_pix * 3;
     for (int g0 = 0; g0 < n_frames; g0 += kBwRecord) {
         const int nf = std::min(kBwRecord, n_frames - g0);
-        for (int f = 0; f < nf; ++f) {
+        for (int slot = 0, P = kBwRecord; P >= 1; P /= 2) {
+            if (!(nf & P)) continue;
+            const size_t f0 = (size_t)g0 + slot;   // the unit's first frame
             LikelihoodArgs la{};
-            la.img = images + (size_t)(g0 + f) * frame_bytes;
+            la.img = images + f0 * frame_bytes;
             la.mean = h->bg_mean;
             la.hinv = h->bg_hinv;
             la.n_pix = h->n_pix;
             la.c0 = h->c0;
             la.sc = h->sc;
-            la.out = h->maps;
+            la.out = h->bw_maps;
             la.zero_word = nullptr;
             la.status = h->d_words;
+            la.img_fstride = (int64_t)frame_bytes;
             {
                 ProfScope ps(h, PSFS_STAGE_LIKELIHOOD);
-                PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, h->stream));
+                if (P > 1)
+                    PSFS_CK(launch_likelihood_group(la, P, h->params.map_dtype, h->stream, 4));
+                else
+                    PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, h->stream));
             }
             BackwardArgs bv = b;
-            bv.d_occ = d_occ + (size_t)(g0 + f) * n_vox;
-            bv.dl = h->dl_rec + f;
+            bv.f = h->bw_fuse;
+            bv.d_occ = d_occ + f0 * n_vox;
+            bv.dl = h->dl_rec + slot;
             bv.dl_stride = kBwRecord;
-            ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL);
-            FuseShape direct = h->shape;
-            direct.staged = 0;
-            PSFS_CK(launch_backward_voxel(bv, direct, h->params.map_dtype, h->stream));
+            {
+                ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL);
+                if (P > 1)
+                    PSFS_CK(launch_backward_voxel_group(bv, kBwShape, P, h->params.map_dtype, (int64_t)n_vox,
+                                                        h->stream));
+                else
+                    PSFS_CK(launch_backward_voxel(bv, kBwShape, h->params.map_dtype, h->stream));
+            }
+            slot += P;
         }
         BackwardArgs bp = b;
         bp.dl = h->dl_rec;

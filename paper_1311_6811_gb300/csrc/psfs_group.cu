@@ -355,30 +355,20 @@ __device__ __forceinline__ void group_epilogue(const FuseArgs &a, int i, int j, 
 }
 
 // The tile decomposition, per-tile camera records and projection are those of
-// the direct fuse kernel; a thread holds F x TZ log-odds accumulators.
+// the direct fuse kernel; a thread holds F x TZ log-odds accumulators.  The
+// gather of one tile: every camera in order 0 .. n_cams - 1, one vector load
+// of the F frames' log ratios per (voxel, camera).  s_flags must hold the
+// tile's camera flags (a barrier after they were written).
 template <typename MapT, int LX, int WY, int TZ, int F>
-__global__ void __launch_bounds__(32 * WY) fuse_group_kernel(const __grid_constant__ FuseArgs a)
+__device__ __forceinline__ void group_gather(const FuseArgs &a, const TileCoords<LX, WY, TZ> &tc,
+                                             const int *s_flags, float (&L)[F][TZ])
 {
     using Words = GroupWords<MapT, F>;
-    __shared__ int s_flags[PSFS_MAX_CAMS];
-    __shared__ uint32_t s_off[F][WY];
-    __shared__ uint32_t s_base[F];
-
-    const int lane = threadIdx.x;
-    const int wy = threadIdx.y;
-    const int tid = wy * 32 + lane;
-    if (tid < a.n_cams) s_flags[tid] = __ldg(&a.tilecam[(int64_t)blockIdx.x * a.n_cams + tid].w) >> 16;
-
-    TileCoords<LX, WY, TZ> tc;
-    tc.init(a, a.tiles[blockIdx.x], lane, wy);
     const uint32_t W = (uint32_t)a.W, H = (uint32_t)a.H;
-    float L[F][TZ];
 #pragma unroll
     for (int f = 0; f < F; ++f)
 #pragma unroll
         for (int t = 0; t < TZ; ++t) L[f][t] = 0.0f;
-    __syncthreads();
-
     const uint32_t *maps = reinterpret_cast<const uint32_t *>(a.maps);
     const uint32_t last_pix = W * H - 1u;
     const uint32_t bias_off = 0u - (kFloorBias * W + kFloorBias);
@@ -415,7 +405,63 @@ __global__ void __launch_bounds__(32 * WY) fuse_group_kernel(const __grid_consta
             }
         }
     }
+}
+
+template <typename MapT, int LX, int WY, int TZ, int F>
+__global__ void __launch_bounds__(32 * WY) fuse_group_kernel(const __grid_constant__ FuseArgs a)
+{
+    __shared__ int s_flags[PSFS_MAX_CAMS];
+    __shared__ uint32_t s_off[F][WY];
+    __shared__ uint32_t s_base[F];
+
+    const int lane = threadIdx.x;
+    const int wy = threadIdx.y;
+    const int tid = wy * 32 + lane;
+    if (tid < a.n_cams) s_flags[tid] = __ldg(&a.tilecam[(int64_t)blockIdx.x * a.n_cams + tid].w) >> 16;
+
+    TileCoords<LX, WY, TZ> tc;
+    tc.init(a, a.tiles[blockIdx.x], lane, wy);
+    float L[F][TZ];
+    __syncthreads();
+    group_gather<MapT, LX, WY, TZ, F>(a, tc, s_flags, L);
     group_epilogue<WY, TZ, F>(a, tc.i, tc.j, tc.k0, L, lane, wy, s_off, s_base);
+}
+
+// The adjoint's voxel pass over F frames of records (psfs_backward_sequence):
+// the log-odds of the F frames exactly as fuse_group_kernel forms them, then
+// per voxel and frame dLoss/dL = d_occ occ (1 - occ), written to slots 0 ..
+// F - 1 of the voxel's record at b.dl + lin * kBwRecord (b.dl already points
+// at the unit's first slot; F <= kBwRecord).  Frame f's d_occ is at b.d_occ +
+// f * docc_fstride.
+template <typename MapT, int LX, int WY, int TZ, int F>
+__global__ void __launch_bounds__(32 * WY) backward_voxel_group_kernel(const __grid_constant__ BackwardArgs b,
+                                                                       int64_t docc_fstride)
+{
+    static_assert(F <= kBwRecord, "a unit fills at most one record");
+    const FuseArgs &a = b.f;
+    __shared__ int s_flags[PSFS_MAX_CAMS];
+    const int lane = threadIdx.x;
+    const int wy = threadIdx.y;
+    const int tid = wy * 32 + lane;
+    if (tid < a.n_cams) s_flags[tid] = __ldg(&a.tilecam[(int64_t)blockIdx.x * a.n_cams + tid].w) >> 16;
+    TileCoords<LX, WY, TZ> tc;
+    tc.init(a, a.tiles[blockIdx.x], lane, wy);
+    float L[F][TZ];
+    __syncthreads();
+    group_gather<MapT, LX, WY, TZ, F>(a, tc, s_flags, L);
+    if (tc.i >= a.nx || tc.j >= a.ny) return;
+#pragma unroll
+    for (int t = 0; t < TZ; ++t) {
+        const int k = tc.k0 + t;
+        if (k >= a.nz) break;
+        const uint32_t lin = (uint32_t)tc.i + (uint32_t)a.nx * ((uint32_t)tc.j + (uint32_t)a.ny * (uint32_t)k);
+        float *rec = b.dl + (size_t)lin * kBwRecord;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const float occ = posterior_of_logodds(L[f][t] + a.logit_prior);
+            rec[f] = __ldg(b.d_occ + f * docc_fstride + lin) * occ * (1.0f - occ);
+        }
+    }
 }
 
 template <typename MapT, int LX, int TZ, int F>
@@ -462,7 +508,40 @@ cudaError_t launch_fg_typed(const FuseArgs &a, const FuseShape &sh, int frames, 
     return cudaErrorInvalidValue;
 }
 
+template <typename MapT, int F>
+cudaError_t launch_bvg(const BackwardArgs &b, const FuseShape &sh, int64_t docc_fstride, cudaStream_t s)
+{
+    if (sh.wy != 4 || sh.staged || sh.tz != 4) return cudaErrorInvalidValue;
+    if (sh.lx == 8)
+        backward_voxel_group_kernel<MapT, 8, 4, 4, F><<<b.f.n_tiles, dim3(32, 4), 0, s>>>(b, docc_fstride);
+    else if (sh.lx == 16)
+        backward_voxel_group_kernel<MapT, 16, 4, 4, F><<<b.f.n_tiles, dim3(32, 4), 0, s>>>(b, docc_fstride);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <typename MapT>
+cudaError_t launch_bvg_typed(const BackwardArgs &b, const FuseShape &sh, int frames, int64_t docc_fstride,
+                             cudaStream_t s)
+{
+    if (((uintptr_t)b.f.maps) & (uintptr_t)(frames * sizeof(MapT) - 1)) return cudaErrorMisalignedAddress;
+    if (frames == 2) return launch_bvg<MapT, 2>(b, sh, docc_fstride, s);
+    if (frames == 4) return launch_bvg<MapT, 4>(b, sh, docc_fstride, s);
+    if (frames == 8) return launch_bvg<MapT, 8>(b, sh, docc_fstride, s);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
+
+cudaError_t launch_backward_voxel_group(const BackwardArgs &b, const FuseShape &shape, int frames, int map_dtype,
+                                        int64_t docc_fstride, cudaStream_t s)
+{
+    if (b.f.n_tiles <= 0) return cudaSuccess;
+    if (map_dtype == PSFS_MAP_F16) return launch_bvg_typed<__half>(b, shape, frames, docc_fstride, s);
+    if (map_dtype == PSFS_MAP_BF16) return launch_bvg_typed<__nv_bfloat16>(b, shape, frames, docc_fstride, s);
+    return launch_bvg_typed<float>(b, shape, frames, docc_fstride, s);
+}
 
 bool group_size_supported(int frames)
 {

@@ -624,6 +624,12 @@ cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map
                                     int ctas_per_sm);
 cudaError_t launch_fuse_group(const FuseArgs &a, const FuseShape &shape, int frames, int map_dtype,
                               cudaStream_t s);
+// The adjoint's voxel pass over a unit of `frames` (2, 4 or 8) frames whose
+// maps are one plane of records ([n_pix][frames], b.f.maps), tile shape
+// lanes_x 8 or 16, voxels_z 4: dLoss/dL of frame f into slot f of each
+// voxel's record (b.dl points at the unit's first slot).
+cudaError_t launch_backward_voxel_group(const BackwardArgs &b, const FuseShape &shape, int frames, int map_dtype,
+                                        int64_t docc_fstride, cudaStream_t s);
 
 // Host planning (psfs_plan.cu): projection matrices, tile order and staging
 // records of the fuse kernel for one grid and camera rig.

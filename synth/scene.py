@@ -522,3 +522,32 @@ def scene_256cube_16cam(seed: int = 2) -> Scene:
     """256^3 grid over a 3.0 m cube, 16 cameras 1280x720 (f = 1200 px), two bodies."""
     return make_scene(seed=seed, grid_n=256, cube_side=3.0, n_cams=16, width=1280, height=720,
                       focal=1200.0, heights=(1.2, 2.2), n_bodies=2)
+
+
+def _scene_from_kwargs(kw):
+    return make_scene(**kw)
+
+
+def batch_64_specs(seed: int = 64, n_frames: int = 64) -> List[dict]:
+    """make_scene arguments of the heterogeneous batch: grids drawn uniformly
+    from {96, 128, 160, 192}^3 over a 2.2 m cube, 4-12 cameras, 640x480
+    (f = 600 px) or 960x540 (f = 900 px), each frame with its own seed (its
+    own rig, background and body pose)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_frames):
+        n = int(rng.choice([96, 128, 160, 192]))
+        K = int(rng.integers(4, 13))
+        W, H, f = (640, 480, 600.0) if rng.random() < 0.5 else (960, 540, 900.0)
+        out.append(dict(seed=100 + k, grid_n=n, cube_side=2.2, n_cams=K, width=W, height=H, focal=f))
+    return out
+
+
+def batch_64_scenes(seed: int = 64, n_frames: int = 64, workers: int = 1) -> List[Scene]:
+    """The 64 heterogeneous frames of the batched launch (batch_64_specs)."""
+    specs = batch_64_specs(seed, n_frames)
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, len(specs))) as pool:
+            return pool.map(_scene_from_kwargs, specs, chunksize=1)
+    return [make_scene(**kw) for kw in specs]

@@ -99,14 +99,8 @@ def test_batch_equals_frame_by_frame_and_oracle():
 def test_batch_64_heterogeneous_frames():
     """64 frames, grids drawn from {96, 128, 160, 192}^3, 4-12 cameras, 640x480
     or 960x540, own pose and background per frame, one graph launch."""
-    rng = np.random.default_rng(64)
-    specs = []
-    for _ in range(64):
-        n = int(rng.choice([96, 128, 160, 192]))
-        K = int(rng.integers(4, 13))
-        W, H, f = (640, 480, 600.0) if rng.random() < 0.5 else (960, 540, 900.0)
-        specs.append((n, 2.2, K, W, H, f))
-    scenes = _frames(specs, seed=100)
+    import os
+    scenes = S.batch_64_scenes(seed=64, workers=max(1, min(8, os.cpu_count() or 1)))
     b, recs, outs = _run_batch(scenes, tune=True)
     for k, ((rec, img), o) in enumerate(zip(recs, outs)):
         g = _host(o)
