@@ -3,6 +3,10 @@ libpsfs (marshalling only: both directions run in the library's kernels).
 
   occ = psfs_occupancy(rec, images, mean, var)   # grads for mean and var
   occ = psfs_occupancy_from_slm(rec, slm)        # grad for the SLM maps
+  occ = psfs_occupancy_sequence(rec, images, mean, var)
+      # F frames [F][n_cams][H][W][3] -> [F][nz][ny][nx]: the sequence path
+      # forward (frame groups) and the batched adjoint; the background is
+      # shared by the frames, so its gradients are summed over them
 
 `rec` is a `Reconstructor`; the forward is recomputed in the backward (only
 the uint8 images, or the maps, are saved), so nothing of size n_voxels x
@@ -52,6 +56,36 @@ class _OccupancyFromSlm(torch.autograd.Function):
         d_slm = torch.empty_like(slm)
         psfs.psfs_backward_slm(ctx.rec.handle, slm, grad_occ.contiguous().float(), d_slm)
         return None, d_slm
+
+
+class _OccupancySequence(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rec, images, mean, var):
+        rec.set_background(mean.detach().contiguous(), var.detach().contiguous())
+        n = images.shape[0]
+        occ = torch.empty((n, *rec.shape), dtype=torch.float32, device=images.device)
+        counts = torch.zeros(n, dtype=torch.int32, device=images.device)
+        # occupancy only: no voxel lists (capacity 0; counts are still formed)
+        psfs.psfs_reconstruct_sequence(rec.handle, n, images, occ, None, 0, counts)
+        ctx.rec = rec
+        ctx.save_for_backward(images)
+        ctx.shapes = (mean.shape, var.shape)
+        return occ
+
+    @staticmethod
+    def backward(ctx, grad_occ):
+        (images,) = ctx.saved_tensors
+        d_mean = torch.empty(ctx.shapes[0], dtype=torch.float32, device=images.device)
+        d_var = torch.empty(ctx.shapes[1], dtype=torch.float32, device=images.device)
+        psfs.psfs_backward_sequence(ctx.rec.handle, images.shape[0], images, grad_occ.contiguous().float(), None,
+                                    d_mean, d_var)
+        return None, None, d_mean, d_var
+
+
+def psfs_occupancy_sequence(rec, images, mean, var):
+    """Posterior occupancy [F][nz][ny][nx] of F frames; differentiable in the
+    shared background `mean` and `var` (gradients summed over the frames)."""
+    return _OccupancySequence.apply(rec, images, mean, var)
 
 
 def psfs_occupancy(rec, images, mean, var):

@@ -14,7 +14,8 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from paper_1311_6811_gb300 import psfs  # noqa: E402
-from paper_1311_6811_gb300.autograd import psfs_occupancy, psfs_occupancy_from_slm  # noqa: E402
+from paper_1311_6811_gb300.autograd import (psfs_occupancy, psfs_occupancy_from_slm,  # noqa: E402
+                                             psfs_occupancy_sequence)
 from synth import scene as S  # noqa: E402
 from tests.gpu_helpers import to_dev  # noqa: E402
 
@@ -326,4 +327,37 @@ def test_reduced_precision_adjoint_error_vs_fp64(dtype, bound):
         errs[name] = float(np.abs(g - w).max() / max(np.abs(w).max(), 1e-30))
     print(dtype, "adjoint error vs FP64 (max |err| / max |grad|):", errs)
     assert max(errs.values()) < bound, errs
+    rec.close()
+
+
+def test_autograd_sequence_function_matches_per_frame():
+    """psfs_occupancy_sequence over 10 frames (the sequence forward and the
+    batched adjoint): its occupancy equals psfs_occupancy frame by frame bit for
+    bit, and its background gradients are the frame-ordered sums of the
+    per-frame Function's."""
+    n = 10
+    sc = S.make_scene(seed=47, grid_n=32, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0,
+                      n_frames=n, walking=True)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 4, 0, 2, 8)
+    imgs = to_dev(sc.images)
+    tgt = torch.from_numpy(np.random.default_rng(47).uniform(0, 1, (n, *rec.shape)).astype(np.float32)).cuda()
+    mean = to_dev(sc.mean).requires_grad_(True)
+    var = to_dev(sc.var).requires_grad_(True)
+    occ = psfs_occupancy_sequence(rec, imgs, mean, var)
+    ((occ - tgt) ** 2).sum().backward()
+    gm, gv = mean.grad.clone(), var.grad.clone()
+    sm = torch.zeros_like(gm)
+    sv = torch.zeros_like(gv)
+    for f in range(n):
+        m1 = to_dev(sc.mean).requires_grad_(True)
+        v1 = to_dev(sc.var).requires_grad_(True)
+        o1 = psfs_occupancy(rec, imgs[f], m1, v1)
+        assert torch.equal(o1, occ[f].detach()), f
+        ((o1 - tgt[f]) ** 2).sum().backward()
+        sm += m1.grad
+        sv += v1.grad
+    torch.cuda.synchronize()
+    assert torch.equal(gm, sm) and torch.equal(gv, sv)
+    assert float(gm.abs().max()) > 0
     rec.close()
