@@ -1129,12 +1129,39 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
         stream.synchronize()
         assert rec.sync() == psfs.PSFS_OK
         out[f"{dtype}_batched_forward_backward_us"] = 1e3 * e[0].elapsed_time(e[3]) / nseq
+        # the same with the adjoint formed from the forward's own occupancy
+        # (psfs_backward_from_occupancy: no recomputed maps or voxel pass)
+        with torch.cuda.stream(stream):
+            for rep in range(2):
+                if rep == 1:
+                    e[0].record(stream)
+                psfs.psfs_reconstruct_sequence(rec.handle, nseq, d_images[:nseq], occ_s, lst_s, cap_s, cnt_s)
+                torch.sub(occ_s, occ_f32[:nseq], out=d_occ_s)
+                d_occ_s.mul_(2.0)
+                psfs.psfs_backward_from_occupancy(rec.handle, nseq, d_images[:nseq], occ_s, d_occ_s, d_slm_s,
+                                                  d_mean, d_var)
+            e[3].record(stream)
+        stream.synchronize()
+        assert rec.sync() == psfs.PSFS_OK
+        out[f"{dtype}_batched_forward_backward_from_occupancy_us"] = 1e3 * e[0].elapsed_time(e[3]) / nseq
+        with torch.cuda.stream(stream):
+            e[0].record(stream)
+            for f in range(F):
+                rec.reconstruct(d_images[f], (o, lst, cnt))
+                torch.sub(o.view(-1), occ_f32[max(f - 1, 0)], out=d_occ)
+                d_occ.mul_(2.0)
+                psfs.psfs_backward_from_occupancy(rec.handle, 1, d_images[f], o, d_occ, d_slm, d_mean, d_var)
+            e[3].record(stream)
+        stream.synchronize()
+        assert rec.sync() == psfs.PSFS_OK
+        out[f"{dtype}_forward_backward_from_occupancy_us"] = 1e3 * e[0].elapsed_time(e[3]) / F
         rec.close()
     out["note"] = ("*_forward_us / *_forward_backward_us: one frame per call (no stream overlap); backward = "
                    "recomputed maps + voxel pass + per-pixel owner pass + chain rule to SLM, mean, var.  "
                    "*_batched_forward_us: psfs_reconstruct_sequence over 32 frames in frame groups; "
                    "*_batched_forward_backward_us: that forward + loss gradient + psfs_backward_sequence "
-                   "(owner passes of 8 frames)")
+                   "(recomputed forward in groups of 8 frames, owner passes of 8 frames); "
+                   "*_from_occupancy_us: the adjoint from the forward's own occupancy (psfs_backward_from_occupancy)")
     return out
 
 

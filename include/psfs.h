@@ -348,8 +348,13 @@ psfs_status psfs_get_log_ratio(psfs_handle *h, const uint8_t *images, void *map_
  *   d_mean  device float32 [n_cams][height][width][3]  dLoss/d mean
  *   d_var   device float32 [n_cams][height][width][3]  dLoss/d var
  * Pixels that no voxel centre projects to get exactly zero.  Deterministic:
- * no atomics; each pixel's sum is formed by the thread that owns it.
- * Errors: INVALID_ARG, NOT_READY, CUDA. */
+ * each pixel's sum over the voxels that project into it is formed by the
+ * thread that owns the pixel, in ascending voxel order, without float
+ * atomics.  The first adjoint call of a handle builds its owner lists (for
+ * every pixel, the voxels whose centre the forward projects into it: 4 bytes
+ * per (voxel, camera) pair plus 4 per pixel, kept until psfs_destroy); it
+ * needs nx * ny * nz * n_cams < 2^32 (else INVALID_ARG).
+ * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */
 psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_occ,
                           float *d_slm, float *d_mean, float *d_var);
 
@@ -358,16 +363,33 @@ psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_
  * (device, 16-byte aligned), and writes d_slm + f * (n_cams * height * width)
  * (may be NULL).  d_mean and d_var (may be NULL) receive the sum over the
  * frames of each frame's gradient, added in frame order (the background model
- * is shared by the frames).  Frames go through the recomputed forward and the
- * voxel pass one by one, and through the per-pixel owner pass in groups of up
- * to 8 frames: one walk of each pixel's ray serves the group.  Each frame's
- * d_slm is bit-identical to psfs_backward's; d_mean and d_var equal the FP32
- * sum, in frame order, of psfs_backward's.  Scratch: 8 * nx * ny * nz floats
- * (first call).  Requirements as psfs_reconstruct_sequence (frame size and
- * voxel count multiples of 16 and 4).  Errors: INVALID_ARG, NOT_READY, NOMEM,
- * CUDA. */
+ * is shared by the frames).  Frames go in groups of up to 8: per group the
+ * recomputed forward reads the background once for up to 8 frames and
+ * gathers each voxel's log ratios of those frames with one load per camera,
+ * dLoss/dL goes into 32-byte per-voxel records of the group's frames, and
+ * one per-pixel owner pass reads one record per owned voxel for the whole
+ * group.  Each frame's d_slm is bit-identical to psfs_backward's; d_mean and
+ * d_var equal the FP32 sum, in frame order, of psfs_backward's.  Scratch
+ * (first call): 8 * nx * ny * nz floats, maps of 8 frames, a tile plan, and
+ * the owner lists of psfs_backward.  Requirements as psfs_reconstruct_sequence
+ * (frame size and voxel count multiples of 16 and 4).  Errors: INVALID_ARG,
+ * NOT_READY, NOMEM, CUDA. */
 psfs_status psfs_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
                                    const float *d_occ, float *d_slm, float *d_mean, float *d_var);
+
+/* The adjoint of psfs_reconstruct / psfs_reconstruct_sequence from the
+ * forward's own output: `occupancy` (device float32 [n_frames][nz][ny][nx])
+ * must be what the forward gave for these `images` on this handle with its
+ * current background.  dLoss/dL = d_occ occ (1 - occ) is then formed
+ * elementwise, so the maps and the log-odds are not recomputed; the pixel
+ * passes and the outputs are those of psfs_backward (n_frames = 1) and
+ * psfs_backward_sequence (n_frames > 1: d_slm per frame [n_frames][n_cams]
+ * [height][width], d_mean and d_var summed over the frames), with the same
+ * bits when `occupancy` is the forward's.  Errors: INVALID_ARG, NOT_READY,
+ * NOMEM, CUDA. */
+psfs_status psfs_backward_from_occupancy(psfs_handle *h, int32_t n_frames, const uint8_t *images,
+                                         const float *occupancy, const float *d_occ, float *d_slm,
+                                         float *d_mean, float *d_var);
 
 /* Adjoint of psfs_fuse_slm: given the SLM maps `slm` of the forward (device
  * float32 [n_cams][height][width]) and d_occ, writes dLoss/dSLM to d_slm

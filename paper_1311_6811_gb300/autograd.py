@@ -8,9 +8,11 @@ libpsfs (marshalling only: both directions run in the library's kernels).
       # forward (frame groups) and the batched adjoint; the background is
       # shared by the frames, so its gradients are summed over them
 
-`rec` is a `Reconstructor`; the forward is recomputed in the backward (only
-the uint8 images, or the maps, are saved), so nothing of size n_voxels x
-n_cams is kept between the two passes.
+`rec` is a `Reconstructor`.  The Functions over images keep the uint8 images
+and their own output (the occupancy) for the backward, which then forms
+dLoss/dL from that occupancy (psfs_backward_from_occupancy) instead of
+recomputing the forward; nothing of size n_voxels x n_cams is kept between
+the two passes.  The SLM Function keeps the maps and recomputes.
 """
 
 from __future__ import annotations
@@ -26,18 +28,19 @@ class _Occupancy(torch.autograd.Function):
         rec.set_background(mean.detach().contiguous(), var.detach().contiguous())
         occ, _, _ = rec.reconstruct(images)
         ctx.rec = rec
-        ctx.save_for_backward(images)
+        ctx.save_for_backward(images, occ)
         ctx.shapes = (mean.shape, var.shape)
-        ctx.mark_non_differentiable()
         return occ
 
     @staticmethod
     def backward(ctx, grad_occ):
-        (images,) = ctx.saved_tensors
+        images, occ = ctx.saved_tensors
         rec = ctx.rec
         d_mean = torch.empty(ctx.shapes[0], dtype=torch.float32, device=images.device)
         d_var = torch.empty(ctx.shapes[1], dtype=torch.float32, device=images.device)
-        psfs.psfs_backward(rec.handle, images, grad_occ.contiguous().float(), None, d_mean, d_var)
+        # the forward's own occupancy: nothing of the forward is recomputed
+        psfs.psfs_backward_from_occupancy(rec.handle, 1, images, occ, grad_occ.contiguous().float(), None, d_mean,
+                                          d_var)
         return None, None, d_mean, d_var
 
 
@@ -68,17 +71,17 @@ class _OccupancySequence(torch.autograd.Function):
         # occupancy only: no voxel lists (capacity 0; counts are still formed)
         psfs.psfs_reconstruct_sequence(rec.handle, n, images, occ, None, 0, counts)
         ctx.rec = rec
-        ctx.save_for_backward(images)
+        ctx.save_for_backward(images, occ)
         ctx.shapes = (mean.shape, var.shape)
         return occ
 
     @staticmethod
     def backward(ctx, grad_occ):
-        (images,) = ctx.saved_tensors
+        images, occ = ctx.saved_tensors
         d_mean = torch.empty(ctx.shapes[0], dtype=torch.float32, device=images.device)
         d_var = torch.empty(ctx.shapes[1], dtype=torch.float32, device=images.device)
-        psfs.psfs_backward_sequence(ctx.rec.handle, images.shape[0], images, grad_occ.contiguous().float(), None,
-                                    d_mean, d_var)
+        psfs.psfs_backward_from_occupancy(ctx.rec.handle, images.shape[0], images, occ,
+                                          grad_occ.contiguous().float(), None, d_mean, d_var)
         return None, None, d_mean, d_var
 
 

@@ -1405,6 +1405,81 @@ psfs_status psfs_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8
     return enqueue_backward_sequence(h, n_frames, images, d_occ, d_slm, d_mean, d_var);
 }
 
+// The adjoint from the forward's own occupancy: dLoss/dL = d_occ occ (1 - occ)
+// elementwise (no recomputed maps, no voxel pass), then the pixel passes of
+// psfs_backward (one frame) or psfs_backward_sequence (records of 8 frames).
+static psfs_status enqueue_backward_from_occupancy(psfs_handle *h, int32_t n_frames, const uint8_t *images,
+                                                   const float *occupancy, const float *d_occ, float *d_slm,
+                                                   float *d_mean, float *d_var)
+{
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    psfs_status st = ensure_owner_lists(h);
+    if (st != PSFS_OK) return st;
+    float **scratch = n_frames == 1 ? &h->dl : &h->dl_rec;
+    const size_t elems = n_frames == 1 ? n_vox : (size_t)kBwRecord * n_vox;
+    if (!*scratch) {
+        if (cudaMalloc(scratch, elems * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PSFS_ERR_NOMEM, "adjoint scratch");
+        }
+    }
+    BackwardArgs b;
+    fill_backward_args(h, b);
+    b.d_mean = d_mean;
+    b.d_var = d_var;
+    if (n_frames == 1) {
+        b.dl = h->dl;
+        b.img = images;
+        b.d_slm = d_slm;
+        {
+            ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL);
+            PSFS_CK(launch_dl_from_occ(occupancy, d_occ, h->dl, (int64_t)n_vox, 1, 1, h->stream));
+        }
+        ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL);
+        PSFS_CK(launch_owner_pixel(b, h->own_off, h->own_vox, h->stream));
+        return PSFS_OK;
+    }
+    const size_t frame_bytes = (size_t)h->n_pix * 3;
+    for (int g0 = 0; g0 < n_frames; g0 += kBwRecord) {
+        const int nf = std::min(kBwRecord, n_frames - g0);
+        {
+            ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL);
+            PSFS_CK(launch_dl_from_occ(occupancy + (size_t)g0 * n_vox, d_occ + (size_t)g0 * n_vox, h->dl_rec,
+                                       (int64_t)n_vox, nf, kBwRecord, h->stream));
+        }
+        BackwardArgs bp = b;
+        bp.dl = h->dl_rec;
+        bp.dl_stride = kBwRecord;
+        bp.img = images + (size_t)g0 * frame_bytes;
+        bp.d_slm = d_slm ? d_slm + (size_t)g0 * h->n_pix : nullptr;
+        ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL);
+        PSFS_CK(launch_owner_pixel_group(bp, h->own_off, h->own_vox, nf, (int64_t)frame_bytes, g0 > 0, h->stream));
+    }
+    return PSFS_OK;
+}
+
+psfs_status psfs_backward_from_occupancy(psfs_handle *h, int32_t n_frames, const uint8_t *images,
+                                         const float *occupancy, const float *d_occ, float *d_slm, float *d_mean,
+                                         float *d_var)
+{
+    if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");
+    if (n_frames < 0) return fail(PSFS_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames == 0) return PSFS_OK;
+    if (!images || !aligned(images, 16)) return fail(PSFS_ERR_INVALID_ARG, "images NULL or not 16-byte aligned");
+    if (n_frames > 1 && (h->n_pix * 3) % 16 != 0)
+        return fail(PSFS_ERR_INVALID_ARG, "frame size not a multiple of 16 bytes");
+    const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
+    if (n_frames > 1 && n_vox % 4 != 0) return fail(PSFS_ERR_INVALID_ARG, "voxel count not a multiple of 4");
+    if (!occupancy || !aligned(occupancy, 16))
+        return fail(PSFS_ERR_INVALID_ARG, "occupancy NULL or not 16-byte aligned");
+    if (!d_occ || !aligned(d_occ, 16)) return fail(PSFS_ERR_INVALID_ARG, "d_occ NULL or not 16-byte aligned");
+    if ((d_slm && !aligned(d_slm, 16)) || (d_mean && !aligned(d_mean, 16)) || (d_var && !aligned(d_var, 16)))
+        return fail(PSFS_ERR_INVALID_ARG, "gradient buffer not 16-byte aligned");
+    if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
+    DeviceGuard guard(h->device);
+    return enqueue_backward_from_occupancy(h, n_frames, images, occupancy, d_occ, d_slm, d_mean, d_var);
+}
+
 psfs_status psfs_backward_slm(psfs_handle *h, const float *slm, const float *d_occ, float *d_slm)
 {
     if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");

@@ -567,6 +567,10 @@ cudaError_t launch_build_owners(const FuseArgs &a, int64_t n_pix, uint32_t *cnt,
 // Pixel pass of one frame (b.dl dense, dl_stride 1), and of n_frames <=
 // kBwRecord frames of records (frame f's colour at b.img + f img_fstride).
 cudaError_t launch_owner_pixel(const BackwardArgs &b, const uint32_t *off, const uint32_t *vox, cudaStream_t s);
+// dLoss/dL = d_occ occ (1 - occ) of n_frames frames (occ and d_occ [n_frames][n_vox]) from a given
+// occupancy: dl[v * dl_stride + f] (dl_stride 1 with one frame, or kBwRecord).
+cudaError_t launch_dl_from_occ(const float *occ, const float *d_occ, float *dl, int64_t n_vox, int n_frames,
+                               int dl_stride, cudaStream_t s);
 cudaError_t launch_owner_pixel_group(const BackwardArgs &b, const uint32_t *off, const uint32_t *vox, int n_frames,
                                      int64_t img_fstride, bool accumulate, cudaStream_t s);
 cudaError_t launch_fuse(const FuseArgs &a, const FuseShape &shape, int map_dtype, cudaStream_t s);

@@ -233,13 +233,43 @@ __global__ void __launch_bounds__(256) owner_pixel_kernel(const __grid_constant_
     }
 }
 
+// Chain rule of one frame from the pixel's background loaded once: h = 1 /
+// (2 var), base = c0 - log(h0 h1 h2) / 2 (pixel_log_base), so that r = base
+// + pixel_quad is pixel_log_odds bit for bit and the result that of
+// chain_rule.
+__device__ __forceinline__ void chain_rule_pre(const BackwardArgs &b, const uint8_t *im, const float (&mu)[3],
+                                               const float (&hh)[3], float base, float acc, float &dslm,
+                                               float (&dm)[3], float (&dv)[3])
+{
+    dslm = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dm[c] = dv[c] = 0.0f;
+    if (acc != 0.0f) {
+        float dd[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dd[c] = (float)im[c] - mu[c];
+        const float r = base + pixel_quad((float)im[0], (float)im[1], (float)im[2], mu[0], mu[1], mu[2], hh[0],
+                                          hh[1], hh[2]);
+        const float s_val = sigmoid_fast(r);
+        const float av = fmaf(b.da, s_val, b.one_minus_pd), bv = fmaf(b.db, s_val, b.one_minus_q);
+        dslm = acc * (b.da / av - b.db / bv);
+        const float dr = acc * dlog_ratio_dr(r, b.sc);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            dm[c] = -2.0f * dr * dd[c] * hh[c];
+            dv[c] = dr * hh[c] * (1.0f - 2.0f * dd[c] * dd[c] * hh[c]);
+        }
+    }
+}
+
 // Up to kBwRecord frames: b.dl holds records of kBwRecord floats per voxel
 // (frame f of voxel v at b.dl[v * kBwRecord + f]), one 32-byte load per
 // owned voxel serves every frame.  Per frame the sum (same voxels, same
 // order) and the chain rule are those of owner_pixel_kernel, so d_slm (frame
 // f at b.d_slm + f n_pix) is bit-identical to one frame per call; d_mean and
 // d_var receive the frames' gradients added in frame order to 0 (or, with
-// `accumulate`, to what they hold).
+// `accumulate`, to what they hold).  The pixel's background is read once for
+// all frames.
 __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_constant__ BackwardArgs b,
                                                                 const uint32_t *off, const uint32_t *vox,
                                                                 int n_frames, int64_t img_fstride, int accumulate)
@@ -251,16 +281,14 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
 #pragma unroll
         for (int f = 0; f < kBwRecord; ++f) acc[f] = 0.0f;
         for (uint32_t e = e0; e < e1; ++e) {
-            const float4 *rec = reinterpret_cast<const float4 *>(b.dl + (size_t)__ldg(vox + e) * kBwRecord);
-            const float4 lo = __ldg(rec), hi = __ldg(rec + 1);
-            acc[0] += lo.x;
-            acc[1] += lo.y;
-            acc[2] += lo.z;
-            acc[3] += lo.w;
-            acc[4] += hi.x;
-            acc[5] += hi.y;
-            acc[6] += hi.z;
-            acc[7] += hi.w;
+            const float *rec = b.dl + (size_t)__ldg(vox + e) * kBwRecord;
+            uint32_t w[8];
+            // one 256-bit read-only load: the voxel's whole record (one sector)
+            asm("ld.global.nc.L1::no_allocate.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                : "l"(rec));
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(w[f]);
         }
         float tm[3] = {0.0f, 0.0f, 0.0f}, tv[3] = {0.0f, 0.0f, 0.0f};
         if (accumulate) {
@@ -270,11 +298,23 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
                 if (b.d_var) tv[c] = b.d_var[3 * p + c];
             }
         }
+        bool any = false;
+#pragma unroll
+        for (int f = 0; f < kBwRecord; ++f) any |= (f < n_frames) & (acc[f] != 0.0f);
+        float mu[3] = {0.0f, 0.0f, 0.0f}, hh[3] = {0.0f, 0.0f, 0.0f}, base = 0.0f;
+        if (any) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                mu[c] = __ldg(b.mean + 3 * p + c);
+                hh[c] = __ldg(b.hinv + 3 * p + c);
+            }
+            base = pixel_log_base(hh[0], hh[1], hh[2], b.c0);
+        }
 #pragma unroll
         for (int f = 0; f < kBwRecord; ++f) {
             if (f < n_frames) {
                 float dslm, dm[3], dv[3];
-                chain_rule(b, p, b.img + f * img_fstride, acc[f], dslm, dm, dv);
+                chain_rule_pre(b, b.img + f * img_fstride + 3 * p, mu, hh, base, acc[f], dslm, dm, dv);
                 if (b.d_slm) b.d_slm[f * b.n_pix + p] = dslm;
                 // separate round-to-nearest adds: the compiler may not fuse
                 // them with the products above, so the sums are those of the
@@ -290,6 +330,23 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
             for (int c = 0; c < 3; ++c) b.d_mean[3 * p + c] = tm[c];
         if (b.d_var)
             for (int c = 0; c < 3; ++c) b.d_var[3 * p + c] = tv[c];
+    }
+}
+
+// dLoss/dL = d_occ occ (1 - occ) from the forward's own occupancy (the
+// expression of the voxel passes, so the same bits as their recomputation):
+// n_frames frames of n_vox voxels, frame f's value into slot slot0 + f of
+// each voxel's record (dl_stride kBwRecord), or densely (dl_stride 1, one
+// frame).
+__global__ void __launch_bounds__(256) dl_from_occ_kernel(const float *occ, const float *d_occ, float *dl,
+                                                          int64_t n_vox, int n_frames, int dl_stride)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_vox; v += stride) {
+        for (int f = 0; f < n_frames; ++f) {
+            const float o = __ldg(occ + f * n_vox + v);
+            dl[v * dl_stride + f] = __ldg(d_occ + f * n_vox + v) * o * (1.0f - o);
+        }
     }
 }
 
@@ -333,6 +390,14 @@ cudaError_t launch_build_owners(const FuseArgs &a, int64_t n_pix, uint32_t *cnt,
     owner_fill_kernel<<<(int)vox_blocks, 256, 0, s>>>(a, off, cnt, vox);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     owner_sort_kernel<<<(int)grid_for(n_pix), 256, 0, s>>>(off, vox, n_pix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dl_from_occ(const float *occ, const float *d_occ, float *dl, int64_t n_vox, int n_frames,
+                               int dl_stride, cudaStream_t s)
+{
+    if (n_frames < 1 || n_frames > dl_stride) return cudaErrorInvalidValue;
+    dl_from_occ_kernel<<<(int)grid_for(n_vox), 256, 0, s>>>(occ, d_occ, dl, n_vox, n_frames, dl_stride);
     return cudaGetLastError();
 }
 

@@ -118,6 +118,7 @@ def load(build_if_missing: bool = True):
             "psfs_get_log_ratio": (st, [_vp, _vp, _vp]),
             "psfs_backward": (st, [_vp, _vp, _vp, _vp, _vp, _vp]),
             "psfs_backward_sequence": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
+            "psfs_backward_from_occupancy": (st, [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
             "psfs_backward_slm": (st, [_vp, _vp, _vp, _vp]),
             "psfs_reconstruct_noalloc": (st, [ctypes.POINTER(psfs_grid), ctypes.POINTER(psfs_camera),
                                               ctypes.c_int32, ctypes.POINTER(psfs_params), _vp, _vp, _vp,
@@ -406,6 +407,20 @@ def psfs_backward_sequence(h: int, n_frames: int, images, d_occ, d_slm=None, d_m
                                          _dev_ptr(d_slm, "d_slm", torch.float32),
                                          _dev_ptr(d_mean, "d_mean", torch.float32),
                                          _dev_ptr(d_var, "d_var", torch.float32)), "psfs_backward_sequence")
+
+
+def psfs_backward_from_occupancy(h: int, n_frames: int, images, occupancy, d_occ, d_slm=None, d_mean=None,
+                                 d_var=None):
+    """The adjoint from the forward's occupancy of these frames (no recomputed
+    forward); outputs as psfs_backward (one frame) / psfs_backward_sequence."""
+    import torch
+    _check(load().psfs_backward_from_occupancy(h, int(n_frames), _dev_ptr(images, "images", torch.uint8),
+                                               _dev_ptr(occupancy, "occupancy", torch.float32),
+                                               _dev_ptr(d_occ, "d_occ", torch.float32),
+                                               _dev_ptr(d_slm, "d_slm", torch.float32),
+                                               _dev_ptr(d_mean, "d_mean", torch.float32),
+                                               _dev_ptr(d_var, "d_var", torch.float32)),
+           "psfs_backward_from_occupancy")
 
 
 PSFS_NOALLOC_MAX_PIXELS = 4 * 1024 * 1024

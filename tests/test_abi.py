@@ -148,6 +148,9 @@ def test_calls_reject_null_handle(lib):
     assert lib.psfs_get_likelihood(None, None, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_backward(None, None, None, None, None, None) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_backward_sequence(None, 2, None, None, None, None, None) == psfs.PSFS_ERR_INVALID_ARG
+    assert lib.psfs_backward_from_occupancy(None, 2, None, None, None, None, None, None) == psfs.PSFS_ERR_INVALID_ARG
+    assert lib.psfs_get_log_ratio(None, None, None) == psfs.PSFS_ERR_INVALID_ARG
+    assert lib.psfs_batch_set_wait_limit(None, 1000000, -1) == psfs.PSFS_ERR_INVALID_ARG
     assert lib.psfs_sync(None) == psfs.PSFS_ERR_INVALID_ARG
     lib.psfs_destroy(None)
 

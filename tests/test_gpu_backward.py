@@ -361,3 +361,46 @@ def test_autograd_sequence_function_matches_per_frame():
     assert torch.equal(gm, sm) and torch.equal(gv, sv)
     assert float(gm.abs().max()) > 0
     rec.close()
+
+
+def test_backward_from_occupancy_equals_recomputing_adjoint():
+    """With the forward's own occupancy the adjoint skips the recomputed maps
+    and voxel pass; its outputs must be those of psfs_backward (one frame) and
+    psfs_backward_sequence (11 frames: groups of 8 and 3) bit for bit."""
+    n = 11
+    sc = S.make_scene(seed=48, grid_n=40, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0,
+                      n_frames=n, walking=True)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    V = rec.n_voxels
+    n_pix = imgs[0].numel() // 3
+    occ = torch.empty((n, V), device="cuda")
+    lst = torch.empty((n, V), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    psfs.psfs_reconstruct_sequence(rec.handle, n, imgs, occ, lst, V, cnt)
+    d_occ = torch.randn((n, V), generator=torch.Generator().manual_seed(3)).cuda()
+    outs = []
+    for fn in ("recompute", "occupancy"):
+        s_ = torch.full((n, n_pix), 7.0, device="cuda")
+        m_ = torch.full((n_pix * 3,), 7.0, device="cuda")
+        v_ = torch.full((n_pix * 3,), 7.0, device="cuda")
+        if fn == "recompute":
+            psfs.psfs_backward_sequence(rec.handle, n, imgs, d_occ, s_, m_, v_)
+        else:
+            psfs.psfs_backward_from_occupancy(rec.handle, n, imgs, occ, d_occ, s_, m_, v_)
+        assert rec.sync() == psfs.PSFS_OK
+        outs.append((s_.cpu(), m_.cpu(), v_.cpu()))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    # one frame
+    s1, m1, v1 = (torch.empty(n_pix, device="cuda"), torch.empty(n_pix * 3, device="cuda"),
+                  torch.empty(n_pix * 3, device="cuda"))
+    s2, m2, v2 = (torch.empty(n_pix, device="cuda"), torch.empty(n_pix * 3, device="cuda"),
+                  torch.empty(n_pix * 3, device="cuda"))
+    psfs.psfs_backward(rec.handle, imgs[4], d_occ[4], s1, m1, v1)
+    psfs.psfs_backward_from_occupancy(rec.handle, 1, imgs[4], occ[4], d_occ[4], s2, m2, v2)
+    assert rec.sync() == psfs.PSFS_OK
+    assert torch.equal(s1, s2) and torch.equal(m1, m2) and torch.equal(v1, v2)
+    assert torch.equal(s1, outs[0][0][4].cuda())
+    rec.close()
