@@ -363,6 +363,57 @@ class OraclePool:
             shm.unlink()
 
 
+def fp64_comparisons(pending, adjoints):
+    """The CPU leg's comparisons of other GPU outputs with the FP64 oracle:
+    `pending` = [(key, scene, [(occ, list, count)])] frames of the other
+    workloads (one per entry, the scene's own frame); `adjoints` = [(key,
+    scene, frame images, d_occ, (d_slm, d_mean, d_var))] GPU gradients for the
+    given loss gradient.  Returns {key: report}."""
+    import oracle
+    oracle.build()
+    out = {}
+    for key, sc, frames in pending:
+        ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+        for occ, lst, count in frames:
+            out.setdefault(key, []).append(_err_report(occ, lst, count, ref))
+    merged = {}
+    for key, reps in out.items():
+        merged[key] = reps[0] if len(reps) == 1 else {
+            "frames": len(reps), "max_abs": max(r["max_abs"] for r in reps),
+            "mean_abs": float(np.mean([r["mean_abs"] for r in reps])),
+            "hamming": sum(r["hamming"] for r in reps),
+            "hamming_unexplained": sum(r["hamming_unexplained"] for r in reps),
+            "boundary_voxels": sum(r["boundary_voxels"] for r in reps)}
+    masks = {}
+    for key, sc, img, d_occ, grads in adjoints:
+        ds, dm, dv = oracle.backward(sc.grid, sc.cams, img, sc.mean, sc.var, d_occ.astype(np.float64), sc.params)
+        # pixels within one pixel of a boundary voxel's projection may own
+        # other voxels in FP32 than in FP64: left out (one mask per frame)
+        tag = (id(sc), hash(img.tobytes()))
+        if tag not in masks:
+            ref = oracle.reconstruct(sc.grid, sc.cams, img, sc.mean, sc.var, sc.params)
+            pix = oracle.voxel_pixels(sc.grid, sc.cams)
+            W, H = sc.cams[0].width, sc.cams[0].height
+            amb = np.zeros((len(sc.cams), H, W), bool)
+            for c in range(len(sc.cams)):
+                p = pix[c][ref["boundary"] & (pix[c] >= 0)]
+                ys, xs = p // W, p % W
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        amb[c, np.clip(ys + dy, 0, H - 1), np.clip(xs + dx, 0, W - 1)] = True
+            masks[tag] = ~amb.ravel()
+        keep = masks[tag]
+        keep3 = np.repeat(keep, 3)
+        rep = {}
+        for name, got, want, k in (("d_slm", grads[0], ds, keep), ("d_mean", grads[1], dm, keep3),
+                                   ("d_var", grads[2], dv, keep3)):
+            g, w = np.asarray(got, np.float64).ravel()[k], want.ravel()[k]
+            rep[name] = float(np.abs(g - w).max() / max(np.abs(w).max(), 1e-30))
+        rep["what"] = "max |GPU - FP64 adjoint| / max |FP64 adjoint| over pixels away from boundary voxels"
+        merged[key] = rep
+    return merged
+
+
 def cpu_baseline(sc, n_frames: int, gpu_outputs=None):
     """The FP64 oracle as it stands: whole frames in parallel on every host
     core (frames are independent), and single-threaded for reference.
@@ -803,8 +854,9 @@ def run_ours(args):
         forms = time_forms(args, sc, d_images, occ, dev, psfs, fuse_cfg, gpu_outputs)
 
     configs = None
+    pending = []
     if not args.no_configs and rank == 0:
-        configs = time_configs(args, dev, psfs)
+        configs = time_configs(args, dev, psfs, pending)
 
     cpu = None
     err_vs_fp64 = None
@@ -820,6 +872,14 @@ def run_ours(args):
             for name, rep in err.items():
                 if name != headline and forms is not None:
                     forms[f"{name}_batched_err_vs_fp64"] = rep
+        extra = fp64_comparisons(pending, (forms or {}).pop("_adjoints", []))
+        for key, rep in extra.items():
+            if configs is not None and key in configs:
+                configs[key]["err_vs_fp64"] = rep
+            elif forms is not None:
+                forms[key] = rep
+    if forms is not None:
+        forms.pop("_adjoints", None)
 
     if batch is not None:
         psfs.psfs_batch_destroy(batch)
@@ -931,13 +991,13 @@ def time_single_frame(psfs, dev, sc, map_dtype, reps, flush=None):
     return ms, prof, res, cfg
 
 
-def time_configs(args, dev, psfs):
-    """The other configurations of the workload list, each with its throughput,
-    the roofline of its dominant kernel and its error against FP64."""
+def time_configs(args, dev, psfs, pending):
+    """The other configurations of the workload list, each with its throughput
+    and the roofline of its dominant kernel.  Their outputs are appended to
+    `pending` as (config key, scene, frame outputs) for the CPU leg, which
+    adds each one's error against the FP64 oracle."""
     import torch
     from synth import scene as S
-    import oracle
-    oracle.build()
     peak, _ = measured_peaks()
     out = {}
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
@@ -946,21 +1006,20 @@ def time_configs(args, dev, psfs):
     sc = S.scene_64cube_4cam(seed=0)
     ms, prof, res, cfg = time_single_frame(psfs, dev, sc, "f32", reps=50, flush=flush)
     V, K, n_pix = sc.grid.n_voxels, sc.n_cams, sc.images.size // 3
-    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    pending.append(("c1", sc, [res]))
     out["c1"] = {"workload": "64^3 grid x 4 cams 320x240, FP32, one frame per psfs_reconstruct call",
                  "ms_per_frame": ms, "frames_per_s": 1e3 / ms, "gvox_cam_per_s": V * K / (ms * 1e-3) / 1e9,
                  "timing": "CUDA events around each call; a 256 MB buffer written before each call (L2 flushed)",
                  "fuse_tile": list(cfg),
                  "roofline": _stage_roofline(prof, {"likelihood": n_pix * (3 + 24 + 4),
-                                                    "fuse": n_pix * 4 + V * 4 + res[2] * 4}, peak),
-                 "err_vs_fp64": _err_report(*res, ref)}
+                                                    "fuse": n_pix * 4 + V * 4 + res[2] * 4}, peak)}
 
     # 256^3 x 16 cameras 1280x720, two bodies, FP16 then BF16 maps (inputs > L2)
     sc = S.scene_256cube_16cam(seed=2)
     V, K, n_pix = sc.grid.n_voxels, sc.n_cams, sc.images.size // 3
-    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
     for dt in ("f16", "bf16"):
         ms, prof, res, cfg = time_single_frame(psfs, dev, sc, dt, reps=10)
+        pending.append((f"c3_{dt}", sc, [res]))
         out[f"c3_{dt}"] = {"workload": f"256^3 grid x 16 cams 1280x720, two bodies, {dt} maps (FP32 accumulation), "
                                        "one frame per psfs_reconstruct call",
                            "ms_per_frame": ms, "frames_per_s": 1e3 / ms,
@@ -968,9 +1027,7 @@ def time_configs(args, dev, psfs):
                            "timing": "CUDA events around back-to-back calls; inputs (398 MB) larger than L2",
                            "fuse_tile": list(cfg),
                            "roofline": _stage_roofline(prof, {"likelihood": n_pix * (3 + 24 + 2),
-                                                              "fuse": n_pix * 2 + V * 4 + res[2] * 4}, peak),
-                           "err_vs_fp64": _err_report(*res, ref)}
-    del ref
+                                                              "fuse": n_pix * 2 + V * 4 + res[2] * 4}, peak)}
 
     # 64 heterogeneous frames in one persistent CUDA-graph launch, FP32
     scenes = S.batch_64_scenes(seed=64, workers=args.workers)
@@ -1003,13 +1060,10 @@ def time_configs(args, dev, psfs):
     evals = sum(sc.grid.n_voxels * sc.n_cams for sc in scenes)
     counts = [int(o[2].item()) & 0xFFFFFFFF for o in outs]
     alg = sum(sc.images.size // 3 * (3 + 24 + 2 * 4) + sc.grid.n_voxels * 4 + c * 4 for sc, c in zip(scenes, counts))
-    errs = {}
     for k in (0, 37):
-        sc = scenes[k]
-        ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
         occ, lst, cnt = outs[k]
-        errs[k] = _err_report(occ.cpu().numpy().ravel(), lst[:min(counts[k], recs[k][0].capacity)].cpu().numpy(),
-                              counts[k], ref)
+        pending.append(("c4", scenes[k], [(occ.cpu().numpy().ravel(),
+                                          lst[:min(counts[k], recs[k][0].capacity)].cpu().numpy(), counts[k])]))
     psfs.psfs_batch_destroy(b)
     for rec, _ in recs:
         rec.close()
@@ -1022,10 +1076,7 @@ def time_configs(args, dev, psfs):
                  "tile": list(best), "autotune_ms": {"x".join(map(str, k)): round(v, 3) for k, v in tune.items()},
                  "roofline": {"bound": "hbm", "kernel": "batch_kernel", "alg_bytes_per_launch": alg, "achieved": ach,
                               "peak": peak, "unit": "GB/s", "frac": ach / peak},
-                 "err_vs_fp64": {"frames": sorted(errs), "max_abs": max(e["max_abs"] for e in errs.values()),
-                                 "hamming": sum(e["hamming"] for e in errs.values()),
-                                 "hamming_unexplained": sum(e["hamming_unexplained"] for e in errs.values()),
-                                 "boundary_voxels": sum(e["boundary_voxels"] for e in errs.values())}}
+                 "err_vs_fp64_frames": [0, 37]}
     del flush
     return out
 
@@ -1034,6 +1085,27 @@ def host_frame(occ, lists, counts, f, cap):
     """(occupancy, voxel list, count) of frame f, copied to the host."""
     n = int(counts[f].item()) & 0xFFFFFFFF
     return (occ[f].cpu().numpy(), lists[f, :min(n, cap)].cpu().numpy(), n)
+
+
+def _adjoint_sample(out, dtype, sc, rec, d_images, occ_f32, stream, psfs):
+    """psfs_backward of frame 1 with the loss gradient 2 (occ - occ of frame 0)
+    (FP32 maps' occupancy as the target), kept with its d_occ for the CPU
+    leg, which compares the gradients with the FP64 oracle's adjoint for the
+    same d_occ."""
+    import torch
+    f1 = 1 if d_images.shape[0] > 1 else 0
+    n_pix = d_images[0].numel() // 3
+    dev = d_images.device
+    with torch.cuda.stream(stream):
+        o, lst, cnt = rec.reconstruct(d_images[f1])
+        d_occ = (2.0 * (o.view(-1) - occ_f32[0])).contiguous()
+        g = (torch.empty(n_pix, device=dev), torch.empty(n_pix * 3, device=dev), torch.empty(n_pix * 3, device=dev))
+        psfs.psfs_backward(rec.handle, d_images[f1], d_occ, *g)
+    stream.synchronize()
+    assert rec.sync() == psfs.PSFS_OK
+    img = d_images[f1].cpu().numpy()
+    out.setdefault("_adjoints", []).append((f"{dtype}_adjoint_err_vs_fp64", sc, img, d_occ.cpu().numpy(),
+                                            tuple(x.cpu().numpy() for x in g)))
 
 
 def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=None):
@@ -1155,7 +1227,14 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
         stream.synchronize()
         assert rec.sync() == psfs.PSFS_OK
         out[f"{dtype}_forward_backward_from_occupancy_us"] = 1e3 * e[0].elapsed_time(e[3]) / F
+        _adjoint_sample(out, dtype, sc, rec, d_images, occ_f32, stream, psfs)
         rec.close()
+    # the adjoint with BF16 maps, for its error against FP64 only
+    with torch.cuda.stream(stream):
+        rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype="bf16", stream=stream, device=dev)
+        rec.set_background(torch.from_numpy(sc.mean).to(dev), torch.from_numpy(sc.var).to(dev))
+    _adjoint_sample(out, "bf16", sc, rec, d_images, occ_f32, stream, psfs)
+    rec.close()
     out["note"] = ("*_forward_us / *_forward_backward_us: one frame per call (no stream overlap); backward = "
                    "recomputed maps + voxel pass + per-pixel owner pass + chain rule to SLM, mean, var.  "
                    "*_batched_forward_us: psfs_reconstruct_sequence over 32 frames in frame groups; "

@@ -10,8 +10,8 @@
  * Every quantity is double precision.  Nothing here is blocked, fused or
  * reordered: each function follows the equations in the paper's order.
  *
- * Conventions (the readings of the paper where it is silent; each is also
- * listed with its reason in the design notes of the repository):
+ * Conventions (the readings of the paper where it is silent or ambiguous,
+ * each with the passage it rests on):
  *   - pixel colour I is an RGB triple; the background likelihood is a single
  *     Gaussian per pixel with independent channels (diagonal covariance,
  *     variance given per channel)                               (Eq. 1, text)

@@ -98,3 +98,21 @@ def test_error_report_against_fp64(monkeypatch):
     assert abs(rep["max_abs"] - 0.25) < 1e-6
     s = bench.summarize_errors({0: rep, 5: rep})
     assert s["frames"] == [0, 5] and s["set_diff_unexplained"] == 2
+
+
+def test_fp64_comparisons_of_other_workloads_and_adjoints():
+    """The CPU leg's comparisons: the oracle's own outputs and gradients
+    report no error; a scaled gradient reports its relative error."""
+    import numpy as np
+    import oracle
+    from synth import scene as S
+    sc = S.make_scene(seed=4, grid_n=12, cube_side=2.0, n_cams=2, width=48, height=36, focal=45.0)
+    ref = oracle.reconstruct(sc.grid, sc.cams, sc.images, sc.mean, sc.var, sc.params)
+    pending = [("c", sc, [(ref["occ"].astype(np.float32), ref["list"], ref["list"].size)])]
+    d_occ = np.random.default_rng(0).normal(size=sc.grid.n_voxels).astype(np.float32)
+    ds, dm, dv = oracle.backward(sc.grid, sc.cams, sc.images, sc.mean, sc.var, d_occ.astype(np.float64), sc.params)
+    adj = [("a", sc, sc.images, d_occ, (ds, dm, dv)), ("b", sc, sc.images, d_occ, (1.01 * ds, dm, dv))]
+    out = bench.fp64_comparisons(pending, adj)
+    assert out["c"]["hamming"] == 0 and out["c"]["max_abs"] < 1e-7
+    assert out["a"]["d_slm"] == 0 and out["a"]["d_mean"] == 0
+    assert abs(out["b"]["d_slm"] - 0.01) < 1e-9 and out["b"]["d_var"] == 0
