@@ -176,11 +176,11 @@ def sequence_units(n_frames, group, voxels_z=4, map_elem=4):
     """Frames per unit of psfs_reconstruct_sequence: groups of `group` frames
     while they fill, then the largest smaller power-of-two groups that fit and
     whose 32-byte pixel records (P = min(g, 32 / map_elem) frames) the tile
-    height supports (voxels_z 4; 8 when P <= 8; 16 when P <= 4), else single
+    height supports (voxels_z 2 or 4; 8 when P <= 8; 16 when P <= 4), else single
     frames."""
     def ok(g):
         p = min(g, 32 // map_elem)
-        return voxels_z == 4 or (voxels_z == 8 and p <= 8) or (voxels_z == 16 and p <= 4)
+        return voxels_z in (2, 4) or (voxels_z == 8 and p <= 8) or (voxels_z == 16 and p <= 4)
 
     units, left = [], n_frames
     while left > 0:

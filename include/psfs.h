@@ -106,7 +106,7 @@ typedef struct {
  * fusion kernel owns: a warp covers lanes_x voxels along x by 32 / lanes_x
  * along y, a CTA `warps` warps stacked along y, and each thread walks
  * voxels_z voxels along z; supported: lanes_x in {8, 16, 32}, warps = 4,
- * voxels_z in {4, 8, 16} (8 or 16 when staged).  staged = 1 selects the
+ * voxels_z in {2, 4, 8, 16} (8 or 16 when staged).  staged = 1 selects the
  * persistent kernel that copies
  * each tile's image footprint per camera into shared memory (bulk copies,
  * double-buffered) before gathering; 0 gathers from global memory.
@@ -120,7 +120,7 @@ typedef struct {
  * records per P frames; one fusion launch per plane projects each voxel once
  * per camera and gathers the plane's P frames with one vector load (each
  * frame's results are bit-identical to one frame per launch).  Groups need
- * staged = 0, lanes_x 8 or 16, and voxels_z 4, or 8 when P <= 8, or 16 when
+ * staged = 0, lanes_x 8 or 16, and voxels_z 2 or 4, or 8 when P <= 8, or 16 when
  * P <= 4; with another shape the sequence path runs one frame per launch.
  * Trailing frames that do not fill a group run in the largest smaller groups
  * that fit, the last odd frame alone.  0 in psfs_set_fuse_config keeps the
@@ -409,9 +409,10 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
  * fastest and writes it to *best (may be NULL) and the mean milliseconds of
  * each candidate to candidate_ms[PSFS_N_FUSE_CANDIDATES] (may be NULL; order:
  * staged 0 then 1, lanes_x 8, 16, 32, voxels_z 8 then 16); then times the
- * sequence path on 16 frames with 1 to 4 likelihood CTAs per SM at one frame
- * per launch, and frame groups of 2, 4, 8 and 16 frames (direct tile shapes,
- * voxels_z 4, 8 and 16, 1 to 3 likelihood CTAs per SM), and keeps the fastest
+ * sequence path on 64 frames (32 above 2^23 voxels; copies of the frame at
+ * distinct addresses) with 1 to 4 likelihood CTAs per SM at one frame per
+ * launch, and frame groups of 2, 4, 8, 16 and 32 frames (direct tile shapes,
+ * voxels_z 2, 4, 8 and 16, 1 to 3 likelihood CTAs per SM), and keeps the fastest
  * sequence configuration (which may change the tile shape).  The choices are
  * remembered for handles of the same grid size, camera count, image size and
  * map type created later in the process.  Allocates and frees its own scratch; waits for the stream.

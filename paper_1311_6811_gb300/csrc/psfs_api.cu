@@ -1642,7 +1642,7 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     const int group_lx = (best_shape.lx == 16) ? 16 : 8;
     const int groups[5] = {2, 4, 8, 16, kMaxGroup};
     for (int gi = 0; gi < 5 && st == PSFS_OK; ++gi) {
-        for (int tz : {4, 8, 16}) {
+        for (int tz : {2, 4, 8, 16}) {
             if (st != PSFS_OK) break;
             const FuseShape gshape = {group_lx, 4, tz, 0};
             if (!group_shape_supported(gshape, groups[gi], (int)h->map_elem)) continue;

@@ -73,18 +73,21 @@ cudaError_t launch_voxel_shape(const BackwardArgs &b, const FuseShape &sh, cudaS
 {
     if (sh.wy != 4) return cudaErrorInvalidValue;
     if (sh.lx == 8) {
+        if (sh.tz == 2) return launch_voxel_typed<MapT, 8, 2>(b, s);
         if (sh.tz == 4) return launch_voxel_typed<MapT, 8, 4>(b, s);
         if (sh.tz == 8) return launch_voxel_typed<MapT, 8, 8>(b, s);
         if (sh.tz == 16) return launch_voxel_typed<MapT, 8, 16>(b, s);
         return cudaErrorInvalidValue;
     }
     if (sh.lx == 16) {
+        if (sh.tz == 2) return launch_voxel_typed<MapT, 16, 2>(b, s);
         if (sh.tz == 4) return launch_voxel_typed<MapT, 16, 4>(b, s);
         if (sh.tz == 8) return launch_voxel_typed<MapT, 16, 8>(b, s);
         if (sh.tz == 16) return launch_voxel_typed<MapT, 16, 16>(b, s);
         return cudaErrorInvalidValue;
     }
     if (sh.lx == 32) {
+        if (sh.tz == 2) return launch_voxel_typed<MapT, 32, 2>(b, s);
         if (sh.tz == 4) return launch_voxel_typed<MapT, 32, 4>(b, s);
         if (sh.tz == 8) return launch_voxel_typed<MapT, 32, 8>(b, s);
         if (sh.tz == 16) return launch_voxel_typed<MapT, 32, 16>(b, s);

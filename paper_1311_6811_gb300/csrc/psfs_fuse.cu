@@ -113,18 +113,21 @@ cudaError_t launch_shape(const FuseArgs &a, const FuseShape &sh, cudaStream_t s)
 {
     if (sh.wy != 4) return cudaErrorInvalidValue;
     if (sh.lx == 8) {
+        if (sh.tz == 2) return launch_typed<MapT, 8, 2>(a, s);
         if (sh.tz == 4) return launch_typed<MapT, 8, 4>(a, s);
         if (sh.tz == 8) return launch_typed<MapT, 8, 8>(a, s);
         if (sh.tz == 16) return launch_typed<MapT, 8, 16>(a, s);
         return cudaErrorInvalidValue;
     }
     if (sh.lx == 16) {
+        if (sh.tz == 2) return launch_typed<MapT, 16, 2>(a, s);
         if (sh.tz == 4) return launch_typed<MapT, 16, 4>(a, s);
         if (sh.tz == 8) return launch_typed<MapT, 16, 8>(a, s);
         if (sh.tz == 16) return launch_typed<MapT, 16, 16>(a, s);
         return cudaErrorInvalidValue;
     }
     if (sh.lx == 32) {
+        if (sh.tz == 2) return launch_typed<MapT, 32, 2>(a, s);
         if (sh.tz == 4) return launch_typed<MapT, 32, 4>(a, s);
         if (sh.tz == 8) return launch_typed<MapT, 32, 8>(a, s);
         if (sh.tz == 16) return launch_typed<MapT, 32, 16>(a, s);

@@ -474,7 +474,8 @@ cudaError_t launch_fg(const FuseArgs &a, cudaStream_t s)
 template <typename MapT, int LX, int F>
 cudaError_t launch_fg_tz(const FuseArgs &a, int tz, cudaStream_t s)
 {
-    // F x TZ accumulators per thread: at most 64
+    // F x TZ accumulators per thread: at most 64 (TZ = 2 with up to 16 frames: 32)
+    if (tz == 2) return launch_fg<MapT, LX, 2, F>(a, s);
     if (tz == 4) return launch_fg<MapT, LX, 4, F>(a, s);
     if constexpr (F <= 8) {
         if (tz == 8) return launch_fg<MapT, LX, 8, F>(a, s);
@@ -553,7 +554,7 @@ bool group_shape_supported(const FuseShape &s, int frames, int map_elem)
     // the fusion kernel holds P x TZ accumulators per thread: at most 64
     const int P = group_plane_frames(frames, map_elem);
     return group_size_supported(frames) && s.wy == 4 && s.staged == 0 && (s.lx == 8 || s.lx == 16) &&
-           (s.tz == 4 || (s.tz == 8 && P <= 8) || (s.tz == 16 && P <= 4));
+           (s.tz == 2 || s.tz == 4 || (s.tz == 8 && P <= 8) || (s.tz == 16 && P <= 4));
 }
 
 cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map_dtype, cudaStream_t s,

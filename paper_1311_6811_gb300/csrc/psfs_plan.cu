@@ -172,7 +172,7 @@ bool encode_map_tensors(void *maps, int map_dtype, int W, int H, int n_cams, CUt
 bool fuse_shape_supported(const FuseShape &s)
 {
     return (s.lx == 8 || s.lx == 16 || s.lx == 32) && s.wy == 4 &&
-           ((s.staged == 0 && (s.tz == 4 || s.tz == 8 || s.tz == 16)) ||
+           ((s.staged == 0 && (s.tz == 2 || s.tz == 4 || s.tz == 8 || s.tz == 16)) ||
             (s.staged == 1 && (s.tz == 8 || s.tz == 16)));
 }
 

@@ -116,3 +116,9 @@ def test_fp64_comparisons_of_other_workloads_and_adjoints():
     assert out["c"]["hamming"] == 0 and out["c"]["max_abs"] < 1e-7
     assert out["a"]["d_slm"] == 0 and out["a"]["d_mean"] == 0
     assert abs(out["b"]["d_slm"] - 0.01) < 1e-9 and out["b"]["d_var"] == 0
+
+
+def test_units_with_two_voxel_tiles():
+    # voxels_z 2 holds 2 x P accumulators: every record size fits
+    assert bench.sequence_units(100, 32, 2, 4) == [32, 32, 32, 4]
+    assert bench.sequence_units(100, 32, 2, 2) == [32, 32, 32, 4]

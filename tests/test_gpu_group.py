@@ -59,11 +59,12 @@ def _plane_frames(group, dtype):
 
 def _shape_ok(group, tz, dtype):
     p = _plane_frames(group, dtype)
-    return tz == 4 or (tz == 8 and p <= 8) or (tz == 16 and p <= 4)
+    return tz in (2, 4) or (tz == 8 and p <= 8) or (tz == 16 and p <= 4)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("group,tz", [(2, 16), (4, 4), (4, 8), (4, 16), (8, 4), (8, 8), (16, 4), (16, 8)])
+@pytest.mark.parametrize("group,tz", [(2, 16), (4, 2), (4, 4), (4, 8), (4, 16), (8, 2), (8, 4), (8, 8), (16, 2),
+                                      (16, 4), (16, 8)])
 def test_groups_equal_frame_by_frame(group, tz, dtype):
     """33 frames: whole groups, then the trailing frames in smaller groups
     and single frames.  16 FP32 frames are two planes of 8-frame records."""
@@ -83,7 +84,7 @@ def test_groups_equal_frame_by_frame(group, tz, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("tz", [4, 8])
+@pytest.mark.parametrize("tz", [2, 4, 8])
 def test_groups_of_32_equal_frame_by_frame(tz, dtype):
     """61 frames: one group of 32 frames (four planes of 8-frame records for
     FP32 maps, two of 16 for 16-bit maps), then groups of 16, 8 and 4 and one
