@@ -222,7 +222,19 @@ __global__ void __launch_bounds__(256) owner_pixel_kernel(const __grid_constant_
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < b.n_pix; p += stride) {
         const uint32_t e0 = __ldg(off + p), e1 = __ldg(off + p + 1);
         float acc = 0.0f;
-        for (uint32_t e = e0; e < e1; ++e) acc += __ldg(b.dl + __ldg(vox + e));
+        // four owners at a time: their index and dL loads are independent,
+        // so they are in flight together; the adds stay in ascending order
+        uint32_t e = e0;
+        for (; e + 4 <= e1; e += 4) {
+            const uint32_t v0 = __ldg(vox + e), v1 = __ldg(vox + e + 1), v2 = __ldg(vox + e + 2),
+                           v3 = __ldg(vox + e + 3);
+            const float d0 = __ldg(b.dl + v0), d1 = __ldg(b.dl + v1), d2 = __ldg(b.dl + v2), d3 = __ldg(b.dl + v3);
+            acc += d0;
+            acc += d1;
+            acc += d2;
+            acc += d3;
+        }
+        for (; e < e1; ++e) acc += __ldg(b.dl + __ldg(vox + e));
         float dslm, dm[3], dv[3];
         chain_rule(b, p, b.img, acc, dslm, dm, dv);
         if (b.d_slm) b.d_slm[p] = dslm;
@@ -262,6 +274,15 @@ __device__ __forceinline__ void chain_rule_pre(const BackwardArgs &b, const uint
     }
 }
 
+// One voxel's 32-byte record of dLoss/dL (kBwRecord frames) with one 256-bit
+// read-only load.
+__device__ __forceinline__ void load_record(const float *rec, uint32_t (&w)[8])
+{
+    asm("ld.global.nc.L1::no_allocate.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+        : "l"(rec));
+}
+
 // Up to kBwRecord frames: b.dl holds records of kBwRecord floats per voxel
 // (frame f of voxel v at b.dl[v * kBwRecord + f]), one 32-byte load per
 // owned voxel serves every frame.  Per frame the sum (same voxels, same
@@ -280,13 +301,22 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
         float acc[kBwRecord];
 #pragma unroll
         for (int f = 0; f < kBwRecord; ++f) acc[f] = 0.0f;
-        for (uint32_t e = e0; e < e1; ++e) {
-            const float *rec = b.dl + (size_t)__ldg(vox + e) * kBwRecord;
+        // two owners at a time (their loads in flight together), added in
+        // ascending order; one 256-bit read-only load per record (one sector)
+        uint32_t e = e0;
+        for (; e + 2 <= e1; e += 2) {
+            const uint32_t va = __ldg(vox + e), vb = __ldg(vox + e + 1);
+            uint32_t wa[8], wb[8];
+            load_record(b.dl + (size_t)va * kBwRecord, wa);
+            load_record(b.dl + (size_t)vb * kBwRecord, wb);
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wa[f]);
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wb[f]);
+        }
+        if (e < e1) {
             uint32_t w[8];
-            // one 256-bit read-only load: the voxel's whole record (one sector)
-            asm("ld.global.nc.L1::no_allocate.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
-                : "l"(rec));
+            load_record(b.dl + (size_t)__ldg(vox + e) * kBwRecord, w);
 #pragma unroll
             for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(w[f]);
         }
