@@ -124,7 +124,12 @@ typedef struct {
  * P <= 4; with another shape the sequence path runs one frame per launch.
  * Trailing frames that do not fill a group run in the largest smaller groups
  * that fit, the last odd frame alone.  0 in psfs_set_fuse_config keeps the
- * current value.  The batch entry points ignore this field. */
+ * current value.  The batch entry points ignore this field.
+ * cameras_per_block (batch entry points only; handles report 1): a batched
+ * fusion item issues the map loads of that many cameras together before it
+ * adds them, still camera by camera in the order 0 .. n_cams - 1, so the
+ * results do not change; 1, 2 (lanes_x 8 or 16, voxels_z 4 or 8) or 4
+ * (lanes_x 8 or 16, voxels_z 4); 0 in psfs_batch_set_config means 1. */
 typedef struct {
     int32_t lanes_x;
     int32_t warps;
@@ -132,6 +137,7 @@ typedef struct {
     int32_t staged;
     int32_t seq_likelihood_ctas;
     int32_t frames_per_group;
+    int32_t cameras_per_block;
 } psfs_fuse_config;
 
 typedef struct psfs_handle psfs_handle;
@@ -493,9 +499,13 @@ psfs_status psfs_batch_sync(psfs_batch *b);
  * re-captures. */
 psfs_status psfs_batch_set_config(psfs_batch *b, const psfs_fuse_config *cfg);
 
-/* Autotuner of the batch: times the whole graph for each of the 6 direct
- * tile shapes (candidate order lanes_x 8, 16, 32 x voxels_z 8, 16; times in
- * candidate_ms[6] if not NULL), keeps the fastest. */
+/* Autotuner of the batch: times the whole graph for each of
+ * PSFS_N_BATCH_CANDIDATES tile shapes and camera blocks (candidate order:
+ * lanes_x 8, 16, 32 x voxels_z 8, 16 with one camera per load block; then
+ * camera blocks of 2 with lanes_x 8, 16 x voxels_z 4, 8; then camera blocks
+ * of 4 with lanes_x 8, 16 and voxels_z 4; times in candidate_ms if not
+ * NULL), keeps the fastest. */
+#define PSFS_N_BATCH_CANDIDATES 12
 psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *best, float *candidate_ms);
 
 /* Failure detection of the batched launch.  A fusion item waits for every

@@ -21,6 +21,8 @@ using namespace psfs;
 
 // Device staging slots of the host-buffer sequence path.
 constexpr int kIoSlots = 3;
+// Candidates of psfs_batch_autotune.
+constexpr int kBatchCandidates = PSFS_N_BATCH_CANDIDATES;
 
 
 struct psfs_handle {
@@ -1522,6 +1524,7 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg)
     cfg->staged = h->shape.staged;
     cfg->seq_likelihood_ctas = h->seq_lk_ctas;
     cfg->frames_per_group = h->seq_group;
+    cfg->cameras_per_block = 1;
     return PSFS_OK;
 }
 
@@ -1760,6 +1763,7 @@ struct psfs_batch {
     int blocks = 0;
     uint64_t wait_ns = kWaitNs;   // limit of the fusion tiles' waits
     int hold_frame = -1;          // test hook: this frame's tiles wait for one chunk too many
+    int cam_block = 1;            // cameras whose loads a fusion item issues together
 };
 
 namespace {
@@ -1878,7 +1882,7 @@ psfs_status batch_build(psfs_batch *b, const FuseShape &shape)
     bl.wait_ns = b->wait_ns;
     PSFS_CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(b->d_words + 16, 0, sizeof(uint32_t) * (size_t)F, b->cap_stream);
-    if (e == cudaSuccess) e = launch_batch(bl, shape, b->map_dtype, b->cap_stream);
+    if (e == cudaSuccess) e = launch_batch(bl, shape, b->cam_block, b->map_dtype, b->cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
     if (e != cudaSuccess) {
@@ -1971,11 +1975,17 @@ psfs_status psfs_batch_set_config(psfs_batch *b, const psfs_fuse_config *cfg)
 {
     if (!b || !cfg) return fail(PSFS_ERR_INVALID_ARG, "NULL argument");
     const FuseShape shape = {cfg->lanes_x, cfg->warps, cfg->voxels_z, 0};
-    if (!fuse_shape_supported(shape) || cfg->staged != 0)
-        return fail(PSFS_ERR_INVALID_ARG, "unsupported batch tile shape (staged is not available in a batch)");
+    const int cb = cfg->cameras_per_block > 0 ? cfg->cameras_per_block : 1;
+    if (cfg->staged != 0 || !batch_shape_supported(shape, cb))
+        return fail(PSFS_ERR_INVALID_ARG,
+                    "unsupported batch tile shape or camera block (staged is not available in a batch)");
     DeviceGuard guard(b->device);
     PSFS_CK(cudaStreamSynchronize(b->user_stream));
-    return batch_build(b, shape);
+    const int old_cb = b->cam_block;
+    b->cam_block = cb;
+    const psfs_status st = batch_build(b, shape);
+    if (st != PSFS_OK) b->cam_block = old_cb;
+    return st;
 }
 
 psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *best, float *candidate_ms)
@@ -1985,16 +1995,25 @@ psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *b
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PSFS_CK(cudaEventCreate(&e0));
     PSFS_CK(cudaEventCreate(&e1));
-    const int lxs[3] = {8, 16, 32}, tzs[2] = {8, 16};
+    // candidates (order of candidate_ms): lanes_x 8, 16, 32 x voxels_z 8, 16 with
+    // one camera per load block, then camera blocks of 2 (lanes_x 8, 16 x
+    // voxels_z 4, 8) and of 4 (lanes_x 8, 16, voxels_z 4)
+    struct Cand {
+        int lx, tz, cb;
+    };
+    const Cand cands[kBatchCandidates] = {{8, 8, 1},  {8, 16, 1}, {16, 8, 1}, {16, 16, 1}, {32, 8, 1}, {32, 16, 1},
+                                          {8, 4, 2},  {8, 8, 2},  {16, 4, 2}, {16, 8, 2},  {8, 4, 4},  {16, 4, 4}};
     FuseShape best_shape = b->shape;
+    int best_cb = b->cam_block;
     float best_ms = 1e30f;
     psfs_status st = PSFS_OK;
-    for (int cand = 0; cand < 6 && st == PSFS_OK; ++cand) {
-        const FuseShape shape = {lxs[cand / 2], 4, tzs[cand % 2], 0};
+    for (int cand = 0; cand < kBatchCandidates && st == PSFS_OK; ++cand) {
+        const FuseShape shape = {cands[cand].lx, 4, cands[cand].tz, 0};
         if (cudaStreamSynchronize(b->user_stream) != cudaSuccess) {
             st = fail(PSFS_ERR_CUDA, "batch autotune sync");
             break;
         }
+        b->cam_block = cands[cand].cb;
         st = batch_build(b, shape);
         if (st != PSFS_OK) break;
         cudaError_t err = cudaGraphLaunch(b->exec, b->user_stream);   // warm-up
@@ -2012,10 +2031,12 @@ psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *b
         if (ms < best_ms) {
             best_ms = ms;
             best_shape = shape;
+            best_cb = cands[cand].cb;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    b->cam_block = best_cb;
     if (st != PSFS_OK) return st;
     st = batch_build(b, best_shape);
     if (st != PSFS_OK) return st;
@@ -2026,6 +2047,8 @@ psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *b
         best->voxels_z = best_shape.tz;
         best->staged = 0;
         best->seq_likelihood_ctas = 0;
+        best->frames_per_group = 0;
+        best->cameras_per_block = best_cb;
     }
     return PSFS_OK;
 }

@@ -38,16 +38,68 @@ __device__ __forceinline__ void store_map<__nv_bfloat16>(__nv_bfloat16 *out, int
     out[p] = __float2bfloat16_rn(v);
 }
 
-template <typename MapT, int LX, int TZ>
+// Shared memory of a CTA: two staging buffers for likelihood chunks (the
+// colours, means and inverse variances of kBatchChunk pixels) filled by bulk
+// copies, so that a CTA's next chunk streams in while it works on its
+// current item.
+struct BatchStage {
+    unsigned char img[2][3 * kBatchChunk];
+    float mean[2][3 * kBatchChunk];
+    float hinv[2][3 * kBatchChunk];
+    uint64_t bar[2];
+};
+
+// Pixels of likelihood chunk `idx` of a frame, and whether the chunk can be
+// bulk-copied (byte counts multiples of 16: a whole number of 16-pixel groups).
+__device__ __forceinline__ int64_t chunk_pixels(const BatchFrame &fr, int64_t idx)
+{
+    return min((int64_t)kBatchChunk, fr.n_pix - idx * kBatchChunk);
+}
+
+template <typename MapT, int LX, int TZ, int CB>
 __global__ void __launch_bounds__(128) batch_kernel(const BatchLaunch b)
 {
     constexpr int WY = 4;
     __shared__ int s_flags[PSFS_MAX_CAMS];
     __shared__ uint32_t s_warp_off[WY];
     __shared__ uint32_t s_base;
+    __shared__ __align__(128) BatchStage st;
     const int lane = threadIdx.x, wy = threadIdx.y, tid = wy * 32 + lane;
 
+    if (tid == 0) {
+        mbar_init(&st.bar[0], 1);
+        mbar_init(&st.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // Issues the bulk copies of item `it` into buffer `buf` if it is a
+    // likelihood chunk that can be copied; the answer is the same for every
+    // thread (it depends on the item list only).
+    auto prefetch = [&](int64_t it, int buf) -> bool {
+        if (it >= b.n_items) return false;
+        const uint64_t e = b.items[it];
+        if ((e >> 39) & 1u) return false;
+        const BatchFrame &fr = b.frames[(uint32_t)(e >> 40)];
+        const int64_t idx = (int64_t)(e & ((1ull << 39) - 1));
+        const int64_t np = chunk_pixels(fr, idx);
+        if (np % 16 != 0) return false;
+        if (tid == 0) {
+            const int64_t p0 = idx * kBatchChunk;
+            mbar_arrive_expect_tx(&st.bar[buf], (uint32_t)(27 * np));
+            bulk_g2s(st.img[buf], fr.img + 3 * p0, (uint32_t)(3 * np), &st.bar[buf]);
+            bulk_g2s(st.mean[buf], fr.mean + 3 * p0, (uint32_t)(12 * np), &st.bar[buf]);
+            bulk_g2s(st.hinv[buf], fr.hinv + 3 * p0, (uint32_t)(12 * np), &st.bar[buf]);
+        }
+        return true;
+    };
+    uint32_t phase[2] = {0u, 0u};
+    int buf = 0;
+    bool staged = prefetch(blockIdx.x, 0);
+
     for (int64_t it = blockIdx.x; it < b.n_items; it += gridDim.x) {
+        // the CTA's next item streams into the other buffer meanwhile (that
+        // buffer was released by the barrier that ended the previous item)
+        const bool staged_next = prefetch(it + gridDim.x, buf ^ 1);
         const uint64_t e = b.items[it];
         const uint32_t f = (uint32_t)(e >> 40);
         const uint32_t kind = (uint32_t)((e >> 39) & 1u);
@@ -56,15 +108,27 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchLaunch b)
         if (kind == 0) {
             // Eq. 1-2 and the log ratio, pixels [idx * chunk, ...) of frame f
             const int64_t p0 = idx * kBatchChunk;
-            const int64_t np = min((int64_t)kBatchChunk, fr.n_pix - p0);
+            const int64_t np = chunk_pixels(fr, idx);
             MapT *out = reinterpret_cast<MapT *>(const_cast<void *>(fr.fa.maps));
-            for (int64_t q = tid; q < np; q += 128) {
-                const int64_t p = p0 + q;
-                const uint8_t *im = fr.img + 3 * p;
-                const float *mu = fr.mean + 3 * p, *hv = fr.hinv + 3 * p;
-                const float r = pixel_log_odds((float)im[0], (float)im[1], (float)im[2], mu[0], mu[1], mu[2], hv[0],
-                                               hv[1], hv[2], fr.c0);
-                store_map<MapT>(out, p, log_ratio_of_r(r, fr.sc));
+            if (staged) {
+                mbar_wait_bounded(&st.bar[buf], phase[buf], b.status);
+                phase[buf] ^= 1u;
+                for (int64_t q = tid; q < np; q += 128) {
+                    const unsigned char *im = st.img[buf] + 3 * q;
+                    const float *mu = st.mean[buf] + 3 * q, *hv = st.hinv[buf] + 3 * q;
+                    const float r = pixel_log_odds((float)im[0], (float)im[1], (float)im[2], mu[0], mu[1], mu[2],
+                                                   hv[0], hv[1], hv[2], fr.c0);
+                    store_map<MapT>(out, p0 + q, log_ratio_of_r(r, fr.sc));
+                }
+            } else {
+                for (int64_t q = tid; q < np; q += 128) {
+                    const int64_t p = p0 + q;
+                    const uint8_t *im = fr.img + 3 * p;
+                    const float *mu = fr.mean + 3 * p, *hv = fr.hinv + 3 * p;
+                    const float r = pixel_log_odds((float)im[0], (float)im[1], (float)im[2], mu[0], mu[1], mu[2],
+                                                   hv[0], hv[1], hv[2], fr.c0);
+                    store_map<MapT>(out, p, log_ratio_of_r(r, fr.sc));
+                }
             }
             if (idx == 0 && tid == 0) *fr.fa.count = 0u;
             __syncthreads();
@@ -99,76 +163,123 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchLaunch b)
 #pragma unroll
             for (int t = 0; t < TZ; ++t) L[t] = 0.0f;
             const MapT *maps = reinterpret_cast<const MapT *>(a.maps);
-            for (int c = 0; c < a.n_cams; ++c) {
-                const int flags = s_flags[c];
-                if (flags & kTcSkip) continue;
-                float m[12];
+            if (CB == 1) {
+                for (int c = 0; c < a.n_cams; ++c) {
+                    const int flags = s_flags[c];
+                    if (flags & kTcSkip) continue;
+                    float m[12];
 #pragma unroll
-                for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
-                float bu, bv, bw;
-                project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
-                gather_global<MapT, TZ, true>(m, bu, bv, bw, tc.fk, maps + (int64_t)c * a.map_stride, W, H,
-                                              (flags & kTcInside) != 0, L);
+                    for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
+                    float bu, bv, bw;
+                    project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
+                    gather_global<MapT, TZ, true>(m, bu, bv, bw, tc.fk, maps + (int64_t)c * a.map_stride, W, H,
+                                                  (flags & kTcInside) != 0, L);
+                }
+            } else {
+                // camera blocks: the loads of CB cameras are issued together,
+                // then added camera by camera, so the sum runs over the
+                // cameras in the order 0 .. n_cams - 1 as in every other kernel
+                for (int c0 = 0; c0 < a.n_cams; c0 += CB) {
+                    float g[CB][TZ];
+                    bool seen[CB][TZ];
+#pragma unroll
+                    for (int cb = 0; cb < CB; ++cb) {
+                        const int c = c0 + cb;
+                        const bool use = c < a.n_cams && !(s_flags[min(c, a.n_cams - 1)] & kTcSkip);
+#pragma unroll
+                        for (int t = 0; t < TZ; ++t) seen[cb][t] = false;
+                        if (use) {
+                            float m[12];
+#pragma unroll
+                            for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
+                            float bu, bv, bw;
+                            project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
+                            const MapT *map = maps + (int64_t)c * a.map_stride;
+#pragma unroll
+                            for (int t = 0; t < TZ; ++t) {
+                                int pix;
+                                seen[cb][t] = proj_pixel(project_biased(m, bu, bv, bw, tc.fk[t]), W, H, &pix);
+                                g[cb][t] = seen[cb][t] ? map_load_coherent(map + pix) : 0.0f;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int cb = 0; cb < CB; ++cb)
+#pragma unroll
+                        for (int t = 0; t < TZ; ++t)
+                            if (seen[cb][t]) L[t] += g[cb][t];
+                }
             }
             tile_epilogue<WY, TZ>(a, tc.i, tc.j, tc.k0, L, lane, wy, s_warp_off, &s_base);
         }
-        __syncthreads();   // s_flags / s_warp_off are reused by the next item
+        __syncthreads();   // s_flags / s_warp_off / the staging buffer are reused by the next item
+        staged = staged_next;
+        buf ^= 1;
     }
 }
 
-template <typename MapT, int LX, int TZ>
+template <typename MapT, int LX, int TZ, int CB>
 cudaError_t launch_typed(const BatchLaunch &b, cudaStream_t s)
 {
-    auto kern = batch_kernel<MapT, LX, TZ>;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto kern = batch_kernel<MapT, LX, TZ, CB>;
+    int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
     if (e != cudaSuccess) return e;
     // every CTA must be resident at once (items wait on items of other CTAs)
-    int blocks = std::max(1, per_sm) * std::max(1, sms);
+    int blocks = std::max(1, per_sm) * device_sm_count();
     if (b.blocks > 0) blocks = std::min(blocks, b.blocks);
     if ((int64_t)blocks > b.n_items) blocks = (int)std::max<int64_t>(1, b.n_items);
     kern<<<blocks, dim3(32, 4), 0, s>>>(b);
     return cudaGetLastError();
 }
 
+template <typename MapT, int LX>
+cudaError_t launch_tz(const BatchLaunch &b, int tz, int cb, cudaStream_t s)
+{
+    if (cb == 1) {
+        if (tz == 2) return launch_typed<MapT, LX, 2, 1>(b, s);
+        if (tz == 4) return launch_typed<MapT, LX, 4, 1>(b, s);
+        if (tz == 8) return launch_typed<MapT, LX, 8, 1>(b, s);
+        if (tz == 16) return launch_typed<MapT, LX, 16, 1>(b, s);
+        return cudaErrorInvalidValue;
+    }
+    if constexpr (LX != 32) {
+        if (cb == 2) {
+            if (tz == 4) return launch_typed<MapT, LX, 4, 2>(b, s);
+            if (tz == 8) return launch_typed<MapT, LX, 8, 2>(b, s);
+        }
+        if (cb == 4 && tz == 4) return launch_typed<MapT, LX, 4, 4>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename MapT>
-cudaError_t launch_shape(const BatchLaunch &b, const FuseShape &sh, cudaStream_t s)
+cudaError_t launch_shape(const BatchLaunch &b, const FuseShape &sh, int cb, cudaStream_t s)
 {
     if (sh.wy != 4) return cudaErrorInvalidValue;
-    if (sh.lx == 8) {
-        if (sh.tz == 2) return launch_typed<MapT, 8, 2>(b, s);
-        if (sh.tz == 4) return launch_typed<MapT, 8, 4>(b, s);
-        if (sh.tz == 8) return launch_typed<MapT, 8, 8>(b, s);
-        if (sh.tz == 16) return launch_typed<MapT, 8, 16>(b, s);
-        return cudaErrorInvalidValue;
-    }
-    if (sh.lx == 16) {
-        if (sh.tz == 2) return launch_typed<MapT, 16, 2>(b, s);
-        if (sh.tz == 4) return launch_typed<MapT, 16, 4>(b, s);
-        if (sh.tz == 8) return launch_typed<MapT, 16, 8>(b, s);
-        if (sh.tz == 16) return launch_typed<MapT, 16, 16>(b, s);
-        return cudaErrorInvalidValue;
-    }
-    if (sh.lx == 32) {
-        if (sh.tz == 2) return launch_typed<MapT, 32, 2>(b, s);
-        if (sh.tz == 4) return launch_typed<MapT, 32, 4>(b, s);
-        if (sh.tz == 8) return launch_typed<MapT, 32, 8>(b, s);
-        if (sh.tz == 16) return launch_typed<MapT, 32, 16>(b, s);
-        return cudaErrorInvalidValue;
-    }
+    if (sh.lx == 8) return launch_tz<MapT, 8>(b, sh.tz, cb, s);
+    if (sh.lx == 16) return launch_tz<MapT, 16>(b, sh.tz, cb, s);
+    if (sh.lx == 32) return launch_tz<MapT, 32>(b, sh.tz, cb, s);
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_batch(const BatchLaunch &b, const FuseShape &shape, int map_dtype, cudaStream_t s)
+bool batch_shape_supported(const FuseShape &sh, int cb)
+{
+    if (sh.wy != 4 || sh.staged || !(sh.lx == 8 || sh.lx == 16 || sh.lx == 32)) return false;
+    if (cb == 1) return sh.tz == 2 || sh.tz == 4 || sh.tz == 8 || sh.tz == 16;
+    if (sh.lx == 32) return false;
+    return (cb == 2 && (sh.tz == 4 || sh.tz == 8)) || (cb == 4 && sh.tz == 4);
+}
+
+cudaError_t launch_batch(const BatchLaunch &b, const FuseShape &shape, int cameras_per_block, int map_dtype,
+                         cudaStream_t s)
 {
     if (b.n_items <= 0) return cudaSuccess;
-    if (map_dtype == PSFS_MAP_F16) return launch_shape<__half>(b, shape, s);
-    if (map_dtype == PSFS_MAP_BF16) return launch_shape<__nv_bfloat16>(b, shape, s);
-    return launch_shape<float>(b, shape, s);
+    if (map_dtype == PSFS_MAP_F16) return launch_shape<__half>(b, shape, cameras_per_block, s);
+    if (map_dtype == PSFS_MAP_BF16) return launch_shape<__nv_bfloat16>(b, shape, cameras_per_block, s);
+    return launch_shape<float>(b, shape, cameras_per_block, s);
 }
 
 }  // namespace psfs

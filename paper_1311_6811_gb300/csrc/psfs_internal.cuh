@@ -553,7 +553,12 @@ struct BatchLaunch {
     uint64_t wait_ns;           // limit of a fusion tile's wait for its frame's chunks
 };
 
-cudaError_t launch_batch(const BatchLaunch &b, const FuseShape &shape, int map_dtype, cudaStream_t s);
+// cameras_per_block: the fusion items issue the loads of that many cameras
+// together (1, 2 or 4; the sum stays in camera order); batch_shape_supported
+// lists the instantiated combinations.
+bool batch_shape_supported(const FuseShape &shape, int cameras_per_block);
+cudaError_t launch_batch(const BatchLaunch &b, const FuseShape &shape, int cameras_per_block, int map_dtype,
+                         cudaStream_t s);
 void plan_backward_inv(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const FuseArgs &f,
                        PixelInv *inv);
 // Owner lists of the adjoint's pixel pass (psfs_owners.cu): for every pixel

@@ -55,7 +55,7 @@ class psfs_params(ctypes.Structure):
 class psfs_fuse_config(ctypes.Structure):
     _fields_ = [("lanes_x", ctypes.c_int32), ("warps", ctypes.c_int32), ("voxels_z", ctypes.c_int32),
                 ("staged", ctypes.c_int32), ("seq_likelihood_ctas", ctypes.c_int32),
-                ("frames_per_group", ctypes.c_int32)]
+                ("frames_per_group", ctypes.c_int32), ("cameras_per_block", ctypes.c_int32)]
 
     def as_tuple(self):
         return (self.lanes_x, self.warps, self.voxels_z, self.staged)
@@ -549,22 +549,27 @@ def psfs_batch_sync(b: int) -> int:
     return st
 
 
-BATCH_CONFIGS = [(lx, 4, tz, 0) for lx in (8, 16, 32) for tz in (8, 16)]
+# candidate order of psfs_batch_autotune: (lanes_x, warps, voxels_z, staged, cameras_per_block)
+BATCH_CONFIGS = ([(lx, 4, tz, 0, 1) for lx in (8, 16, 32) for tz in (8, 16)] +
+                 [(lx, 4, tz, 0, 2) for lx in (8, 16) for tz in (4, 8)] +
+                 [(lx, 4, 4, 0, 4) for lx in (8, 16)])
 
 
-def psfs_batch_set_config(b: int, lanes_x: int, warps: int, voxels_z: int):
-    cfg = psfs_fuse_config(lanes_x, warps, voxels_z, 0, 0)
+def psfs_batch_set_config(b: int, lanes_x: int, warps: int, voxels_z: int, cameras_per_block: int = 1):
+    cfg = psfs_fuse_config(lanes_x, warps, voxels_z, 0, 0, 0, cameras_per_block)
     _check(load().psfs_batch_set_config(b, ctypes.byref(cfg)), "psfs_batch_set_config")
 
 
 def psfs_batch_autotune(b: int, reps: int = 3, timings: Optional[dict] = None) -> tuple:
+    """Times every batch candidate; returns the chosen (lanes_x, warps,
+    voxels_z, staged, cameras_per_block)."""
     cfg = psfs_fuse_config()
     ms = (ctypes.c_float * len(BATCH_CONFIGS))()
     _check(load().psfs_batch_autotune(b, int(reps), ctypes.byref(cfg), ms), "psfs_batch_autotune")
     if timings is not None:
         for c, t in zip(BATCH_CONFIGS, ms):
             timings[c] = float(t)
-    return cfg.as_tuple()
+    return cfg.as_tuple() + (cfg.cameras_per_block,)
 
 
 def psfs_batch_set_wait_limit(b: int, limit_ns: int, hold_frame: int = -1):

@@ -58,8 +58,11 @@ def _host(out):
     return occ.cpu().numpy().ravel(), psfs.voxel_list(lst, cnt, cap).numpy(), int(cnt.item())
 
 
+# odd camera counts leave partial camera blocks; 3 x 101 x 77 pixels leave a
+# last likelihood chunk of 291 pixels (not bulk-copied: plain loads)
 SPECS = [(32, 2.0, 3, 160, 120, 150.0), (40, 2.0, 5, 200, 150, 190.0), ((48, 40, 36), 2.0, 4, 160, 120, 150.0),
-         (24, 2.0, 6, 128, 96, 120.0), (37, 2.0, 4, 104, 77, 95.0), (56, 2.2, 7, 200, 150, 190.0)]
+         (24, 2.0, 6, 128, 96, 120.0), (37, 2.0, 4, 104, 77, 95.0), (56, 2.2, 7, 200, 150, 190.0),
+         (23, 2.0, 3, 101, 77, 95.0)]
 
 
 def test_batch_equals_frame_by_frame_and_oracle():
@@ -78,13 +81,15 @@ def test_batch_equals_frame_by_frame_and_oracle():
         np.testing.assert_array_equal(_host(o)[0], g[0])
     # every tile shape, and the autotuner's pick, give the same bits
     for cfg in psfs.BATCH_CONFIGS:
-        psfs.psfs_batch_set_config(b, *cfg[:3])
+        psfs.psfs_batch_set_config(b, *cfg[:3], cameras_per_block=cfg[4])
         psfs.psfs_batch_run(b)
         assert psfs.psfs_batch_sync(b) == psfs.PSFS_OK
         for o, g in zip(outs, got):
             np.testing.assert_array_equal(_host(o)[0], g[0])
     best = psfs.psfs_batch_autotune(b, reps=1)
     assert best in psfs.BATCH_CONFIGS
+    with pytest.raises(psfs.PsfsError):
+        psfs.psfs_batch_set_config(b, 32, 4, 4, cameras_per_block=2)   # not an instantiated combination
     # FP64 oracle on two frames
     for n in (1, 2):
         sc = scenes[n]
