@@ -56,7 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fuse-config", default=None,
-                    help="lanes_x,warps,voxels_z,staged[,likelihood_ctas[,frames_per_group]]: skip the autotuner")
+                    help="lanes_x,warps,voxels_z,staged[,likelihood_ctas[,frames_per_group[,seq_lanes_x,seq_voxels_z]]]: "
+                         "skip the autotuner")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the per-frame FP32/FP16 forward and forward+backward timings")
     ap.add_argument("--forms-frames", type=int, default=20)
@@ -633,7 +634,7 @@ def run_ours(args):
     # nf occupancy grids and lists.
     map_elem = 4 if args.map_dtype == "f32" else 2
     G = fuse_cfg[5] if batch is None else 1
-    units = sequence_units(F, G, fuse_cfg[2], map_elem)
+    units = sequence_units(F, G, fuse_cfg[7], map_elem)   # the sequence path's tile height
     fuse_frame_bytes = n_pix * map_elem + V * 4 + mean_count * 4
     step_bytes = {"likelihood": sum(n_pix * (24 + nf * (3 + map_elem)) for nf in units),
                   "fuse": F * fuse_frame_bytes,
@@ -670,7 +671,7 @@ def run_ours(args):
     # the fusion kernel of a group runs per plane of 32-byte records: its
     # launch depends on the frames per record, the likelihood's on G
     traffic = ncu_traffic(kern_names.get(dom, dom),
-                          {"lanes_x": fuse_cfg[0], "voxels_z": fuse_cfg[2],
+                          {"lanes_x": fuse_cfg[6], "voxels_z": fuse_cfg[7],
                            "frames_per_group": min(G, plane) if dom == "fuse" else G})
     roofline = {"bound": "hbm", "kernel": kern_names.get(dom, dom), "achieved": ach, "peak": peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
@@ -898,6 +899,7 @@ def run_ours(args):
                            "sequence_across_ranks": gathered,
                            "fuse_tile": {"lanes_x": fuse_cfg[0], "warps": fuse_cfg[1], "voxels_z": fuse_cfg[2],
                                          "staged": fuse_cfg[3]},
+                           "sequence_tile": {"lanes_x": fuse_cfg[6], "warps": 4, "voxels_z": fuse_cfg[7]},
                            "likelihood_ctas_per_sm": fuse_cfg[4],
                            "frames_per_group": G,
                            "autotune_fuse_us": {"x".join(map(str, k)): round(1e3 * v, 2) for k, v in tune_ms.items()},
@@ -1161,8 +1163,9 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
         # size, at least 16 frames for 16-bit maps)
         nseq = min(32, d_images.shape[0])
         G = max(int(fuse_cfg[5]), 16) if dtype != "f32" else max(int(fuse_cfg[5]), 1)
-        lx = fuse_cfg[0] if fuse_cfg[0] in (8, 16) else 8
-        psfs.psfs_set_fuse_config(rec.handle, lx, 4, 4, 0, fuse_cfg[4], G)
+        lx = fuse_cfg[6] if fuse_cfg[6] in (8, 16) else 8
+        tz = fuse_cfg[7] if fuse_cfg[7] in (2, 4) else 4   # 16-frame records need a tile height of 2 or 4
+        psfs.psfs_set_fuse_config(rec.handle, *fuse_cfg[:4], fuse_cfg[4], G, lx, tz)
         cap_s = 1 << 17
         occ_s = torch.empty((nseq, V), dtype=torch.float32, device=dev)
         lst_s = torch.empty((nseq, cap_s), dtype=torch.int32, device=dev)

@@ -129,7 +129,12 @@ typedef struct {
  * fusion item issues the map loads of that many cameras together before it
  * adds them, still camera by camera in the order 0 .. n_cams - 1, so the
  * results do not change; 1, 2 (lanes_x 8 or 16, voxels_z 4 or 8) or 4
- * (lanes_x 8 or 16, voxels_z 4); 0 in psfs_batch_set_config means 1. */
+ * (lanes_x 8 or 16, voxels_z 4); 0 in psfs_batch_set_config means 1.
+ * seq_lanes_x, seq_voxels_z: the tile shape of the sequence path (warps 4,
+ * staged 0) when it differs from the one-frame-per-call shape above: 0 in
+ * psfs_set_fuse_config makes the sequence path use lanes_x / voxels_z;
+ * psfs_get_fuse_config reports the shape the sequence path uses (and
+ * frames_per_group is checked against it). */
 typedef struct {
     int32_t lanes_x;
     int32_t warps;
@@ -138,6 +143,8 @@ typedef struct {
     int32_t seq_likelihood_ctas;
     int32_t frames_per_group;
     int32_t cameras_per_block;
+    int32_t seq_lanes_x;
+    int32_t seq_voxels_z;
 } psfs_fuse_config;
 
 typedef struct psfs_handle psfs_handle;
@@ -419,7 +426,9 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
  * distinct addresses) with 1 to 4 likelihood CTAs per SM at one frame per
  * launch, and frame groups of 2, 4, 8, 16 and 32 frames (direct tile shapes,
  * voxels_z 2, 4, 8 and 16, 1 to 3 likelihood CTAs per SM), and keeps the fastest
- * sequence configuration (which may change the tile shape).  The choices are
+ * sequence configuration.  The best one-frame shape stays the handle's tile
+ * shape for one frame per call; when frame groups win with another shape,
+ * the sequence path gets that shape and a tile plan of its own.  The choices are
  * remembered for handles of the same grid size, camera count, image size and
  * map type created later in the process.  Allocates and frees its own scratch; waits for the stream.
  * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */

@@ -73,6 +73,14 @@ struct psfs_handle {
     int seq_group = 1;
     void *gmaps[2] = {nullptr, nullptr};
     int group_cap = 0;
+    // the sequence path's own tile shape and plan (seq_own), when it differs
+    // from `shape` (the autotuner keeps the best shape for one frame per call
+    // in `shape` and the best one for frame groups here)
+    bool seq_own = false;
+    FuseShape seq_shape = kDefaultFuseShape;
+    uint64_t *seq_tiles = nullptr;
+    int4 *seq_tilecam = nullptr;
+    int seq_n_tiles = 0;
 
     // host-buffer sequence path (first use): kIoSlots chunk slots of device
     // staging, copies in and out on two streams of their own
@@ -211,6 +219,8 @@ void free_handle(psfs_handle *h)
     cudaFreeHost(h->h_words);
     cudaFree(h->tiles);
     cudaFree(h->tilecam);
+    cudaFree(h->seq_tiles);
+    cudaFree(h->seq_tilecam);
     cudaFree(h->st_images);
     cudaFree(h->st_occ);
     cudaFree(h->st_list);
@@ -324,6 +334,8 @@ struct Tuned {
     FuseShape shape;
     int seq_lk_ctas;
     int seq_group;
+    bool seq_own;
+    FuseShape seq_shape;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, Tuned> g_tuned;
@@ -372,6 +384,43 @@ psfs_status replan(psfs_handle *h, const FuseShape &shape)
     h->shape = shape;
     return PSFS_OK;
 }
+
+// Plans the sequence path's own tile shape (a direct shape of the frame-group
+// kernels) into seq_tiles / seq_tilecam.
+psfs_status replan_seq(psfs_handle *h, const FuseShape &shape)
+{
+    std::vector<uint64_t> tiles;
+    std::vector<int4> tilecam;
+    FuseArgs f{};
+    plan_fuse(h->grid, h->cams.data(), h->n_cams, h->params, shape, &f, &tiles, &tilecam);
+    uint64_t *d_tiles = nullptr;
+    int4 *d_tilecam = nullptr;
+    if (cudaMalloc(&d_tiles, tiles.size() * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&d_tilecam, tilecam.size() * sizeof(int4)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_tiles);
+        return fail(PSFS_ERR_NOMEM, "sequence tile plan allocation");
+    }
+    cudaError_t e = cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_tilecam, tilecam.data(), tilecam.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_tiles);
+        cudaFree(d_tilecam);
+        return fail_cuda(e, "sequence tile plan upload");
+    }
+    cudaFree(h->seq_tiles);
+    cudaFree(h->seq_tilecam);
+    h->seq_tiles = d_tiles;
+    h->seq_tilecam = d_tilecam;
+    h->seq_n_tiles = f.n_tiles;
+    h->seq_shape = shape;
+    h->seq_own = true;
+    return PSFS_OK;
+}
+
+// The tile shape of the sequence path.
+const FuseShape &seq_shape_of(const psfs_handle *h) { return h->seq_own ? h->seq_shape : h->shape; }
 
 }  // namespace
 
@@ -486,9 +535,12 @@ psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t 
             shape = it->second.shape;
             h->seq_lk_ctas = it->second.seq_lk_ctas;
             h->seq_group = it->second.seq_group;
+            h->seq_own = it->second.seq_own;
+            h->seq_shape = it->second.seq_shape;
         }
     }
     st = replan(h, shape);
+    if (st == PSFS_OK && h->seq_own) st = replan_seq(h, h->seq_shape);
     if (st != PSFS_OK) {
         free_handle(h);
         return st;
@@ -627,7 +679,7 @@ static psfs_status ensure_group_maps(psfs_handle *h, int frames)
 static int unit_frames(const psfs_handle *h, int group, int remaining)
 {
     for (int g = group; g >= 2; g >>= 1)
-        if (g <= remaining && group_shape_supported(h->shape, g, (int)h->map_elem)) return g;
+        if (g <= remaining && group_shape_supported(seq_shape_of(h), g, (int)h->map_elem)) return g;
     return 1;
 }
 
@@ -646,7 +698,8 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
 {
     psfs_status st = seq_setup(h);
     if (st != PSFS_OK) return st;
-    if (group > 1 && !group_shape_supported(h->shape, group, (int)h->map_elem)) group = 1;
+    const FuseShape sshape = seq_shape_of(h);
+    if (group > 1 && !group_shape_supported(sshape, group, (int)h->map_elem)) group = 1;
     const int first_unit = unit_frames(h, group, n_frames);   // the largest
     if (first_unit > 1) {
         st = ensure_group_maps(h, first_unit);
@@ -688,6 +741,11 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
         fill_fuse_args(h, occupancy + (size_t)f * occ_stride, voxel_lists + (size_t)f * list_stride, capacity,
                        counts + (size_t)f * count_stride, &fa);
         fa.maps = buf;
+        if (h->seq_own) {   // the sequence path's own tile plan
+            fa.tiles = h->seq_tiles;
+            fa.tilecam = h->seq_tilecam;
+            fa.n_tiles = h->seq_n_tiles;
+        }
         if (nf > 1) {
             fa.tmap_ok = 0;
             fa.occ_fstride = (int64_t)occ_stride;
@@ -700,9 +758,9 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
         {
             ProfScope ps(h, PSFS_STAGE_FUSE, sf);
             if (nf > 1) {
-                PSFS_CK(launch_fuse_group(fa, h->shape, nf, h->params.map_dtype, sf));
+                PSFS_CK(launch_fuse_group(fa, sshape, nf, h->params.map_dtype, sf));
             } else {
-                PSFS_CK(launch_fuse(fa, h->shape, h->params.map_dtype, sf));
+                PSFS_CK(launch_fuse(fa, sshape, h->params.map_dtype, sf));
             }
         }
         PSFS_CK(cudaEventRecord(h->seq_ev_fused[b], sf));
@@ -1499,8 +1557,12 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
     if (!fuse_shape_supported(shape)) return fail(PSFS_ERR_INVALID_ARG, "unsupported fuse tile shape");
     if (cfg->seq_likelihood_ctas < 0 || cfg->seq_likelihood_ctas > 4)
         return fail(PSFS_ERR_INVALID_ARG, "seq_likelihood_ctas outside [0, 4]");
+    const bool own = cfg->seq_lanes_x > 0 || cfg->seq_voxels_z > 0;
+    const FuseShape sshape = own ? FuseShape{cfg->seq_lanes_x, 4, cfg->seq_voxels_z, 0} : shape;
+    if (own && !fuse_shape_supported(sshape))
+        return fail(PSFS_ERR_INVALID_ARG, "unsupported sequence tile shape (seq_lanes_x, seq_voxels_z)");
     if (cfg->frames_per_group < 0 ||
-        (cfg->frames_per_group > 1 && !group_shape_supported(shape, cfg->frames_per_group, (int)h->map_elem)))
+        (cfg->frames_per_group > 1 && !group_shape_supported(sshape, cfg->frames_per_group, (int)h->map_elem)))
         return fail(PSFS_ERR_INVALID_ARG,
                     "frames_per_group: 0, 1, or 2 / 4 / 8 / 16 / 32 with staged 0, lanes_x 8 or 16, voxels_z 4 "
                     "(8 when a 32-byte pixel record holds at most 8 frames, 16 when at most 4)");
@@ -1512,7 +1574,11 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
     }
     if (cfg->seq_likelihood_ctas > 0) h->seq_lk_ctas = cfg->seq_likelihood_ctas;
     if (cfg->frames_per_group > 0) h->seq_group = cfg->frames_per_group;
-    return replan(h, shape);
+    psfs_status st = replan(h, shape);
+    if (st != PSFS_OK) return st;
+    if (own) return replan_seq(h, sshape);
+    h->seq_own = false;
+    return PSFS_OK;
 }
 
 psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg)
@@ -1525,6 +1591,8 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg)
     cfg->seq_likelihood_ctas = h->seq_lk_ctas;
     cfg->frames_per_group = h->seq_group;
     cfg->cameras_per_block = 1;
+    cfg->seq_lanes_x = seq_shape_of(h).lx;
+    cfg->seq_voxels_z = seq_shape_of(h).tz;
     return PSFS_OK;
 }
 
@@ -1631,9 +1699,11 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
         *ms_out = ms;
         return PSFS_OK;
     };
-    if (st == PSFS_OK) st = replan(h, best_shape);
+    if (st == PSFS_OK) st = replan(h, best_shape);   // the best shape for one frame per call
+    h->seq_own = false;
     float best_seq = 1e30f;
     int best_group = 1;
+    FuseShape best_seq_shape = best_shape;
     for (int lk = 1; lk <= 4 && st == PSFS_OK; ++lk) {
         float ms = 0.0f;
         st = time_sequence(lk, 1, &ms);
@@ -1649,14 +1719,14 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
             if (st != PSFS_OK) break;
             const FuseShape gshape = {group_lx, 4, tz, 0};
             if (!group_shape_supported(gshape, groups[gi], (int)h->map_elem)) continue;
-            st = replan(h, gshape);
+            st = replan_seq(h, gshape);
             for (int lk = 1; lk <= 3 && st == PSFS_OK; ++lk) {
                 float ms = 0.0f;
                 st = time_sequence(lk, groups[gi], &ms);
                 if (st == PSFS_OK && ms < best_seq) {
                     best_seq = ms;
                     best_group = groups[gi];
-                    best_shape = gshape;
+                    best_seq_shape = gshape;
                     h->seq_lk_ctas = lk;
                 }
             }
@@ -1672,11 +1742,17 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     cudaFree(tune_imgs);
     cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t), h->stream);   // the scratch list never overflows
     if (st != PSFS_OK) return st;
-    st = replan(h, best_shape);
-    if (st != PSFS_OK) return st;
+    // one frame per call keeps the best single-frame shape; the sequence path
+    // gets its own plan when frame groups won with another shape
+    h->seq_own = false;
+    if (best_group > 1 && !(best_seq_shape.lx == best_shape.lx && best_seq_shape.tz == best_shape.tz &&
+                            best_seq_shape.staged == best_shape.staged)) {
+        st = replan_seq(h, best_seq_shape);
+        if (st != PSFS_OK) return st;
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[tune_key(h)] = Tuned{best_shape, h->seq_lk_ctas, h->seq_group};
+        g_tuned[tune_key(h)] = Tuned{best_shape, h->seq_lk_ctas, h->seq_group, h->seq_own, h->seq_shape};
     }
     if (best) psfs_get_fuse_config(h, best);
     return PSFS_OK;

@@ -8,7 +8,7 @@
 //   dLoss/dg_kp  = sum over voxels v whose centre projects to pixel p of
 //                  camera k of dLoss/dL_v                         (pixel pass)
 //   dLoss/ds     = dLoss/dg ((2 P_D - 1) / a - (2 q - 1) / b)
-//   dLoss/dr     = dLoss/dg dg/dr,  r = log U - log N
+//   dLoss/dr     = dLoss/ds s (1 - s),  s = sigmoid(r), r = log U - log N
 //   dLoss/dmu_c  = dLoss/dr (-(I_c - mu_c) / var_c)
 //   dLoss/dvar_c = dLoss/dr (1 / (2 var_c) - (I_c - mu_c)^2 / (2 var_c^2))
 //

@@ -413,24 +413,6 @@ __device__ __forceinline__ float log_ratio_of_r(float r, const SensorConsts &c)
     return log_fast(div_fast(A, B));
 }
 
-// dg/dr of the function above, from the same e^-|r| terms:
-//   d/dr log(P_D e^r + 1 - P_D) = P_D e^r / (P_D e^r + 1 - P_D)
-__device__ __forceinline__ float dlog_ratio_dr(float r, const SensorConsts &c)
-{
-    const float ar = fabsf(r);
-    const float u = exp_fast(-ar);
-    if (r > 0.0f) {
-        const float A = fmaf(c.one_minus_pd, u, c.pd), B = fmaf(c.one_minus_q, u, c.q);
-        // A = e^-r exactly when P_D = 0: the first term is 0
-        const float t1 = c.a_zero_const_pos ? 0.0f : div_fast(c.pd, A);
-        return t1 - div_fast(c.q, B);
-    }
-    const float A = fmaf(c.pd, u, c.one_minus_pd), B = fmaf(c.q, u, c.one_minus_q);
-    // A = P_D u exactly when P_D = 1: the first term is 1
-    const float t1 = c.a_zero_const_neg ? 1.0f : div_fast(c.pd * u, A);
-    return t1 - div_fast(c.q * u, B);
-}
-
 // The text that psfs_last_error_message returns: every failing entry point
 // records it (per calling thread) and returns the status it is given
 // (psfs_api.cu).

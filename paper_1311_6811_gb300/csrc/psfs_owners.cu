@@ -175,43 +175,47 @@ __global__ void __launch_bounds__(256) scan_add_kernel(uint32_t *out, int64_t n,
         out[i] += sums[i / kScanChunk];
 }
 
-// Chain rule of pixel p for one frame: dLoss/dg = acc to the SLM and, from
-// the frame's colour `img` ([n_pix][3]; NULL: the caller's SLM), to the
-// background mean and variance.
-__device__ __forceinline__ void chain_rule(const BackwardArgs &b, int64_t p, const uint8_t *img, float acc,
-                                           float &dslm, float (&dm)[3], float (&dv)[3])
+// Chain rule of one frame from the pixel's background loaded once (mu, h =
+// 1 / (2 var), base = c0 - log(h0 h1 h2) / 2 = pixel_log_base, so that r =
+// base + pixel_quad is pixel_log_odds bit for bit):
+//   s = sigmoid(r) (the bits of sigmoid_fast), from u = e^-|r|;
+//   dLoss/ds = acc (da / a(s) - db / b(s))            (Eq. 5-9, a, b linear in s)
+//   dLoss/dr = dLoss/ds s (1 - s), with s (1 - s) = u / (1 + u)^2 (no cancellation)
+//   dLoss/dmu_c, dLoss/dvar_c from dLoss/dr (Eq. 1).
+__device__ __forceinline__ void chain_rule_pre(const BackwardArgs &b, const uint8_t *im, const float (&mu)[3],
+                                               const float (&hh)[3], float base, float acc, float &dslm,
+                                               float (&dm)[3], float (&dv)[3])
 {
     dslm = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) dm[c] = dv[c] = 0.0f;
     if (acc != 0.0f) {
-        float s_val;
-        float r = 0.0f, dd[3] = {0.0f, 0.0f, 0.0f}, hh[3] = {0.0f, 0.0f, 0.0f};
-        if (img) {
-            const uint8_t *im = img + 3 * p;
-            const float *mu = b.mean + 3 * p, *hv = b.hinv + 3 * p;
+        float dd[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                dd[c] = (float)im[c] - mu[c];
-                hh[c] = hv[c];
-            }
-            r = pixel_log_odds((float)im[0], (float)im[1], (float)im[2], mu[0], mu[1], mu[2], hh[0], hh[1], hh[2],
-                               b.c0);
-            s_val = sigmoid_fast(r);
-        } else {
-            s_val = __ldg(b.slm + p);
-        }
+        for (int c = 0; c < 3; ++c) dd[c] = (float)im[c] - mu[c];
+        const float r = base + pixel_quad((float)im[0], (float)im[1], (float)im[2], mu[0], mu[1], mu[2], hh[0],
+                                          hh[1], hh[2]);
+        const float u = exp_fast(-fabsf(r));
+        const float inv = rcp_approx(1.0f + u);
+        const float s_val = r > 0.0f ? inv : u * inv;
         const float av = fmaf(b.da, s_val, b.one_minus_pd), bv = fmaf(b.db, s_val, b.one_minus_q);
-        dslm = acc * (b.da / av - b.db / bv);
-        if (img) {
-            const float dr = acc * dlog_ratio_dr(r, b.sc);
+        dslm = acc * (div_fast(b.da, av) - div_fast(b.db, bv));
+        const float dr = dslm * (u * inv * inv);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                dm[c] = -2.0f * dr * dd[c] * hh[c];
-                dv[c] = dr * hh[c] * (1.0f - 2.0f * dd[c] * dd[c] * hh[c]);
-            }
+        for (int c = 0; c < 3; ++c) {
+            dm[c] = -2.0f * dr * dd[c] * hh[c];
+            dv[c] = dr * hh[c] * (1.0f - 2.0f * dd[c] * dd[c] * hh[c]);
         }
     }
+}
+
+// dLoss/dSLM of pixel p from a caller-supplied SLM (psfs_backward_slm).
+__device__ __forceinline__ float chain_rule_slm(const BackwardArgs &b, int64_t p, float acc)
+{
+    if (acc == 0.0f) return 0.0f;
+    const float s_val = __ldg(b.slm + p);
+    const float av = fmaf(b.da, s_val, b.one_minus_pd), bv = fmaf(b.db, s_val, b.one_minus_q);
+    return acc * (div_fast(b.da, av) - div_fast(b.db, bv));
 }
 
 // One frame: pixel p sums b.dl over its segment in ascending voxel order.
@@ -236,41 +240,27 @@ __global__ void __launch_bounds__(256) owner_pixel_kernel(const __grid_constant_
         }
         for (; e < e1; ++e) acc += __ldg(b.dl + __ldg(vox + e));
         float dslm, dm[3], dv[3];
-        chain_rule(b, p, b.img, acc, dslm, dm, dv);
+        if (b.img) {
+            float mu[3] = {0.0f, 0.0f, 0.0f}, hh[3] = {0.0f, 0.0f, 0.0f}, base = 0.0f;
+            if (acc != 0.0f) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    mu[c] = __ldg(b.mean + 3 * p + c);
+                    hh[c] = __ldg(b.hinv + 3 * p + c);
+                }
+                base = pixel_log_base(hh[0], hh[1], hh[2], b.c0);
+            }
+            chain_rule_pre(b, b.img + 3 * p, mu, hh, base, acc, dslm, dm, dv);
+        } else {
+            dslm = chain_rule_slm(b, p, acc);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dm[c] = dv[c] = 0.0f;
+        }
         if (b.d_slm) b.d_slm[p] = dslm;
         if (b.d_mean)
             for (int c = 0; c < 3; ++c) b.d_mean[3 * p + c] = dm[c];
         if (b.d_var)
             for (int c = 0; c < 3; ++c) b.d_var[3 * p + c] = dv[c];
-    }
-}
-
-// Chain rule of one frame from the pixel's background loaded once: h = 1 /
-// (2 var), base = c0 - log(h0 h1 h2) / 2 (pixel_log_base), so that r = base
-// + pixel_quad is pixel_log_odds bit for bit and the result that of
-// chain_rule.
-__device__ __forceinline__ void chain_rule_pre(const BackwardArgs &b, const uint8_t *im, const float (&mu)[3],
-                                               const float (&hh)[3], float base, float acc, float &dslm,
-                                               float (&dm)[3], float (&dv)[3])
-{
-    dslm = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) dm[c] = dv[c] = 0.0f;
-    if (acc != 0.0f) {
-        float dd[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dd[c] = (float)im[c] - mu[c];
-        const float r = base + pixel_quad((float)im[0], (float)im[1], (float)im[2], mu[0], mu[1], mu[2], hh[0],
-                                          hh[1], hh[2]);
-        const float s_val = sigmoid_fast(r);
-        const float av = fmaf(b.da, s_val, b.one_minus_pd), bv = fmaf(b.db, s_val, b.one_minus_q);
-        dslm = acc * (b.da / av - b.db / bv);
-        const float dr = acc * dlog_ratio_dr(r, b.sc);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            dm[c] = -2.0f * dr * dd[c] * hh[c];
-            dv[c] = dr * hh[c] * (1.0f - 2.0f * dd[c] * dd[c] * hh[c]);
-        }
     }
 }
 

@@ -77,7 +77,7 @@ def test_groups_equal_frame_by_frame(group, tz, dtype):
     cap = rec.n_voxels
     for lx in (8, 16):
         psfs.psfs_set_fuse_config(rec.handle, lx, 4, tz, 0, 2, group)
-        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, group)
+        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, group, lx, tz)
         occ, lists, counts = _run_sequence(rec, imgs, cap)
         _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap)
     rec.close()
@@ -98,7 +98,7 @@ def test_groups_of_32_equal_frame_by_frame(tz, dtype):
     cap = rec.n_voxels
     for lx in (8, 16):
         psfs.psfs_set_fuse_config(rec.handle, lx, 4, tz, 0, 2, 32)
-        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, 32)
+        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, 32, lx, tz)
         occ, lists, counts = _run_sequence(rec, imgs, cap)
         _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap)
     rec.close()
@@ -292,7 +292,38 @@ def test_autotune_picks_a_sequence_configuration():
     psfs.psfs_autotune(rec.handle, to_dev(sc.images[0]), reps=1)
     cfg = psfs.psfs_get_fuse_config(rec.handle, full=True)
     assert cfg[5] in (1, 2, 4, 8, 16, 32) and 1 <= cfg[4] <= 4
+    # the one-frame shape is one of the one-frame candidates; the sequence
+    # path's shape supports its group size
+    assert cfg[:4] in psfs.FUSE_CONFIGS
+    assert cfg[5] == 1 or cfg[7] in (2, 4, 8, 16)
     assert rec.sync() == psfs.PSFS_OK
+    rec.close()
+
+
+def test_sequence_with_its_own_tile_shape():
+    """A sequence tile shape of its own (seq_lanes_x, seq_voxels_z) while one
+    frame per call keeps another shape: both give the same bits."""
+    sc = _scene(5)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    F, V = imgs.shape[0], rec.n_voxels
+    psfs.psfs_set_fuse_config(rec.handle, 32, 4, 16, 0, 2, 4, 16, 2)
+    assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (32, 4, 16, 0, 2, 4, 16, 2)
+    occ = torch.empty((F, V), device="cuda")
+    lst = torch.empty((F, V), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(F, dtype=torch.int32, device="cuda")
+    psfs.psfs_reconstruct_sequence(rec.handle, F, imgs, occ, lst, V, cnt)
+    assert rec.sync() == psfs.PSFS_OK
+    for f in range(F):
+        o1, _, c1 = rec.reconstruct(imgs[f])
+        assert rec.sync() == psfs.PSFS_OK
+        assert torch.equal(o1.view(-1), occ[f]) and int(c1.item()) == int(cnt[f])
+    # back to one shape for both
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 4, 0, 2, 4)
+    assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (8, 4, 4, 0, 2, 4, 8, 4)
+    with pytest.raises(psfs.PsfsError):
+        psfs.psfs_set_fuse_config(rec.handle, 8, 4, 4, 0, 2, 4, 12, 2)   # no such sequence shape
     rec.close()
 
 
