@@ -678,19 +678,20 @@ def run_ours(args):
                 "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": traffic,
                 "alg_bytes_per_launch": stages[dom]["alg_bytes_per_launch"],
                 "units_per_step": units,
-                "note": ("the fusion kernels are bound by L1 gather throughput (ncu: 72 % of L1 peak, 66 % of its data pipe, for "
-                         "fuse_group_kernel), not by HBM")
+                "note": ("the fusion kernels are bound by their gathers' L2 -> L1 sectors (ncu: L2 62 %, L1 77 % busy for "
+                         "fuse_group_kernel; one 32-byte sector per voxel, camera and plane of 8 frames), not by HBM; "
+                         "roofline_sequence gives the whole step against HBM")
                         if dom == "fuse" else None}
-    # the whole step against the per-frame algorithmic bytes of the single-frame
-    # method (images 3 + background 24 + maps 2 x map bytes per pixel,
-    # occupancy 4 per voxel, list): what frame groups save shows up as a
-    # figure the DRAM does not actually move
-    per_frame_bytes = n_pix * (3 + 24 + 2 * map_elem) + V * 4 + mean_count * 4
-    seq_gbs = per_frame_bytes * F * args.steps / (ms_local * 1e-3) / 1e9
-    roofline_sequence = {"alg_bytes_per_frame": per_frame_bytes, "achieved": seq_gbs, "peak": peak,
+    # the whole step against the bytes the grouped method moves: per unit of
+    # nf frames the background once (24 B per pixel), nf images (3 B per
+    # pixel), nf maps written and read back (2 x map bytes per pixel), nf
+    # occupancy grids (4 B per voxel) and lists
+    step_alg = sum(n_pix * 24 + nf * (n_pix * (3 + 2 * map_elem) + V * 4 + mean_count * 4) for nf in units)
+    seq_gbs = step_alg * args.steps / (ms_local * 1e-3) / 1e9
+    roofline_sequence = {"alg_bytes_per_frame": step_alg / F, "achieved": seq_gbs, "peak": peak,
                          "unit": "GB/s", "frac": seq_gbs / peak,
-                         "note": "per-frame bytes as if the background were read every frame; frame groups read "
-                                 "it once per group, so this can exceed the DRAM traffic"}
+                         "note": "whole step: the bytes the grouped method moves per frame (background once per "
+                                 "unit, images, maps written and read, occupancy, lists) over the step time"}
 
     # inner-voxel removal on the step's lists (all frames in one call), timed
     # with events on the handle's stream; not part of the headline value
