@@ -996,7 +996,7 @@ psfs_status psfs_reproject(psfs_handle *h, int32_t n_frames, const uint32_t *vox
     DeviceGuard guard(h->device);
     ReprojectArgs a{};
     for (int c = 0; c < h->n_cams; ++c) a.cam[c] = h->fuse.cam[c];
-    plan_backward_inv(h->grid, h->cams.data(), h->n_cams, h->fuse, a.inv);
+    plan_pixel_rays(h->grid, h->cams.data(), h->n_cams, h->fuse, a.inv);
     a.lists = voxel_lists;
     a.list_stride = list_stride;
     a.counts = counts;

@@ -435,11 +435,8 @@ cudaError_t launch_likelihood(const LikelihoodArgs &a, int map_dtype, bool slm_o
                               int ctas_per_sm = 4);
 cudaError_t launch_slm_to_map(const SlmToMapArgs &a, int map_dtype, cudaStream_t s);
 
-// Adjoint (psfs_backward.cu).  The voxel pass recomputes the log-odds of
-// every voxel from the maps (exactly as the forward) and writes
-// dLoss/dL = dLoss/docc occ (1 - occ); the pixel pass forms per pixel the sum
-// of dLoss/dL over the voxels whose centre projects into it, then the chain
-// rule to the SLM, mean and variance.
+// A camera seen from its pixels (for the silhouettes of listed voxels): the
+// ray of a pixel in voxel-index coordinates.
 struct PixelInv {
     float qc[3];    // camera centre in continuous voxel-index coordinates (voxel centres at integers)
     float minv[9];  // pixel (x, y, 1) -> ray direction in voxel-index coordinates, row-major
@@ -482,6 +479,11 @@ cudaError_t launch_weights(const WeightArgs &a, int n_particles, cudaStream_t s)
 // pixel pass): frame f of voxel v at dl[v * kBwRecord + f], 32 bytes per voxel.
 constexpr int kBwRecord = 8;
 
+// Adjoint (psfs_backward.cu, psfs_owners.cu).  The voxel pass recomputes the
+// log-odds of every voxel from the maps (exactly as the forward) and writes
+// dLoss/dL = dLoss/docc occ (1 - occ); the pixel pass forms per pixel the sum
+// of dLoss/dL over the voxels whose centre projects into it (its owner list),
+// then the chain rule to the SLM, mean and variance.
 struct BackwardArgs {
     FuseArgs f;                   // grid, cameras, maps (for the voxel pass), tiles
     const float *d_occ;           // [n_vox]
@@ -541,8 +543,8 @@ struct BatchLaunch {
 bool batch_shape_supported(const FuseShape &shape, int cameras_per_block);
 cudaError_t launch_batch(const BatchLaunch &b, const FuseShape &shape, int cameras_per_block, int map_dtype,
                          cudaStream_t s);
-void plan_backward_inv(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const FuseArgs &f,
-                       PixelInv *inv);
+void plan_pixel_rays(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const FuseArgs &f,
+                     PixelInv *inv);
 // Owner lists of the adjoint's pixel pass (psfs_owners.cu): for every pixel
 // of every camera, the voxels whose centre the forward projects into it, in
 // ascending order: segment p is vox[off[p] .. off[p + 1]).  Buffers: cnt

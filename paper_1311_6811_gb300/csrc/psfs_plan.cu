@@ -229,8 +229,8 @@ void plan_fuse(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const
     build_tilecam(grid, cams, n_cams, f, shape, params.map_dtype, *tiles_out, *tilecam_out);
 }
 
-void plan_backward_inv(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const FuseArgs &f,
-                       PixelInv *inv)
+void plan_pixel_rays(const psfs_grid &grid, const psfs_camera *cams, int n_cams, const FuseArgs &f,
+                     PixelInv *inv)
 {
     const double vs = grid.voxel_size;
     const double eps32 = std::ldexp(1.0, -24);
