@@ -810,7 +810,7 @@ def run_ours(args):
         h_occ = torch.empty((F, V), dtype=torch.float32).pin_memory()
         h_list = torch.empty((F, cap_e2e), dtype=torch.int32).pin_memory()
         h_cnt = torch.zeros((F,), dtype=torch.int32).pin_memory()
-        e2e_steps = max(1, min(args.steps, 5))
+        e2e_steps = max(1, min(args.steps, 10))
         psfs.psfs_reconstruct_sequence_host(h, F, h_images, h_occ, h_list, cap_e2e, h_cnt)   # warm-up
         d2h = 0
         barrier()
