@@ -218,39 +218,27 @@ __device__ __forceinline__ float chain_rule_slm(const BackwardArgs &b, int64_t p
     return acc * (div_fast(b.da, av) - div_fast(b.db, bv));
 }
 
-// The pixel passes stage their owners' dLoss/dL in shared memory.  A CTA
-// owns kOwnerPixels consecutive pixels, whose owner segments are consecutive
-// in `vox`: [E0, E1).  The CTA walks that range in chunks of kCap entries:
-// every thread gathers entries of the chunk (coalesced index loads, many
-// independent dL loads in flight), then each thread adds the entries of its
-// own segment that lie in the chunk, in ascending order.  Chunks go in
-// ascending order too, so each pixel's sum is the same sequence of adds as a
-// walk of its own segment: ascending voxel order, no float atomics.
-constexpr int kOwnerPixels = 256;
-constexpr int kOwnerCap = 2048;        // one-frame dL values per chunk (8 KB)
-constexpr int kOwnerCapRec = 768;      // 32-byte records per chunk (24 KB)
-
 // One frame: pixel p sums b.dl over its segment in ascending voxel order.
-__global__ void __launch_bounds__(kOwnerPixels) owner_pixel_kernel(const __grid_constant__ BackwardArgs b,
-                                                                   const uint32_t *off, const uint32_t *vox)
+__global__ void __launch_bounds__(256) owner_pixel_kernel(const __grid_constant__ BackwardArgs b, const uint32_t *off,
+                                                          const uint32_t *vox)
 {
-    __shared__ float s_dl[kOwnerCap];
-    const int t = threadIdx.x;
-    for (int64_t p0 = (int64_t)blockIdx.x * kOwnerPixels; p0 < b.n_pix; p0 += (int64_t)gridDim.x * kOwnerPixels) {
-        const int64_t p = p0 + t;
-        const bool have = p < b.n_pix;
-        const uint32_t e0 = have ? __ldg(off + p) : 0u, e1 = have ? __ldg(off + p + 1) : 0u;
-        const uint32_t E0 = __ldg(off + p0), E1 = __ldg(off + min(p0 + kOwnerPixels, b.n_pix));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < b.n_pix; p += stride) {
+        const uint32_t e0 = __ldg(off + p), e1 = __ldg(off + p + 1);
         float acc = 0.0f;
-        for (uint32_t c0 = E0; c0 < E1; c0 += kOwnerCap) {
-            const uint32_t c1 = min(c0 + (uint32_t)kOwnerCap, E1);
-            for (uint32_t e = c0 + t; e < c1; e += kOwnerPixels) s_dl[e - c0] = __ldg(b.dl + __ldg(vox + e));
-            __syncthreads();
-            const uint32_t lo = max(e0, c0), hi = min(e1, c1);
-            for (uint32_t e = lo; e < hi; ++e) acc += s_dl[e - c0];
-            __syncthreads();
+        // four owners at a time: their index and dL loads are independent,
+        // so they are in flight together; the adds stay in ascending order
+        uint32_t e = e0;
+        for (; e + 4 <= e1; e += 4) {
+            const uint32_t v0 = __ldg(vox + e), v1 = __ldg(vox + e + 1), v2 = __ldg(vox + e + 2),
+                           v3 = __ldg(vox + e + 3);
+            const float d0 = __ldg(b.dl + v0), d1 = __ldg(b.dl + v1), d2 = __ldg(b.dl + v2), d3 = __ldg(b.dl + v3);
+            acc += d0;
+            acc += d1;
+            acc += d2;
+            acc += d3;
         }
-        if (!have) continue;
+        for (; e < e1; ++e) acc += __ldg(b.dl + __ldg(vox + e));
         float dslm, dm[3], dv[3];
         if (b.img) {
             float mu[3] = {0.0f, 0.0f, 0.0f}, hh[3] = {0.0f, 0.0f, 0.0f}, base = 0.0f;
@@ -286,52 +274,42 @@ __device__ __forceinline__ void load_record(const float *rec, uint32_t (&w)[8])
 }
 
 // Up to kBwRecord frames: b.dl holds records of kBwRecord floats per voxel
-// (frame f of voxel v at b.dl[v * kBwRecord + f]); the chunks hold whole
-// records, one 32-byte load per owned voxel serving every frame.  Per frame
-// the sum (same voxels, same order) and the chain rule are those of
-// owner_pixel_kernel, so d_slm (frame f at b.d_slm + f n_pix) is
-// bit-identical to one frame per call; d_mean and d_var receive the frames'
-// gradients added in frame order to 0 (or, with `accumulate`, to what they
-// hold).  The pixel's background is read once for all frames.
-__global__ void __launch_bounds__(kOwnerPixels) owner_pixel_group_kernel(const __grid_constant__ BackwardArgs b,
-                                                                         const uint32_t *off, const uint32_t *vox,
-                                                                         int n_frames, int64_t img_fstride,
-                                                                         int accumulate)
+// (frame f of voxel v at b.dl[v * kBwRecord + f]), one 32-byte load per
+// owned voxel serves every frame.  Per frame the sum (same voxels, same
+// order) and the chain rule are those of owner_pixel_kernel, so d_slm (frame
+// f at b.d_slm + f n_pix) is bit-identical to one frame per call; d_mean and
+// d_var receive the frames' gradients added in frame order to 0 (or, with
+// `accumulate`, to what they hold).  The pixel's background is read once for
+// all frames.
+__global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_constant__ BackwardArgs b,
+                                                                const uint32_t *off, const uint32_t *vox,
+                                                                int n_frames, int64_t img_fstride, int accumulate)
 {
-    __shared__ uint4 s_rec[kOwnerCapRec][2];
-    const int t = threadIdx.x;
-    for (int64_t p0 = (int64_t)blockIdx.x * kOwnerPixels; p0 < b.n_pix; p0 += (int64_t)gridDim.x * kOwnerPixels) {
-        const int64_t p = p0 + t;
-        const bool have = p < b.n_pix;
-        const uint32_t e0 = have ? __ldg(off + p) : 0u, e1 = have ? __ldg(off + p + 1) : 0u;
-        const uint32_t E0 = __ldg(off + p0), E1 = __ldg(off + min(p0 + kOwnerPixels, b.n_pix));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < b.n_pix; p += stride) {
+        const uint32_t e0 = __ldg(off + p), e1 = __ldg(off + p + 1);
         float acc[kBwRecord];
 #pragma unroll
         for (int f = 0; f < kBwRecord; ++f) acc[f] = 0.0f;
-        for (uint32_t c0 = E0; c0 < E1; c0 += kOwnerCapRec) {
-            const uint32_t c1 = min(c0 + (uint32_t)kOwnerCapRec, E1);
-            for (uint32_t e = c0 + t; e < c1; e += kOwnerPixels) {
-                uint32_t w[8];
-                load_record(b.dl + (size_t)__ldg(vox + e) * kBwRecord, w);
-                s_rec[e - c0][0] = make_uint4(w[0], w[1], w[2], w[3]);
-                s_rec[e - c0][1] = make_uint4(w[4], w[5], w[6], w[7]);
-            }
-            __syncthreads();
-            const uint32_t lo = max(e0, c0), hi = min(e1, c1);
-            for (uint32_t e = lo; e < hi; ++e) {
-                const uint4 x = s_rec[e - c0][0], y = s_rec[e - c0][1];
-                acc[0] += __uint_as_float(x.x);
-                acc[1] += __uint_as_float(x.y);
-                acc[2] += __uint_as_float(x.z);
-                acc[3] += __uint_as_float(x.w);
-                acc[4] += __uint_as_float(y.x);
-                acc[5] += __uint_as_float(y.y);
-                acc[6] += __uint_as_float(y.z);
-                acc[7] += __uint_as_float(y.w);
-            }
-            __syncthreads();
+        // two owners at a time (their loads in flight together), added in
+        // ascending order; one 256-bit read-only load per record (one sector)
+        uint32_t e = e0;
+        for (; e + 2 <= e1; e += 2) {
+            const uint32_t va = __ldg(vox + e), vb = __ldg(vox + e + 1);
+            uint32_t wa[8], wb[8];
+            load_record(b.dl + (size_t)va * kBwRecord, wa);
+            load_record(b.dl + (size_t)vb * kBwRecord, wb);
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wa[f]);
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wb[f]);
         }
-        if (!have) continue;
+        if (e < e1) {
+            uint32_t w[8];
+            load_record(b.dl + (size_t)__ldg(vox + e) * kBwRecord, w);
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(w[f]);
+        }
         float tm[3] = {0.0f, 0.0f, 0.0f}, tv[3] = {0.0f, 0.0f, 0.0f};
         if (accumulate) {
 #pragma unroll
@@ -445,7 +423,7 @@ cudaError_t launch_dl_from_occ(const float *occ, const float *d_occ, float *dl, 
 
 cudaError_t launch_owner_pixel(const BackwardArgs &b, const uint32_t *off, const uint32_t *vox, cudaStream_t s)
 {
-    owner_pixel_kernel<<<(int)grid_for(b.n_pix), kOwnerPixels, 0, s>>>(b, off, vox);
+    owner_pixel_kernel<<<(int)grid_for(b.n_pix), 256, 0, s>>>(b, off, vox);
     return cudaGetLastError();
 }
 
@@ -454,8 +432,8 @@ cudaError_t launch_owner_pixel_group(const BackwardArgs &b, const uint32_t *off,
 {
     if (n_frames < 1 || n_frames > kBwRecord || !b.img || ((uintptr_t)b.dl & 31u))
         return cudaErrorInvalidValue;
-    owner_pixel_group_kernel<<<(int)grid_for(b.n_pix), kOwnerPixels, 0, s>>>(b, off, vox, n_frames, img_fstride,
-                                                                               accumulate ? 1 : 0);
+    owner_pixel_group_kernel<<<(int)grid_for(b.n_pix), 256, 0, s>>>(b, off, vox, n_frames, img_fstride,
+                                                                      accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 
