@@ -5,7 +5,7 @@
 // camera centre through the pixel centre meets, in front of the camera, the
 // cube of a listed voxel.
 //
-// One thread per (listed voxel, camera): the eight cube corners are projected
+// One thread per (camera, listed voxel): the eight cube corners are projected
 // with the forward kernels' matrices, the pixels whose centres can fall
 // inside that projection (its bounding box, widened against float32
 // rounding) are tested with a float32 slab test of their centre rays in
@@ -34,8 +34,13 @@ __global__ void __launch_bounds__(kRpThreads) reproject_kernel(const __grid_cons
     const uint64_t n_items = (uint64_t)m_cnt * K;
     for (uint64_t it = (uint64_t)blockIdx.x * kRpThreads + threadIdx.x; it < n_items;
          it += (uint64_t)gridDim.x * kRpThreads) {
-        const uint32_t e = (uint32_t)(it / K);
-        const int c = (int)(it - (uint64_t)e * K);
+        // camera-major: the lanes of a warp take consecutive listed voxels of
+        // one camera.  Consecutive voxels of a list are neighbours in space
+        // (the fusion compacts tile by tile), so their pixel boxes overlap
+        // and a warp's byte stores land in few sectors; the camera's
+        // matrices are the same for the whole warp.
+        const int c = (int)(it / m_cnt);
+        const uint32_t e = (uint32_t)(it - (uint64_t)c * m_cnt);
         const uint32_t v = __ldg(list + e);
         if (v >= a.n_vox) continue;
         const uint32_t kz = v / nxy, r = v - kz * nxy, jy = r / nx, ix = r - jy * nx;
