@@ -173,14 +173,16 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # helpers
 # --------------------------------------------------------------------------- #
-def sequence_units(n_frames, group, voxels_z=4, map_elem=4):
+def sequence_units(n_frames, group, voxels_z=4, map_elem=4, record_bytes=32):
     """Frames per unit of psfs_reconstruct_sequence: groups of `group` frames
     while they fill, then the largest smaller power-of-two groups that fit and
-    whose 32-byte pixel records (P = min(g, 32 / map_elem) frames) the tile
-    height supports (voxels_z 2 or 4; 8 when P <= 8; 16 when P <= 4), else single
-    frames."""
+    whose pixel records (P = min(g, record_bytes / map_elem) frames) the tile
+    height supports (voxels_z 2 or 4; 8 when P <= 8; 16 when P <= 4; only 2 or
+    4 for a 64-byte record, two lanes per voxel), else single frames."""
     def ok(g):
-        p = min(g, 32 // map_elem)
+        p = min(g, record_bytes // map_elem)
+        if p * map_elem == 64:
+            return voxels_z in (2, 4)
         return voxels_z in (2, 4) or (voxels_z == 8 and p <= 8) or (voxels_z == 16 and p <= 4)
 
     units, left = [], n_frames
@@ -634,18 +636,22 @@ def run_ours(args):
     # nf occupancy grids and lists.
     map_elem = 4 if args.map_dtype == "f32" else 2
     G = fuse_cfg[5] if batch is None else 1
-    units = sequence_units(F, G, fuse_cfg[7], map_elem)   # the sequence path's tile height
+    rec_bytes = fuse_cfg[8]
+    units = sequence_units(F, G, fuse_cfg[7], map_elem, rec_bytes)   # the sequence path's tile height
     fuse_frame_bytes = n_pix * map_elem + V * 4 + mean_count * 4
     step_bytes = {"likelihood": sum(n_pix * (24 + nf * (3 + map_elem)) for nf in units),
                   "fuse": F * fuse_frame_bytes,
                   "batch": F * (n_pix * (3 + 24 + map_elem) + fuse_frame_bytes)}
     grouped = G > 1
+    # frames per plane of pixel records; a plane of 64-byte records runs the
+    # two-lanes-per-voxel fusion kernel
+    plane = rec_bytes // map_elem
+    pair = grouped and min(G, plane) * map_elem == 64
     kern_names = {"likelihood": "likelihood_group_kernel" if grouped else "likelihood_kernel",
-                  "fuse": "fuse_group_kernel" if grouped else "fuse_kernel",
+                  "fuse": ("fuse_pair_kernel" if pair else "fuse_group_kernel") if grouped else "fuse_kernel",
                   "batch": "batch_kernel"}
     # kernel launches: one likelihood launch per unit, one fusion launch per
-    # plane of 32-byte pixel records (a unit's stage events span its planes)
-    plane = 32 // map_elem
+    # plane of pixel records (a unit's stage events span its planes)
     fuse_launches = sum(-(-nf // plane) if nf > 1 else 1 for nf in units)
     if batch is None:
         gpu_launches = args.steps * (len(units) + fuse_launches)
@@ -678,8 +684,8 @@ def run_ours(args):
                 "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": traffic,
                 "alg_bytes_per_launch": stages[dom]["alg_bytes_per_launch"],
                 "units_per_step": units,
-                "note": ("the fusion kernels are bound by their gathers' L2 -> L1 sectors (ncu: L2 62 %, L1 77 % busy for "
-                         "fuse_group_kernel; one 32-byte sector per voxel, camera and plane of 8 frames), not by HBM; "
+                "note": ("the fusion kernels are bound by the L2 -> L1 sector rate of their gathers (one 32-byte "
+                         "sector per voxel, camera and 8 FP32 frames; ncu: L2 62 %, L1 77 % busy), not by HBM; "
                          "roofline_sequence gives the whole step against HBM")
                         if dom == "fuse" else None}
     # the whole step against the bytes the grouped method moves: per unit of
@@ -900,14 +906,15 @@ def run_ours(args):
                            "sequence_across_ranks": gathered,
                            "fuse_tile": {"lanes_x": fuse_cfg[0], "warps": fuse_cfg[1], "voxels_z": fuse_cfg[2],
                                          "staged": fuse_cfg[3]},
-                           "sequence_tile": {"lanes_x": fuse_cfg[6], "warps": 4, "voxels_z": fuse_cfg[7]},
+                           "sequence_tile": {"lanes_x": fuse_cfg[6], "warps": 4, "voxels_z": fuse_cfg[7],
+                                             "record_bytes": rec_bytes},
                            "likelihood_ctas_per_sm": fuse_cfg[4],
                            "frames_per_group": G,
                            "autotune_fuse_us": {"x".join(map(str, k)): round(1e3 * v, 2) for k, v in tune_ms.items()},
                            "launch": ("psfs_batch_run (one persistent kernel, CUDA graph)" if batch is not None
                                       else f"psfs_reconstruct_sequence (frame groups of {G}: one background pass "
-                                      f"per group, one fusion launch per plane of {min(max(G, 1), 32 // map_elem)} "
-                                      "frames; 2 streams, double-buffered maps)"),
+                                      f"per group, one fusion launch per plane of {min(max(G, 1), plane)} "
+                                      f"frames ({rec_bytes}-byte pixel records); 2 streams, double-buffered maps)"),
                            "background_l2_resident": not args.no_l2_background},
                 "err_vs_fp64": err_vs_fp64,
                 "configs": configs,
@@ -1166,7 +1173,7 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
         G = max(int(fuse_cfg[5]), 16) if dtype != "f32" else max(int(fuse_cfg[5]), 1)
         lx = fuse_cfg[6] if fuse_cfg[6] in (8, 16) else 8
         tz = fuse_cfg[7] if fuse_cfg[7] in (2, 4) else 4   # 16-frame records need a tile height of 2 or 4
-        psfs.psfs_set_fuse_config(rec.handle, *fuse_cfg[:4], fuse_cfg[4], G, lx, tz)
+        psfs.psfs_set_fuse_config(rec.handle, *fuse_cfg[:4], fuse_cfg[4], G, lx, tz, fuse_cfg[8])
         cap_s = 1 << 17
         occ_s = torch.empty((nseq, V), dtype=torch.float32, device=dev)
         lst_s = torch.empty((nseq, cap_s), dtype=torch.int32, device=dev)

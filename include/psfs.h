@@ -115,13 +115,15 @@ typedef struct {
  * frames_per_group: frames per launch on the sequence path: 1 = one frame
  * per likelihood and fusion launch; 2, 4, 8, 16 or 32 = frame groups, where
  * one likelihood launch reads the background once for the whole group and
- * writes the group's maps as 32-byte pixel records of P frames (P = 8 for
- * FP32 maps, 16 for 16-bit maps, the group size when smaller), one plane of
- * records per P frames; one fusion launch per plane projects each voxel once
- * per camera and gathers the plane's P frames with one vector load (each
- * frame's results are bit-identical to one frame per launch).  Groups need
- * staged = 0, lanes_x 8 or 16, and voxels_z 2 or 4, or 8 when P <= 8, or 16 when
- * P <= 4; with another shape the sequence path runs one frame per launch.
+ * writes the group's maps as pixel records of seq_record_bytes bytes holding
+ * P frames (P = seq_record_bytes / map element size, the group size when
+ * smaller), one plane of records per P frames; one fusion launch per plane
+ * projects each voxel once per camera and gathers the plane's P frames with
+ * one 32-byte vector load per lane (two lanes per voxel for a 64-byte
+ * record; each frame's results are bit-identical to one frame per launch).
+ * Groups need staged = 0, lanes_x 8 or 16, and voxels_z 2 or 4, or 8 when a
+ * lane holds at most 8 frames, or 16 when at most 4 (2 or 4 with 64-byte
+ * records); with another shape the sequence path runs one frame per launch.
  * Trailing frames that do not fill a group run in the largest smaller groups
  * that fit, the last odd frame alone.  0 in psfs_set_fuse_config keeps the
  * current value.  The batch entry points ignore this field.
@@ -134,7 +136,13 @@ typedef struct {
  * staged 0) when it differs from the one-frame-per-call shape above: 0 in
  * psfs_set_fuse_config makes the sequence path use lanes_x / voxels_z;
  * psfs_get_fuse_config reports the shape the sequence path uses (and
- * frames_per_group is checked against it). */
+ * frames_per_group is checked against it).
+ * seq_record_bytes: 32 or 64, the pixel record of the sequence path's map
+ * planes (0 in psfs_set_fuse_config keeps the current value; default 32).
+ * A 32-byte record is one L2 sector per (voxel, camera) and plane; a 64-byte
+ * record holds twice the frames per plane, read by two lanes in one warp
+ * request (one L1 wavefront for both sectors of the line), in planes of
+ * twice the size. */
 typedef struct {
     int32_t lanes_x;
     int32_t warps;
@@ -145,6 +153,7 @@ typedef struct {
     int32_t cameras_per_block;
     int32_t seq_lanes_x;
     int32_t seq_voxels_z;
+    int32_t seq_record_bytes;
 } psfs_fuse_config;
 
 typedef struct psfs_handle psfs_handle;
@@ -425,8 +434,9 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
  * sequence path on 64 frames (32 above 2^23 voxels; copies of the frame at
  * distinct addresses) with 1 to 4 likelihood CTAs per SM at one frame per
  * launch, and frame groups of 2, 4, 8, 16 and 32 frames (direct tile shapes,
- * voxels_z 2, 4, 8 and 16, 1 to 3 likelihood CTAs per SM), and keeps the fastest
- * sequence configuration.  The best one-frame shape stays the handle's tile
+ * voxels_z 2, 4, 8 and 16, 1 to 3 likelihood CTAs per SM, pixel records of 32
+ * and, where a group fills more than 32 bytes per pixel, 64 bytes), and keeps
+ * the fastest sequence configuration.  The best one-frame shape stays the handle's tile
  * shape for one frame per call; when frame groups win with another shape,
  * the sequence path gets that shape and a tile plan of its own.  The choices are
  * remembered for handles of the same grid size, camera count, image size and

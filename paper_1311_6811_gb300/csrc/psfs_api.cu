@@ -71,6 +71,7 @@ struct psfs_handle {
     // frame groups: frames per group on the sequence path (1 = one frame per
     // launch) and the two group map buffers [n_pix][group_cap] (first use)
     int seq_group = 1;
+    int seq_rec = 32;   // bytes per pixel record of a group's map planes (32 or 64)
     void *gmaps[2] = {nullptr, nullptr};
     int group_cap = 0;
     // the sequence path's own tile shape and plan (seq_own), when it differs
@@ -336,6 +337,7 @@ struct Tuned {
     int seq_group;
     bool seq_own;
     FuseShape seq_shape;
+    int seq_rec;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, Tuned> g_tuned;
@@ -537,6 +539,7 @@ psfs_status psfs_create(const psfs_grid *grid, const psfs_camera *cams, int32_t 
             h->seq_group = it->second.seq_group;
             h->seq_own = it->second.seq_own;
             h->seq_shape = it->second.seq_shape;
+            h->seq_rec = it->second.seq_rec;
         }
     }
     st = replan(h, shape);
@@ -679,7 +682,7 @@ static psfs_status ensure_group_maps(psfs_handle *h, int frames)
 static int unit_frames(const psfs_handle *h, int group, int remaining)
 {
     for (int g = group; g >= 2; g >>= 1)
-        if (g <= remaining && group_shape_supported(seq_shape_of(h), g, (int)h->map_elem)) return g;
+        if (g <= remaining && group_shape_supported(seq_shape_of(h), g, (int)h->map_elem, h->seq_rec)) return g;
     return 1;
 }
 
@@ -699,7 +702,7 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
     psfs_status st = seq_setup(h);
     if (st != PSFS_OK) return st;
     const FuseShape sshape = seq_shape_of(h);
-    if (group > 1 && !group_shape_supported(sshape, group, (int)h->map_elem)) group = 1;
+    if (group > 1 && !group_shape_supported(sshape, group, (int)h->map_elem, h->seq_rec)) group = 1;
     const int first_unit = unit_frames(h, group, n_frames);   // the largest
     if (first_unit > 1) {
         st = ensure_group_maps(h, first_unit);
@@ -731,7 +734,7 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
         {
             ProfScope ps(h, PSFS_STAGE_LIKELIHOOD, sl);
             if (nf > 1)
-                PSFS_CK(launch_likelihood_group(la, nf, h->params.map_dtype, sl, lk_ctas));
+                PSFS_CK(launch_likelihood_group(la, nf, h->params.map_dtype, sl, lk_ctas, h->seq_rec));
             else
                 PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, sl, lk_ctas));
         }
@@ -758,7 +761,7 @@ static psfs_status enqueue_sequence(psfs_handle *h, int32_t n_frames, const uint
         {
             ProfScope ps(h, PSFS_STAGE_FUSE, sf);
             if (nf > 1) {
-                PSFS_CK(launch_fuse_group(fa, sshape, nf, h->params.map_dtype, sf));
+                PSFS_CK(launch_fuse_group(fa, sshape, nf, h->params.map_dtype, sf, h->seq_rec));
             } else {
                 PSFS_CK(launch_fuse(fa, sshape, h->params.map_dtype, sf));
             }
@@ -1561,11 +1564,14 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
     const FuseShape sshape = own ? FuseShape{cfg->seq_lanes_x, 4, cfg->seq_voxels_z, 0} : shape;
     if (own && !fuse_shape_supported(sshape))
         return fail(PSFS_ERR_INVALID_ARG, "unsupported sequence tile shape (seq_lanes_x, seq_voxels_z)");
+    if (cfg->seq_record_bytes != 0 && cfg->seq_record_bytes != 32 && cfg->seq_record_bytes != 64)
+        return fail(PSFS_ERR_INVALID_ARG, "seq_record_bytes: 0, 32 or 64");
+    const int rec = cfg->seq_record_bytes ? cfg->seq_record_bytes : h->seq_rec;
     if (cfg->frames_per_group < 0 ||
-        (cfg->frames_per_group > 1 && !group_shape_supported(sshape, cfg->frames_per_group, (int)h->map_elem)))
+        (cfg->frames_per_group > 1 && !group_shape_supported(sshape, cfg->frames_per_group, (int)h->map_elem, rec)))
         return fail(PSFS_ERR_INVALID_ARG,
-                    "frames_per_group: 0, 1, or 2 / 4 / 8 / 16 / 32 with staged 0, lanes_x 8 or 16, voxels_z 4 "
-                    "(8 when a 32-byte pixel record holds at most 8 frames, 16 when at most 4)");
+                    "frames_per_group: 0, 1, or 2 / 4 / 8 / 16 / 32 with staged 0, lanes_x 8 or 16, voxels_z 2 or 4 "
+                    "(8 when a pixel record holds at most 8 frames per lane, 16 when at most 4)");
     DeviceGuard guard(h->device);
     PSFS_CK(cudaStreamSynchronize(h->stream));
     if (h->seq_stream[0]) {
@@ -1574,6 +1580,7 @@ psfs_status psfs_set_fuse_config(psfs_handle *h, const psfs_fuse_config *cfg)
     }
     if (cfg->seq_likelihood_ctas > 0) h->seq_lk_ctas = cfg->seq_likelihood_ctas;
     if (cfg->frames_per_group > 0) h->seq_group = cfg->frames_per_group;
+    h->seq_rec = rec;
     psfs_status st = replan(h, shape);
     if (st != PSFS_OK) return st;
     if (own) return replan_seq(h, sshape);
@@ -1593,6 +1600,7 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg)
     cfg->cameras_per_block = 1;
     cfg->seq_lanes_x = seq_shape_of(h).lx;
     cfg->seq_voxels_z = seq_shape_of(h).tz;
+    cfg->seq_record_bytes = h->seq_rec;
     return PSFS_OK;
 }
 
@@ -1703,7 +1711,9 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     h->seq_own = false;
     float best_seq = 1e30f;
     int best_group = 1;
+    int best_rec = 32;
     FuseShape best_seq_shape = best_shape;
+    h->seq_rec = 32;
     for (int lk = 1; lk <= 4 && st == PSFS_OK; ++lk) {
         float ms = 0.0f;
         st = time_sequence(lk, 1, &ms);
@@ -1715,24 +1725,31 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     const int group_lx = (best_shape.lx == 16) ? 16 : 8;
     const int groups[5] = {2, 4, 8, 16, kMaxGroup};
     for (int gi = 0; gi < 5 && st == PSFS_OK; ++gi) {
-        for (int tz : {2, 4, 8, 16}) {
-            if (st != PSFS_OK) break;
-            const FuseShape gshape = {group_lx, 4, tz, 0};
-            if (!group_shape_supported(gshape, groups[gi], (int)h->map_elem)) continue;
-            st = replan_seq(h, gshape);
-            for (int lk = 1; lk <= 3 && st == PSFS_OK; ++lk) {
-                float ms = 0.0f;
-                st = time_sequence(lk, groups[gi], &ms);
-                if (st == PSFS_OK && ms < best_seq) {
-                    best_seq = ms;
-                    best_group = groups[gi];
-                    best_seq_shape = gshape;
-                    h->seq_lk_ctas = lk;
+        for (int rec : {32, 64}) {
+            // 64-byte records only differ once a group fills more than 32 bytes per pixel
+            if (rec == 64 && groups[gi] * (int)h->map_elem <= 32) continue;
+            for (int tz : {2, 4, 8, 16}) {
+                if (st != PSFS_OK) break;
+                const FuseShape gshape = {group_lx, 4, tz, 0};
+                if (!group_shape_supported(gshape, groups[gi], (int)h->map_elem, rec)) continue;
+                st = replan_seq(h, gshape);
+                h->seq_rec = rec;
+                for (int lk = 1; lk <= 3 && st == PSFS_OK; ++lk) {
+                    float ms = 0.0f;
+                    st = time_sequence(lk, groups[gi], &ms);
+                    if (st == PSFS_OK && ms < best_seq) {
+                        best_seq = ms;
+                        best_group = groups[gi];
+                        best_rec = rec;
+                        best_seq_shape = gshape;
+                        h->seq_lk_ctas = lk;
+                    }
                 }
             }
         }
     }
     h->seq_group = best_group;
+    h->seq_rec = best_rec;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(h->stream);
@@ -1752,7 +1769,7 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[tune_key(h)] = Tuned{best_shape, h->seq_lk_ctas, h->seq_group, h->seq_own, h->seq_shape};
+        g_tuned[tune_key(h)] = Tuned{best_shape, h->seq_lk_ctas, h->seq_group, h->seq_own, h->seq_shape, h->seq_rec};
     }
     if (best) psfs_get_fuse_config(h, best);
     return PSFS_OK;

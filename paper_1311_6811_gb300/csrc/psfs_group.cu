@@ -5,16 +5,20 @@
 //
 //   * likelihood: one pass over the packed background (24 B per pixel, the
 //     largest input) computes the log ratio g of Eq. 5-9 for all F frames of
-//     the group.  The maps are written as 32-byte pixel records of P frames
-//     (P = 8 for FP32, 16 for 16-bit maps, F when F is smaller):
-//     [F / P planes][n_cams][H][W][P], one vector store per pixel and plane.
+//     the group.  The maps are written as pixel records of RB = 32 or 64 bytes
+//     holding P frames (P = RB / element size, F when F is smaller):
+//     [F / P planes][n_cams][H][W][P], one or two vector stores per pixel and
+//     plane.
 //   * fusion, one launch per plane: each voxel centre is projected into each
-//     camera once (Eq. 3) and one vector load gathers g of that pixel for the
-//     P frames of the plane; every frame keeps its own log-odds accumulator,
-//     output grid and list.  Records of one 32-byte sector keep the gather at
-//     one sector per (voxel, camera) and a plane of a 128^3 x 8 x 640 x 480
-//     rig (79 MB) inside L2; groups of 16 or 32 frames only add planes, so
-//     the background pass is shared by more frames at the same fusion cost.
+//     camera once (Eq. 3) and vector loads gather g of that pixel for the P
+//     frames of the plane; every frame keeps its own log-odds accumulator,
+//     output grid and list.  A 32-byte record is one sector per (voxel,
+//     camera), and a plane of a 128^3 x 8 x 640 x 480 rig (79 MB) stays in
+//     L2.  A 64-byte record is read by two lanes (one 32-byte half each) in
+//     the same warp request: the L1 serves both sectors of the line in one
+//     wavefront, so a plane costs half the wavefronts per frame, with planes
+//     of twice the size.  Groups of more frames only add planes, so the
+//     background pass is shared by more frames at the same fusion cost.
 //
 // Per frame and per pixel / voxel the arithmetic is exactly that of the
 // single-frame kernels (the same helper functions, the same camera order of
@@ -149,6 +153,7 @@ __device__ __forceinline__ void load_words(const uint32_t *src, uint32_t *w)
 // Likelihood of a frame group
 // ---------------------------------------------------------------------------
 constexpr int kGThreads = 256;
+constexpr int kPairWarps = 8;   // warps of fuse_pair_kernel: 4 warps' voxel columns, two lanes per column
 template <int F>
 struct GLayout {
     static constexpr int kChunk = F >= 32 ? 256 : 512;              // pixels per chunk (multiple of 16)
@@ -159,28 +164,30 @@ struct GLayout {
     static constexpr int kSmem = kStages * kStage + kStages * 8;    // + mbarriers
 };
 
-template <typename OutT, int F>
+template <typename OutT, int F, int RB>
 __device__ __forceinline__ void group_pixel(const LikelihoodArgs &a, OutT *out, int64_t p, const unsigned char *im,
                                             int64_t im_stride, const float *m, const float *h)
 {
-    GroupWords<OutT, F> pk;
     const float m0 = m[0], m1 = m[1], m2 = m[2], h0 = h[0], h1 = h[1], h2 = h[2];
     const float base = pixel_log_base(h0, h1, h2, a.c0);   // r = base + quad, as pixel_log_odds
+    // planes of RB-byte records (one plane [n_pix][F] when the F frames fit
+    // one record): each plane's record is stored as soon as its frames are
+    // formed, so only one record's words are live (a 32-frame group in one
+    // record array held 80 registers per thread, which the fusion kernel
+    // running beside it on the SM then lacked)
+    constexpr int kP = RB / (int)sizeof(OutT);
+    constexpr int kPlane = F < kP ? F : kP;
+    constexpr int kWords = GroupWords<OutT, kPlane>::kWords;
 #pragma unroll
-    for (int f = 0; f < F; ++f) {
-        const unsigned char *q = im + f * im_stride;
-        const float r = base + pixel_quad((float)q[0], (float)q[1], (float)q[2], m0, m1, m2, h0, h1, h2);
-        pk.set(f, to_map<OutT>(log_ratio_of_r(r, a.sc)));
-    }
-    constexpr int kWords = GroupWords<OutT, F>::kWords;
-    if constexpr (kWords <= 8) {
-        store_words<kWords>(reinterpret_cast<uint32_t *>(out + p * F), pk.w);   // one plane: [n_pix][F]
-    } else {
-        // planes of 32-byte records: words 8q to 8q + 7 go to plane q
-        constexpr int kP = 32 / (int)sizeof(OutT);
+    for (int q = 0; q < F / kPlane; ++q) {
+        GroupWords<OutT, kPlane> pk;
 #pragma unroll
-        for (int q = 0; q < kWords / 8; ++q)
-            store_words<8>(reinterpret_cast<uint32_t *>(out + ((int64_t)q * a.n_pix + p) * kP), pk.w + 8 * q);
+        for (int e = 0; e < kPlane; ++e) {
+            const unsigned char *px = im + (q * kPlane + e) * im_stride;
+            const float r = base + pixel_quad((float)px[0], (float)px[1], (float)px[2], m0, m1, m2, h0, h1, h2);
+            pk.set(e, to_map<OutT>(log_ratio_of_r(r, a.sc)));
+        }
+        store_words<kWords>(reinterpret_cast<uint32_t *>(out + ((int64_t)q * a.n_pix + p) * kPlane), pk.w);
     }
 }
 
@@ -189,7 +196,7 @@ __device__ __forceinline__ void group_pixel(const LikelihoodArgs &a, OutT *out, 
 // with bulk copies through a 4-stage mbarrier ring.  n_tma_pix = n_pix
 // rounded down to 16 pixels; CTA 0 computes the last < 16 pixels with plain
 // loads.
-template <typename OutT, int F>
+template <typename OutT, int F, int RB>
 __global__ void __launch_bounds__(kGThreads) likelihood_group_kernel(const LikelihoodArgs a, int64_t n_tma_pix)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -236,21 +243,21 @@ __global__ void __launch_bounds__(kGThreads) likelihood_group_kernel(const Likel
         const float *mu = stage_mean(s);
         const float *hv = stage_hinv(s);
         for (int q = tid; q < np; q += kGThreads)
-            group_pixel<OutT, F>(a, out, p0 + q, im + 3 * q, GLayout<F>::kImgBytes, mu + 3 * q, hv + 3 * q);
+            group_pixel<OutT, F, RB>(a, out, p0 + q, im + 3 * q, GLayout<F>::kImgBytes, mu + 3 * q, hv + 3 * q);
         __syncthreads();   // every thread is done with stage s before it is refilled
         if (tid == 0 && k + GLayout<F>::kStages < my_chunks) issue(k + GLayout<F>::kStages);
     }
 
     if (blockIdx.x == 0) {
         for (int64_t p = n_tma_pix + tid; p < a.n_pix; p += kGThreads)
-            group_pixel<OutT, F>(a, out, p, a.img + 3 * p, a.img_fstride, a.mean + 3 * p, a.hinv + 3 * p);
+            group_pixel<OutT, F, RB>(a, out, p, a.img + 3 * p, a.img_fstride, a.mean + 3 * p, a.hinv + 3 * p);
     }
 }
 
-template <typename OutT, int F>
+template <typename OutT, int F, int RB>
 cudaError_t launch_lk_group(const LikelihoodArgs &a, cudaStream_t s, int ctas_per_sm)
 {
-    auto kern = likelihood_group_kernel<OutT, F>;
+    auto kern = likelihood_group_kernel<OutT, F, RB>;
     constexpr int smem = GLayout<F>::kSmem;
     static bool configured[64] = {false};
     static int max_ctas[64] = {0};
@@ -276,17 +283,22 @@ cudaError_t launch_lk_group(const LikelihoodArgs &a, cudaStream_t s, int ctas_pe
 }
 
 template <typename OutT>
-cudaError_t launch_lk_group_typed(const LikelihoodArgs &a, int frames, cudaStream_t s, int ctas_per_sm)
+cudaError_t launch_lk_group_typed(const LikelihoodArgs &a, int frames, cudaStream_t s, int ctas_per_sm, int rec)
 {
     // bulk copies need 16-byte aligned sources and sizes: refuse rather than fault
     if (((uintptr_t)a.img | (uintptr_t)a.mean | (uintptr_t)a.hinv | (uintptr_t)a.img_fstride) & 15u)
         return cudaErrorMisalignedAddress;
     if (((uintptr_t)a.out) & (uintptr_t)(frames * sizeof(OutT) - 1)) return cudaErrorMisalignedAddress;
-    if (frames == 2) return launch_lk_group<OutT, 2>(a, s, ctas_per_sm);
-    if (frames == 4) return launch_lk_group<OutT, 4>(a, s, ctas_per_sm);
-    if (frames == 8) return launch_lk_group<OutT, 8>(a, s, ctas_per_sm);
-    if (frames == 16) return launch_lk_group<OutT, 16>(a, s, ctas_per_sm);
-    if (frames == 32) return launch_lk_group<OutT, 32>(a, s, ctas_per_sm);
+    if (rec != 32 && rec != 64) return cudaErrorInvalidValue;
+    // the record size only matters once the F frames fill more than 32 bytes
+    const bool wide = rec == 64 && frames * (int)sizeof(OutT) > 32;
+    if (frames == 2) return launch_lk_group<OutT, 2, 32>(a, s, ctas_per_sm);
+    if (frames == 4) return launch_lk_group<OutT, 4, 32>(a, s, ctas_per_sm);
+    if (frames == 8) return launch_lk_group<OutT, 8, 32>(a, s, ctas_per_sm);
+    if (frames == 16)
+        return wide ? launch_lk_group<OutT, 16, 64>(a, s, ctas_per_sm) : launch_lk_group<OutT, 16, 32>(a, s, ctas_per_sm);
+    if (frames == 32)
+        return wide ? launch_lk_group<OutT, 32, 64>(a, s, ctas_per_sm) : launch_lk_group<OutT, 32, 32>(a, s, ctas_per_sm);
     return cudaErrorInvalidValue;
 }
 
@@ -357,13 +369,16 @@ __device__ __forceinline__ void group_epilogue(const FuseArgs &a, int i, int j, 
 // The tile decomposition, per-tile camera records and projection are those of
 // the direct fuse kernel; a thread holds F x TZ log-odds accumulators.  The
 // gather of one tile: every camera in order 0 .. n_cams - 1, one vector load
-// of the F frames' log ratios per (voxel, camera).  s_flags must hold the
-// tile's camera flags (a barrier after they were written).
-template <typename MapT, int LX, int WY, int TZ, int F>
+// of the F frames' log ratios per (voxel, camera).  A pixel record holds S
+// such F-frame parts (S lanes share a voxel); this lane reads part `part`.
+// s_flags must hold the tile's camera flags (a barrier after they were
+// written).
+template <typename MapT, int LX, int WY, int TZ, int F, int S = 1>
 __device__ __forceinline__ void group_gather(const FuseArgs &a, const TileCoords<LX, WY, TZ> &tc,
-                                             const int *s_flags, float (&L)[F][TZ])
+                                             const int *s_flags, float (&L)[F][TZ], int part = 0)
 {
     using Words = GroupWords<MapT, F>;
+    constexpr int kRec = S * Words::kWords;   // words per pixel record
     const uint32_t W = (uint32_t)a.W, H = (uint32_t)a.H;
 #pragma unroll
     for (int f = 0; f < F; ++f)
@@ -380,7 +395,7 @@ __device__ __forceinline__ void group_gather(const FuseArgs &a, const TileCoords
         for (int q = 0; q < 12; ++q) m[q] = a.cam[c].m[q];
         float bu, bv, bw;
         project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
-        const uint32_t *map = maps + (int64_t)c * a.map_stride * Words::kWords;
+        const uint32_t *map = maps + (int64_t)c * a.map_stride * kRec + part * Words::kWords;
         if (flags & kTcInside) {
 #pragma unroll
             for (int t = 0; t < TZ; ++t) {
@@ -388,7 +403,7 @@ __device__ __forceinline__ void group_gather(const FuseArgs &a, const TileCoords
                 // the host proved the pixel lies in the image; min() only guards the buffer
                 const uint32_t pix = min(p.by * W + p.bx + bias_off, last_pix);
                 Words g;
-                load_words<Words::kWords>(map + (size_t)pix * Words::kWords, g.w);
+                load_words<Words::kWords>(map + (size_t)pix * kRec, g.w);
 #pragma unroll
                 for (int f = 0; f < F; ++f) L[f][t] += g.get(f);
             }
@@ -398,7 +413,7 @@ __device__ __forceinline__ void group_gather(const FuseArgs &a, const TileCoords
                 int pix;
                 if (proj_pixel(project_biased(m, bu, bv, bw, tc.fk[t]), W, H, &pix)) {
                     Words g;
-                    load_words<Words::kWords>(map + (size_t)pix * Words::kWords, g.w);
+                    load_words<Words::kWords>(map + (size_t)pix * kRec, g.w);
 #pragma unroll
                     for (int f = 0; f < F; ++f) L[f][t] += g.get(f);
                 }
@@ -425,6 +440,103 @@ __global__ void __launch_bounds__(32 * WY) fuse_group_kernel(const __grid_consta
     __syncthreads();
     group_gather<MapT, LX, WY, TZ, F>(a, tc, s_flags, L);
     group_epilogue<WY, TZ, F>(a, tc.i, tc.j, tc.k0, L, lane, wy, s_off, s_base);
+}
+
+// Epilogue of a plane of 64-byte records: the two half-warps hold frames
+// 0 .. FL - 1 and FL .. 2 FL - 1 of the same 16 voxel columns.  Per frame the
+// posterior, threshold and compaction of group_epilogue (the same per-voxel
+// arithmetic); a ballot serves both halves' frames (low and high 16 bits).
+template <int TZ, int FL>
+__device__ __forceinline__ void pair_epilogue(const FuseArgs &a, int i, int j, int k0, const float (&L)[FL][TZ],
+                                              int lane, int wy, int half, uint32_t (*s_off)[kPairWarps],
+                                              uint32_t *s_base)
+{
+    constexpr int P = 2 * FL;
+    const bool in_xy = (i < a.nx) && (j < a.ny);
+    const uint32_t zstride = (uint32_t)a.nx * (uint32_t)a.ny;
+    const uint32_t lin0 = (uint32_t)i + (uint32_t)a.nx * ((uint32_t)j + (uint32_t)a.ny * (uint32_t)k0);
+#pragma unroll
+    for (int e = 0; e < FL; ++e) {
+        float *occ = a.occ + (half * FL + e) * a.occ_fstride;
+        uint32_t c_lo = 0, c_hi = 0;
+#pragma unroll
+        for (int t = 0; t < TZ; ++t) {
+            const bool valid = in_xy && (k0 + t < a.nz);
+            const float lo = L[e][t] + a.logit_prior;
+            if (valid) __stcs(occ + lin0 + (uint32_t)t * zstride, posterior_of_logodds(lo));
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, valid && (lo > a.logit_tau));
+            c_lo += __popc(b & 0xFFFFu);
+            c_hi += __popc(b >> 16);
+        }
+        if (lane == 0) {
+            s_off[e][wy] = c_lo;
+            s_off[FL + e][wy] = c_hi;
+        }
+    }
+    __syncthreads();
+    const int tid = wy * 32 + lane;
+    if (tid < P) {
+        uint32_t total = 0;
+#pragma unroll
+        for (int w = 0; w < kPairWarps; ++w) {
+            const uint32_t c = s_off[tid][w];
+            s_off[tid][w] = total;
+            total += c;
+        }
+        uint32_t base = 0;
+        if (total) {
+            base = atomicAdd(a.count + tid * a.count_fstride, total);
+            if ((uint64_t)base + total > (uint64_t)a.capacity) atomicOr(a.status, kStatusCapacity);
+        }
+        s_base[tid] = base;
+    }
+    __syncthreads();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t half_mask = half ? 0xFFFF0000u : 0x0000FFFFu;
+#pragma unroll
+    for (int e = 0; e < FL; ++e) {
+        const int f = half * FL + e;
+        uint32_t *list = a.list + f * a.list_fstride;
+        uint32_t pos = s_base[f] + s_off[f][wy];
+#pragma unroll
+        for (int t = 0; t < TZ; ++t) {
+            const bool valid = in_xy && (k0 + t < a.nz);
+            const float lo = L[e][t] + a.logit_prior;
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, valid && (lo > a.logit_tau)) & half_mask;
+            if ((b >> lane) & 1u) {
+                const uint32_t q = pos + __popc(b & lt_mask);
+                if (q < a.capacity) list[q] = lin0 + (uint32_t)t * zstride;
+            }
+            pos += __popc(b);
+        }
+    }
+}
+
+// Fusion of one plane of 64-byte records (16 FP32 or 32 16-bit frames per
+// pixel).  kPairWarps warps cover the tile of the 4-warp fuse_group_kernel:
+// lane l of warp w takes the voxel column of that kernel's thread
+// 16 w + (l & 15) and the frames of record half l >> 4, so both 32-byte
+// halves of a record are loaded by the same warp request.
+template <typename MapT, int LX, int TZ, int FL>
+__global__ void __launch_bounds__(32 * kPairWarps) fuse_pair_kernel(const __grid_constant__ FuseArgs a)
+{
+    __shared__ int s_flags[PSFS_MAX_CAMS];
+    __shared__ uint32_t s_off[2 * FL][kPairWarps];
+    __shared__ uint32_t s_base[2 * FL];
+
+    const int lane = threadIdx.x;
+    const int wy = threadIdx.y;
+    const int tid = wy * 32 + lane;
+    const int half = lane >> 4;
+    const int vt = wy * 16 + (lane & 15);   // thread of the 4-warp tile whose voxel column this lane takes
+    if (tid < a.n_cams) s_flags[tid] = __ldg(&a.tilecam[(int64_t)blockIdx.x * a.n_cams + tid].w) >> 16;
+
+    TileCoords<LX, 4, TZ> tc;
+    tc.init(a, a.tiles[blockIdx.x], vt & 31, vt >> 5);
+    float L[FL][TZ];
+    __syncthreads();
+    group_gather<MapT, LX, 4, TZ, FL, 2>(a, tc, s_flags, L, half);
+    pair_epilogue<TZ, FL>(a, tc.i, tc.j, tc.k0, L, lane, wy, half, s_off, s_base);
 }
 
 // The adjoint's voxel pass over F frames of records (psfs_backward_sequence):
@@ -495,6 +607,26 @@ cudaError_t launch_fg_shape(const FuseArgs &a, const FuseShape &sh, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
+template <typename MapT, int LX, int TZ>
+cudaError_t launch_fp(const FuseArgs &a, cudaStream_t s)
+{
+    constexpr int FL = 32 / (int)sizeof(MapT);   // frames per lane: one 32-byte half of the record
+    fuse_pair_kernel<MapT, LX, TZ, FL><<<a.n_tiles, dim3(32, kPairWarps), 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// One plane of 64-byte records.
+template <typename MapT>
+cudaError_t launch_fp_typed(const FuseArgs &a, const FuseShape &sh, cudaStream_t s)
+{
+    if (((uintptr_t)a.maps) & 63u) return cudaErrorMisalignedAddress;
+    if (sh.wy != 4 || sh.staged || (sh.lx != 8 && sh.lx != 16)) return cudaErrorInvalidValue;
+    // FL x TZ accumulators per thread: at most 32
+    if (sh.tz == 2) return sh.lx == 8 ? launch_fp<MapT, 8, 2>(a, s) : launch_fp<MapT, 16, 2>(a, s);
+    if (sh.tz == 4) return sh.lx == 8 ? launch_fp<MapT, 8, 4>(a, s) : launch_fp<MapT, 16, 4>(a, s);
+    return cudaErrorInvalidValue;
+}
+
 // One plane of P frames (records of at most 32 bytes).
 template <typename MapT>
 cudaError_t launch_fg_typed(const FuseArgs &a, const FuseShape &sh, int frames, cudaStream_t s)
@@ -549,29 +681,35 @@ bool group_size_supported(int frames)
     return frames == 2 || frames == 4 || frames == 8 || frames == 16 || frames == kMaxGroup;
 }
 
-bool group_shape_supported(const FuseShape &s, int frames, int map_elem)
+bool group_shape_supported(const FuseShape &s, int frames, int map_elem, int rec)
 {
-    // the fusion kernel holds P x TZ accumulators per thread: at most 64
-    const int P = group_plane_frames(frames, map_elem);
-    return group_size_supported(frames) && s.wy == 4 && s.staged == 0 && (s.lx == 8 || s.lx == 16) &&
-           (s.tz == 2 || s.tz == 4 || (s.tz == 8 && P <= 8) || (s.tz == 16 && P <= 4));
+    if (rec != 32 && rec != 64) return false;
+    // a thread holds (frames per lane) x TZ accumulators: at most 64 with
+    // 32-byte records (32 with 64-byte records, two lanes per voxel)
+    const int P = group_plane_frames(frames, map_elem, rec);
+    const bool pair = P * map_elem == 64;
+    if (!(group_size_supported(frames) && s.wy == 4 && s.staged == 0 && (s.lx == 8 || s.lx == 16))) return false;
+    if (pair) return s.tz == 2 || s.tz == 4;
+    return s.tz == 2 || s.tz == 4 || (s.tz == 8 && P <= 8) || (s.tz == 16 && P <= 4);
 }
 
 cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map_dtype, cudaStream_t s,
-                                    int ctas_per_sm)
+                                    int ctas_per_sm, int rec)
 {
-    if (map_dtype == PSFS_MAP_F16) return launch_lk_group_typed<__half>(a, frames, s, ctas_per_sm);
-    if (map_dtype == PSFS_MAP_BF16) return launch_lk_group_typed<__nv_bfloat16>(a, frames, s, ctas_per_sm);
-    return launch_lk_group_typed<float>(a, frames, s, ctas_per_sm);
+    if (map_dtype == PSFS_MAP_F16) return launch_lk_group_typed<__half>(a, frames, s, ctas_per_sm, rec);
+    if (map_dtype == PSFS_MAP_BF16) return launch_lk_group_typed<__nv_bfloat16>(a, frames, s, ctas_per_sm, rec);
+    return launch_lk_group_typed<float>(a, frames, s, ctas_per_sm, rec);
 }
 
 cudaError_t launch_fuse_group(const FuseArgs &a, const FuseShape &shape, int frames, int map_dtype,
-                              cudaStream_t s)
+                              cudaStream_t s, int rec)
 {
     if (a.n_tiles <= 0) return cudaSuccess;
     const bool half = map_dtype == PSFS_MAP_F16 || map_dtype == PSFS_MAP_BF16;
-    const int P = group_plane_frames(frames, half ? 2 : 4);
-    const int64_t plane_bytes = (int64_t)a.n_cams * a.map_stride * 32;
+    const int elem = half ? 2 : 4;
+    const int P = group_plane_frames(frames, elem, rec);
+    const bool pair = P * elem == 64;
+    const int64_t plane_bytes = (int64_t)a.n_cams * a.map_stride * P * elem;
     for (int q = 0; q * P < frames; ++q) {
         // plane q: frames qP to qP + P - 1
         FuseArgs fq = a;
@@ -581,11 +719,11 @@ cudaError_t launch_fuse_group(const FuseArgs &a, const FuseShape &shape, int fra
         fq.count = a.count + (int64_t)q * P * a.count_fstride;
         cudaError_t e;
         if (map_dtype == PSFS_MAP_F16)
-            e = launch_fg_typed<__half>(fq, shape, P, s);
+            e = pair ? launch_fp_typed<__half>(fq, shape, s) : launch_fg_typed<__half>(fq, shape, P, s);
         else if (map_dtype == PSFS_MAP_BF16)
-            e = launch_fg_typed<__nv_bfloat16>(fq, shape, P, s);
+            e = pair ? launch_fp_typed<__nv_bfloat16>(fq, shape, s) : launch_fg_typed<__nv_bfloat16>(fq, shape, P, s);
         else
-            e = launch_fg_typed<float>(fq, shape, P, s);
+            e = pair ? launch_fp_typed<float>(fq, shape, s) : launch_fg_typed<float>(fq, shape, P, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -603,20 +603,23 @@ cudaError_t launch_smooth(const SmoothArgs &a, int n_frames, cudaStream_t s);
 
 // Frame groups of the sequence path (psfs_group.cu), F = 2, 4, 8, 16 or 32
 // frames: the F frames share one pass over the background (likelihood), and
-// the fusion projects each voxel once per camera for all frames of a 32-byte
-// pixel record.  The group's maps are planes of such records: a record holds
-// P = min(F, 32 / map_elem) frames (8 for FP32, 16 for 16-bit maps), plane q
-// (frames qP to qP + P - 1) is [n_cams][H][W][P], and the F / P planes follow
-// one another; one fusion launch per plane.  Each frame's arithmetic is that
-// of the single-frame kernels.
+// the fusion projects each voxel once per camera for all frames of a pixel
+// record of `rec` = 32 or 64 bytes.  The group's maps are planes of such
+// records: a record holds P = min(F, rec / map_elem) frames, plane q (frames
+// qP to qP + P - 1) is [n_cams][H][W][P], and the F / P planes follow one
+// another; one fusion launch per plane (two lanes per voxel when a record is
+// 64 bytes).  Each frame's arithmetic is that of the single-frame kernels.
 constexpr int kMaxGroup = 32;
-inline int group_plane_frames(int frames, int map_elem) { return frames < 32 / map_elem ? frames : 32 / map_elem; }
+inline int group_plane_frames(int frames, int map_elem, int rec = 32)
+{
+    return frames < rec / map_elem ? frames : rec / map_elem;
+}
 bool group_size_supported(int frames);
-bool group_shape_supported(const FuseShape &s, int frames, int map_elem);
+bool group_shape_supported(const FuseShape &s, int frames, int map_elem, int rec = 32);
 cudaError_t launch_likelihood_group(const LikelihoodArgs &a, int frames, int map_dtype, cudaStream_t s,
-                                    int ctas_per_sm);
+                                    int ctas_per_sm, int rec = 32);
 cudaError_t launch_fuse_group(const FuseArgs &a, const FuseShape &shape, int frames, int map_dtype,
-                              cudaStream_t s);
+                              cudaStream_t s, int rec = 32);
 // The adjoint's voxel pass over a unit of `frames` (2, 4 or 8) frames whose
 // maps are one plane of records ([n_pix][frames], b.f.maps), tile shape
 // lanes_x 8 or 16, voxels_z 4: dLoss/dL of frame f into slot f of each

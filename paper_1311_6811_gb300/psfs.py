@@ -56,7 +56,8 @@ class psfs_fuse_config(ctypes.Structure):
     _fields_ = [("lanes_x", ctypes.c_int32), ("warps", ctypes.c_int32), ("voxels_z", ctypes.c_int32),
                 ("staged", ctypes.c_int32), ("seq_likelihood_ctas", ctypes.c_int32),
                 ("frames_per_group", ctypes.c_int32), ("cameras_per_block", ctypes.c_int32),
-                ("seq_lanes_x", ctypes.c_int32), ("seq_voxels_z", ctypes.c_int32)]
+                ("seq_lanes_x", ctypes.c_int32), ("seq_voxels_z", ctypes.c_int32),
+                ("seq_record_bytes", ctypes.c_int32)]
 
     def as_tuple(self):
         return (self.lanes_x, self.warps, self.voxels_z, self.staged)
@@ -489,23 +490,24 @@ def psfs_destroy(h: int):
 
 def psfs_set_fuse_config(h: int, lanes_x: int, warps: int, voxels_z: int, staged: int = 0,
                          seq_likelihood_ctas: int = 0, frames_per_group: int = 0, seq_lanes_x: int = 0,
-                         seq_voxels_z: int = 0):
+                         seq_voxels_z: int = 0, seq_record_bytes: int = 0):
     """One-frame tile shape, the sequence path's likelihood CTAs per SM and
-    frames per group, and (seq_lanes_x, seq_voxels_z > 0) a tile shape of the
-    sequence path's own."""
+    frames per group, (seq_lanes_x, seq_voxels_z > 0) a tile shape of the
+    sequence path's own, and (seq_record_bytes 32 or 64) the pixel record of
+    its map planes; 0 keeps the current value."""
     cfg = psfs_fuse_config(lanes_x, warps, voxels_z, staged, seq_likelihood_ctas, frames_per_group, 0, seq_lanes_x,
-                           seq_voxels_z)
+                           seq_voxels_z, seq_record_bytes)
     _check(load().psfs_set_fuse_config(h, ctypes.byref(cfg)), "psfs_set_fuse_config")
 
 
 def psfs_get_fuse_config(h: int, full: bool = False) -> tuple:
     """(lanes_x, warps, voxels_z, staged), plus (seq_likelihood_ctas,
-    frames_per_group, seq_lanes_x, seq_voxels_z) of the sequence path when
-    `full`."""
+    frames_per_group, seq_lanes_x, seq_voxels_z, seq_record_bytes) of the
+    sequence path when `full` (the argument order of psfs_set_fuse_config)."""
     cfg = psfs_fuse_config()
     _check(load().psfs_get_fuse_config(h, ctypes.byref(cfg)), "psfs_get_fuse_config")
-    return cfg.as_tuple() + ((cfg.seq_likelihood_ctas, cfg.frames_per_group, cfg.seq_lanes_x, cfg.seq_voxels_z)
-                             if full else ())
+    return cfg.as_tuple() + ((cfg.seq_likelihood_ctas, cfg.frames_per_group, cfg.seq_lanes_x, cfg.seq_voxels_z,
+                              cfg.seq_record_bytes) if full else ())
 
 
 def psfs_autotune(h: int, images, reps: int = 5, timings: Optional[dict] = None) -> tuple:

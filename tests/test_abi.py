@@ -55,6 +55,8 @@ int main(void) {
          offsetof(psfs_camera, R), offsetof(psfs_camera, t));
   printf("%zu %zu %zu %zu\n", sizeof(psfs_params), offsetof(psfs_params, threshold),
          offsetof(psfs_params, log_fg_density), offsetof(psfs_params, map_dtype));
+  printf("%zu %zu %zu %zu\n", sizeof(psfs_fuse_config), offsetof(psfs_fuse_config, cameras_per_block),
+         offsetof(psfs_fuse_config, seq_voxels_z), offsetof(psfs_fuse_config, seq_record_bytes));
   return 0;
 }
 ''')
@@ -68,6 +70,8 @@ int main(void) {
                        psfs.psfs_camera.R.offset, psfs.psfs_camera.t.offset]
     assert rows[2] == [ctypes.sizeof(psfs.psfs_params), psfs.psfs_params.threshold.offset,
                        psfs.psfs_params.log_fg_density.offset, psfs.psfs_params.map_dtype.offset]
+    assert rows[3] == [ctypes.sizeof(psfs.psfs_fuse_config), psfs.psfs_fuse_config.cameras_per_block.offset,
+                       psfs.psfs_fuse_config.seq_voxels_z.offset, psfs.psfs_fuse_config.seq_record_bytes.offset]
 
 
 def test_defaults_and_status_strings(lib):

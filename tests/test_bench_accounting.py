@@ -29,10 +29,20 @@ def test_sequence_units_respect_the_tile_height():
 def test_units_cover_every_frame():
     for n in (1, 7, 31, 32, 33, 100, 257):
         for g in (1, 2, 4, 8, 16, 32):
-            for tz in (4, 8, 16):
+            for tz in (2, 4, 8, 16):
                 for elem in (2, 4):
-                    u = bench.sequence_units(n, g, tz, elem)
-                    assert sum(u) == n and all(x >= 1 for x in u)
+                    for rb in (32, 64):
+                        u = bench.sequence_units(n, g, tz, elem, rb)
+                        assert sum(u) == n and all(x >= 1 for x in u)
+
+
+def test_sequence_units_with_64_byte_records():
+    # 64-byte records: 16 FP32 / 32 16-bit frames per plane, tile heights 2 and 4 only
+    assert bench.sequence_units(100, 32, 4, 4, 64) == [32, 32, 32, 4]
+    assert bench.sequence_units(40, 32, 8, 4, 64) == [8, 8, 8, 8, 8]    # groups of 16 and 32 need voxels_z <= 4
+    assert bench.sequence_units(40, 32, 8, 2, 64) == [8, 8, 8, 8, 8]    # 16-bit groups of 16 and 32 too
+    assert bench.sequence_units(40, 16, 8, 2, 32) == [8, 8, 8, 8, 8]
+    assert bench.sequence_units(37, 32, 2, 2, 64) == [32, 4, 1]
 
 
 def test_ncu_traffic_matches_sources_and_shape(tmp_path, monkeypatch):

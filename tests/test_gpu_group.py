@@ -1,7 +1,8 @@
 """Frame groups of the sequence path: F frames per likelihood launch (one
 pass over the background) and per fusion launch (one projection per voxel
 and camera, one vector gather per 32-byte pixel record: 8 FP32 or 16
-16-bit frames, one fusion launch per plane of records).  Each frame's occupancy,
+16-bit frames, one fusion launch per plane of records; or 64-byte records
+read by two lanes per voxel).  Each frame's occupancy,
 count and voxel set must be bit-identical to one psfs_reconstruct per frame
 with the same tile shape, for every group size, map type and a frame count
 that leaves trailing frames outside the last group; one group's frame is also
@@ -76,8 +77,8 @@ def test_groups_equal_frame_by_frame(group, tz, dtype):
     imgs = to_dev(sc.images)
     cap = rec.n_voxels
     for lx in (8, 16):
-        psfs.psfs_set_fuse_config(rec.handle, lx, 4, tz, 0, 2, group)
-        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, group, lx, tz)
+        psfs.psfs_set_fuse_config(rec.handle, lx, 4, tz, 0, 2, group, 0, 0, 32)
+        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, group, lx, tz, 32)
         occ, lists, counts = _run_sequence(rec, imgs, cap)
         _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap)
     rec.close()
@@ -97,8 +98,8 @@ def test_groups_of_32_equal_frame_by_frame(tz, dtype):
     imgs = to_dev(sc.images)
     cap = rec.n_voxels
     for lx in (8, 16):
-        psfs.psfs_set_fuse_config(rec.handle, lx, 4, tz, 0, 2, 32)
-        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, 32, lx, tz)
+        psfs.psfs_set_fuse_config(rec.handle, lx, 4, tz, 0, 2, 32, 0, 0, 32)
+        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, 32, lx, tz, 32)
         occ, lists, counts = _run_sequence(rec, imgs, cap)
         _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap)
     rec.close()
@@ -117,7 +118,7 @@ def test_group_of_32_ragged_grid_and_views():
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
     imgs = to_dev(sc.images)
     for tz, lk in ((4, 1), (8, 2), (8, 3)):
-        psfs.psfs_set_fuse_config(rec.handle, 8, 4, tz, 0, lk, 32)
+        psfs.psfs_set_fuse_config(rec.handle, 8, 4, tz, 0, lk, 32, 0, 0, 32)
         occ, lists, counts = _run_sequence(rec, imgs, rec.n_voxels)
         _assert_frame_by_frame(rec, imgs, occ, lists, counts, rec.n_voxels)
     rec.close()
@@ -154,6 +155,86 @@ def test_group_of_32_matches_oracle_and_capacity():
     assert (lf >= 0).all() and (lf < V).all()
     for f in range(n):
         assert np.isin(lf[f], psfs.voxel_list(lists[f], counts[f:f + 1], V).numpy()).all()
+    rec.close()
+
+
+@pytest.mark.parametrize("dtype,group,tz", [("f32", 16, 2), ("f32", 16, 4), ("f32", 32, 2), ("f32", 32, 4),
+                                            ("f16", 32, 2), ("f16", 32, 4), ("bf16", 32, 2)])
+def test_64_byte_records_equal_frame_by_frame(dtype, group, tz):
+    """64-byte pixel records (16 FP32 or 32 16-bit frames per plane, two
+    lanes per voxel, one 32-byte half each): 61 frames run as groups of
+    `group` frames and the trailing units (whose smaller records take the
+    one-lane kernel), every frame bit-identical to one frame per call, with
+    both lanes_x."""
+    sc = _scene(61)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype=dtype)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    cap = rec.n_voxels
+    for lx in (8, 16):
+        psfs.psfs_set_fuse_config(rec.handle, lx, 4, tz, 0, 2, group, 0, 0, 64)
+        assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (lx, 4, tz, 0, 2, group, lx, tz, 64)
+        occ, lists, counts = _run_sequence(rec, imgs, cap)
+        _assert_frame_by_frame(rec, imgs, occ, lists, counts, cap)
+    rec.close()
+
+
+def test_64_byte_records_ragged_grid_oracle_and_capacity():
+    """64-byte records on the ragged 37 x 29 x 24 grid with 3 cameras whose
+    views miss part of it (57 frames: groups of 32 and 16, then 8 and 1);
+    one frame of the 32-frame group against the FP64 oracle; then a capacity
+    below every frame's count (the two half-warps' frames share the CTA's
+    per-frame reservations): full counts, valid entries, PSFS_ERR_CAPACITY."""
+    grid = S.Grid(37, 29, 24, (-0.9, -0.7, 0.1), 0.05)
+    sc = S.make_scene(seed=23, grid_n=48, cube_side=2.0, n_cams=3, width=104, height=80, focal=95.0,
+                      n_frames=57, walking=True)
+    rec = psfs.Reconstructor(grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    imgs = to_dev(sc.images)
+    n, V = imgs.shape[0], rec.n_voxels
+    for tz, lk in ((2, 1), (4, 3)):
+        psfs.psfs_set_fuse_config(rec.handle, 8, 4, tz, 0, lk, 32, 0, 0, 64)
+        occ, lists, counts = _run_sequence(rec, imgs, V)
+        _assert_frame_by_frame(rec, imgs, occ, lists, counts, V)
+    f = 21
+    got = {"occ": occ[f].cpu().numpy().astype(np.float64), "count": int(counts[f]) & 0xFFFFFFFF,
+           "list": psfs.voxel_list(lists[f], counts[f:f + 1], V).numpy(), "status": psfs.PSFS_OK}
+    ref = oracle.reconstruct(grid, sc.cams, sc.images[f], sc.mean, sc.var, sc.params)
+    assert ref["list"].size > 100
+    print(compare(got, ref))
+    full = [int(c) for c in counts]
+    cap = min(full) // 2
+    occ2 = torch.empty((n, V), dtype=torch.float32, device="cuda")
+    counts2 = torch.zeros((n,), dtype=torch.int32, device="cuda")
+    lists_flat = torch.full((n * cap,), -1, dtype=torch.int32, device="cuda")
+    psfs.psfs_reconstruct_sequence(rec.handle, n, imgs, occ2, lists_flat, cap, counts2)
+    assert rec.sync() == psfs.PSFS_ERR_CAPACITY
+    assert [int(c) for c in counts2] == full
+    assert torch.equal(occ2, occ)
+    lf = lists_flat.view(n, cap).cpu().numpy()
+    assert (lf >= 0).all() and (lf < V).all()
+    for f in range(n):
+        assert np.isin(lf[f], psfs.voxel_list(lists[f], counts[f:f + 1], V).numpy()).all()
+        assert np.unique(lf[f]).size == cap
+    rec.close()
+
+
+def test_64_byte_record_validation():
+    """Record sizes 32 and 64 only; with 64-byte records a lane holds 8 FP32
+    (16 16-bit) frames of a 16-frame (32-frame) plane: voxels_z 2 or 4; 0
+    keeps the current record size; groups whose frames fit 32 bytes keep
+    any tile height."""
+    sc = _scene(2)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    for bad in [(8, 4, 4, 0, 0, 32, 0, 0, 48), (8, 4, 4, 0, 0, 32, 0, 0, 128), (8, 4, 8, 0, 0, 16, 0, 0, 64),
+                (8, 4, 8, 0, 0, 32, 0, 0, 64), (8, 4, 4, 0, 0, 32, 0, 0, -32)]:
+        with pytest.raises(psfs.PsfsError):
+            psfs.psfs_set_fuse_config(rec.handle, *bad)
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 0, 8, 0, 0, 64)    # 8 FP32 frames fit 32 bytes
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 4, 0, 0, 32, 0, 0, 0)
+    assert psfs.psfs_get_fuse_config(rec.handle, full=True)[8] == 64
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 0, 32, 0, 0, 32)
+    assert psfs.psfs_get_fuse_config(rec.handle, full=True)[5:] == (32, 8, 8, 32)
     rec.close()
 
 
@@ -267,14 +348,14 @@ def test_group_config_validation():
         with pytest.raises(psfs.PsfsError):
             psfs.psfs_set_fuse_config(rec.handle, *bad)
     # FP32 records hold 8 frames: 16 and 32 frames with voxels_z 8 are fine
-    for good in [(8, 4, 8, 0, 0, 16), (16, 4, 8, 0, 0, 32)]:
+    for good in [(8, 4, 8, 0, 0, 16, 0, 0, 32), (16, 4, 8, 0, 0, 32, 0, 0, 32)]:
         psfs.psfs_set_fuse_config(rec.handle, *good)
     # 16-bit records hold 16 frames: voxels_z 4 only from 16 frames on
     rec16 = psfs.Reconstructor(sc.grid, sc.cams, sc.params, map_dtype="f16")
     for bad in [(8, 4, 8, 0, 0, 16), (8, 4, 8, 0, 0, 32)]:
         with pytest.raises(psfs.PsfsError):
             psfs.psfs_set_fuse_config(rec16.handle, *bad)
-    psfs.psfs_set_fuse_config(rec16.handle, 8, 4, 8, 0, 0, 8)
+    psfs.psfs_set_fuse_config(rec16.handle, 8, 4, 8, 0, 0, 8, 0, 0, 32)
     psfs.psfs_set_fuse_config(rec16.handle, 8, 4, 4, 0, 0, 32)
     rec16.close()
     psfs.psfs_set_fuse_config(rec.handle, 8, 4, 8, 0, 0, 4)
@@ -308,8 +389,8 @@ def test_sequence_with_its_own_tile_shape():
     rec.set_background(to_dev(sc.mean), to_dev(sc.var))
     imgs = to_dev(sc.images)
     F, V = imgs.shape[0], rec.n_voxels
-    psfs.psfs_set_fuse_config(rec.handle, 32, 4, 16, 0, 2, 4, 16, 2)
-    assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (32, 4, 16, 0, 2, 4, 16, 2)
+    psfs.psfs_set_fuse_config(rec.handle, 32, 4, 16, 0, 2, 4, 16, 2, 32)
+    assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (32, 4, 16, 0, 2, 4, 16, 2, 32)
     occ = torch.empty((F, V), device="cuda")
     lst = torch.empty((F, V), dtype=torch.int32, device="cuda")
     cnt = torch.zeros(F, dtype=torch.int32, device="cuda")
@@ -320,8 +401,8 @@ def test_sequence_with_its_own_tile_shape():
         assert rec.sync() == psfs.PSFS_OK
         assert torch.equal(o1.view(-1), occ[f]) and int(c1.item()) == int(cnt[f])
     # back to one shape for both
-    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 4, 0, 2, 4)
-    assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (8, 4, 4, 0, 2, 4, 8, 4)
+    psfs.psfs_set_fuse_config(rec.handle, 8, 4, 4, 0, 2, 4, 0, 0, 32)
+    assert psfs.psfs_get_fuse_config(rec.handle, full=True) == (8, 4, 4, 0, 2, 4, 8, 4, 32)
     with pytest.raises(psfs.PsfsError):
         psfs.psfs_set_fuse_config(rec.handle, 8, 4, 4, 0, 2, 4, 12, 2)   # no such sequence shape
     rec.close()

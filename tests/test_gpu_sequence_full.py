@@ -37,8 +37,9 @@ def seq():
     return S.scene_128cube_8cam(seed=1, n_frames=N_FRAMES, workers=workers)
 
 
-@pytest.mark.parametrize("dtype,lanes_x,voxels_z", [("f32", 8, 4), ("f32", 16, 2), ("f16", 8, 2)])
-def test_sequence_groups_of_32_full_size(seq, dtype, lanes_x, voxels_z):
+@pytest.mark.parametrize("dtype,lanes_x,voxels_z,rec_bytes", [("f32", 8, 4, 32), ("f32", 16, 2, 32), ("f16", 8, 2, 32),
+                                                              ("f32", 8, 2, 64), ("f16", 16, 2, 64)])
+def test_sequence_groups_of_32_full_size(seq, dtype, lanes_x, voxels_z, rec_bytes):
     sc = seq
     V = sc.grid.n_voxels
     cap = 1 << 17
@@ -55,8 +56,8 @@ def test_sequence_groups_of_32_full_size(seq, dtype, lanes_x, voxels_z):
     psfs.psfs_set_background_l2(h, True)
     # the one-frame reference keeps its own shape; the sequence path gets the
     # shape under test (as the autotuner leaves a handle)
-    psfs.psfs_set_fuse_config(h, 8, 4, 16, 0, 2, 32, lanes_x, voxels_z)
-    assert psfs.psfs_get_fuse_config(h, full=True)[5:] == (32, lanes_x, voxels_z)
+    psfs.psfs_set_fuse_config(h, 8, 4, 16, 0, 2, 32, lanes_x, voxels_z, rec_bytes)
+    assert psfs.psfs_get_fuse_config(h, full=True)[5:] == (32, lanes_x, voxels_z, rec_bytes)
     with torch.cuda.stream(stream):
         psfs.psfs_reconstruct_sequence(h, N_FRAMES, imgs, occ, lists, cap, counts)
     assert rec.sync() == psfs.PSFS_OK
