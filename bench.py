@@ -1098,7 +1098,7 @@ def host_frame(occ, lists, counts, f, cap):
 
 
 def _adjoint_sample(out, dtype, sc, rec, d_images, occ_f32, stream, psfs):
-    """psfs_backward of frame 1 with the loss gradient 2 (occ - occ of frame 0)
+    """psfs_backward of frame 1 with the loss gradient occ - occ of frame 0
     (FP32 maps' occupancy as the target), kept with its d_occ for the CPU
     leg, which compares the gradients with the FP64 oracle's adjoint for the
     same d_occ."""
@@ -1108,7 +1108,7 @@ def _adjoint_sample(out, dtype, sc, rec, d_images, occ_f32, stream, psfs):
     dev = d_images.device
     with torch.cuda.stream(stream):
         o, lst, cnt = rec.reconstruct(d_images[f1])
-        d_occ = (2.0 * (o.view(-1) - occ_f32[0])).contiguous()
+        d_occ = (o.view(-1) - occ_f32[0]).contiguous()
         g = (torch.empty(n_pix, device=dev), torch.empty(n_pix * 3, device=dev), torch.empty(n_pix * 3, device=dev))
         psfs.psfs_backward(rec.handle, d_images[f1], d_occ, *g)
     stream.synchronize()
@@ -1120,8 +1120,9 @@ def _adjoint_sample(out, dtype, sc, rec, d_images, occ_f32, stream, psfs):
 
 def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=None):
     """Per-frame device time of the plain FP32 forward, and of forward +
-    adjoint with FP32 and with FP16 maps (the loss is sum (occ - target)^2 with
-    the previous frame's FP32 occupancy as target), CUDA events on the
+    adjoint with FP32 and with FP16 maps (the loss is 1/2 sum (occ - target)^2
+    with the previous frame's FP32 occupancy as target, so its gradient
+    occ - target is one elementwise kernel), CUDA events on the
     handle's stream.  Also the FP16 forward's occupancy error against FP32."""
     import torch
     F = min(args.forms_frames, d_images.shape[0])
@@ -1143,7 +1144,6 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
             for f in range(2):   # warm-up (the torch ops of the loss too: their first launch loads them)
                 rec.reconstruct(d_images[f], (o, lst, cnt))
                 torch.sub(o.view(-1), occ_f32[f], out=d_occ)
-                d_occ.mul_(2.0)
                 psfs.psfs_backward(rec.handle, d_images[f], d_occ, d_slm, d_mean, d_var)
                 err = max(err, float((o.view(-1) - occ_f32[f]).abs().max()))
             err = 0.0
@@ -1155,7 +1155,6 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
             for f in range(F):
                 rec.reconstruct(d_images[f], (o, lst, cnt))
                 torch.sub(o.view(-1), occ_f32[max(f - 1, 0)], out=d_occ)
-                d_occ.mul_(2.0)
                 psfs.psfs_backward(rec.handle, d_images[f], d_occ, d_slm, d_mean, d_var)
             e[2].record(stream)
             for f in range(min(F, 4)):
@@ -1211,7 +1210,6 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
                     e[0].record(stream)
                 psfs.psfs_reconstruct_sequence(rec.handle, nseq, d_images[:nseq], occ_s, lst_s, cap_s, cnt_s)
                 torch.sub(occ_s, occ_f32[:nseq], out=d_occ_s)
-                d_occ_s.mul_(2.0)
                 psfs.psfs_backward_sequence(rec.handle, nseq, d_images[:nseq], d_occ_s, d_slm_s, d_mean, d_var)
             e[3].record(stream)
         stream.synchronize()
@@ -1225,7 +1223,6 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
                     e[0].record(stream)
                 psfs.psfs_reconstruct_sequence(rec.handle, nseq, d_images[:nseq], occ_s, lst_s, cap_s, cnt_s)
                 torch.sub(occ_s, occ_f32[:nseq], out=d_occ_s)
-                d_occ_s.mul_(2.0)
                 psfs.psfs_backward_from_occupancy(rec.handle, nseq, d_images[:nseq], occ_s, d_occ_s, d_slm_s,
                                                   d_mean, d_var)
             e[3].record(stream)
@@ -1237,7 +1234,6 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
             for f in range(F):
                 rec.reconstruct(d_images[f], (o, lst, cnt))
                 torch.sub(o.view(-1), occ_f32[max(f - 1, 0)], out=d_occ)
-                d_occ.mul_(2.0)
                 psfs.psfs_backward_from_occupancy(rec.handle, 1, d_images[f], o, d_occ, d_slm, d_mean, d_var)
             e[3].record(stream)
         stream.synchronize()

@@ -355,17 +355,32 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
 
 // dLoss/dL = d_occ occ (1 - occ) from the forward's own occupancy (the
 // expression of the voxel passes, so the same bits as their recomputation):
-// n_frames frames of n_vox voxels, frame f's value into slot slot0 + f of
-// each voxel's record (dl_stride kBwRecord), or densely (dl_stride 1, one
-// frame).
+// n_frames frames of n_vox voxels, frame f's value into slot f of each
+// voxel's 8-slot record (slots n_frames .. 7 set to 0; the whole 32-byte
+// record in one vector store), or densely (dl_stride 1, one frame).
 __global__ void __launch_bounds__(256) dl_from_occ_kernel(const float *occ, const float *d_occ, float *dl,
                                                           int64_t n_vox, int n_frames, int dl_stride)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_vox; v += stride) {
-        for (int f = 0; f < n_frames; ++f) {
-            const float o = __ldg(occ + f * n_vox + v);
-            dl[v * dl_stride + f] = __ldg(d_occ + f * n_vox + v) * o * (1.0f - o);
+        if (dl_stride == kBwRecord) {
+            float r[kBwRecord];
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) {
+                r[f] = 0.0f;
+                if (f < n_frames) {
+                    const float o = __ldg(occ + f * n_vox + v);
+                    r[f] = __ldg(d_occ + f * n_vox + v) * o * (1.0f - o);
+                }
+            }
+            float4 *rec = reinterpret_cast<float4 *>(dl + v * kBwRecord);
+            rec[0] = make_float4(r[0], r[1], r[2], r[3]);
+            rec[1] = make_float4(r[4], r[5], r[6], r[7]);
+        } else {
+            for (int f = 0; f < n_frames; ++f) {
+                const float o = __ldg(occ + f * n_vox + v);
+                dl[v * dl_stride + f] = __ldg(d_occ + f * n_vox + v) * o * (1.0f - o);
+            }
         }
     }
 }
@@ -417,6 +432,7 @@ cudaError_t launch_dl_from_occ(const float *occ, const float *d_occ, float *dl, 
                                int dl_stride, cudaStream_t s)
 {
     if (n_frames < 1 || n_frames > dl_stride) return cudaErrorInvalidValue;
+    if (dl_stride == kBwRecord && ((uintptr_t)dl & 31u)) return cudaErrorMisalignedAddress;
     dl_from_occ_kernel<<<(int)grid_for(n_vox), 256, 0, s>>>(occ, d_occ, dl, n_vox, n_frames, dl_stride);
     return cudaGetLastError();
 }

@@ -107,3 +107,31 @@ def test_camera_inside_the_grid():
     got = _gpu_masks(rec, lists, counts, s_.size)
     _check(sc.grid, sc.cams, s_.astype(np.uint32), got[0])
     rec.close()
+
+
+@pytest.mark.parametrize("width,height,n_set", [(66, 50, 300), (320, 240, 300)])
+def test_staged_and_direct_paths(width, height, n_set):
+    """A CTA stages its chunk of 256 voxels in shared memory when the union of
+    their boxes fits 32 KB of 4-byte-aligned rows, and stores directly
+    otherwise: rows not a multiple of 4 bytes wide (66 px, direct), scattered
+    voxels in a 320 x 240 image (unions larger than 32 KB, direct) and a
+    solid box in the same rig (staged chunks)."""
+    sc = S.make_scene(seed=43, grid_n=24, cube_side=2.0, n_cams=3, width=width, height=height,
+                      focal=0.9 * width)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    V = sc.grid.n_voxels
+    rng = np.random.default_rng(4)
+    box = np.zeros((24, 24, 24), bool)
+    box[6:18, 8:16, 4:20] = True
+    sets = [rng.choice(V, n_set, replace=False), np.flatnonzero(box.ravel())]
+    stride = max(s.size for s in sets)
+    lists = torch.zeros((len(sets), stride), dtype=torch.int32)
+    counts = torch.zeros((len(sets),), dtype=torch.int32)
+    for f, s_ in enumerate(sets):
+        lists[f, :s_.size] = torch.from_numpy(s_.astype(np.int32))
+        counts[f] = s_.size
+    got = _gpu_masks(rec, lists.cuda(), counts.cuda(), stride)
+    for f, s_ in enumerate(sets):
+        _check(sc.grid, sc.cams, s_.astype(np.uint32), got[f])
+        assert got[f].sum() > 100
+    rec.close()
