@@ -50,8 +50,10 @@ def _check(shape, prob_f32, got_sm, got_list, got_count, threshold):
     return int(diff.size)
 
 
-@pytest.mark.parametrize("dims", [(37, 29, 23), (64, 64, 64), (8, 8, 8), (33, 9, 17)])
+@pytest.mark.parametrize("dims", [(37, 29, 23), (64, 64, 64), (8, 8, 8), (33, 9, 17), (150, 20, 12), (132, 35, 9)])
 def test_random_fields(dims):
+    """Ragged grids: partial tiles along x, y and z, several tiles along
+    each axis (150 and 132 columns, 35 rows), odd and small extents."""
     nx, ny, nz = dims
     grid = S.Grid(nx, ny, nz, (-1.0, -1.0, 0.0), 0.05)
     rec = _rec(grid)
