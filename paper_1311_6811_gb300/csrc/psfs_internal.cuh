@@ -123,6 +123,13 @@ constexpr int kBoxClasses = 3;
 // the rows are not 16-byte aligned or the encoder is unavailable.
 bool encode_map_tensors(void *maps, int map_dtype, int W, int H, int n_cams, CUtensorMap *out);
 
+// Encodes a 4-D tensor map {nx, ny, nz, n_frames} of float32 grids with boxes
+// of box_x x box_y x 1 x 1 elements (elements outside the grids read as
+// zero); false when the rows are not 16-byte multiples, the base is not
+// 16-byte aligned or the encoder is unavailable.
+bool encode_grid_tensor(const float *grids, int nx, int ny, int nz, int n_frames, int box_x, int box_y,
+                        CUtensorMap *out);
+
 // Tile shape of the fuse kernel (see psfs_fuse_config): a warp is LX voxels
 // along x by 32 / LX along y, a CTA WY warps along y, TZ voxels per thread
 // along z.
@@ -590,6 +597,7 @@ cudaError_t launch_surface(const SurfaceArgs &a, int n_frames, cudaStream_t s);
 // its list at lists + f * capacity, its count at counts[f] (zeroed by the
 // launcher).
 struct SmoothArgs {
+    CUtensorMap tmap;   // {nx, ny, nz, n_frames} over prob, boxes of 136 x 10 (smooth_tma_kernel)
     const float *prob;
     float *smoothed;
     uint32_t *lists;

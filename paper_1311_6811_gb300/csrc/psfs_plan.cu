@@ -169,6 +169,22 @@ bool encode_map_tensors(void *maps, int map_dtype, int W, int H, int n_cams, CUt
     return true;
 }
 
+bool encode_grid_tensor(const float *grids, int nx, int ny, int nz, int n_frames, int box_x, int box_y,
+                        CUtensorMap *out)
+{
+    if (((int64_t)nx * 4) % 16 != 0 || ((uintptr_t)grids & 15u) || box_x > 256 || box_y > 256 || (box_x * 4) % 16)
+        return false;
+    EncodeTiledFn fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)n_frames};
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nz * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(grids), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool fuse_shape_supported(const FuseShape &s)
 {
     return (s.lx == 8 || s.lx == 16 || s.lx == 32) && s.wy == 4 &&
