@@ -828,6 +828,19 @@ def run_ours(args):
             d2h += F * V * 4 + F * 4 + 4 * int(torch.clamp(h_cnt.long(), max=cap_e2e).sum())
         dt = max_over_ranks(time.perf_counter() - t0, dev)
         barrier()
+        # the same with the voxel lists and counts as the only result copied
+        # out (the reconstruction's output downstream; no occupancy grids)
+        psfs.psfs_reconstruct_sequence_host(h, F, h_images, None, h_list, cap_e2e, h_cnt)   # warm-up
+        d2h_l = 0
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            st_e = psfs.psfs_reconstruct_sequence_host(h, F, h_images, None, h_list, cap_e2e, h_cnt)
+            if st_e != psfs.PSFS_OK:
+                raise RuntimeError(f"host-buffer sequence failed: {psfs.psfs_status_string(st_e)}")
+            d2h_l += F * 4 + 4 * int(torch.clamp(h_cnt.long(), max=cap_e2e).sum())
+        dt_l = max_over_ranks(time.perf_counter() - t0, dev)
+        barrier()
         # the host link alone, same pinned buffers: one copy each way
         d_img_tmp = torch.empty(images.shape, dtype=torch.uint8, device=dev)
         link = {}
@@ -855,7 +868,13 @@ def run_ours(args):
                "steps": e2e_steps, "ms_per_step": 1e3 * dt / e2e_steps,
                "link_alone": {k: round(v, 1) for k, v in link.items()},
                "path": "psfs_reconstruct_sequence_host over the step's frames (pinned host buffers; "
-                       "copies in and out overlap the kernels)"}
+                       "copies in and out overlap the kernels)",
+               "lists_only": {"value": sum_over_ranks(float(F * V * K * e2e_steps), dev) / dt_l / 1e9,
+                              "unit": UNIT, "h2d_bytes_per_step": F * n_pix * 3,
+                              "d2h_bytes_per_step": int(d2h_l / e2e_steps),
+                              "ms_per_step": 1e3 * dt_l / e2e_steps,
+                              "note": "the same call with no occupancy grids copied out (h_occupancy NULL): "
+                                      "images in, counts and voxel lists out"}}
 
     forms = None
     if not args.no_forms:
