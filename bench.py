@@ -817,30 +817,33 @@ def run_ours(args):
         h_list = torch.empty((F, cap_e2e), dtype=torch.int32).pin_memory()
         h_cnt = torch.zeros((F,), dtype=torch.int32).pin_memory()
         e2e_steps = max(1, min(args.steps, 10))
-        psfs.psfs_reconstruct_sequence_host(h, F, h_images, h_occ, h_list, cap_e2e, h_cnt)   # warm-up
-        d2h = 0
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            st_e = psfs.psfs_reconstruct_sequence_host(h, F, h_images, h_occ, h_list, cap_e2e, h_cnt)
-            if st_e != psfs.PSFS_OK:
-                raise RuntimeError(f"host-buffer sequence failed: {psfs.psfs_status_string(st_e)}")
-            d2h += F * V * 4 + F * 4 + 4 * int(torch.clamp(h_cnt.long(), max=cap_e2e).sum())
-        dt = max_over_ranks(time.perf_counter() - t0, dev)
-        barrier()
+
+        def host_blocks(occ_out, n_blocks=3):
+            """n_blocks blocks of e2e_steps calls each (the host link is shared
+            with the rest of the machine, so single blocks vary); returns the
+            seconds of each block (max over ranks) and the bytes copied out
+            per step."""
+            psfs.psfs_reconstruct_sequence_host(h, F, h_images, occ_out, h_list, cap_e2e, h_cnt)   # warm-up
+            secs, out_b = [], 0
+            for _ in range(n_blocks):
+                barrier()
+                t0 = time.perf_counter()
+                for _ in range(e2e_steps):
+                    st_e = psfs.psfs_reconstruct_sequence_host(h, F, h_images, occ_out, h_list, cap_e2e, h_cnt)
+                    if st_e != psfs.PSFS_OK:
+                        raise RuntimeError(f"host-buffer sequence failed: {psfs.psfs_status_string(st_e)}")
+                    out_b = (F * V * 4 if occ_out is not None else 0) + F * 4 + \
+                        4 * int(torch.clamp(h_cnt.long(), max=cap_e2e).sum())
+                secs.append(max_over_ranks(time.perf_counter() - t0, dev))
+            barrier()
+            return secs, out_b
+
+        secs_full, d2h_step = host_blocks(h_occ)
         # the same with the voxel lists and counts as the only result copied
         # out (the reconstruction's output downstream; no occupancy grids)
-        psfs.psfs_reconstruct_sequence_host(h, F, h_images, None, h_list, cap_e2e, h_cnt)   # warm-up
-        d2h_l = 0
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            st_e = psfs.psfs_reconstruct_sequence_host(h, F, h_images, None, h_list, cap_e2e, h_cnt)
-            if st_e != psfs.PSFS_OK:
-                raise RuntimeError(f"host-buffer sequence failed: {psfs.psfs_status_string(st_e)}")
-            d2h_l += F * 4 + 4 * int(torch.clamp(h_cnt.long(), max=cap_e2e).sum())
-        dt_l = max_over_ranks(time.perf_counter() - t0, dev)
-        barrier()
+        secs_lists, d2h_step_l = host_blocks(None)
+        dt = sorted(secs_full)[len(secs_full) // 2]     # the median block
+        dt_l = sorted(secs_lists)[len(secs_lists) // 2]
         # the host link alone, same pinned buffers: one copy each way
         d_img_tmp = torch.empty(images.shape, dtype=torch.uint8, device=dev)
         link = {}
@@ -864,15 +867,18 @@ def run_ours(args):
         link["both_gbs"] = (h_images.numel() + occ.numel() * 4) / (time.perf_counter() - t0) / 1e9
         del d_img_tmp
         e2e = {"value": sum_over_ranks(float(F * V * K * e2e_steps), dev) / dt / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": F * n_pix * 3, "d2h_bytes_per_step": int(d2h / e2e_steps),
+               "h2d_bytes_per_step": F * n_pix * 3, "d2h_bytes_per_step": int(d2h_step),
                "steps": e2e_steps, "ms_per_step": 1e3 * dt / e2e_steps,
+               "blocks_ms_per_step": [round(1e3 * x / e2e_steps, 3) for x in secs_full],
+               "timing": f"median of {len(secs_full)} blocks of {e2e_steps} steps",
                "link_alone": {k: round(v, 1) for k, v in link.items()},
                "path": "psfs_reconstruct_sequence_host over the step's frames (pinned host buffers; "
                        "copies in and out overlap the kernels)",
                "lists_only": {"value": sum_over_ranks(float(F * V * K * e2e_steps), dev) / dt_l / 1e9,
                               "unit": UNIT, "h2d_bytes_per_step": F * n_pix * 3,
-                              "d2h_bytes_per_step": int(d2h_l / e2e_steps),
+                              "d2h_bytes_per_step": int(d2h_step_l),
                               "ms_per_step": 1e3 * dt_l / e2e_steps,
+                              "blocks_ms_per_step": [round(1e3 * x / e2e_steps, 3) for x in secs_lists],
                               "note": "the same call with no occupancy grids copied out (h_occupancy NULL): "
                                       "images in, counts and voxel lists out"}}
 
