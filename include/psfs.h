@@ -390,12 +390,16 @@ psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_
  * gathers each voxel's log ratios of those frames with one load per camera,
  * dLoss/dL goes into 32-byte per-voxel records of the group's frames, and
  * one per-pixel owner pass reads one record per owned voxel for the whole
- * group.  Each frame's d_slm is bit-identical to psfs_backward's; d_mean and
- * d_var equal the FP32 sum, in frame order, of psfs_backward's.  Scratch
- * (first call): 8 * nx * ny * nz floats, maps of 8 frames, a tile plan, and
- * the owner lists of psfs_backward.  Requirements as psfs_reconstruct_sequence
- * (frame size and voxel count multiples of 16 and 4).  Errors: INVALID_ARG,
- * NOT_READY, NOMEM, CUDA. */
+ * group.  The records alternate between two buffers, so that one group's
+ * recomputed forward (one stream) overlaps the previous group's owner pass (a
+ * second stream); the call is ordered after earlier work on the handle's
+ * stream and later work waits for it.  Each frame's d_slm is bit-identical
+ * to psfs_backward's; d_mean and d_var equal the FP32 sum, in frame order, of
+ * psfs_backward's.  Scratch (first call): 2 * 8 * nx * ny * nz floats, maps
+ * of 8 frames, a tile plan, the sequence streams, and the owner lists of
+ * psfs_backward.  Requirements as psfs_reconstruct_sequence (frame size and
+ * voxel count multiples of 16 and 4).  Errors: INVALID_ARG, NOT_READY, NOMEM,
+ * CUDA. */
 psfs_status psfs_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
                                    const float *d_occ, float *d_slm, float *d_mean, float *d_var);
 
@@ -406,9 +410,11 @@ psfs_status psfs_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8
  * elementwise, so the maps and the log-odds are not recomputed; the pixel
  * passes and the outputs are those of psfs_backward (n_frames = 1) and
  * psfs_backward_sequence (n_frames > 1: d_slm per frame [n_frames][n_cams]
- * [height][width], d_mean and d_var summed over the frames), with the same
- * bits when `occupancy` is the forward's.  Errors: INVALID_ARG, NOT_READY,
- * NOMEM, CUDA. */
+ * [height][width], d_mean and d_var summed over the frames; the records of
+ * consecutive groups alternate between two buffers, one group's records
+ * formed while the previous group's owner pass runs), with the same bits when
+ * `occupancy` is the forward's.  Errors: INVALID_ARG, NOT_READY, NOMEM,
+ * CUDA. */
 psfs_status psfs_backward_from_occupancy(psfs_handle *h, int32_t n_frames, const uint8_t *images,
                                          const float *occupancy, const float *d_occ, float *d_slm,
                                          float *d_mean, float *d_var);

@@ -108,6 +108,7 @@ struct psfs_handle {
     // adjoint scratch (allocated on first use)
     float *dl = nullptr;        // [n_vox] dLoss / dlogodds
     float *dl_rec = nullptr;    // [n_vox][kBwRecord] the same for psfs_backward_sequence
+    float *dl_rec2 = nullptr;   // its second buffer: group g's records in buffer g & 1
     // owner lists of the pixel pass (built by the first adjoint call): pixel
     // p owns own_vox[own_off[p] .. own_off[p + 1])
     uint32_t *own_off = nullptr;   // [n_pix + 1]
@@ -227,6 +228,7 @@ void free_handle(psfs_handle *h)
     cudaFree(h->st_list);
     cudaFree(h->dl);
     cudaFree(h->dl_rec);
+    cudaFree(h->dl_rec2);
     cudaFree(h->own_off);
     cudaFree(h->own_vox);
     cudaFree(h->own_cnt);
@@ -1326,15 +1328,25 @@ static void fill_backward_args(psfs_handle *h, BackwardArgs &b)
 // 8, voxels_z 4), planned once per handle on first use.
 constexpr FuseShape kBwShape = {8, 4, 4, 0};
 
-static psfs_status ensure_backward_group(psfs_handle *h)
+// The two dLoss/dL record buffers of the batched adjoint (group g in buffer
+// g & 1) and the sequence streams it pipelines on.
+static psfs_status ensure_dl_records(psfs_handle *h)
 {
     const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
-    if (!h->dl_rec) {
-        if (cudaMalloc(&h->dl_rec, (size_t)kBwRecord * n_vox * sizeof(float)) != cudaSuccess) {
+    for (float **buf : {&h->dl_rec, &h->dl_rec2}) {
+        if (*buf) continue;
+        if (cudaMalloc(buf, (size_t)kBwRecord * n_vox * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return fail(PSFS_ERR_NOMEM, "adjoint sequence scratch");
         }
     }
+    return seq_setup(h);
+}
+
+static psfs_status ensure_backward_group(psfs_handle *h)
+{
+    psfs_status st = ensure_dl_records(h);
+    if (st != PSFS_OK) return st;
     if (!h->bw_maps) {
         if (cudaMalloc(&h->bw_maps, (size_t)h->n_pix * kBwRecord * h->map_elem) != cudaSuccess) {
             cudaGetLastError();
@@ -1374,7 +1386,9 @@ static psfs_status ensure_backward_group(psfs_handle *h)
 // likelihood pass over the background for its P frames (maps as one plane
 // of P-frame records) and one voxel pass that gathers each record once per
 // (voxel, camera) and writes dLoss/dL of the P frames into their slots; then
-// one pixel pass for the group.  Per frame the arithmetic is that of
+// one pixel pass for the group.  The record buffers alternate between groups,
+// so a group's likelihood and voxel passes (stream 0) overlap the previous
+// group's pixel pass (stream 1).  Per frame the arithmetic is that of
 // psfs_backward, so d_slm is bit-identical to it.
 static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8_t *images,
                                              const float *d_occ, float *d_slm, float *d_mean, float *d_var)
@@ -1388,8 +1402,19 @@ static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, c
     b.d_mean = d_mean;
     b.d_var = d_var;
     const size_t frame_bytes = (size_t)h->n_pix * 3;
-    for (int g0 = 0; g0 < n_frames; g0 += kBwRecord) {
+    // group g's records are formed on stream 0 (likelihood and voxel passes)
+    // into buffer g & 1 while stream 1 runs group g - 1's pixel pass from the
+    // other buffer; the pixel passes stay in group order on stream 1 (they
+    // accumulate d_mean and d_var)
+    cudaStream_t sa = h->seq_stream[0], sb = h->seq_stream[1];
+    float *bufs[2] = {h->dl_rec, h->dl_rec2};
+    PSFS_CK(cudaEventRecord(h->seq_ev_in, h->stream));
+    PSFS_CK(cudaStreamWaitEvent(sa, h->seq_ev_in, 0));
+    PSFS_CK(cudaStreamWaitEvent(sb, h->seq_ev_in, 0));
+    for (int g = 0, g0 = 0; g0 < n_frames; ++g, g0 += kBwRecord) {
         const int nf = std::min(kBwRecord, n_frames - g0);
+        const int q = g & 1;
+        if (g >= 2) PSFS_CK(cudaStreamWaitEvent(sa, h->seq_ev_fused[q], 0));   // group g - 2's pixel pass is done with it
         for (int slot = 0, P = kBwRecord; P >= 1; P /= 2) {
             if (!(nf & P)) continue;
             const size_t f0 = (size_t)g0 + slot;   // the unit's first frame
@@ -1405,35 +1430,43 @@ static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, c
             la.status = h->d_words;
             la.img_fstride = (int64_t)frame_bytes;
             {
-                ProfScope ps(h, PSFS_STAGE_LIKELIHOOD);
+                ProfScope ps(h, PSFS_STAGE_LIKELIHOOD, sa);
                 if (P > 1)
-                    PSFS_CK(launch_likelihood_group(la, P, h->params.map_dtype, h->stream, 4));
+                    PSFS_CK(launch_likelihood_group(la, P, h->params.map_dtype, sa, 4));
                 else
-                    PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, h->stream));
+                    PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, sa));
             }
             BackwardArgs bv = b;
             bv.f = h->bw_fuse;
             bv.d_occ = d_occ + f0 * n_vox;
-            bv.dl = h->dl_rec + slot;
+            bv.dl = bufs[q] + slot;
             bv.dl_stride = kBwRecord;
             {
-                ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL);
+                ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL, sa);
                 if (P > 1)
-                    PSFS_CK(launch_backward_voxel_group(bv, kBwShape, P, h->params.map_dtype, (int64_t)n_vox,
-                                                        h->stream));
+                    PSFS_CK(launch_backward_voxel_group(bv, kBwShape, P, h->params.map_dtype, (int64_t)n_vox, sa));
                 else
-                    PSFS_CK(launch_backward_voxel(bv, kBwShape, h->params.map_dtype, h->stream));
+                    PSFS_CK(launch_backward_voxel(bv, kBwShape, h->params.map_dtype, sa));
             }
             slot += P;
         }
+        PSFS_CK(cudaEventRecord(h->seq_ev_map[q], sa));
+        PSFS_CK(cudaStreamWaitEvent(sb, h->seq_ev_map[q], 0));
         BackwardArgs bp = b;
-        bp.dl = h->dl_rec;
+        bp.dl = bufs[q];
         bp.dl_stride = kBwRecord;
         bp.img = images + (size_t)g0 * frame_bytes;
         bp.d_slm = d_slm ? d_slm + (size_t)g0 * h->n_pix : nullptr;
-        ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL);
-        PSFS_CK(launch_owner_pixel_group(bp, h->own_off, h->own_vox, nf, (int64_t)frame_bytes, g0 > 0, h->stream));
+        {
+            ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL, sb);
+            PSFS_CK(launch_owner_pixel_group(bp, h->own_off, h->own_vox, nf, (int64_t)frame_bytes, g0 > 0, sb));
+        }
+        PSFS_CK(cudaEventRecord(h->seq_ev_fused[q], sb));
     }
+    PSFS_CK(cudaEventRecord(h->seq_ev_done[0], sa));
+    PSFS_CK(cudaEventRecord(h->seq_ev_done[1], sb));
+    PSFS_CK(cudaStreamWaitEvent(h->stream, h->seq_ev_done[0], 0));
+    PSFS_CK(cudaStreamWaitEvent(h->stream, h->seq_ev_done[1], 0));
     return PSFS_OK;
 }
 
@@ -1478,10 +1511,8 @@ static psfs_status enqueue_backward_from_occupancy(psfs_handle *h, int32_t n_fra
     const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
     psfs_status st = ensure_owner_lists(h);
     if (st != PSFS_OK) return st;
-    float **scratch = n_frames == 1 ? &h->dl : &h->dl_rec;
-    const size_t elems = n_frames == 1 ? n_vox : (size_t)kBwRecord * n_vox;
-    if (!*scratch) {
-        if (cudaMalloc(scratch, elems * sizeof(float)) != cudaSuccess) {
+    if (n_frames == 1 && !h->dl) {
+        if (cudaMalloc(&h->dl, n_vox * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return fail(PSFS_ERR_NOMEM, "adjoint scratch");
         }
@@ -1502,22 +1533,42 @@ static psfs_status enqueue_backward_from_occupancy(psfs_handle *h, int32_t n_fra
         PSFS_CK(launch_owner_pixel(b, h->own_off, h->own_vox, h->stream));
         return PSFS_OK;
     }
+    // group g's records (stream 0) into buffer g & 1 while stream 1 runs
+    // group g - 1's pixel pass from the other buffer
+    st = ensure_dl_records(h);
+    if (st != PSFS_OK) return st;
     const size_t frame_bytes = (size_t)h->n_pix * 3;
-    for (int g0 = 0; g0 < n_frames; g0 += kBwRecord) {
+    cudaStream_t sa = h->seq_stream[0], sb = h->seq_stream[1];
+    float *bufs[2] = {h->dl_rec, h->dl_rec2};
+    PSFS_CK(cudaEventRecord(h->seq_ev_in, h->stream));
+    PSFS_CK(cudaStreamWaitEvent(sa, h->seq_ev_in, 0));
+    PSFS_CK(cudaStreamWaitEvent(sb, h->seq_ev_in, 0));
+    for (int g = 0, g0 = 0; g0 < n_frames; ++g, g0 += kBwRecord) {
         const int nf = std::min(kBwRecord, n_frames - g0);
+        const int q = g & 1;
+        if (g >= 2) PSFS_CK(cudaStreamWaitEvent(sa, h->seq_ev_fused[q], 0));
         {
-            ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL);
-            PSFS_CK(launch_dl_from_occ(occupancy + (size_t)g0 * n_vox, d_occ + (size_t)g0 * n_vox, h->dl_rec,
-                                       (int64_t)n_vox, nf, kBwRecord, h->stream));
+            ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL, sa);
+            PSFS_CK(launch_dl_from_occ(occupancy + (size_t)g0 * n_vox, d_occ + (size_t)g0 * n_vox, bufs[q],
+                                       (int64_t)n_vox, nf, kBwRecord, sa));
         }
+        PSFS_CK(cudaEventRecord(h->seq_ev_map[q], sa));
+        PSFS_CK(cudaStreamWaitEvent(sb, h->seq_ev_map[q], 0));
         BackwardArgs bp = b;
-        bp.dl = h->dl_rec;
+        bp.dl = bufs[q];
         bp.dl_stride = kBwRecord;
         bp.img = images + (size_t)g0 * frame_bytes;
         bp.d_slm = d_slm ? d_slm + (size_t)g0 * h->n_pix : nullptr;
-        ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL);
-        PSFS_CK(launch_owner_pixel_group(bp, h->own_off, h->own_vox, nf, (int64_t)frame_bytes, g0 > 0, h->stream));
+        {
+            ProfScope ps(h, PSFS_STAGE_BACKWARD_PIXEL, sb);
+            PSFS_CK(launch_owner_pixel_group(bp, h->own_off, h->own_vox, nf, (int64_t)frame_bytes, g0 > 0, sb));
+        }
+        PSFS_CK(cudaEventRecord(h->seq_ev_fused[q], sb));
     }
+    PSFS_CK(cudaEventRecord(h->seq_ev_done[0], sa));
+    PSFS_CK(cudaEventRecord(h->seq_ev_done[1], sb));
+    PSFS_CK(cudaStreamWaitEvent(h->stream, h->seq_ev_done[0], 0));
+    PSFS_CK(cudaStreamWaitEvent(h->stream, h->seq_ev_done[1], 0));
     return PSFS_OK;
 }
 

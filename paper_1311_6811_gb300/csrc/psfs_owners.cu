@@ -291,9 +291,26 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
         float acc[kBwRecord];
 #pragma unroll
         for (int f = 0; f < kBwRecord; ++f) acc[f] = 0.0f;
-        // two owners at a time (their loads in flight together), added in
+        // four owners at a time (their loads in flight together), added in
         // ascending order; one 256-bit read-only load per record (one sector)
         uint32_t e = e0;
+        for (; e + 4 <= e1; e += 4) {
+            const uint32_t va = __ldg(vox + e), vb = __ldg(vox + e + 1), vc = __ldg(vox + e + 2),
+                           vd = __ldg(vox + e + 3);
+            uint32_t wa[8], wb[8], wc[8], wd[8];
+            load_record(b.dl + (size_t)va * kBwRecord, wa);
+            load_record(b.dl + (size_t)vb * kBwRecord, wb);
+            load_record(b.dl + (size_t)vc * kBwRecord, wc);
+            load_record(b.dl + (size_t)vd * kBwRecord, wd);
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wa[f]);
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wb[f]);
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wc[f]);
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wd[f]);
+        }
         for (; e + 2 <= e1; e += 2) {
             const uint32_t va = __ldg(vox + e), vb = __ldg(vox + e + 1);
             uint32_t wa[8], wb[8];
