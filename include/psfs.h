@@ -452,6 +452,28 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
 psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, psfs_fuse_config *best,
                           float *candidate_ms);
 
+/* The autotuner's choices as a file, so that later processes start with them.
+ * psfs_autotune remembers, per (grid size, camera count, image size, map
+ * type), the tile shape for one frame per call and the sequence path's
+ * configuration; psfs_create applies them to handles of that kind.
+ * psfs_tune_cache_save writes every remembered choice to `path` as text: a
+ * line "psfs-tune 1", then one line per kind of 19 integers: nx ny nz n_cams
+ * width height map_dtype, lanes_x warps voxels_z staged (one frame per call),
+ * seq_likelihood_ctas frames_per_group, own_sequence_shape (0 or 1), lanes_x
+ * warps voxels_z staged (sequence path), seq_record_bytes.
+ * psfs_tune_cache_load reads such a file and adds its choices (replacing
+ * those of the same kinds); it changes nothing unless every line is valid
+ * (supported shapes and sizes).  Handles created earlier keep their
+ * configuration.  psfs_tune_cache_clear forgets every choice;
+ * psfs_tune_cache_entries returns how many kinds are remembered.  The cache
+ * is shared by the threads of the process (guarded).  Errors: INVALID_ARG
+ * (NULL path, a file that cannot be opened, read or written, or an invalid
+ * line; the message names the line). */
+psfs_status psfs_tune_cache_save(const char *path);
+psfs_status psfs_tune_cache_load(const char *path);
+void psfs_tune_cache_clear(void);
+int32_t psfs_tune_cache_entries(void);
+
 /* Waits for the handle's stream, then returns and clears the first problem
  * recorded on the device since the last psfs_sync (PSFS_ERR_CAPACITY), or
  * PSFS_OK.  Errors: CUDA. */

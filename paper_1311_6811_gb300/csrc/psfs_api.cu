@@ -1826,6 +1826,116 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     return PSFS_OK;
 }
 
+psfs_status psfs_tune_cache_save(const char *path)
+{
+    if (!path) return fail(PSFS_ERR_INVALID_ARG, "path is NULL");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    FILE *fp = std::fopen(path, "w");
+    if (!fp) return fail(PSFS_ERR_INVALID_ARG, "tune cache file cannot be opened for writing");
+    bool ok = std::fprintf(fp, "psfs-tune 1\n") > 0;
+    for (const auto &kv : g_tuned) {
+        const TuneKey &k = kv.first;
+        const Tuned &t = kv.second;
+        ok = ok && std::fprintf(fp, "%d %d %d %d %d %d %d  %d %d %d %d  %d %d  %d %d %d %d %d  %d\n", std::get<0>(k),
+                                std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k),
+                                std::get<6>(k), t.shape.lx, t.shape.wy, t.shape.tz, t.shape.staged, t.seq_lk_ctas,
+                                t.seq_group, t.seq_own ? 1 : 0, t.seq_shape.lx, t.seq_shape.wy, t.seq_shape.tz,
+                                t.seq_shape.staged, t.seq_rec) > 0;
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(PSFS_ERR_INVALID_ARG, "tune cache file could not be written");
+    return PSFS_OK;
+}
+
+psfs_status psfs_tune_cache_load(const char *path)
+{
+    if (!path) return fail(PSFS_ERR_INVALID_ARG, "path is NULL");
+    FILE *fp = std::fopen(path, "r");
+    if (!fp) return fail(PSFS_ERR_INVALID_ARG, "tune cache file cannot be opened for reading");
+    std::map<TuneKey, Tuned> add;
+    char line[512];
+    int lineno = 0;
+    bool ok = true;
+    static thread_local char msg[128];
+    auto bad = [&](const char *why) {
+        std::snprintf(msg, sizeof(msg), "tune cache line %d: %s", lineno, why);
+        ok = false;
+    };
+    while (ok && std::fgets(line, sizeof(line), fp)) {
+        ++lineno;
+        if (lineno == 1) {
+            int version = 0;
+            if (std::sscanf(line, "psfs-tune %d", &version) != 1 || version != 1) bad("not a psfs-tune 1 file");
+            continue;
+        }
+        bool blank = true;
+        for (const char *c = line; *c; ++c) blank = blank && (*c == ' ' || *c == '\t' || *c == '\n' || *c == '\r');
+        if (blank) continue;
+        int v[19], used = 0;
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d%n", &v[0], &v[1], &v[2],
+                        &v[3], &v[4], &v[5], &v[6], &v[7], &v[8], &v[9], &v[10], &v[11], &v[12], &v[13], &v[14],
+                        &v[15], &v[16], &v[17], &v[18], &used) != 19) {
+            bad("not 19 integers");
+            break;
+        }
+        for (const char *c = line + used; *c; ++c)
+            if (!(*c == ' ' || *c == '\t' || *c == '\n' || *c == '\r')) {
+                bad("trailing characters");
+                break;
+            }
+        if (!ok) break;
+        const int nx = v[0], ny = v[1], nz = v[2], K = v[3], W = v[4], H = v[5], dt = v[6];
+        if (nx < 1 || ny < 1 || nz < 1 || nx > (1 << 24) || ny > (1 << 24) || nz > (1 << 24) || K < 1 ||
+            K > PSFS_MAX_CAMS || W < 1 || H < 1 || (dt != PSFS_MAP_F32 && dt != PSFS_MAP_F16 && dt != PSFS_MAP_BF16)) {
+            bad("grid, camera count, image size or map type out of range");
+            break;
+        }
+        Tuned t;
+        t.shape = FuseShape{v[7], v[8], v[9], v[10]};
+        t.seq_lk_ctas = v[11];
+        t.seq_group = v[12];
+        t.seq_own = v[13] != 0;
+        t.seq_shape = FuseShape{v[14], v[15], v[16], v[17]};
+        t.seq_rec = v[18];
+        const int elem = dt == PSFS_MAP_F32 ? 4 : 2;
+        const FuseShape &sshape = t.seq_own ? t.seq_shape : t.shape;
+        if (!fuse_shape_supported(t.shape) || (v[13] != 0 && v[13] != 1) ||
+            (t.seq_own && (!fuse_shape_supported(t.seq_shape) || t.seq_shape.staged != 0)) || t.seq_lk_ctas < 1 ||
+            t.seq_lk_ctas > 4 || (t.seq_rec != 32 && t.seq_rec != 64) ||
+            !(t.seq_group == 1 || group_shape_supported(sshape, t.seq_group, elem, t.seq_rec))) {
+            bad("unsupported configuration");
+            break;
+        }
+        if (!t.seq_own) t.seq_shape = t.shape;
+        add[TuneKey(nx, ny, nz, K, W, H, dt)] = t;
+    }
+    if (ok && std::ferror(fp)) {
+        std::snprintf(msg, sizeof(msg), "tune cache file could not be read");
+        ok = false;
+    }
+    if (ok && lineno == 0) {
+        std::snprintf(msg, sizeof(msg), "tune cache file is empty");
+        ok = false;
+    }
+    std::fclose(fp);
+    if (!ok) return fail(PSFS_ERR_INVALID_ARG, msg);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto &kv : add) g_tuned[kv.first] = kv.second;
+    return PSFS_OK;
+}
+
+void psfs_tune_cache_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+}
+
+int32_t psfs_tune_cache_entries(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (int32_t)g_tuned.size();
+}
+
 psfs_status psfs_sync(psfs_handle *h)
 {
     if (!h) return fail(PSFS_ERR_INVALID_ARG, "handle is NULL");

@@ -131,6 +131,10 @@ def load(build_if_missing: bool = True):
             "psfs_get_fuse_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
             "psfs_autotune": (st, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(psfs_fuse_config),
                                    ctypes.POINTER(ctypes.c_float)]),
+            "psfs_tune_cache_save": (st, [ctypes.c_char_p]),
+            "psfs_tune_cache_load": (st, [ctypes.c_char_p]),
+            "psfs_tune_cache_clear": (None, []),
+            "psfs_tune_cache_entries": (ctypes.c_int32, []),
             "psfs_batch_create": (st, [ctypes.POINTER(psfs_frame), ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
             "psfs_batch_run": (st, [_vp]),
             "psfs_batch_sync": (st, [_vp]),
@@ -522,6 +526,27 @@ def psfs_autotune(h: int, images, reps: int = 5, timings: Optional[dict] = None)
         for c, t in zip(FUSE_CONFIGS, ms):
             timings[c] = float(t)
     return cfg.as_tuple()
+
+
+def psfs_tune_cache_save(path: str):
+    """Writes the autotuner's remembered choices (per grid size, camera
+    count, image size and map type) to a text file."""
+    _check(load().psfs_tune_cache_save(os.fsencode(path)), "psfs_tune_cache_save")
+
+
+def psfs_tune_cache_load(path: str):
+    """Adds the choices of a file written by psfs_tune_cache_save; handles
+    created afterwards start with them.  Raises PsfsError (nothing changed)
+    on an invalid file."""
+    _check(load().psfs_tune_cache_load(os.fsencode(path)), "psfs_tune_cache_load")
+
+
+def psfs_tune_cache_clear():
+    load().psfs_tune_cache_clear()
+
+
+def psfs_tune_cache_entries() -> int:
+    return int(load().psfs_tune_cache_entries())
 
 
 def psfs_batch_create(frames, stream=None) -> int:

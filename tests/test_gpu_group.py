@@ -381,6 +381,29 @@ def test_autotune_picks_a_sequence_configuration():
     rec.close()
 
 
+def test_autotune_cache_file(tmp_path):
+    """The autotuner's choice saved to a file, forgotten, loaded again: a
+    handle created afterwards for the same kind of rig starts with it."""
+    sc = _scene(2)
+    rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    rec.set_background(to_dev(sc.mean), to_dev(sc.var))
+    psfs.psfs_autotune(rec.handle, to_dev(sc.images[0]), reps=1)
+    tuned = psfs.psfs_get_fuse_config(rec.handle, full=True)
+    rec.close()
+    path = str(tmp_path / "tune.txt")
+    psfs.psfs_tune_cache_save(path)
+    psfs.psfs_tune_cache_clear()
+    fresh = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    default = psfs.psfs_get_fuse_config(fresh.handle, full=True)
+    fresh.close()
+    psfs.psfs_tune_cache_load(path)
+    assert psfs.psfs_tune_cache_entries() >= 1
+    again = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
+    assert psfs.psfs_get_fuse_config(again.handle, full=True) == tuned
+    again.close()
+    print("tuned", tuned, "default", default)
+
+
 def test_sequence_with_its_own_tile_shape():
     """A sequence tile shape of its own (seq_lanes_x, seq_voxels_z) while one
     frame per call keeps another shape: both give the same bits."""
