@@ -65,7 +65,9 @@ typedef enum {
     PSFS_ERR_CAPACITY = 3,     /* voxel list overflow: count holds the true count */
     PSFS_ERR_CUDA = 4,         /* a CUDA runtime call failed                      */
     PSFS_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out              */
-    PSFS_ERR_NOMEM = 6         /* device or pinned allocation failed              */
+    PSFS_ERR_NOMEM = 6,        /* device or pinned allocation failed              */
+    PSFS_ERR_BOUNDS = 7        /* bounds-checked build only: a device-side index
+                                  check failed and the access was skipped       */
 } psfs_status;
 
 typedef enum {

@@ -440,6 +440,7 @@ const char *psfs_status_string(psfs_status s)
     case PSFS_ERR_CUDA: return "CUDA error";
     case PSFS_ERR_TIMEOUT: return "device wait timed out";
     case PSFS_ERR_NOMEM: return "out of memory";
+    case PSFS_ERR_BOUNDS: return "bounds check failed";
     }
     return "unknown status";
 }
@@ -1016,6 +1017,7 @@ psfs_status psfs_reproject(psfs_handle *h, int32_t n_frames, const uint32_t *vox
     a.cj = h->fuse.cj;
     a.ck = h->fuse.ck;
     a.n_vox = (uint32_t)((uint64_t)h->grid.nx * h->grid.ny * h->grid.nz);
+    a.status = h->d_words;
     ProfScope ps(h, PSFS_STAGE_REPROJECT);
     PSFS_CK(launch_reproject(a, n_frames, h->stream));
     return PSFS_OK;
@@ -1944,6 +1946,7 @@ psfs_status psfs_sync(psfs_handle *h)
     PSFS_CK(cudaMemsetAsync(h->d_words, 0, sizeof(uint32_t), h->stream));
     PSFS_CK(cudaStreamSynchronize(h->stream));
     const uint32_t w = h->h_words[0];
+    if (w & kStatusBounds) return fail(PSFS_ERR_BOUNDS, "a bounds check failed; the access was skipped");
     if (w & kStatusCapacity) return fail(PSFS_ERR_CAPACITY, "voxel list capacity exceeded");
     if (w & kStatusTimeout) return fail(PSFS_ERR_TIMEOUT, "device wait timed out");
     return PSFS_OK;
@@ -2220,6 +2223,7 @@ psfs_status psfs_batch_sync(psfs_batch *b)
     PSFS_CK(cudaMemsetAsync(b->d_words, 0, sizeof(uint32_t), b->user_stream));
     PSFS_CK(cudaStreamSynchronize(b->user_stream));
     const uint32_t w = b->h_words[0];
+    if (w & kStatusBounds) return fail(PSFS_ERR_BOUNDS, "a bounds check failed; the access was skipped");
     if (w & kStatusTimeout) return fail(PSFS_ERR_TIMEOUT, "a batched work item timed out waiting for its frame");
     if (w & kStatusCapacity) return fail(PSFS_ERR_CAPACITY, "voxel list capacity exceeded");
     return PSFS_OK;

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(32 * WY) backward_voxel_kernel(const __grid_co
         float bu, bv, bw;
         project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
         gather_global<MapT, TZ>(m, bu, bv, bw, tc.fk, maps + (int64_t)c * a.map_stride, W, H,
-                                (flags & kTcInside) != 0, L);
+                                (flags & kTcInside) != 0, L, a.status);
     }
     if (tc.i >= a.nx || tc.j >= a.ny) return;
 #pragma unroll

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchLaunch b)
                     float bu, bv, bw;
                     project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
                     gather_global<MapT, TZ, true>(m, bu, bv, bw, tc.fk, maps + (int64_t)c * a.map_stride, W, H,
-                                                  (flags & kTcInside) != 0, L);
+                                                  (flags & kTcInside) != 0, L, a.status);
                 }
             } else {
                 // camera blocks: the loads of CB cameras are issued together,

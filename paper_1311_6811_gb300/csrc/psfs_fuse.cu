@@ -75,8 +75,10 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
                 const Proj p0 = project_biased(m0, bu0, bv0, bw0, tc.fk[t]);
                 const Proj p1 = project_biased(m1, bu1, bv1, bw1, tc.fk[t]);
                 // the host proved both pixels lie in the image; min() only guards the buffer
-                g0[t] = map_load<MapT>(map0 + min(p0.by * W + p0.bx + bias_off, last_pix));
-                g1[t] = map_load<MapT>(map1 + min(p1.by * W + p1.bx + bias_off, last_pix));
+                g0[t] = PSFS_IN_BOUNDS(proved_inside(p0, W, H), a.status)
+                            ? map_load<MapT>(map0 + min(p0.by * W + p0.bx + bias_off, last_pix)) : 0.0f;
+                g1[t] = PSFS_IN_BOUNDS(proved_inside(p1, W, H), a.status)
+                            ? map_load<MapT>(map1 + min(p1.by * W + p1.bx + bias_off, last_pix)) : 0.0f;
             }
 #pragma unroll
             for (int t = 0; t < TZ; ++t) L[t] = (L[t] + g0[t]) + g1[t];
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(32 * WY) fuse_kernel(const __grid_constant__ F
             float bu, bv, bw;
             project_base(m, tc.fi, tc.fj, &bu, &bv, &bw);
             gather_global<MapT, TZ>(m, bu, bv, bw, tc.fk, maps + (int64_t)c * a.map_stride, W, H,
-                                    (flags & kTcInside) != 0, L);
+                                    (flags & kTcInside) != 0, L, a.status);
         }
         ++c;
     }

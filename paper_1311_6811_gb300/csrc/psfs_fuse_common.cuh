@@ -113,10 +113,19 @@ __device__ __forceinline__ float gather_load(const MapT *p)
     return map_load<MapT>(p);
 }
 
+// The planner's claim for a tile and camera marked inside: the voxel's pixel
+// lies in the image (tested in the bounds-checked build only).
+__device__ __forceinline__ bool proved_inside(const Proj &p, uint32_t W, uint32_t H)
+{
+    return (p.bx - kFloorBias) < W && (p.by - kFloorBias) < H;
+}
+
 template <typename MapT, int TZ, bool kCoherent = false>
 __device__ __forceinline__ void gather_global(const float *m, float bu, float bv, float bw, const float *fk,
-                                              const MapT *map, uint32_t W, uint32_t H, bool inside, float *L)
+                                              const MapT *map, uint32_t W, uint32_t H, bool inside, float *L,
+                                              uint32_t *status = nullptr)
 {
+    (void)status;
     if (inside) {
         const uint32_t last_pix = W * H - 1u;
         // (by - B) W + (bx - B) = by W + bx + bias_off (mod 2^32)
@@ -125,7 +134,8 @@ __device__ __forceinline__ void gather_global(const float *m, float bu, float bv
         for (int t = 0; t < TZ; ++t) {
             const Proj p = project_biased(m, bu, bv, bw, fk[t]);
             // the host proved the pixel lies in the image; min() only guards the buffer
-            L[t] += gather_load<MapT, TZ, kCoherent>(map + min(p.by * W + p.bx + bias_off, last_pix));
+            if (PSFS_IN_BOUNDS(proved_inside(p, W, H), status))
+                L[t] += gather_load<MapT, TZ, kCoherent>(map + min(p.by * W + p.bx + bias_off, last_pix));
         }
     } else {
 #pragma unroll

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(32 * WY) fuse_staged_kernel(const __grid_const
                 }
             } else {
                 gather_global<MapT, TZ>(m, bu, bv, bw, tc.fk, maps + (int64_t)c * a.map_stride, W, H,
-                                        (flags & kTcInside) != 0, L);
+                                        (flags & kTcInside) != 0, L, a.status);
             }
         }
         __syncthreads();   // every thread is done with buffer b

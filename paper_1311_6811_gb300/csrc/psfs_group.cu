@@ -402,6 +402,7 @@ __device__ __forceinline__ void group_gather(const FuseArgs &a, const TileCoords
                 const Proj p = project_biased(m, bu, bv, bw, tc.fk[t]);
                 // the host proved the pixel lies in the image; min() only guards the buffer
                 const uint32_t pix = min(p.by * W + p.bx + bias_off, last_pix);
+                if (!PSFS_IN_BOUNDS(proved_inside(p, W, H), a.status)) continue;
                 Words g;
                 load_words<Words::kWords>(map + (size_t)pix * kRec, g.w);
 #pragma unroll

@@ -32,6 +32,24 @@ namespace psfs {
 constexpr uint32_t kStatusCapacity = 1u;
 constexpr uint32_t kStatusTimeout = 2u;
 constexpr uint32_t kStatusBadValue = 4u;
+constexpr uint32_t kStatusBounds = 8u;   // an access outside its buffer was skipped (bounds-checked build)
+
+// The bounds-checked build (-DPSFS_BOUNDS_CHECK): at the accesses whose index
+// rests on the kernels' own arithmetic or on a host-side proof (a pixel the
+// planner proved inside the image, an owner's voxel index, a silhouette row),
+// the index is tested; a failing access is skipped and kStatusBounds recorded
+// in the status word (psfs_sync then returns PSFS_ERR_BOUNDS).  In the normal
+// build PSFS_IN_BOUNDS is the constant true and compiles to nothing.
+#ifdef PSFS_BOUNDS_CHECK
+__device__ __forceinline__ bool psfs_in_bounds(bool ok, uint32_t *status)
+{
+    if (!ok && status) atomicOr(status, kStatusBounds);
+    return ok;
+}
+#define PSFS_IN_BOUNDS(cond, status) ::psfs::psfs_in_bounds((cond), (status))
+#else
+#define PSFS_IN_BOUNDS(cond, status) true
+#endif
 
 // Projection of voxel index space into one camera: (u, v, w) = M (i', j', k', 1)
 // with i' = i - (nx - 1) / 2 (likewise j', k'), rows u, v, w of 4 floats.
@@ -463,6 +481,7 @@ struct ReprojectArgs {
     int n_cams, W, H, nx, ny, nz;
     float ci, cj, ck;
     uint32_t n_vox;
+    uint32_t *status;   // status word (bounds-checked build)
 };
 cudaError_t launch_reproject(const ReprojectArgs &a, int n_frames, cudaStream_t s);
 

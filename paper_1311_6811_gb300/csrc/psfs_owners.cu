@@ -224,7 +224,16 @@ __global__ void __launch_bounds__(256) owner_pixel_kernel(const __grid_constant_
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < b.n_pix; p += stride) {
-        const uint32_t e0 = __ldg(off + p), e1 = __ldg(off + p + 1);
+        const uint32_t e0 = __ldg(off + p);
+        uint32_t e1 = __ldg(off + p + 1);
+#ifdef PSFS_BOUNDS_CHECK
+        {   // the pixel's segment lies in the lists and names voxels of the grid
+            const uint64_t n_vox = (uint64_t)b.f.nx * b.f.ny * b.f.nz;
+            bool seg_ok = PSFS_IN_BOUNDS(e0 <= e1 && e1 <= __ldg(off + b.n_pix), b.f.status);
+            for (uint32_t e = e0; seg_ok && e < e1; ++e) seg_ok = PSFS_IN_BOUNDS(__ldg(vox + e) < n_vox, b.f.status);
+            if (!seg_ok) e1 = e0;
+        }
+#endif
         float acc = 0.0f;
         // four owners at a time: their index and dL loads are independent,
         // so they are in flight together; the adds stay in ascending order
@@ -287,7 +296,16 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < b.n_pix; p += stride) {
-        const uint32_t e0 = __ldg(off + p), e1 = __ldg(off + p + 1);
+        const uint32_t e0 = __ldg(off + p);
+        uint32_t e1 = __ldg(off + p + 1);
+#ifdef PSFS_BOUNDS_CHECK
+        {   // the pixel's segment lies in the lists and names voxels of the grid
+            const uint64_t n_vox = (uint64_t)b.f.nx * b.f.ny * b.f.nz;
+            bool seg_ok = PSFS_IN_BOUNDS(e0 <= e1 && e1 <= __ldg(off + b.n_pix), b.f.status);
+            for (uint32_t e = e0; seg_ok && e < e1; ++e) seg_ok = PSFS_IN_BOUNDS(__ldg(vox + e) < n_vox, b.f.status);
+            if (!seg_ok) e1 = e0;
+        }
+#endif
         float acc[kBwRecord];
 #pragma unroll
         for (int f = 0; f < kBwRecord; ++f) acc[f] = 0.0f;

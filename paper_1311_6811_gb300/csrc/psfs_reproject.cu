@@ -326,6 +326,9 @@ __global__ void __launch_bounds__(kRpThreads, 4) reproject_kernel(const __grid_c
                 for (int y = P.ya; y <= P.yb; ++y) {
                     int xs, xe;
                     polygon_row(P, y, xs, xe);
+                    if (xs > xe ||
+                        !PSFS_IN_BOUNDS(y >= Y0 && y - Y0 < rh && xs >= X0 && xe - X0 < rw, a.status))
+                        continue;
                     uint8_t *row = st + (y - Y0) * rw - X0;
                     for (int x = xs; x <= xe; ++x) row[x] = 1;
                 }
@@ -343,7 +346,8 @@ __global__ void __launch_bounds__(kRpThreads, 4) reproject_kernel(const __grid_c
             for (int y = P.ya; y <= P.yb; ++y) {
                 int xs, xe;
                 polygon_row(P, y, xs, xe);
-                if (xs <= xe) set_run(mask + (size_t)y * W, xs, xe, words);
+                if (xs <= xe && PSFS_IN_BOUNDS(y >= 0 && y < H && xs >= 0 && xe < W, a.status))
+                    set_run(mask + (size_t)y * W, xs, xe, words);
             }
         }
         if (have && P.n < 3) slab_test_pixels(a, c, P, mask);

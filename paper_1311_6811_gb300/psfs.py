@@ -29,6 +29,7 @@ PSFS_ERR_CAPACITY = 3
 PSFS_ERR_CUDA = 4
 PSFS_ERR_TIMEOUT = 5
 PSFS_ERR_NOMEM = 6
+PSFS_ERR_BOUNDS = 7
 
 PSFS_MAP_F32 = 0
 PSFS_MAP_F16 = 1
@@ -84,7 +85,9 @@ _vp = ctypes.c_void_p
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library this process loads: the bounds-checked build when the
+    environment sets PSFS_BOUNDS_CHECK=1, else the product build."""
+    return _build.BOUNDS_LIB if os.environ.get("PSFS_BOUNDS_CHECK") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -93,11 +96,11 @@ def load(build_if_missing: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        path = lib_path()
         if not os.path.exists(path):
             if not build_if_missing:
                 raise OSError(f"libpsfs.so not built ({path})")
-            _build.build()
+            _build.build(bounds_check=path == _build.BOUNDS_LIB)
         lib = ctypes.CDLL(path)
         st = ctypes.c_int
         sig = {
