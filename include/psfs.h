@@ -438,7 +438,9 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
  * as psfs_reconstruct) with CUDA events, `reps` launches each, keeps the
  * fastest and writes it to *best (may be NULL) and the mean milliseconds of
  * each candidate to candidate_ms[PSFS_N_FUSE_CANDIDATES] (may be NULL; order:
- * staged 0 then 1, lanes_x 8, 16, 32, voxels_z 8 then 16); then times the
+ * staged 0 with lanes_x 8, 16, 32 and voxels_z 2, 4, 8, 16, then staged 1
+ * with lanes_x 8, 16, 32 and voxels_z 8, 16; small grids favour the short
+ * tiles, which give more CTAs); then times the
  * sequence path on 64 frames (32 above 2^23 voxels; copies of the frame at
  * distinct addresses) with 1 to 4 likelihood CTAs per SM at one frame per
  * launch, and frame groups of 2, 4, 8, 16 and 32 frames (direct tile shapes,
@@ -450,7 +452,7 @@ psfs_status psfs_get_fuse_config(psfs_handle *h, psfs_fuse_config *cfg);
  * remembered for handles of the same grid size, camera count, image size and
  * map type created later in the process.  Allocates and frees its own scratch; waits for the stream.
  * Errors: INVALID_ARG, NOT_READY, NOMEM, CUDA. */
-#define PSFS_N_FUSE_CANDIDATES 12
+#define PSFS_N_FUSE_CANDIDATES 18
 psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, psfs_fuse_config *best,
                           float *candidate_ms);
 

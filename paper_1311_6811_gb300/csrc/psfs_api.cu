@@ -1686,12 +1686,21 @@ psfs_status psfs_autotune(psfs_handle *h, const uint8_t *images, int32_t reps, p
     psfs_status st = PSFS_OK;
     FuseShape best_shape = h->shape;
     float best_ms = 1e30f;
-    const int lxs[3] = {8, 16, 32}, tzs[2] = {8, 16};
+    // the candidates, in the order of candidate_ms: direct tiles (lanes_x 8,
+    // 16, 32; voxels_z 2, 4, 8, 16), then staged ones (voxels_z 8, 16)
+    FuseShape cands[PSFS_N_FUSE_CANDIDATES];
+    {
+        int n = 0;
+        for (int lx : {8, 16, 32})
+            for (int tz : {2, 4, 8, 16}) cands[n++] = FuseShape{lx, 4, tz, 0};
+        for (int lx : {8, 16, 32})
+            for (int tz : {8, 16}) cands[n++] = FuseShape{lx, 4, tz, 1};
+    }
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(PSFS_ERR_CUDA, "cudaEventCreate");
     // the maps of this frame, once: only the fuse kernel depends on the shape
     if (st == PSFS_OK) st = enqueue_reconstruct(h, images, occ, list, (uint32_t)n_vox, h->d_words + 3);
-    for (int cand = 0; cand < 12 && st == PSFS_OK; ++cand) {
-            const FuseShape shape = {lxs[(cand / 2) % 3], 4, tzs[cand % 2], cand / 6};
+    for (int cand = 0; cand < PSFS_N_FUSE_CANDIDATES && st == PSFS_OK; ++cand) {
+            const FuseShape shape = cands[cand];
             if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
                 st = fail(PSFS_ERR_CUDA, "autotune sync");
                 break;

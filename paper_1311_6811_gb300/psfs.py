@@ -64,8 +64,9 @@ class psfs_fuse_config(ctypes.Structure):
         return (self.lanes_x, self.warps, self.voxels_z, self.staged)
 
 
-# candidate order of psfs_autotune's timings
-FUSE_CONFIGS = [(lx, 4, tz, st) for st in (0, 1) for lx in (8, 16, 32) for tz in (8, 16)]
+# candidate order of psfs_autotune's timings (PSFS_N_FUSE_CANDIDATES)
+FUSE_CONFIGS = ([(lx, 4, tz, 0) for lx in (8, 16, 32) for tz in (2, 4, 8, 16)] +
+                [(lx, 4, tz, 1) for lx in (8, 16, 32) for tz in (8, 16)])
 
 
 class psfs_frame(ctypes.Structure):
