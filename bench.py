@@ -1103,13 +1103,18 @@ def time_configs(args, dev, psfs, pending):
     for rec, _ in recs:
         rec.close()
     ach = alg / (ms * 1e-3) / 1e9
+    frame_launch = len(best) > 5 and best[5] == 1
     out["c4"] = {"workload": "64 frames, grids from {96,128,160,192}^3, 4-12 cams, 640x480 or 960x540, own pose and "
-                             "background each, FP32, one persistent kernel per psfs_batch_run (CUDA graph)",
+                             "background each, FP32, one psfs_batch_run (CUDA graph) per step: "
+                             + ("each frame's likelihood and fusion launches, frames alternating between two "
+                                "streams" if frame_launch else "one persistent kernel over all frames"),
+                 "launch": "per-frame launches" if frame_launch else "persistent kernel",
                  "ms_per_launch": ms, "ms_per_frame": ms / len(scenes), "frames_per_s": len(scenes) / (ms * 1e-3),
                  "gvox_cam_per_s": evals / (ms * 1e-3) / 1e9, "voxel_camera_evals": evals,
                  "timing": "CUDA events around back-to-back graph launches; inputs (GBs) larger than L2",
                  "tile": list(best), "autotune_ms": {"x".join(map(str, k)): round(v, 3) for k, v in tune.items()},
-                 "roofline": {"bound": "hbm", "kernel": "batch_kernel", "alg_bytes_per_launch": alg, "achieved": ach,
+                 "roofline": {"bound": "hbm", "kernel": "fuse_kernel + likelihood_kernel" if frame_launch else "batch_kernel",
+                              "alg_bytes_per_launch": alg, "achieved": ach,
                               "peak": peak, "unit": "GB/s", "frac": ach / peak},
                  "err_vs_fp64_frames": [0, 37]}
     del flush

@@ -134,6 +134,14 @@ typedef struct {
  * adds them, still camera by camera in the order 0 .. n_cams - 1, so the
  * results do not change; 1, 2 (lanes_x 8 or 16, voxels_z 4 or 8) or 4
  * (lanes_x 8 or 16, voxels_z 4); 0 in psfs_batch_set_config means 1.
+ * batch_launch (batch entry points only): 0 = one persistent kernel whose
+ * work list interleaves the frames' likelihood chunks and fusion tiles (the
+ * tile shape and camera block above apply); 1 = a graph of each frame's own
+ * likelihood and fusion launches (the kernels of psfs_reconstruct, each
+ * frame with its handle's one-frame tile shape, a direct one if that is
+ * staged), frame f on stream f mod 4, so that frames' likelihoods run
+ * beside earlier frames' fusions and small frames share the GPU.  Results
+ * are the same bits either way.
  * seq_lanes_x, seq_voxels_z: the tile shape of the sequence path (warps 4,
  * staged 0) when it differs from the one-frame-per-call shape above: 0 in
  * psfs_set_fuse_config makes the sequence path use lanes_x / voxels_z;
@@ -156,6 +164,7 @@ typedef struct {
     int32_t seq_lanes_x;
     int32_t seq_voxels_z;
     int32_t seq_record_bytes;
+    int32_t batch_launch;
 } psfs_fuse_config;
 
 typedef struct psfs_handle psfs_handle;
@@ -543,20 +552,22 @@ psfs_status psfs_batch_create(const psfs_frame *frames, int32_t n_frames, void *
 psfs_status psfs_batch_run(psfs_batch *b);
 
 /* Waits for the batch's stream; returns and clears the first device-side
- * problem (PSFS_ERR_TIMEOUT, PSFS_ERR_CAPACITY) or PSFS_OK. */
+ * problem (PSFS_ERR_TIMEOUT, PSFS_ERR_CAPACITY, PSFS_ERR_BOUNDS) or PSFS_OK. */
 psfs_status psfs_batch_sync(psfs_batch *b);
 
-/* Tile shape of the batch's fusion items (staged must be 0); re-plans and
- * re-captures. */
+/* The batch's launch form (batch_launch) and, for the persistent kernel, the
+ * tile shape of its fusion items (staged must be 0) and camera block;
+ * re-plans and re-captures. */
 psfs_status psfs_batch_set_config(psfs_batch *b, const psfs_fuse_config *cfg);
 
 /* Autotuner of the batch: times the whole graph for each of
- * PSFS_N_BATCH_CANDIDATES tile shapes and camera blocks (candidate order:
- * lanes_x 8, 16, 32 x voxels_z 8, 16 with one camera per load block; then
+ * PSFS_N_BATCH_CANDIDATES candidates (order: the persistent kernel with
+ * lanes_x 8, 16, 32 x voxels_z 8, 16 and one camera per load block; then
  * camera blocks of 2 with lanes_x 8, 16 x voxels_z 4, 8; then camera blocks
- * of 4 with lanes_x 8, 16 and voxels_z 4; times in candidate_ms if not
- * NULL), keeps the fastest. */
-#define PSFS_N_BATCH_CANDIDATES 12
+ * of 4 with lanes_x 8, 16 and voxels_z 4; last the graph of per-frame
+ * launches; times in candidate_ms if not NULL), keeps the fastest and
+ * reports it in *best (batch_launch 1 for the last candidate). */
+#define PSFS_N_BATCH_CANDIDATES 13
 psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *best, float *candidate_ms);
 
 /* Failure detection of the batched launch.  A fusion item waits for every
@@ -567,8 +578,9 @@ psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *b
  * sets that limit (1 us to 10 s) and, for tests of the timeout path only,
  * `hold_frame`: a frame whose items then wait for one chunk more than the
  * frame has, so that their wait must run out (-1: none; the results of a
- * launch with a held frame are invalid).  Re-plans and re-captures the graph.
- * Errors: INVALID_ARG, CUDA, NOMEM. */
+ * launch with a held frame are invalid).  Re-plans and re-captures the graph
+ * as the persistent kernel (the per-frame launch graph has no device-side
+ * waits).  Errors: INVALID_ARG, CUDA, NOMEM. */
 psfs_status psfs_batch_set_wait_limit(psfs_batch *b, uint64_t limit_ns, int32_t hold_frame);
 
 void psfs_batch_destroy(psfs_batch *b);

@@ -23,6 +23,8 @@ using namespace psfs;
 constexpr int kIoSlots = 3;
 // Candidates of psfs_batch_autotune.
 constexpr int kBatchCandidates = PSFS_N_BATCH_CANDIDATES;
+// Streams of the batch's graph of per-frame launches.
+constexpr int kBatchStreams = 4;
 
 
 struct psfs_handle {
@@ -2013,7 +2015,11 @@ struct psfs_batch {
     int device = 0;
     cudaStream_t user_stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // the other streams of the frame-launch graph, and its fork and join events
+    cudaStream_t cap_more[kBatchStreams - 1] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kBatchStreams - 1] = {};
     int map_dtype = PSFS_MAP_F32;
+    int launch = 0;               // 0: one persistent kernel; 1: a graph of per-frame launches
     std::vector<psfs_frame> frames;
     FuseShape shape = kDefaultFuseShape;
     BatchFrame *d_frames = nullptr;
@@ -2063,6 +2069,11 @@ void batch_free(psfs_batch *b)
     cudaFree(b->d_words);
     cudaFreeHost(b->h_words);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int k = 0; k < kBatchStreams - 1; ++k) {
+        if (b->cap_more[k]) cudaStreamDestroy(b->cap_more[k]);
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     cudaSetDevice(prev);
     delete b;
 }
@@ -2159,6 +2170,88 @@ psfs_status batch_build(psfs_batch *b, const FuseShape &shape)
     b->graph = g;
     PSFS_CK(cudaGraphInstantiate(&b->exec, g, 0));
     b->shape = shape;
+    b->launch = 0;
+    return PSFS_OK;
+}
+
+// The other launch form: a graph of each frame's own likelihood and fusion
+// launches (the kernels of psfs_reconstruct, each frame with its handle's
+// one-frame tile shape, a direct one when that is staged, planned here so
+// that later changes to the handles leave the graph valid), frame f on
+// stream f mod kBatchStreams, so that frames' likelihoods run beside earlier
+// frames' fusions and small frames share the GPU.  No device-side waits: the
+// streams order each frame's two stages.
+psfs_status batch_build_frames(psfs_batch *b)
+{
+    batch_free_plan(b);
+    const int F = (int)b->frames.size();
+    std::vector<FuseArgs> fas(F);
+    std::vector<FuseShape> shapes(F);
+    for (int f = 0; f < F; ++f) {
+        const psfs_frame &fr = b->frames[f];
+        psfs_handle *h = fr.handle;
+        shapes[f] = h->shape.staged ? kDefaultFuseShape : h->shape;
+        std::vector<uint64_t> tiles;
+        std::vector<int4> tilecam;
+        FuseArgs &fa = fas[f];
+        plan_fuse(h->grid, h->cams.data(), h->n_cams, h->params, shapes[f], &fa, &tiles, &tilecam);
+        uint64_t *dt = nullptr;
+        int4 *dtc = nullptr;
+        if (cudaMalloc(&dt, std::max<size_t>(1, tiles.size()) * sizeof(uint64_t)) != cudaSuccess ||
+            cudaMalloc(&dtc, std::max<size_t>(1, tilecam.size()) * sizeof(int4)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(dt);
+            return fail(PSFS_ERR_NOMEM, "batch plan allocation");
+        }
+        b->tiles.push_back(dt);
+        b->tilecam.push_back(dtc);
+        PSFS_CK(cudaMemcpy(dt, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+        PSFS_CK(cudaMemcpy(dtc, tilecam.data(), tilecam.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        fa.maps = b->maps[f];
+        fa.tmap_ok = 0;
+        fa.tiles = dt;
+        fa.tilecam = dtc;
+        fa.occ = fr.occupancy;
+        fa.list = fr.voxel_list;
+        fa.capacity = fr.capacity;
+        fa.count = fr.count;
+        fa.status = b->d_words;
+    }
+    PSFS_CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(b->ev_fork, b->cap_stream);
+    for (int k = 0; k < kBatchStreams - 1 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->cap_more[k], b->ev_fork, 0);
+    for (int f = 0; f < F && e == cudaSuccess; ++f) {
+        const psfs_frame &fr = b->frames[f];
+        psfs_handle *h = fr.handle;
+        const int k = f % kBatchStreams;
+        cudaStream_t s = k == 0 ? b->cap_stream : b->cap_more[k - 1];
+        LikelihoodArgs la{};
+        la.img = fr.images;
+        la.mean = h->bg_mean;
+        la.hinv = h->bg_hinv;
+        la.n_pix = h->n_pix;
+        la.c0 = h->c0;
+        la.sc = h->sc;
+        la.out = b->maps[f];
+        la.zero_word = fr.count;
+        la.status = b->d_words;
+        e = launch_likelihood(la, b->map_dtype, false, s);
+        if (e == cudaSuccess) e = launch_fuse(fas[f], shapes[f], b->map_dtype, s);
+    }
+    for (int k = 0; k < kBatchStreams - 1 && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->ev_join[k], b->cap_more[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap_stream, b->ev_join[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail_cuda(e, "batch frame-launch capture");
+    }
+    if (e2 != cudaSuccess) return fail_cuda(e2, "cudaStreamEndCapture");
+    b->graph = g;
+    PSFS_CK(cudaGraphInstantiate(&b->exec, g, 0));
+    b->launch = 1;
     return PSFS_OK;
 }
 
@@ -2190,6 +2283,7 @@ psfs_status psfs_batch_create(const psfs_frame *frames, int32_t n_frames, void *
     b->frames.assign(frames, frames + n_frames);
     DeviceGuard guard(b->device);
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&b->d_words, sizeof(uint32_t) * (16 + (size_t)n_frames)) != cudaSuccess ||
         cudaMallocHost(&b->h_words, sizeof(uint32_t) * 16) != cudaSuccess) {
         cudaGetLastError();
@@ -2197,6 +2291,14 @@ psfs_status psfs_batch_create(const psfs_frame *frames, int32_t n_frames, void *
         return fail(PSFS_ERR_NOMEM, "batch allocation");
     }
     cudaMemset(b->d_words, 0, sizeof(uint32_t) * (16 + (size_t)n_frames));
+    for (int k = 0; k < kBatchStreams - 1; ++k) {
+        if (cudaStreamCreateWithFlags(&b->cap_more[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            batch_free(b);
+            return fail(PSFS_ERR_CUDA, "batch streams");
+        }
+    }
     const size_t elem = dtype == PSFS_MAP_F32 ? 4 : 2;
     for (int f = 0; f < n_frames; ++f) {
         void *m = nullptr;
@@ -2241,6 +2343,12 @@ psfs_status psfs_batch_sync(psfs_batch *b)
 psfs_status psfs_batch_set_config(psfs_batch *b, const psfs_fuse_config *cfg)
 {
     if (!b || !cfg) return fail(PSFS_ERR_INVALID_ARG, "NULL argument");
+    if (cfg->batch_launch != 0 && cfg->batch_launch != 1) return fail(PSFS_ERR_INVALID_ARG, "batch_launch: 0 or 1");
+    if (cfg->batch_launch == 1) {
+        DeviceGuard guard(b->device);
+        PSFS_CK(cudaStreamSynchronize(b->user_stream));
+        return batch_build_frames(b);
+    }
     const FuseShape shape = {cfg->lanes_x, cfg->warps, cfg->voxels_z, 0};
     const int cb = cfg->cameras_per_block > 0 ? cfg->cameras_per_block : 1;
     if (cfg->staged != 0 || !batch_shape_supported(shape, cb))
@@ -2268,13 +2376,13 @@ psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *b
     struct Cand {
         int lx, tz, cb;
     };
-    const Cand cands[kBatchCandidates] = {{8, 8, 1},  {8, 16, 1}, {16, 8, 1}, {16, 16, 1}, {32, 8, 1}, {32, 16, 1},
-                                          {8, 4, 2},  {8, 8, 2},  {16, 4, 2}, {16, 8, 2},  {8, 4, 4},  {16, 4, 4}};
+    const Cand cands[kBatchCandidates - 1] = {{8, 8, 1}, {8, 16, 1}, {16, 8, 1}, {16, 16, 1}, {32, 8, 1}, {32, 16, 1},
+                                              {8, 4, 2}, {8, 8, 2},  {16, 4, 2}, {16, 8, 2},  {8, 4, 4},  {16, 4, 4}};
     FuseShape best_shape = b->shape;
     int best_cb = b->cam_block;
     float best_ms = 1e30f;
     psfs_status st = PSFS_OK;
-    for (int cand = 0; cand < kBatchCandidates && st == PSFS_OK; ++cand) {
+    for (int cand = 0; cand < kBatchCandidates - 1 && st == PSFS_OK; ++cand) {
         const FuseShape shape = {cands[cand].lx, 4, cands[cand].tz, 0};
         if (cudaStreamSynchronize(b->user_stream) != cudaSuccess) {
             st = fail(PSFS_ERR_CUDA, "batch autotune sync");
@@ -2301,11 +2409,30 @@ psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *b
             best_cb = cands[cand].cb;
         }
     }
+    // the last candidate: the graph of per-frame launches
+    bool frames_win = false;
+    if (st == PSFS_OK && cudaStreamSynchronize(b->user_stream) != cudaSuccess) st = fail(PSFS_ERR_CUDA, "batch autotune sync");
+    if (st == PSFS_OK) st = batch_build_frames(b);
+    if (st == PSFS_OK) {
+        cudaError_t err = cudaGraphLaunch(b->exec, b->user_stream);   // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(e0, b->user_stream);
+        for (int r = 0; r < reps && err == cudaSuccess; ++r) err = cudaGraphLaunch(b->exec, b->user_stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, b->user_stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) {
+            st = fail_cuda(err, "batch autotune timing");
+        } else {
+            if (candidate_ms) candidate_ms[kBatchCandidates - 1] = ms / (float)reps;
+            frames_win = ms < best_ms;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->cam_block = best_cb;
     if (st != PSFS_OK) return st;
-    st = batch_build(b, best_shape);
+    st = frames_win ? PSFS_OK : batch_build(b, best_shape);   // the frame-launch graph is built already
     if (st != PSFS_OK) return st;
     cudaMemsetAsync(b->d_words, 0, sizeof(uint32_t), b->user_stream);
     if (best) {
@@ -2316,6 +2443,7 @@ psfs_status psfs_batch_autotune(psfs_batch *b, int32_t reps, psfs_fuse_config *b
         best->seq_likelihood_ctas = 0;
         best->frames_per_group = 0;
         best->cameras_per_block = best_cb;
+        best->batch_launch = frames_win ? 1 : 0;
     }
     return PSFS_OK;
 }

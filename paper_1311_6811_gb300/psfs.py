@@ -58,7 +58,7 @@ class psfs_fuse_config(ctypes.Structure):
                 ("staged", ctypes.c_int32), ("seq_likelihood_ctas", ctypes.c_int32),
                 ("frames_per_group", ctypes.c_int32), ("cameras_per_block", ctypes.c_int32),
                 ("seq_lanes_x", ctypes.c_int32), ("seq_voxels_z", ctypes.c_int32),
-                ("seq_record_bytes", ctypes.c_int32)]
+                ("seq_record_bytes", ctypes.c_int32), ("batch_launch", ctypes.c_int32)]
 
     def as_tuple(self):
         return (self.lanes_x, self.warps, self.voxels_z, self.staged)
@@ -588,27 +588,36 @@ def psfs_batch_sync(b: int) -> int:
     return st
 
 
-# candidate order of psfs_batch_autotune: (lanes_x, warps, voxels_z, staged, cameras_per_block)
-BATCH_CONFIGS = ([(lx, 4, tz, 0, 1) for lx in (8, 16, 32) for tz in (8, 16)] +
-                 [(lx, 4, tz, 0, 2) for lx in (8, 16) for tz in (4, 8)] +
-                 [(lx, 4, 4, 0, 4) for lx in (8, 16)])
+# candidate order of psfs_batch_autotune: (lanes_x, warps, voxels_z, staged,
+# cameras_per_block, batch_launch); the last one is the graph of per-frame
+# launches, whose tile shapes are each frame handle's own
+FRAME_LAUNCH = (0, 0, 0, 0, 0, 1)
+BATCH_CONFIGS = ([(lx, 4, tz, 0, 1, 0) for lx in (8, 16, 32) for tz in (8, 16)] +
+                 [(lx, 4, tz, 0, 2, 0) for lx in (8, 16) for tz in (4, 8)] +
+                 [(lx, 4, 4, 0, 4, 0) for lx in (8, 16)] + [FRAME_LAUNCH])
 
 
-def psfs_batch_set_config(b: int, lanes_x: int, warps: int, voxels_z: int, cameras_per_block: int = 1):
+def psfs_batch_set_config(b: int, lanes_x: int, warps: int, voxels_z: int, cameras_per_block: int = 1,
+                          launch: int = 0):
+    """The persistent kernel's tile shape and camera block (launch 0), or the
+    graph of per-frame launches (launch 1; the shape is then not used)."""
     cfg = psfs_fuse_config(lanes_x, warps, voxels_z, 0, 0, 0, cameras_per_block)
+    cfg.batch_launch = int(launch)
     _check(load().psfs_batch_set_config(b, ctypes.byref(cfg)), "psfs_batch_set_config")
 
 
 def psfs_batch_autotune(b: int, reps: int = 3, timings: Optional[dict] = None) -> tuple:
-    """Times every batch candidate; returns the chosen (lanes_x, warps,
-    voxels_z, staged, cameras_per_block)."""
+    """Times every batch candidate; returns the chosen one as in
+    BATCH_CONFIGS."""
     cfg = psfs_fuse_config()
     ms = (ctypes.c_float * len(BATCH_CONFIGS))()
     _check(load().psfs_batch_autotune(b, int(reps), ctypes.byref(cfg), ms), "psfs_batch_autotune")
     if timings is not None:
         for c, t in zip(BATCH_CONFIGS, ms):
             timings[c] = float(t)
-    return cfg.as_tuple() + (cfg.cameras_per_block,)
+    if cfg.batch_launch == 1:
+        return FRAME_LAUNCH
+    return cfg.as_tuple() + (cfg.cameras_per_block, 0)
 
 
 def psfs_batch_set_wait_limit(b: int, limit_ns: int, hold_frame: int = -1):

@@ -81,7 +81,7 @@ def test_batch_equals_frame_by_frame_and_oracle():
         np.testing.assert_array_equal(_host(o)[0], g[0])
     # every tile shape, and the autotuner's pick, give the same bits
     for cfg in psfs.BATCH_CONFIGS:
-        psfs.psfs_batch_set_config(b, *cfg[:3], cameras_per_block=cfg[4])
+        psfs.psfs_batch_set_config(b, *cfg[:3], cameras_per_block=cfg[4], launch=cfg[5])
         psfs.psfs_batch_run(b)
         assert psfs.psfs_batch_sync(b) == psfs.PSFS_OK
         for o, g in zip(outs, got):
