@@ -5,24 +5,27 @@
 // camera centre through the pixel centre meets, in front of the camera, the
 // cube of a listed voxel.
 //
-// One thread per (camera, listed voxel), with the forward kernels' matrices.
-// When all eight cube corners lie in front of the camera, a centre ray meets
-// the cube iff the pixel centre lies in the cube's projection: a convex
-// polygon whose vertices are the projections of the cube's silhouette loop
-// (the corners between faces turned towards the camera and faces turned
-// away).  Which corners form that loop, and in which cyclic order, depends
-// only on where the camera centre lies relative to the cube's three slabs
-// (below, within or above each: 26 cases outside the cube), so a table made
-// once on the host gives the 4 or 6 corners to project.  A row of pixel
-// centres meets the polygon in one interval whose ends are the row's
-// crossings with its edges; the interval's pixels are set with 4-byte stores
-// where whole aligned words are covered.  Otherwise (a corner not in front,
-// or a projection too large for float32 rows) the pixels whose centres can
-// fall inside the projection's bounding box are tested with a float32 slab
-// test of their centre rays in voxel-index coordinates.  A hit stores 1 (every writer stores the same value, so no
-// atomics are needed).  Run on the surface list, the work is proportional to
-// the body's surface; the silhouette of a solid equals that of its surface
-// voxels.
+// One thread per (camera, listed voxel), with the forward kernels' matrices;
+// a CTA takes chunks of 256 consecutive listed voxels of one camera.  When
+// all eight cube corners lie in front of the camera, a centre ray meets the
+// cube iff the pixel centre lies in the cube's projection: a convex polygon
+// whose vertices are the projections of the cube's silhouette loop (the
+// corners between faces turned towards the camera and faces turned away).
+// Which corners form that loop, and in which cyclic order, depends only on
+// where the camera centre lies relative to the cube's three slabs (below,
+// within or above each: 26 cases outside the cube), so a table made once on
+// the host gives the 4 or 6 corners to project.  A row of pixel centres
+// meets the polygon in one interval whose ends are the row's crossings with
+// its edges.  The chunk's intervals are set in shared memory when the union
+// of their boxes fits the stage, and each non-zero 4-byte word of the stage
+// is then OR-ed into the mask once; otherwise each interval is stored
+// directly (4-byte stores where whole aligned words are covered).  Cubes not
+// wholly in front of the camera, and projections too large for float32 rows,
+// take a float32 slab test of the centre ray of every pixel whose centre can
+// fall inside the projection's bounding box.  Every writer writes 1, so no
+// value is lost between writers.  Run on the surface list, the work is
+// proportional to the body's surface; the silhouette of a solid equals that
+// of its surface voxels.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -44,9 +47,10 @@ struct SilTable {
     uint32_t e[27];
 };
 
-// Projects the unit cube's corners from a point of each region (2, 0.5 or -1
-// voxel beyond the faces) along the view towards the cube's centre and keeps
-// the convex hull of the projections (Andrew's monotone chain), in order.
+// Projects the unit cube's corners from a point of each region (along each
+// axis 3 cube sizes below the lower face, at the centre, or 3 above the
+// upper face) along the view towards the cube's centre and keeps the convex
+// hull of the projections (Andrew's monotone chain), in order.
 SilTable make_sil_table()
 {
     SilTable t{};
