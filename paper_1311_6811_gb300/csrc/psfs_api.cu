@@ -871,12 +871,14 @@ psfs_status psfs_reconstruct_sequence_host(psfs_handle *h, int32_t n_frames, con
     if (n_vox % 4 != 0) return fail(PSFS_ERR_INVALID_ARG, "voxel count not a multiple of 4");
     if (!h->bg_ready) return fail(PSFS_ERR_NOT_READY, "psfs_set_background has not succeeded");
     DeviceGuard guard(h->device);
-    // chunks of 8 frames per slot: the copies of one chunk overlap the
+    // chunks of 4 frames per slot: the copies of one chunk overlap the
     // kernels of the next.  The host link (about 200 GB/s each way) is slower
-    // than the kernels by several times, so short chunks, which shorten the
-    // first copy in and the last copy out that nothing overlaps, beat the
-    // larger frame groups that longer chunks would allow.
-    const int chunk = std::min<int>(n_frames, 8);
+    // than the kernels by several times, so the chunk size is set by the
+    // copies: at 128^3 x 8 x 640 x 480 chunks of 4 frames took 5.49 ms per
+    // 100 frames with the grids copied out, against 5.52-5.57 for 3, 5 or 6
+    // frames, 5.66 for 8 and 6.45 for 1 (the counts and lists alone: 3.66
+    // ms for 4 or 8 frames).
+    const int chunk = std::min<int>(n_frames, 4);
     psfs_status st = io_setup(h, chunk, capacity);
     if (st != PSFS_OK) return st;
     const size_t frame_bytes = (size_t)h->n_pix * 3;

@@ -434,8 +434,9 @@ def test_sequence_with_its_own_tile_shape():
 @pytest.mark.parametrize("pinned", [True, False])
 def test_sequence_host_equals_device(pinned):
     """psfs_reconstruct_sequence_host (copies in and out overlapping the
-    kernels, three staging slots of 8 frames reused across 9 chunks) gives
-    the device sequence's occupancy, counts and voxel sets."""
+    kernels, three staging slots of 4 frames reused across 18 chunks, the
+    last of 2 frames) gives the device sequence's occupancy, counts and
+    voxel sets."""
     n = 70
     sc = _scene(n)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
