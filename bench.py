@@ -1231,7 +1231,7 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
                         gpu_outputs[f][dtype] = host_frame(occ_s, lst_s, cnt_s, f, cap_s)
         # batched forward + adjoint: the sequence forward, the loss gradient
         # against the FP32 occupancy, psfs_backward_sequence (owner passes of
-        # 8 frames; d_slm per frame, d_mean and d_var summed over the frames)
+        # 16 frames; d_slm per frame, d_mean and d_var summed over the frames)
         d_occ_s = torch.empty((nseq, V), dtype=torch.float32, device=dev)
         d_slm_s = torch.empty((nseq, n_pix), dtype=torch.float32, device=dev)
         with torch.cuda.stream(stream):
@@ -1281,7 +1281,7 @@ def time_forms(args, sc, d_images, occ_f32, dev, psfs, fuse_cfg, gpu_outputs=Non
                    "recomputed maps + voxel pass + per-pixel owner pass + chain rule to SLM, mean, var.  "
                    "*_batched_forward_us: psfs_reconstruct_sequence over 32 frames in frame groups; "
                    "*_batched_forward_backward_us: that forward + loss gradient + psfs_backward_sequence "
-                   "(recomputed forward in groups of 8 frames, owner passes of 8 frames); "
+                   "(recomputed forward in parts of up to 8 frames, owner passes of 16 frames); "
                    "*_from_occupancy_us: the adjoint from the forward's own occupancy (psfs_backward_from_occupancy)")
     return out
 

@@ -227,7 +227,7 @@ psfs_status psfs_reconstruct_sequence(psfs_handle *h, int32_t n_frames, const ui
  * h_occupancy + f * (nx * ny * nz) (h_occupancy may be NULL: no occupancy
  * copy), h_counts[f] and the first min(h_counts[f], capacity) entries of
  * h_lists + f * capacity.  Frames go through three device staging slots of
- * 8 frames each (allocated on first use, grown on demand): the copy in of
+ * 4 frames each (allocated on first use, grown on demand): the copy in of
  * one slot and the copy out of another overlap the kernels of the third.  Pinned
  * host buffers (cudaHostAlloc / cudaHostRegister) let the copies run
  * asynchronously; pageable ones work but serialise them.  Returns after the
@@ -396,17 +396,19 @@ psfs_status psfs_backward(psfs_handle *h, const uint8_t *images, const float *d_
  * (device, 16-byte aligned), and writes d_slm + f * (n_cams * height * width)
  * (may be NULL).  d_mean and d_var (may be NULL) receive the sum over the
  * frames of each frame's gradient, added in frame order (the background model
- * is shared by the frames).  Frames go in groups of up to 8: per group the
- * recomputed forward reads the background once for up to 8 frames and
- * gathers each voxel's log ratios of those frames with one load per camera,
- * dLoss/dL goes into 32-byte per-voxel records of the group's frames, and
- * one per-pixel owner pass reads one record per owned voxel for the whole
- * group.  The records alternate between two buffers, so that one group's
+ * is shared by the frames).  Frames go in groups of up to 16, each in one or
+ * two parts of up to 8: per part the recomputed forward reads the background
+ * once for up to 8 frames and gathers each voxel's log ratios of those frames
+ * with one load per camera, and dLoss/dL goes into 32-byte per-voxel records
+ * of the part's frames; one per-pixel owner pass then reads one record per
+ * part and owned voxel for the whole group, so the owner lists, background
+ * and d_mean / d_var are read once per 16 frames.  The records alternate
+ * between two buffers, so that one group's
  * recomputed forward (one stream) overlaps the previous group's owner pass (a
  * second stream); the call is ordered after earlier work on the handle's
  * stream and later work waits for it.  Each frame's d_slm is bit-identical
  * to psfs_backward's; d_mean and d_var equal the FP32 sum, in frame order, of
- * psfs_backward's.  Scratch (first call): 2 * 8 * nx * ny * nz floats, maps
+ * psfs_backward's.  Scratch (first call): 2 * 16 * nx * ny * nz floats, maps
  * of 8 frames, a tile plan, the sequence streams, and the owner lists of
  * psfs_backward.  Requirements as psfs_reconstruct_sequence (frame size and
  * voxel count multiples of 16 and 4).  Errors: INVALID_ARG, NOT_READY, NOMEM,

@@ -109,7 +109,7 @@ struct psfs_handle {
 
     // adjoint scratch (allocated on first use)
     float *dl = nullptr;        // [n_vox] dLoss / dlogodds
-    float *dl_rec = nullptr;    // [n_vox][kBwRecord] the same for psfs_backward_sequence
+    float *dl_rec = nullptr;    // [2][n_vox][kBwRecord] the same for psfs_backward_sequence
     float *dl_rec2 = nullptr;   // its second buffer: group g's records in buffer g & 1
     // owner lists of the pixel pass (built by the first adjoint call): pixel
     // p owns own_vox[own_off[p] .. own_off[p + 1])
@@ -1336,12 +1336,17 @@ constexpr FuseShape kBwShape = {8, 4, 4, 0};
 
 // The two dLoss/dL record buffers of the batched adjoint (group g in buffer
 // g & 1) and the sequence streams it pipelines on.
+// Frames per owner pass of the batched adjoint: two planes of kBwRecord-frame
+// records, so that the owner lists, the background and d_mean / d_var are
+// read once per 16 frames.
+constexpr int kBwGroup = 2 * kBwRecord;
+
 static psfs_status ensure_dl_records(psfs_handle *h)
 {
     const uint64_t n_vox = (uint64_t)h->grid.nx * h->grid.ny * h->grid.nz;
     for (float **buf : {&h->dl_rec, &h->dl_rec2}) {
         if (*buf) continue;
-        if (cudaMalloc(buf, (size_t)kBwRecord * n_vox * sizeof(float)) != cudaSuccess) {
+        if (cudaMalloc(buf, (size_t)kBwGroup * n_vox * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return fail(PSFS_ERR_NOMEM, "adjoint sequence scratch");
         }
@@ -1386,13 +1391,15 @@ static psfs_status ensure_backward_group(psfs_handle *h)
     return PSFS_OK;
 }
 
-// Frames in groups of kBwRecord.  A group of nf frames runs in units of 8, 4,
-// 2 and 1 frames (the binary digits of nf, largest first, so that a unit of
-// P frames starts at a record slot that is a multiple of P): per unit one
-// likelihood pass over the background for its P frames (maps as one plane
-// of P-frame records) and one voxel pass that gathers each record once per
-// (voxel, camera) and writes dLoss/dL of the P frames into their slots; then
-// one pixel pass for the group.  The record buffers alternate between groups,
+// Frames in groups of kBwGroup = 16: frames 0-7 of a group fill the first
+// plane of 8-frame records, frames 8-15 the second.  A plane of nf frames runs
+// in units of 8, 4, 2 and 1 frames (the binary digits of nf, largest first,
+// so that a unit of P frames starts at a record slot that is a multiple of
+// P): per unit one likelihood pass over the background for its P frames
+// (maps as one plane of P-frame records) and one voxel pass that gathers each
+// map record once per (voxel, camera) and writes dLoss/dL of the P frames
+// into their slots; then one pixel pass for the group's 16 frames.  The
+// record buffers alternate between groups,
 // so a group's likelihood and voxel passes (stream 0) overlap the previous
 // group's pixel pass (stream 1).  Per frame the arithmetic is that of
 // psfs_backward, so d_slm is bit-identical to it.
@@ -1417,44 +1424,47 @@ static psfs_status enqueue_backward_sequence(psfs_handle *h, int32_t n_frames, c
     PSFS_CK(cudaEventRecord(h->seq_ev_in, h->stream));
     PSFS_CK(cudaStreamWaitEvent(sa, h->seq_ev_in, 0));
     PSFS_CK(cudaStreamWaitEvent(sb, h->seq_ev_in, 0));
-    for (int g = 0, g0 = 0; g0 < n_frames; ++g, g0 += kBwRecord) {
-        const int nf = std::min(kBwRecord, n_frames - g0);
+    for (int g = 0, g0 = 0; g0 < n_frames; ++g, g0 += kBwGroup) {
+        const int nf = std::min(kBwGroup, n_frames - g0);
         const int q = g & 1;
         if (g >= 2) PSFS_CK(cudaStreamWaitEvent(sa, h->seq_ev_fused[q], 0));   // group g - 2's pixel pass is done with it
-        for (int slot = 0, P = kBwRecord; P >= 1; P /= 2) {
-            if (!(nf & P)) continue;
-            const size_t f0 = (size_t)g0 + slot;   // the unit's first frame
-            LikelihoodArgs la{};
-            la.img = images + f0 * frame_bytes;
-            la.mean = h->bg_mean;
-            la.hinv = h->bg_hinv;
-            la.n_pix = h->n_pix;
-            la.c0 = h->c0;
-            la.sc = h->sc;
-            la.out = h->bw_maps;
-            la.zero_word = nullptr;
-            la.status = h->d_words;
-            la.img_fstride = (int64_t)frame_bytes;
-            {
-                ProfScope ps(h, PSFS_STAGE_LIKELIHOOD, sa);
-                if (P > 1)
-                    PSFS_CK(launch_likelihood_group(la, P, h->params.map_dtype, sa, 4));
-                else
-                    PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, sa));
+        for (int r = 0; r * kBwRecord < nf; ++r) {
+            const int nr = std::min(kBwRecord, nf - r * kBwRecord);   // frames of record plane r
+            for (int slot = 0, P = kBwRecord; P >= 1; P /= 2) {
+                if (!(nr & P)) continue;
+                const size_t f0 = (size_t)g0 + r * kBwRecord + slot;   // the unit's first frame
+                LikelihoodArgs la{};
+                la.img = images + f0 * frame_bytes;
+                la.mean = h->bg_mean;
+                la.hinv = h->bg_hinv;
+                la.n_pix = h->n_pix;
+                la.c0 = h->c0;
+                la.sc = h->sc;
+                la.out = h->bw_maps;
+                la.zero_word = nullptr;
+                la.status = h->d_words;
+                la.img_fstride = (int64_t)frame_bytes;
+                {
+                    ProfScope ps(h, PSFS_STAGE_LIKELIHOOD, sa);
+                    if (P > 1)
+                        PSFS_CK(launch_likelihood_group(la, P, h->params.map_dtype, sa, 4));
+                    else
+                        PSFS_CK(launch_likelihood(la, h->params.map_dtype, false, sa));
+                }
+                BackwardArgs bv = b;
+                bv.f = h->bw_fuse;
+                bv.d_occ = d_occ + f0 * n_vox;
+                bv.dl = bufs[q] + (size_t)r * kBwRecord * n_vox + slot;
+                bv.dl_stride = kBwRecord;
+                {
+                    ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL, sa);
+                    if (P > 1)
+                        PSFS_CK(launch_backward_voxel_group(bv, kBwShape, P, h->params.map_dtype, (int64_t)n_vox, sa));
+                    else
+                        PSFS_CK(launch_backward_voxel(bv, kBwShape, h->params.map_dtype, sa));
+                }
+                slot += P;
             }
-            BackwardArgs bv = b;
-            bv.f = h->bw_fuse;
-            bv.d_occ = d_occ + f0 * n_vox;
-            bv.dl = bufs[q] + slot;
-            bv.dl_stride = kBwRecord;
-            {
-                ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL, sa);
-                if (P > 1)
-                    PSFS_CK(launch_backward_voxel_group(bv, kBwShape, P, h->params.map_dtype, (int64_t)n_vox, sa));
-                else
-                    PSFS_CK(launch_backward_voxel(bv, kBwShape, h->params.map_dtype, sa));
-            }
-            slot += P;
         }
         PSFS_CK(cudaEventRecord(h->seq_ev_map[q], sa));
         PSFS_CK(cudaStreamWaitEvent(sb, h->seq_ev_map[q], 0));
@@ -1509,7 +1519,8 @@ psfs_status psfs_backward_sequence(psfs_handle *h, int32_t n_frames, const uint8
 
 // The adjoint from the forward's own occupancy: dLoss/dL = d_occ occ (1 - occ)
 // elementwise (no recomputed maps, no voxel pass), then the pixel passes of
-// psfs_backward (one frame) or psfs_backward_sequence (records of 8 frames).
+// psfs_backward (one frame) or psfs_backward_sequence (groups of 16 frames in
+// two planes of 8-frame records).
 static psfs_status enqueue_backward_from_occupancy(psfs_handle *h, int32_t n_frames, const uint8_t *images,
                                                    const float *occupancy, const float *d_occ, float *d_slm,
                                                    float *d_mean, float *d_var)
@@ -1549,14 +1560,16 @@ static psfs_status enqueue_backward_from_occupancy(psfs_handle *h, int32_t n_fra
     PSFS_CK(cudaEventRecord(h->seq_ev_in, h->stream));
     PSFS_CK(cudaStreamWaitEvent(sa, h->seq_ev_in, 0));
     PSFS_CK(cudaStreamWaitEvent(sb, h->seq_ev_in, 0));
-    for (int g = 0, g0 = 0; g0 < n_frames; ++g, g0 += kBwRecord) {
-        const int nf = std::min(kBwRecord, n_frames - g0);
+    for (int g = 0, g0 = 0; g0 < n_frames; ++g, g0 += kBwGroup) {
+        const int nf = std::min(kBwGroup, n_frames - g0);
         const int q = g & 1;
         if (g >= 2) PSFS_CK(cudaStreamWaitEvent(sa, h->seq_ev_fused[q], 0));
-        {
+        for (int r = 0; r * kBwRecord < nf; ++r) {
+            const size_t f0 = (size_t)g0 + r * kBwRecord;
             ProfScope ps(h, PSFS_STAGE_BACKWARD_VOXEL, sa);
-            PSFS_CK(launch_dl_from_occ(occupancy + (size_t)g0 * n_vox, d_occ + (size_t)g0 * n_vox, bufs[q],
-                                       (int64_t)n_vox, nf, kBwRecord, sa));
+            PSFS_CK(launch_dl_from_occ(occupancy + f0 * n_vox, d_occ + f0 * n_vox,
+                                       bufs[q] + (size_t)r * kBwRecord * n_vox, (int64_t)n_vox,
+                                       std::min(kBwRecord, nf - r * kBwRecord), kBwRecord, sa));
         }
         PSFS_CK(cudaEventRecord(h->seq_ev_map[q], sa));
         PSFS_CK(cudaStreamWaitEvent(sb, h->seq_ev_map[q], 0));

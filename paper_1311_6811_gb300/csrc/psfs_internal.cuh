@@ -580,7 +580,9 @@ bool owner_lists_supported(const FuseArgs &a, int64_t n_pix);
 cudaError_t launch_build_owners(const FuseArgs &a, int64_t n_pix, uint32_t *cnt, uint32_t *sums, uint32_t *off,
                                 uint32_t *vox, cudaStream_t s);
 // Pixel pass of one frame (b.dl dense, dl_stride 1), and of n_frames <=
-// kBwRecord frames of records (frame f's colour at b.img + f img_fstride).
+// 2 kBwRecord frames of records (frame f's colour at b.img + f img_fstride;
+// frames kBwRecord and up in a second plane of records at b.dl + n_vox
+// kBwRecord).
 cudaError_t launch_owner_pixel(const BackwardArgs &b, const uint32_t *off, const uint32_t *vox, cudaStream_t s);
 // dLoss/dL = d_occ occ (1 - occ) of n_frames frames (occ and d_occ [n_frames][n_vox]) from a given
 // occupancy: dl[v * dl_stride + f] (dl_stride 1 with one frame, or kBwRecord).

@@ -282,18 +282,44 @@ __device__ __forceinline__ void load_record(const float *rec, uint32_t (&w)[8])
         : "l"(rec));
 }
 
-// Up to kBwRecord frames: b.dl holds records of kBwRecord floats per voxel
-// (frame f of voxel v at b.dl[v * kBwRecord + f]), one 32-byte load per
-// owned voxel serves every frame.  Per frame the sum (same voxels, same
-// order) and the chain rule are those of owner_pixel_kernel, so d_slm (frame
-// f at b.d_slm + f n_pix) is bit-identical to one frame per call; d_mean and
-// d_var receive the frames' gradients added in frame order to 0 (or, with
-// `accumulate`, to what they hold).  The pixel's background is read once for
-// all frames.
+// Adds K consecutive owners (vox[e .. e + K)) of R record planes: their
+// loads are issued together, then added in ascending owner order per frame.
+template <int R, int K>
+__device__ __forceinline__ void add_owners(const float *dl, size_t plane, const uint32_t *vox, uint32_t e,
+                                           float (&acc)[R * kBwRecord])
+{
+    uint32_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = __ldg(vox + e + k);
+    uint32_t w[K][R][8];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int r = 0; r < R; ++r) load_record(dl + r * plane + (size_t)v[k] * kBwRecord, w[k][r]);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int f = 0; f < kBwRecord; ++f) acc[r * kBwRecord + f] += __uint_as_float(w[k][r][f]);
+}
+
+// Up to R * kBwRecord frames: b.dl holds R planes of records of kBwRecord
+// floats per voxel (frame r * kBwRecord + f of voxel v at b.dl[r * n_vox *
+// kBwRecord + v * kBwRecord + f]); one 32-byte load per owned voxel and
+// plane serves its frames, so the owner list, the background and d_mean /
+// d_var are read once per R * kBwRecord frames.  Per frame the sum (same
+// voxels, same order) and the chain rule are those of owner_pixel_kernel, so
+// d_slm (frame f at b.d_slm + f n_pix) is bit-identical to one frame per
+// call; d_mean and d_var receive the frames' gradients added in frame order
+// to 0 (or, with `accumulate`, to what they hold).
+template <int R>
 __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_constant__ BackwardArgs b,
                                                                 const uint32_t *off, const uint32_t *vox,
                                                                 int n_frames, int64_t img_fstride, int accumulate)
 {
+    constexpr int kF = R * kBwRecord;
+    const size_t plane = (size_t)b.f.nx * b.f.ny * b.f.nz * kBwRecord;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < b.n_pix; p += stride) {
         const uint32_t e0 = __ldg(off + p);
@@ -306,45 +332,17 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
             if (!seg_ok) e1 = e0;
         }
 #endif
-        float acc[kBwRecord];
+        float acc[kF];
 #pragma unroll
-        for (int f = 0; f < kBwRecord; ++f) acc[f] = 0.0f;
-        // four owners at a time (their loads in flight together), added in
-        // ascending order; one 256-bit read-only load per record (one sector)
+        for (int f = 0; f < kF; ++f) acc[f] = 0.0f;
+        // four record loads in flight (four owners of one plane, two of two
+        // planes), then the rest two and one at a time
         uint32_t e = e0;
-        for (; e + 4 <= e1; e += 4) {
-            const uint32_t va = __ldg(vox + e), vb = __ldg(vox + e + 1), vc = __ldg(vox + e + 2),
-                           vd = __ldg(vox + e + 3);
-            uint32_t wa[8], wb[8], wc[8], wd[8];
-            load_record(b.dl + (size_t)va * kBwRecord, wa);
-            load_record(b.dl + (size_t)vb * kBwRecord, wb);
-            load_record(b.dl + (size_t)vc * kBwRecord, wc);
-            load_record(b.dl + (size_t)vd * kBwRecord, wd);
-#pragma unroll
-            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wa[f]);
-#pragma unroll
-            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wb[f]);
-#pragma unroll
-            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wc[f]);
-#pragma unroll
-            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wd[f]);
+        if constexpr (R == 1) {
+            for (; e + 4 <= e1; e += 4) add_owners<R, 4>(b.dl, plane, vox, e, acc);
         }
-        for (; e + 2 <= e1; e += 2) {
-            const uint32_t va = __ldg(vox + e), vb = __ldg(vox + e + 1);
-            uint32_t wa[8], wb[8];
-            load_record(b.dl + (size_t)va * kBwRecord, wa);
-            load_record(b.dl + (size_t)vb * kBwRecord, wb);
-#pragma unroll
-            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wa[f]);
-#pragma unroll
-            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(wb[f]);
-        }
-        if (e < e1) {
-            uint32_t w[8];
-            load_record(b.dl + (size_t)__ldg(vox + e) * kBwRecord, w);
-#pragma unroll
-            for (int f = 0; f < kBwRecord; ++f) acc[f] += __uint_as_float(w[f]);
-        }
+        for (; e + 2 <= e1; e += 2) add_owners<R, 2>(b.dl, plane, vox, e, acc);
+        if (e < e1) add_owners<R, 1>(b.dl, plane, vox, e, acc);
         float tm[3] = {0.0f, 0.0f, 0.0f}, tv[3] = {0.0f, 0.0f, 0.0f};
         if (accumulate) {
 #pragma unroll
@@ -355,7 +353,7 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
         }
         bool any = false;
 #pragma unroll
-        for (int f = 0; f < kBwRecord; ++f) any |= (f < n_frames) & (acc[f] != 0.0f);
+        for (int f = 0; f < kF; ++f) any |= (f < n_frames) & (acc[f] != 0.0f);
         float mu[3] = {0.0f, 0.0f, 0.0f}, hh[3] = {0.0f, 0.0f, 0.0f}, base = 0.0f;
         if (any) {
 #pragma unroll
@@ -366,7 +364,7 @@ __global__ void __launch_bounds__(256) owner_pixel_group_kernel(const __grid_con
             base = pixel_log_base(hh[0], hh[1], hh[2], b.c0);
         }
 #pragma unroll
-        for (int f = 0; f < kBwRecord; ++f) {
+        for (int f = 0; f < kF; ++f) {
             if (f < n_frames) {
                 float dslm, dm[3], dv[3];
                 chain_rule_pre(b, b.img + f * img_fstride + 3 * p, mu, hh, base, acc[f], dslm, dm, dv);
@@ -481,10 +479,14 @@ cudaError_t launch_owner_pixel(const BackwardArgs &b, const uint32_t *off, const
 cudaError_t launch_owner_pixel_group(const BackwardArgs &b, const uint32_t *off, const uint32_t *vox, int n_frames,
                                      int64_t img_fstride, bool accumulate, cudaStream_t s)
 {
-    if (n_frames < 1 || n_frames > kBwRecord || !b.img || ((uintptr_t)b.dl & 31u))
+    if (n_frames < 1 || n_frames > 2 * kBwRecord || !b.img || ((uintptr_t)b.dl & 31u))
         return cudaErrorInvalidValue;
-    owner_pixel_group_kernel<<<(int)grid_for(b.n_pix), 256, 0, s>>>(b, off, vox, n_frames, img_fstride,
-                                                                      accumulate ? 1 : 0);
+    if (n_frames > kBwRecord)
+        owner_pixel_group_kernel<2><<<(int)grid_for(b.n_pix), 256, 0, s>>>(b, off, vox, n_frames, img_fstride,
+                                                                             accumulate ? 1 : 0);
+    else
+        owner_pixel_group_kernel<1><<<(int)grid_for(b.n_pix), 256, 0, s>>>(b, off, vox, n_frames, img_fstride,
+                                                                             accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 

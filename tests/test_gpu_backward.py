@@ -221,11 +221,11 @@ def test_backward_full_size_128cube():
 
 
 def test_backward_sequence_equals_per_frame():
-    """11 frames (pixel passes of 8 and 3 frames): psfs_backward_sequence's
-    d_slm of every frame is bit-identical to psfs_backward's, and its d_mean
-    and d_var are the frame-ordered FP32 sums of psfs_backward's; NULL outputs
-    are skipped."""
-    n = 11
+    """27 frames (pixel passes of 16 frames, records of 8 + 8, and of 11
+    frames, records of 8 + 3): psfs_backward_sequence's d_slm of every frame
+    is bit-identical to psfs_backward's, and its d_mean and d_var are the
+    frame-ordered FP32 sums of psfs_backward's; NULL outputs are skipped."""
+    n = 27
     sc = S.make_scene(seed=31, grid_n=48, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0,
                       n_frames=n, walking=True)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
@@ -366,8 +366,8 @@ def test_autograd_sequence_function_matches_per_frame():
 def test_backward_from_occupancy_equals_recomputing_adjoint():
     """With the forward's own occupancy the adjoint skips the recomputed maps
     and voxel pass; its outputs must be those of psfs_backward (one frame) and
-    psfs_backward_sequence (11 frames: groups of 8 and 3) bit for bit."""
-    n = 11
+    psfs_backward_sequence (19 frames: groups of 16 and 3) bit for bit."""
+    n = 19
     sc = S.make_scene(seed=48, grid_n=40, cube_side=2.0, n_cams=4, width=160, height=120, focal=150.0,
                       n_frames=n, walking=True)
     rec = psfs.Reconstructor(sc.grid, sc.cams, sc.params)
