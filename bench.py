@@ -244,6 +244,65 @@ def ncu_traffic(kernel: str, config: dict):
         return None
 
 
+def fusion_rows(sc, tile=(16, 8, 2)):
+    """Row of each (voxel, camera) pair that a fusion launch reads: camera c's
+    pixel p of the voxel centre's projection (Eq. 3, in float64) is row c *
+    n_pix + p of a plane of pixel records.  Pairs outside the image are left
+    out; the order is the fusion's (tiles of tile[0] x tile[1] x tile[2]
+    voxels in x, y, z, and in each tile camera by camera).  Measurement set-up
+    only: the rows to time the device's gather ceiling on."""
+    g = sc.grid
+    nx, ny, nz = g.nx, g.ny, g.nz
+    tx, ty, tz = tile
+    if nx % tx or ny % ty or nz % tz:
+        return None
+    o = np.asarray(g.origin, dtype=np.float64)
+    i = (np.arange(nx) + 0.5) * g.voxel_size + o[0]
+    j = (np.arange(ny) + 0.5) * g.voxel_size + o[1]
+    k = (np.arange(nz) + 0.5) * g.voxel_size + o[2]
+    Z, Y, X = np.meshgrid(k, j, i, indexing="ij")   # [nz][ny][nx]
+    P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=0)
+    n_pix = sc.cams[0].width * sc.cams[0].height
+    rows = np.empty((len(sc.cams), nz * ny * nx), dtype=np.int32)
+    for c, cam in enumerate(sc.cams):
+        uvw = cam.K @ (cam.R @ P + cam.t.reshape(3, 1))
+        w = uvw[2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u, v = np.floor(uvw[0] / w), np.floor(uvw[1] / w)
+        ok = (w > 0) & (u >= 0) & (u < cam.width) & (v >= 0) & (v < cam.height)
+        rows[c] = np.where(ok, c * n_pix + v * cam.width + u, -1).astype(np.int32)
+    # [c][nz/tz][tz][ny/ty][ty][nx/tx][tx] -> tiles (z, y, x), then camera, then voxel in the tile
+    r = rows.reshape(len(sc.cams), nz // tz, tz, ny // ty, ty, nx // tx, tx).transpose(1, 3, 5, 0, 2, 4, 6).ravel()
+    return np.ascontiguousarray(r[r >= 0]), len(sc.cams) * n_pix
+
+
+def gather_ceiling(psfs, dev, sc, record_bytes: int, reps: int = 5):
+    """The device's rate for the fusion's reads: psfs_gather_rows over the
+    rows of every (voxel, camera) pair of the rig that projects into its
+    image, in the fusion's order, from a plane of record_bytes-byte records
+    (CUDA events, median of `reps` after a warm-up).  Returns (GB/s of rows
+    gathered, pairs per frame) or None."""
+    import torch
+    fr = fusion_rows(sc)
+    if fr is None:
+        return None
+    idx, n_rows = fr
+    plane = torch.zeros(n_rows * record_bytes // 4, dtype=torch.int32, device=dev)
+    d_idx = torch.from_numpy(idx).to(dev)
+    ck = torch.zeros(1, dtype=torch.int32, device=dev)
+    psfs.psfs_gather_rows(plane, record_bytes, d_idx, ck)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        psfs.psfs_gather_rows(plane, record_bytes, d_idx, ck)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    t = sorted(ms)[len(ms) // 2]
+    return idx.size * record_bytes / (t * 1e-3) / 1e9, int(idx.size)
+
+
 def make_scene(args):
     """This rank's frames: with N ranks the sequence has N x `--frames` frames
     and rank r renders frames r, r + N, ... of it (round-robin partition;
@@ -699,6 +758,27 @@ def run_ours(args):
                          "note": "whole step: the bytes the grouped method moves per frame (background once per "
                                  "unit, images, maps written and read, occupancy, lists) over the step time"}
 
+    # the fusion against the device's own ceiling for its reads: each (voxel,
+    # camera) pair that projects into the image reads map_elem bytes per frame
+    # once (one pixel-record row per plane); psfs_gather_rows times the same
+    # rows of a plane of the same records with the same loads and nothing else
+    roofline_gather = None
+    plane_rec = min(G, plane) * map_elem
+    if batch is None and grouped and plane_rec in (32, 64) and "fuse" in stages:
+        gc = gather_ceiling(psfs, dev, sc, plane_rec)
+        if gc is not None:
+            ceil_gbs, pairs = gc
+            fuse_s = stages["fuse"]["avg_us"] * stages["fuse"]["launches"] / args.steps * 1e-6
+            g_bytes = pairs * F * map_elem
+            g_ach = g_bytes / fuse_s / 1e9
+            roofline_gather = {"kernel": kern_names["fuse"], "bound": "gather", "achieved": g_ach,
+                               "ceiling": ceil_gbs, "unit": "GB/s", "frac": g_ach / ceil_gbs,
+                               "pairs_per_frame": pairs, "gathered_bytes_per_step": g_bytes,
+                               "record_bytes": plane_rec,
+                               "note": "fusion stage time of the step (beside the likelihood on the other stream) "
+                                       "against psfs_gather_rows timed alone over the same (voxel, camera) rows "
+                                       "of one plane: the device's rate for these reads, measured live"}
+
     # inner-voxel removal on the step's lists (all frames in one call), timed
     # with events on the handle's stream; not part of the headline value
     nxt = None
@@ -944,6 +1024,7 @@ def run_ours(args):
                 "err_vs_fp64": err_vs_fp64,
                 "configs": configs,
                 "stages": stages, "roofline": roofline, "roofline_sequence": roofline_sequence,
+                "roofline_gather": roofline_gather,
                 "cpu_baseline": cpu, "e2e": e2e, "forms": forms,
                 "next": nxt,
                 "gpu_launches": gpu_launches, "clocks": clk}

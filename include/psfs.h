@@ -622,6 +622,24 @@ psfs_status psfs_reconstruct_noalloc(const psfs_grid *grid, const psfs_camera *c
                                      const uint8_t *images, float *occupancy, uint32_t *voxel_list,
                                      uint32_t capacity, uint32_t *count, void *stream);
 
+/* Measurement of the gather rate that bounds the fusion kernels (Eq. 3: each
+ * voxel reads the pixel record at its projection in every camera).  Reads the
+ * rows idx[0 .. n) of `rows` with the fusion kernels' own loads — one 256-bit
+ * read-only load per lane and 32-byte half of a row, two rows in flight per
+ * lane — and XORs every 32-bit word read into *checksum, which it does not
+ * clear.  Nothing else is computed, so rows gathered per second over a given
+ * index list is the device's ceiling for the fusion's reads of the same rows.
+ *   rows         device, n_rows rows of record_bytes (32 or 64) bytes,
+ *                aligned to record_bytes
+ *   idx          device int32 [n] row indices; entries outside [0, n_rows)
+ *                are skipped (read nothing)
+ *   stream       cudaStream_t to enqueue on (NULL = legacy default stream)
+ *   checksum     device uint32, 4-byte aligned
+ * Enqueues one kernel on the current device and returns.  Errors (described
+ * by psfs_last_error_message): INVALID_ARG, CUDA. */
+psfs_status psfs_gather_rows(const void *rows, int64_t n_rows, int32_t record_bytes, const int32_t *idx, int64_t n,
+                             void *stream, uint32_t *checksum);
+
 /* Static English name of a status code. */
 const char *psfs_status_string(psfs_status s);
 

@@ -129,6 +129,7 @@ def load(build_if_missing: bool = True):
             "psfs_reconstruct_noalloc": (st, [ctypes.POINTER(psfs_grid), ctypes.POINTER(psfs_camera),
                                               ctypes.c_int32, ctypes.POINTER(psfs_params), _vp, _vp, _vp,
                                               _vp, _vp, ctypes.c_uint32, _vp, _vp]),
+            "psfs_gather_rows": (st, [_vp, ctypes.c_int64, ctypes.c_int32, _vp, ctypes.c_int64, _vp, _vp]),
             "psfs_sync": (st, [_vp]),
             "psfs_destroy": (None, [_vp]),
             "psfs_set_fuse_config": (st, [_vp, ctypes.POINTER(psfs_fuse_config)]),
@@ -475,6 +476,26 @@ def psfs_reconstruct_noalloc(grid, cams, params, mean, var, images, occupancy, v
                                            _dev_ptr(occupancy, "occupancy", torch.float32, n_vox),
                                            _dev_ptr(voxel_list, "voxel_list"), int(capacity),
                                            _dev_ptr(count, "count"), _vp(stream)), "psfs_reconstruct_noalloc")
+
+
+def psfs_gather_rows(rows, record_bytes: int, idx, checksum, stream=None):
+    """Gathers the rows idx of `rows` (CUDA tensor of whole record_bytes-byte
+    rows) with the fusion kernels' loads, XOR-ing every word into checksum
+    (int32 CUDA tensor of one element, not cleared); enqueued on `stream`
+    (default: torch's current stream)."""
+    import torch
+    nbytes = rows.numel() * rows.element_size()
+    if nbytes % int(record_bytes) != 0:
+        raise ValueError("rows: not a whole number of records")
+    if checksum.numel() != 1:
+        raise ValueError("checksum: expected one element")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _check(load().psfs_gather_rows(_dev_ptr(rows, "rows"), nbytes // int(record_bytes), int(record_bytes),
+                                   _dev_ptr(idx, "idx", torch.int32), idx.numel(), _vp(stream),
+                                   _dev_ptr(checksum, "checksum", torch.int32)), "psfs_gather_rows")
 
 
 def psfs_backward_slm(h: int, slm, d_occ, d_slm):

@@ -159,6 +159,30 @@ def test_calls_reject_null_handle(lib):
     lib.psfs_destroy(None)
 
 
+@pytest.mark.parametrize("case", ["record_48", "negative_n", "null_rows", "misaligned_rows", "null_idx",
+                                  "misaligned_checksum"])
+def test_gather_rows_rejects_bad_arguments_before_any_cuda_call(lib, case):
+    """psfs_gather_rows checks its arguments on the host and returns
+    PSFS_ERR_INVALID_ARG with a message; the stand-in addresses are never
+    dereferenced."""
+    buf = 1 << 20
+    rows, n_rows, rb, idx, n, ck = buf, 100, 64, buf, 10, buf
+    if case == "record_48":
+        rb = 48
+    elif case == "negative_n":
+        n = -1
+    elif case == "null_rows":
+        rows = None
+    elif case == "misaligned_rows":
+        rows = buf + 32
+    elif case == "null_idx":
+        idx = None
+    elif case == "misaligned_checksum":
+        ck = buf + 2
+    assert lib.psfs_gather_rows(rows, n_rows, rb, idx, n, None, ck) == psfs.PSFS_ERR_INVALID_ARG
+    assert psfs.psfs_last_error_message()
+
+
 @pytest.mark.parametrize("case", ["null_grid", "null_images", "null_list", "misaligned_occ", "n_cams0",
                                   "n_cams_big", "axis_2_24", "f16_maps", "too_many_pixels", "bad_prior"])
 def test_noalloc_rejects_bad_arguments_before_any_cuda_call(lib, case):

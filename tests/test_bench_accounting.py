@@ -3,6 +3,9 @@ sequence path, and the lookup of committed ncu DRAM traffic, which must
 refuse a record taken on other kernel sources or another launch shape."""
 
 import json
+import math
+
+import numpy as np
 
 import bench
 
@@ -132,3 +135,36 @@ def test_units_with_two_voxel_tiles():
     # voxels_z 2 holds 2 x P accumulators: every record size fits
     assert bench.sequence_units(100, 32, 2, 4) == [32, 32, 32, 4]
     assert bench.sequence_units(100, 32, 2, 2) == [32, 32, 32, 4]
+
+
+def test_fusion_rows_order_and_membership():
+    """The rows the gather ceiling is timed on: per tile of 16 x 8 x 2 voxels,
+    camera by camera, the pixel row of every voxel centre that projects into
+    the image (checked voxel by voxel with a pinhole projection written out
+    here), and nothing else."""
+    from synth import scene as S
+    sc = S.make_scene(seed=3, grid_n=16, cube_side=2.0, n_cams=3, width=64, height=48, focal=60.0)
+    idx, n_rows = bench.fusion_rows(sc)
+    g, W, H = sc.grid, 64, 48
+    assert n_rows == 3 * W * H
+    want = []
+    for tz in range(g.nz // 2):
+        for ty in range(g.ny // 8):
+            for tx in range(g.nx // 16):
+                for c, cam in enumerate(sc.cams):
+                    for dz in range(2):
+                        for dy in range(8):
+                            for dx in range(16):
+                                i, j, k = 16 * tx + dx, 8 * ty + dy, 2 * tz + dz
+                                X = np.asarray(g.origin) + (np.array([i, j, k]) + 0.5) * g.voxel_size
+                                u, v, w = cam.K @ (cam.R @ X + cam.t)
+                                if w <= 0:
+                                    continue
+                                px, py = math.floor(u / w), math.floor(v / w)
+                                if 0 <= px < W and 0 <= py < H:
+                                    want.append(c * W * H + py * W + px)
+    assert 0 < len(want) < 3 * g.n_voxels
+    np.testing.assert_array_equal(idx, np.asarray(want, dtype=np.int32))
+    # a grid that the tile does not divide has no row list
+    sc2 = S.make_scene(seed=3, grid_n=12, cube_side=2.0, n_cams=2, width=64, height=48, focal=60.0)
+    assert bench.fusion_rows(sc2) is None
