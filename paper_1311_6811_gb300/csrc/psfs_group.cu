@@ -92,6 +92,40 @@ struct GroupWords {
     }
 };
 
+
+// L += g for two 16-bit map values packed in one word (low half first), one
+// mixed-precision add each (sm_100+): the 16-bit value is widened exactly
+// and added in FP32 with one rounding, so the sum is that of converting
+// first and adding, in one instruction instead of two.
+template <typename T>
+__device__ __forceinline__ void add_pair(uint32_t w, float &a, float &b);
+template <>
+__device__ __forceinline__ void add_pair<__half>(uint32_t w, float &a, float &b)
+{
+    asm("{\n .reg .f16 lo, hi;\n mov.b32 {lo, hi}, %2;\n add.rn.f32.f16 %0, lo, %0;\n add.rn.f32.f16 %1, hi, %1;\n}\n"
+        : "+f"(a), "+f"(b) : "r"(w));
+}
+template <>
+__device__ __forceinline__ void add_pair<__nv_bfloat16>(uint32_t w, float &a, float &b)
+{
+    asm("{\n .reg .b16 lo, hi;\n mov.b32 {lo, hi}, %2;\n add.rn.f32.bf16 %0, lo, %0;\n add.rn.f32.bf16 %1, hi, %1;\n}\n"
+        : "+f"(a), "+f"(b) : "r"(w));
+}
+
+// L[f][t] += frame f's log ratio of one gathered record, for the F frames.
+template <typename MapT, int F, int TZ>
+__device__ __forceinline__ void add_words(const GroupWords<MapT, F> &g, float (&L)[F][TZ], int t)
+{
+    if constexpr (sizeof(MapT) == 4) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) L[f][t] += g.get(f);
+    } else {
+        static_assert(F % 2 == 0, "16-bit records hold pairs of frames");
+#pragma unroll
+        for (int q = 0; q < F / 2; ++q) add_pair<MapT>(g.w[q], L[2 * q][t], L[2 * q + 1][t]);
+    }
+}
+
 // Vector store / read-only vector load of the F * sizeof(T) bytes of one
 // pixel (4, 8, 16 or 32 bytes; the address is a multiple of that size, the
 // buffers are 256-byte aligned).
@@ -405,8 +439,7 @@ __device__ __forceinline__ void group_gather(const FuseArgs &a, const TileCoords
                 if (!PSFS_IN_BOUNDS(proved_inside(p, W, H), a.status)) continue;
                 Words g;
                 load_words<Words::kWords>(map + (size_t)pix * kRec, g.w);
-#pragma unroll
-                for (int f = 0; f < F; ++f) L[f][t] += g.get(f);
+                add_words<MapT, F, TZ>(g, L, t);
             }
         } else {
 #pragma unroll
@@ -415,8 +448,7 @@ __device__ __forceinline__ void group_gather(const FuseArgs &a, const TileCoords
                 if (proj_pixel(project_biased(m, bu, bv, bw, tc.fk[t]), W, H, &pix)) {
                     Words g;
                     load_words<Words::kWords>(map + (size_t)pix * kRec, g.w);
-#pragma unroll
-                    for (int f = 0; f < F; ++f) L[f][t] += g.get(f);
+                    add_words<MapT, F, TZ>(g, L, t);
                 }
             }
         }
