@@ -501,8 +501,9 @@ struct WeightArgs {
 };
 cudaError_t launch_weights(const WeightArgs &a, int n_particles, cudaStream_t s);
 
-// Frames per record of dLoss/dL in the batched adjoint (and per pass of its
-// pixel pass): frame f of voxel v at dl[v * kBwRecord + f], 32 bytes per voxel.
+// Frames per record of dLoss/dL in the batched adjoint (a pixel pass reads
+// one or two planes of such records): frame f of voxel v at dl[v * kBwRecord
+// + f], 32 bytes per voxel.
 constexpr int kBwRecord = 8;
 
 // Adjoint (psfs_backward.cu, psfs_owners.cu).  The voxel pass recomputes the
