@@ -12,6 +12,12 @@ P(O) = 1/2 under detection rate P_D and false-alarm rate P_FA:
 With P_D = 1 and P_FA = 0 this is Eq. 6-9 as printed.  Uses only the
 standard library (fractions): no value comes from the oracle or the GPU
 path.  Run from the repository root:  python tests/golden/make_one_voxel_posteriors.py
+
+It also writes one_voxel_adjoint.txt: for the same cases with every a > 0,
+d occ / d s_k = occ (1 - occ) (a_k' / a_k - b_k' / b_k), the derivative of
+that posterior with respect to camera k's SLM value, where a' = 2 P_D - 1
+and b' = (a' + f') / 2 with f' = 2 P_FA - 1 (the chain rule through the
+log-odds; its derivation is the quotient rule on occ).
 """
 import os
 from decimal import Decimal, localcontext
@@ -51,6 +57,25 @@ def main():
         for slms in SLMS:
             occ = posterior(Fr(pd), Fr(pfa), Fr(prior), [Fr(s) for s in slms])
             lines.append(f"{pd} {pfa} {prior} {','.join(slms)} {decimal_of(occ)}")
+    with open(out, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "one_voxel_adjoint.txt")
+    lines = ["# One voxel, K cameras: exact d occ / d s_k of the posterior in one_voxel_posteriors.txt",
+             "# (cases with every a > 0).  Written by make_one_voxel_posteriors.py (exact rationals).",
+             "# columns: p_detect p_false_alarm prior s_1,...,s_K d_1,...,d_K (25 significant digits)"]
+    for pd, pfa, prior in RATES:
+        P_D, P_FA, PRIOR = Fr(pd), Fr(pfa), Fr(prior)
+        for slms in SLMS:
+            s_ = [Fr(s) for s in slms]
+            a = [P_D * s + (1 - P_D) * (1 - s) for s in s_]
+            if any(x == 0 for x in a):
+                continue
+            occ = posterior(P_D, P_FA, PRIOR, s_)
+            da = 2 * P_D - 1
+            db = (da + 2 * P_FA - 1) / 2
+            b = [(P_FA * s + (1 - P_FA) * (1 - s) + ak) / 2 for s, ak in zip(s_, a)]
+            d = [occ * (1 - occ) * (da / ak - db / bk) for ak, bk in zip(a, b)]
+            lines.append(f"{pd} {pfa} {prior} {','.join(slms)} {','.join(decimal_of(x) for x in d)}")
     with open(out, "w") as fh:
         fh.write("\n".join(lines) + "\n")
 

@@ -45,3 +45,29 @@ def test_oracle_matches_exact_posterior(pd, pfa, prior, slms, occ):
     assert abs(out["occ"][0] - occ) < 1e-14
     if abs(occ - 0.5) > 1e-12:
         assert bool(out["occupied"][0]) == (occ > 0.5)
+
+
+GOLDEN_ADJ = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "one_voxel_adjoint.txt")
+
+
+def _adjoint_cases():
+    with open(GOLDEN_ADJ) as fh:
+        for ln in fh:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            pd, pfa, prior, slms, ds = ln.split()
+            yield (float(Fraction(pd)), float(Fraction(pfa)), float(Fraction(prior)),
+                   [float(Fraction(s)) for s in slms.split(",")], [float(d) for d in ds.split(",")])
+
+
+ADJ_CASES = list(_adjoint_cases())
+
+
+@pytest.mark.parametrize("pd,pfa,prior,slms,ds", ADJ_CASES)
+def test_oracle_adjoint_matches_exact_derivative(pd, pfa, prior, slms, ds):
+    """dLoss/dSLM with dLoss/docc = 1 is d occ / d s_k for every camera k."""
+    assert len(ADJ_CASES) >= 30
+    maps = np.array([[[s]] for s in slms])
+    got = oracle.backward_slm(ONE_VOXEL_GRID, [CAM] * len(slms), maps, np.array([1.0]),
+                              {"p_detect": pd, "p_false_alarm": pfa, "prior": prior})
+    np.testing.assert_allclose(got.reshape(-1), ds, rtol=1e-12, atol=1e-15)
